@@ -1,0 +1,250 @@
+"""Oracle multigrid layer (test infrastructure only).
+
+The local-smoothing V-cycle of Sec. 2.3 (Algorithm 2 with the splitting
+V_l = V_l^S + V_l^I + V_l^L), preconditioning an outer CG on the leaf mesh,
+written with assembled scipy matrices in FP64.
+
+Readings of points the paper leaves open (each also listed in the design
+notes of the repository):
+
+* Chebyshev recurrence: the paper names Chebyshev iteration on the Jacobi
+  method (Sec. 4.1, citing Adams et al. 2003) but prints no recurrence; this
+  uses Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1 with
+  preconditioner D^{-1}.  Degree m = number of updates of x, so m-1 matrix
+  products from a zero start and m from a nonzero one.
+* Eigenvalue estimate (Sec. 4.1): 10 Jacobi-preconditioned CG steps on
+  A^S y = b0, b0_i = -5.5 + (c(i) mod 12) with c(i) the rank of S-node i in
+  canonical (z, y, x) order; lambda = largest eigenvalue of the Lanczos
+  tridiagonal built from the CG coefficients (Saad Sec. 6.7.3).  The
+  iteration stops early once r.z has dropped below 1e-24 of its start value
+  or after n_S steps.
+* Right-hand side of a level: every unknown x is copied to one level only,
+  level(x) = the coarsest level of the leaves containing x, where it is an
+  S-node; g^I = 0 on every level (the residual r^L is deferred to the lower
+  levels, Sec. 2.3).
+* Coarse solve: dense Cholesky of A_0 (a "direct solver", Sec. 2.2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .fem import Discretization, lookup
+from .mesh import build_forest
+
+
+# --------------------------------------------------------------- smoother
+def chebyshev_coefficients(lam_max: float, lo: float = 0.08, hi: float = 1.2):
+    """theta, delta, sigma for the eigenvalue range [lo*lam, hi*lam] (Sec. 4.1)."""
+    a, b = lo * lam_max, hi * lam_max
+    theta = 0.5 * (b + a)
+    delta = 0.5 * (b - a)
+    return theta, delta, theta / delta
+
+
+def chebyshev(A, dinv, x0, b, lam_max, degree, x0_is_zero=False, lo=0.08, hi=1.2):
+    """Chebyshev iteration on D^{-1} A (Saad Alg. 12.1); returns x after ``degree`` updates."""
+    theta, delta, sigma = chebyshev_coefficients(lam_max, lo, hi)
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = np.array(b, dtype=np.float64, copy=True) if x0_is_zero else b - A @ x
+    rho = 1.0 / sigma
+    d = dinv * r / theta
+    for step in range(degree):
+        x = x + d
+        if step == degree - 1:
+            break
+        r = r - A @ d
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * (dinv * r)
+        rho = rho_new
+    return x
+
+
+def estimate_lambda_max(A, dinv, b0, iters: int = 10) -> float:
+    """Largest Ritz value of D^{-1} A after ``iters`` PCG steps from y0 = 0."""
+    n = A.shape[0]
+    r = np.array(b0, dtype=np.float64, copy=True)
+    z = dinv * r
+    p = z.copy()
+    rz = float(r @ z)
+    rz0 = rz
+    alphas, betas = [], []
+    for j in range(min(iters, n)):
+        Ap = A @ p
+        alpha = rz / float(p @ Ap)
+        alphas.append(alpha)
+        r = r - alpha * Ap
+        z = dinv * r
+        rz_new = float(r @ z)
+        if j == min(iters, n) - 1 or rz_new <= 1e-24 * rz0:
+            break
+        beta = rz_new / rz
+        betas.append(beta)
+        p = z + beta * p
+        rz = rz_new
+    m = len(alphas)
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    return float(np.linalg.eigvalsh(T)[-1])
+
+
+def eigen_start_vector(n: int) -> np.ndarray:
+    """(-5.5, -4.5, ..., 5.5, -5.5, ...) of length n (Sec. 4.1)."""
+    return -5.5 + (np.arange(n) % 12).astype(np.float64)
+
+
+# -------------------------------------------------------------- hierarchy
+@dataclass
+class Level:
+    keys: np.ndarray          # S u I nodes, canonical order
+    iface: np.ndarray         # True on I
+    A: sp.csr_matrix          # level-l cells, on S u I
+    S: np.ndarray = None      # indices of S nodes
+    I: np.ndarray = None      # indices of I nodes
+    A_S: sp.csr_matrix = None
+    A_SI: sp.csr_matrix = None
+    A_IS: sp.csr_matrix = None
+    dinv: np.ndarray = None   # 1 / diag(A^S)
+    lam: float = 0.0
+    P: sp.csr_matrix = None   # from level l-1 to level l (None on level 0)
+
+
+@dataclass
+class Hierarchy:
+    disc: Discretization
+    levels: List[Level]
+    home_index: np.ndarray    # position of each unknown in its home level's vector
+    cheb_degree: int
+    eig_lo: float = 0.08
+    eig_hi: float = 1.2
+    coarse_chol: object = None
+
+
+def build_hierarchy(disc: Discretization, cheb_degree: int, eig_iters: int = 10,
+                    lambdas: Optional[List[float]] = None, eig_lo=0.08, eig_hi=1.2) -> Hierarchy:
+    levels = []
+    for l in range(disc.L + 1):
+        keys, iface, A = disc.level_space(l)
+        lev = Level(keys=keys, iface=iface, A=A)
+        lev.S = np.nonzero(~iface)[0]
+        lev.I = np.nonzero(iface)[0]
+        lev.A_S = A[lev.S][:, lev.S].tocsr()
+        lev.A_SI = A[lev.S][:, lev.I].tocsr()
+        lev.A_IS = A[lev.I][:, lev.S].tocsr()
+        lev.dinv = 1.0 / lev.A_S.diagonal()
+        if l > 0:
+            lev.P = disc.prolongation(l, keys, levels[l - 1].keys)
+            if lambdas is not None:
+                lev.lam = float(lambdas[l])
+            else:
+                # S nodes are already in canonical order, so rank = position
+                b0 = eigen_start_vector(len(lev.S))
+                lev.lam = estimate_lambda_max(lev.A_S, lev.dinv, b0, eig_iters)
+        else:
+            assert len(lev.I) == 0
+        levels.append(lev)
+    home = np.zeros(disc.n, dtype=np.int64)
+    for l in range(disc.L + 1):
+        sel = np.nonzero(disc.home_level == l)[0]
+        idx = lookup(levels[l].keys, disc.unknown_keys[sel])
+        assert np.all(idx >= 0)
+        assert not np.any(levels[l].iface[idx]), "an unknown must be an S-node on its home level"
+        home[sel] = idx
+    H = Hierarchy(disc, levels, home, cheb_degree, eig_lo, eig_hi)
+    H.coarse_chol = sla.cho_factor(levels[0].A.toarray())
+    return H
+
+
+# ---------------------------------------------------------------- V-cycle
+def vcycle(H: Hierarchy, r: np.ndarray) -> np.ndarray:
+    """z = B r: one local-smoothing V-cycle (Algorithm 2, Sec. 2.3)."""
+    lv = H.levels
+    L = len(lv) - 1
+    m = H.cheb_degree
+    g = [np.zeros(len(x.keys)) for x in lv]
+    for l in range(L + 1):
+        sel = np.nonzero(H.disc.home_level == l)[0]
+        g[l][H.home_index[sel]] = r[sel]
+    u = [np.zeros(len(x.keys)) for x in lv]
+    for l in range(L, 0, -1):
+        x = lv[l]
+        # pre-smoothing on V^S from zero; u^I stays 0
+        u[l][x.S] = chebyshev(x.A_S, x.dinv, np.zeros(len(x.S)), g[l][x.S], x.lam, m,
+                              x0_is_zero=True, lo=H.eig_lo, hi=H.eig_hi)
+        # residual on S u I: t^S = g^S - A^S u^S, t^I = g^I - A^IS u^S
+        t = np.zeros(len(x.keys))
+        t[x.S] = g[l][x.S] - x.A_S @ u[l][x.S]
+        t[x.I] = g[l][x.I] - x.A_IS @ u[l][x.S]
+        g[l - 1] += x.P.T @ t  # R = P^T
+    u[0] = sla.cho_solve(H.coarse_chol, g[0])
+    for l in range(1, L + 1):
+        x = lv[l]
+        u[l] += x.P @ u[l - 1]
+        # post-smoothing on V^S with the edge term A^SI u^I moved to the right
+        gs = g[l][x.S] - x.A_SI @ u[l][x.I]
+        u[l][x.S] = chebyshev(x.A_S, x.dinv, u[l][x.S], gs, x.lam, m,
+                              lo=H.eig_lo, hi=H.eig_hi)
+    z = np.zeros_like(r)
+    for l in range(L + 1):
+        sel = np.nonzero(H.disc.home_level == l)[0]
+        z[sel] = u[l][H.home_index[sel]]
+    return z
+
+
+# --------------------------------------------------------------------- CG
+@dataclass
+class CGResult:
+    x: np.ndarray
+    iterations: int
+    converged: bool
+    residuals: List[float] = field(default_factory=list)
+
+
+def pcg(A, b, precond, tol: float, max_iter: int = 1000, fixed_iterations: Optional[int] = None):
+    """Preconditioned CG from x0 = 0; stops when ||r||_2 <= tol ||b||_2 (unpreconditioned,
+    relative).  ``fixed_iterations`` runs exactly that many steps instead."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    nb = float(np.linalg.norm(b))
+    res = [1.0]
+    if nb == 0.0:
+        return CGResult(x, 0, True, res)
+    z = precond(r)
+    p = z.copy()
+    rz = float(r @ z)
+    limit = fixed_iterations if fixed_iterations is not None else max_iter
+    for it in range(1, limit + 1):
+        Ap = A @ p
+        alpha = rz / float(p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        rel = float(np.linalg.norm(r)) / nb
+        res.append(rel)
+        if fixed_iterations is None and rel <= tol:
+            return CGResult(x, it, True, res)
+        if it == limit:
+            break
+        z = precond(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return CGResult(x, limit, fixed_iterations is not None, res)
+
+
+def solve(H: Hierarchy, b: np.ndarray, tol: float = 1e-8, max_iter: int = 1000,
+          fixed_iterations: Optional[int] = None) -> CGResult:
+    return pcg(H.disc.A, b, lambda r: vcycle(H, r), tol, max_iter, fixed_iterations)
+
+
+def setup(workload, cheb_degree: Optional[int] = None, lambdas=None) -> Hierarchy:
+    """Forest, discretisation and hierarchy for an ``inputs.Workload``."""
+    forest = build_forest(workload.coarse, workload.rounds)
+    disc = Discretization(forest, workload.degree, workload.coeff)
+    return build_hierarchy(disc, cheb_degree or workload.cheb_degree, lambdas=lambdas)

@@ -1,0 +1,238 @@
+"""Seeded synthetic inputs: which leaves to refine, coefficients, random values.
+
+This module is shared by the CUDA path's callers (tests, bench, smoke) and by
+the CPU oracle.  It holds none of the multigrid method's arithmetic: no mesh
+closure, no degrees of freedom, no element integrals.  It only answers
+"which of these leaf cells does this refinement round flag?", "what is the
+coefficient of this coarse cell?" and "which uniform random numbers does this
+seed give?".  Every function takes plain integer cell descriptions
+(level, lattice coordinates) and returns numpy arrays, so each side can call
+it on the leaves of its own mesh.
+
+Mesh shapes follow the refinement rules of Sec. 3.5 of the paper (circle,
+shell, uniform rounds, each followed by closure) and the configurations of
+the solver experiments in Sec. 4.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Callable, List, Optional, Sequence
+
+import numpy as np
+
+_MASK64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x) -> np.ndarray:
+    """SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+
+    Maps each 64-bit input to a well-mixed 64-bit output.  Used with
+    ``x = seed + counter * golden_gamma`` as a counter-based generator.
+    """
+    z = np.asarray(x, dtype=np.uint64).copy()
+    with np.errstate(over="ignore"):
+        z = z + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, counters) -> np.ndarray:
+    """Uniform doubles in [0, 1) from (seed, counter) pairs, 53 random bits each."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        x = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) ^ (c * np.uint64(0xD1B54A32D192ED03))
+    bits = splitmix64(x) >> np.uint64(11)
+    return bits.astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def uniform_pm1(seed: int, counters) -> np.ndarray:
+    """Uniform doubles in [-1, 1) from (seed, counter) pairs."""
+    return 2.0 * uniform01(seed, counters) - 1.0
+
+
+def cell_hash_key(level, coords) -> np.ndarray:
+    """A 64-bit counter that names a cell (level, lattice coordinates) uniquely.
+
+    ``coords`` has shape (n, 3); unused dimensions are 0.  Coordinates must be
+    below 2**20, levels below 16.
+    """
+    level = np.asarray(level, dtype=np.uint64)
+    c = np.asarray(coords, dtype=np.uint64)
+    return ((level << np.uint64(60)) | (c[:, 2] << np.uint64(40))
+            | (c[:, 1] << np.uint64(20)) | c[:, 0])
+
+
+@dataclasses.dataclass(frozen=True)
+class CoarseMesh:
+    """A Cartesian brick [lo, hi] split into n0[0] x n0[1] (x n0[2]) coarse cells."""
+
+    dim: int
+    n0: Sequence[int]
+    lo: Sequence[float]
+    hi: Sequence[float]
+
+    def cells_per_dim(self, level: int) -> np.ndarray:
+        n = np.ones(3, dtype=np.int64)
+        n[: self.dim] = np.asarray(self.n0[: self.dim], dtype=np.int64) << level
+        return n
+
+    def boxes(self, level, coords):
+        """Lower and upper corners (n, dim) of the cells given by level and lattice coords."""
+        level = np.asarray(level, dtype=np.int64)
+        coords = np.asarray(coords, dtype=np.int64)
+        lo = np.asarray(self.lo[: self.dim], dtype=np.float64)
+        hi = np.asarray(self.hi[: self.dim], dtype=np.float64)
+        n0 = np.asarray(self.n0[: self.dim], dtype=np.float64)
+        h = (hi - lo)[None, :] / (n0[None, :] * np.ldexp(1.0, level)[:, None])
+        blo = lo[None, :] + coords[:, : self.dim] * h
+        return blo, blo + h
+
+
+# A refinement round: (coarse, level, coords, finest_level) -> bool flags.
+RoundFn = Callable[[CoarseMesh, np.ndarray, np.ndarray, int], np.ndarray]
+
+
+def round_uniform() -> RoundFn:
+    """Flag every leaf (one global refinement)."""
+
+    def fn(cm, level, coords, finest):
+        return np.ones(len(level), dtype=bool)
+
+    return fn
+
+
+def round_sphere_surface(center, radius, finest_only: bool = True) -> RoundFn:
+    """Flag leaves whose closed box meets the sphere (circle in 2D) |x - center| = radius.
+
+    A closed box meets the sphere iff its nearest point to the centre lies
+    inside (or on) the sphere and its farthest point lies outside (or on) it.
+    With ``finest_only`` only leaves on the current finest level are flagged.
+    """
+    center = np.asarray(center, dtype=np.float64)
+    r2 = float(radius) ** 2
+
+    def fn(cm, level, coords, finest):
+        blo, bhi = cm.boxes(level, coords)
+        c = center[None, : cm.dim]
+        near = np.clip(c, blo, bhi) - c
+        far = np.maximum(np.abs(blo - c), np.abs(bhi - c))
+        dmin = np.sum(near * near, axis=1)
+        dmax = np.sum(far * far, axis=1)
+        hit = (dmin <= r2) & (dmax >= r2)
+        if finest_only:
+            hit &= np.asarray(level) == finest
+        return hit
+
+    return fn
+
+
+def round_shell(center, r_in, r_out) -> RoundFn:
+    """Flag leaves whose closed box meets the shell r_in <= |x - center| <= r_out."""
+    center = np.asarray(center, dtype=np.float64)
+
+    def fn(cm, level, coords, finest):
+        blo, bhi = cm.boxes(level, coords)
+        c = center[None, : cm.dim]
+        near = np.clip(c, blo, bhi) - c
+        far = np.maximum(np.abs(blo - c), np.abs(bhi - c))
+        dmin = np.sum(near * near, axis=1)
+        dmax = np.sum(far * far, axis=1)
+        return (dmin <= r_out * r_out) & (dmax >= r_in * r_in)
+
+    return fn
+
+
+def round_random_interface(seed: int, round_index: int, prob: float,
+                           planes_per_unit: int = 4) -> RoundFn:
+    """Flag, with probability ``prob``, each finest-level leaf that has a face on an
+    interior plane x_i = m / planes_per_unit (m = 1 .. planes_per_unit-1) of the
+    unit brick.  The draw is keyed by (seed, round, cell), so it does not depend
+    on the order in which the leaves are listed.
+    """
+
+    def fn(cm, level, coords, finest):
+        level = np.asarray(level, dtype=np.int64)
+        coords = np.asarray(coords, dtype=np.int64)
+        on_plane = np.zeros(len(level), dtype=bool)
+        for d in range(cm.dim):
+            cells = np.asarray(cm.n0[d], dtype=np.int64) << level
+            # plane spacing in level-l lattice units; requires n0 * 2^l divisible
+            step = cells // planes_per_unit
+            ok = step * planes_per_unit == cells
+            lo_face = coords[:, d]
+            hi_face = coords[:, d] + 1
+            for face in (lo_face, hi_face):
+                m = np.where(ok, face // np.maximum(step, 1), 0)
+                hit = ok & (face % np.maximum(step, 1) == 0) & (m > 0) & (m < planes_per_unit)
+                on_plane |= hit
+        key = cell_hash_key(level, coords) ^ (np.uint64(round_index) << np.uint64(56))
+        u = uniform01(seed, key)
+        return on_plane & (level == finest) & (u < prob)
+
+    return fn
+
+
+def checkerboard_coefficients(cm: CoarseMesh, low: float = 1.0, high: float = 100.0) -> np.ndarray:
+    """Coefficient per coarse cell: ``high`` where the coarse-cell index sum is odd.
+
+    Coarse cells are listed lexicographically with x fastest.
+    """
+    n = [cm.n0[d] if d < cm.dim else 1 for d in range(3)]
+    iz, iy, ix = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    odd = ((ix + iy + iz) % 2 == 1).ravel()
+    return np.where(odd, high, low).astype(np.float64)
+
+
+def random_rhs(seed: int, n: int) -> np.ndarray:
+    """Right-hand side entries U[-1, 1) for unknowns 0..n-1 in canonical order."""
+    return uniform_pm1(seed, np.arange(n, dtype=np.uint64))
+
+
+@dataclasses.dataclass
+class Workload:
+    """A synthetic problem: brick, degree, refinement rounds, coefficient, rhs."""
+
+    name: str
+    coarse: CoarseMesh
+    degree: int
+    rounds: List[RoundFn]
+    coeff: Optional[np.ndarray]  # per coarse cell, None = 1
+    rhs: str  # "sine" (manufactured u = prod sin(pi x_i)) or "random"
+    cheb_degree: int
+    seed: int = 0
+    tol: float = 1e-8
+
+
+def poisson2d_circle(global_refinements: int = 3, adaptive_rounds: int = 3) -> Workload:
+    """2D Poisson on [0,1]^2, Q1, 4x4 coarse quads, refined near the circle
+    |x - (0.5, 0.5)| = 0.3; manufactured u = sin(pi x) sin(pi y)."""
+    cm = CoarseMesh(2, (4, 4, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    rounds = [round_uniform()] * global_refinements
+    rounds += [round_sphere_surface((0.5, 0.5), 0.3)] * adaptive_rounds
+    return Workload(f"poisson2d_q1_circle_g{global_refinements}_a{adaptive_rounds}", cm, 1,
+                    rounds, None, "sine", 2)
+
+
+def poisson3d_sphere(global_refinements: int = 5, adaptive_rounds: int = 2,
+                     degree: int = 2) -> Workload:
+    """3D Poisson on [0,1]^3, Q2, 4^3 coarse hexes, refined near the sphere
+    |x - (0.5, 0.5, 0.5)| = 0.25; manufactured u = prod sin(pi x_i)."""
+    cm = CoarseMesh(3, (4, 4, 4), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    rounds = [round_uniform()] * global_refinements
+    rounds += [round_sphere_surface((0.5, 0.5, 0.5), 0.25)] * adaptive_rounds
+    return Workload(f"poisson3d_q{degree}_sphere_g{global_refinements}_a{adaptive_rounds}", cm,
+                    degree, rounds, None, "sine", 4)
+
+
+def checkerboard3d(global_refinements: int = 5, finest_level: int = 9, seed: int = 20190403,
+                   prob: float = 0.3) -> Workload:
+    """3D variable coefficient on [0,1]^3, Q2: a in {1, 100} on the 4x4x4 subcube
+    checkerboard, refined near the subcube interfaces by seeded random rounds."""
+    cm = CoarseMesh(3, (4, 4, 4), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    rounds = [round_uniform()] * global_refinements
+    for r in range(finest_level - global_refinements):
+        rounds.append(round_random_interface(seed, r, prob))
+    return Workload(f"checkerboard3d_q2_g{global_refinements}_L{finest_level}", cm, 2, rounds,
+                    checkerboard_coefficients(cm), "random", 4, seed=seed)
