@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark: solved DoFs/s of the adaptive local-smoothing GMG-CG solver.
+
+One step = one full solve gmg_solve(b -> x) to relative residual 1e-8 of
+-lap u = f on the 3D Q2 sphere-refined mesh of [0,1]^3 (4^3 coarse cells,
+5 global refinements, 2 refinements of the cells meeting the sphere
+|x - c| = 0.25; about 23M unknowns), FP32 V-cycle inside FP64 CG, with the
+right-hand side already resident on the device.  The same solve with an
+FP64 V-cycle is timed beside it, and the end-to-end variant copies b from
+pinned host memory and x back every step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmg|reference]
+Under torchrun each rank solves its own replica (no data-path collective).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved DoFs/s to rel. residual 1e-8 (FP32-vcycle vs FP64); GB/s vs HBM; p99 latency"
+TOL = 1e-8
+GLOBAL_REF, ADAPTIVE_REF = 5, 2
+SAMPLE_GLOBAL, SAMPLE_ADAPTIVE = 2, 2  # bounded CPU sample of the same generator
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# FP64 arithmetic peak of the part: 1.25 TFLOP/s nominal (dense FP64, incl. FMA = 2 flops)
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(steps=1, min_seconds=8.0):
+    """The oracle (FP64, scipy sparse, single thread) on a bounded sample of the
+    same generator; returns (DoFs/s, sample description, seconds)."""
+    from oracle import gmg as ogmg
+    from paper_1904_03317_gb300 import inputs
+    w = inputs.poisson3d_sphere(SAMPLE_GLOBAL, SAMPLE_ADAPTIVE)
+    H = ogmg.setup(w)
+    b = H.disc.rhs_sine()
+    n, solves, t = H.disc.n, 0, 0.0
+    while solves < steps or t < min_seconds:
+        t0 = time.perf_counter()
+        res = ogmg.solve(H, b, TOL)
+        t += time.perf_counter() - t0
+        solves += 1
+    desc = (f"oracle FP64 local-smoothing GMG-CG (scipy sparse) on the same sphere generator with "
+            f"{SAMPLE_GLOBAL} global + {SAMPLE_ADAPTIVE} adaptive refinements ({n} unknowns), "
+            f"{solves} solves to 1e-8 ({res.iterations} its)")
+    return n * solves / t, desc, t, n
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle import gmg as ogmg
+    from paper_1904_03317_gb300 import inputs
+    w = inputs.poisson3d_sphere(SAMPLE_GLOBAL, SAMPLE_ADAPTIVE)
+    H = ogmg.setup(w)
+    b = H.disc.rhs_sine()
+    for _ in range(args.warmup):
+        ogmg.solve(H, b, TOL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = ogmg.solve(H, b, TOL)
+    t = time.perf_counter() - t0
+    v = H.disc.n * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoFs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"poisson3d_q2_sphere_g{SAMPLE_GLOBAL}_a{SAMPLE_ADAPTIVE} (bounded CPU sample "
+                                   f"of the g{GLOBAL_REF}_a{ADAPTIVE_REF} workload)", "unknowns": H.disc.n,
+                       "tol": TOL, "cheb_degree": w.cheb_degree},
+            "cpu_baseline": {"value": v, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} oracle solves of {H.disc.n} unknowns ({res.iterations} its)"},
+            "e2e": {"value": v, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_solves(torch, H, b, x, steps, stream):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st = None
+    for _ in range(steps):
+        st = H.solve(b, x, tol=TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, st
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gmg", choices=["gmg", "reference"])
+    ap.add_argument("--global-ref", type=int, default=GLOBAL_REF)
+    ap.add_argument("--adaptive-ref", type=int, default=ADAPTIVE_REF)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1904_03317_gb300 import gmg as G
+    from paper_1904_03317_gb300 import inputs
+
+    w = inputs.poisson3d_sphere(args.global_ref, args.adaptive_ref)
+    t0 = time.perf_counter()
+    mesh = G.build_mesh(w)
+    t_mesh = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    ctx = G.Context(local, stream.cuda_stream)
+    t0 = time.perf_counter()
+    H = G.Hierarchy(ctx, mesh, w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32)
+    t_setup = time.perf_counter() - t0
+    info = H.info
+    n = H.n
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+    H.assemble_rhs(b)
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup):
+        H.solve(b, x, tol=TOL)
+
+    # ---- timed region: K solves, per-kernel CUDA events on the solve stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    H.profile_reset(timing=True)
+    barrier()
+    secs, st = time_solves(torch, H, b, x, args.steps, stream)
+    barrier()
+    kern = H.profile_read()
+    clocks = sampler.stop()
+    t_max = max_over_ranks(secs)
+    total_dofs = sum_over_ranks(float(n) * args.steps)
+    value = total_dofs / t_max
+    iters = st.iterations
+
+    # ---- end to end through host buffers: pinned b in, x out, every step
+    hb = b.cpu().pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    db = torch.empty_like(b)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        db.copy_(hb, non_blocking=True)
+        H.solve(db, x, tol=TOL)
+        hx.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_secs = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    e2e_value = total_dofs / e2e_secs
+    x32 = x.clone()
+
+    # ---- the FP64 V-cycle path on the same problem
+    fp64 = None
+    if not args.no_fp64:
+        H64 = G.Hierarchy(ctx, mesh, w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP64)
+        x64 = torch.zeros_like(b)
+        H64.solve(b, x64, tol=TOL)
+        s64, st64 = time_solves(torch, H64, b, x64, max(1, min(args.steps, 3)), stream)
+        s64 = max_over_ranks(s64)
+        steps64 = max(1, min(args.steps, 3))
+        diff = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
+        fp64 = {"value": sum_over_ranks(float(n) * steps64) / s64, "unit": "DoFs/s",
+                "ms_per_step": 1e3 * s64 / steps64, "iterations": st64.iterations,
+                "rel_diff_fp32_vs_fp64_solution": diff}
+        H64.close()
+
+    # ---- roofline of the dominant kernel (largest share of the timed region)
+    pk = peaks()
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    kd = kern[dom]
+    if dom == "active_apply":
+        achieved = kd["flops"] / (kd["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_src": "nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2070 MHz x 2)"}
+    else:
+        achieved = kd["bytes"] / (kd["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"]}
+    t_all = sum(v["ms"] for v in kern.values())
+    kernels = {}
+    for k, v in kern.items():
+        if v["launches"] == 0:
+            continue
+        kernels[k] = {"launches": v["launches"], "ms": round(v["ms"], 3),
+                      "share": round(v["ms"] / t_all, 4) if t_all else None,
+                      "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] else None,
+                      "TFLOP/s": round(v["flops"] / (v["ms"] / 1e3) / 1e12, 3) if v["ms"] else None}
+    launches = int(sum(v["launches"] for v in kern.values()))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, secs_cpu, ncpu = cpu_baseline()
+        cpu = {"value": v, "unit": "DoFs/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG",
+            "data": "synthetic",
+            "config": {"workload": f"poisson3d_q2_sphere_g{args.global_ref}_a{args.adaptive_ref}",
+                       "unknowns": n, "leaves": int(info.n_leaves), "levels": int(info.n_levels),
+                       "tol": TOL, "cheb_degree": w.cheb_degree, "cg_iterations": iters,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 (active vector {8 * n / 1e6:.0f} MB)",
+                       "setup_s": {"mesh": round(t_mesh, 3), "hierarchy_host": round(info.setup_host_s, 3),
+                                   "hierarchy_device": round(info.setup_device_s, 3),
+                                   "total": round(t_setup, 3)}},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "roofline": roof,
+            "kernels": kernels,
+            "fp64_vcycle": fp64,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,697 @@
+// Device setup and drivers: V-cycle (Algorithm 2, local smoothing of
+// Sec. 2.3), Chebyshev-Jacobi smoothing and eigenvalue estimate (Sec. 4.1),
+// and the outer preconditioned CG.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+
+#include "device_common.cuh"
+
+namespace gmg {
+
+namespace {
+
+template <typename T>
+gmg_status dev_alloc(DeviceState* d, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return GMG_OK;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? GMG_ENOMEM : GMG_ECUDA;
+  }
+  d->bytes += n * sizeof(T);
+  return GMG_OK;
+}
+
+template <typename T>
+gmg_status upload(DeviceState* d, T** p, const std::vector<T>& v) {
+  gmg_status st = dev_alloc(d, p, v.size());
+  if (st != GMG_OK) return st;
+  if (!v.empty()) GMG_CUDA_TRY(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return GMG_OK;
+}
+
+#define GMG_TRY(expr)                  \
+  do {                                 \
+    gmg_status s_ = (expr);            \
+    if (s_ != GMG_OK) return s_;       \
+  } while (0)
+
+int ipow_h(int b, int e) {
+  int r = 1;
+  while (e--) r *= b;
+  return r;
+}
+
+}  // namespace
+
+// ------------------------------------------------------ launch accounting
+static cudaEvent_t take_event(Profile& p) {
+  if (!p.pool.empty()) {
+    cudaEvent_t e = p.pool.back();
+    p.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void drain(DeviceState* d) {
+  Profile& p = d->prof;
+  if (p.pending.empty()) return;
+  cudaStreamSynchronize(d->stream);
+  for (auto& q : p.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) p.ms[q.kind] += ms;
+    p.pool.push_back(q.a);
+    p.pool.push_back(q.b);
+  }
+  p.pending.clear();
+}
+
+// Counts one launch of `kind`; with timing on, brackets it with events.
+struct Track {
+  DeviceState* d;
+  int kind;
+  cudaEvent_t a = nullptr;
+  Track(DeviceState* dd, int k, double bytes, double flops) : d(dd), kind(k) {
+    Profile& p = d->prof;
+    p.launches[k] += 1;
+    p.bytes[k] += bytes;
+    p.flops[k] += flops;
+    if (p.timing) {
+      if (p.pending.size() > 30000) drain(d);
+      a = take_event(p);
+      cudaEventRecord(a, d->stream);
+    }
+  }
+  ~Track() {
+    if (!a) return;
+    cudaEvent_t b = take_event(d->prof);
+    cudaEventRecord(b, d->stream);
+    d->prof.pending.push_back({kind, a, b});
+  }
+};
+
+void profile_reset(Hier& h, bool timing) {
+  DeviceState* d = h.dev;
+  drain(d);
+  Profile& p = d->prof;
+  for (int k = 0; k < GMG_NUM_KERNEL_KINDS; ++k) p.launches[k] = 0, p.ms[k] = p.bytes[k] = p.flops[k] = 0.0;
+  p.timing = timing;
+}
+
+void profile_read(Hier& h, gmg_kernel_stats* out) {
+  DeviceState* d = h.dev;
+  drain(d);
+  cudaStreamSynchronize(d->stream);
+  for (int k = 0; k < GMG_NUM_KERNEL_KINDS; ++k) {
+    out->launches[k] = d->prof.launches[k];
+    out->ms[k] = d->prof.ms[k];
+    out->bytes[k] = d->prof.bytes[k];
+    out->flops[k] = d->prof.flops[k];
+  }
+}
+
+// floating-point operations of one sibling group in the smoothing kernel
+// (nonzeros of the extended 1-D matrices per sum-factorisation stage)
+static double cheb_group_flops(int dim, int k) {
+  std::vector<double> M, K, E;
+  reference_1d(k, M, K, E);
+  const int NH = 3 * k + 1, NE = 2 * k + 1, n1 = k + 1;
+  auto nnz = [&](const std::vector<double>& B) {
+    int c = 0;
+    for (int e = 0; e < NE; ++e)
+      for (int col = 0; col < NH; ++col) {
+        int p = col - k;
+        double v = 0;
+        if (e < 2 * k) {
+          for (int cell = 0; cell < 2; ++cell) {
+            int lo = k * cell;
+            if (e >= lo && e <= lo + k && p >= lo && p <= lo + k) v += std::fabs(B[(e - lo) * n1 + (p - lo)]);
+          }
+        } else if (p >= -k && p <= 0) {
+          v = std::fabs(B[k * n1 + p + k]);
+        }
+        c += v != 0.0;
+      }
+    return c;
+  };
+  double nm = nnz(M), nk = nnz(K);
+  double fma = dim == 3 ? NH * NH * (nm + nk) + NH * NE * (2 * nm + nk) + NE * NE * (nm + nk + NH)
+                        : NH * (nm + nk) + NE * (nm + nk);
+  return 2.0 * fma + 4.0 * std::pow(2 * k, dim);
+}
+
+static double ipow_d(int b, int e) {
+  double r = 1;
+  while (e--) r *= b;
+  return r;
+}
+
+static LevelArgs level_args(const Hier& h, int l) {
+  const LevelDev& L = h.dev->lv[l];
+  LevelArgs a;
+  a.n_groups = L.n_groups;
+  a.nbr = L.nbr;
+  a.state = L.state;
+  a.coeff = L.coeff;
+  a.parent = L.parent;
+  a.nbr_coarse = l >= 2 ? h.dev->lv[l - 1].nbr : nullptr;
+  for (int d = 0; d < 3; ++d) {
+    a.coarse_lat[d] = h.coarse_lattice[d];
+    a.scale[d] = L.scale[d];
+  }
+  a.level = l;
+  return a;
+}
+
+static ActiveArgs active_args(const Hier& h) {
+  ActiveArgs a;
+  a.n_cells = h.dev->n_cells;
+  a.cell_nodes = h.dev->cell_nodes;
+  a.cell_coeff = h.dev->cell_coeff;
+  a.cell_level = h.dev->cell_level;
+  a.hang_ptr = h.dev->hang_ptr;
+  a.hang_col = h.dev->hang_col;
+  a.hang_w = h.dev->hang_w;
+  return a;
+}
+
+// K-term factors s_i = prod_{j != i} h_j / h_i of a level's cells
+static void level_scales(const Hier& h, int l, double* s, double* hh) {
+  for (int d = 0; d < 3; ++d) hh[d] = d < h.dim ? (h.hi[d] - h.lo[d]) / ((double)h.n0[d] * (double)(1ll << l)) : 1.0;
+  for (int i = 0; i < 3; ++i) {
+    if (i >= h.dim) {
+      s[i] = 0.0;
+      continue;
+    }
+    double v = 1.0 / hh[i];
+    for (int j = 0; j < h.dim; ++j)
+      if (j != i) v *= hh[j];
+    s[i] = v;
+  }
+}
+
+void device_free(Hier& h) {
+  DeviceState* d = h.dev;
+  if (!d) return;
+  for (auto& L : d->lv) {
+    cudaFree(L.nbr);
+    cudaFree(L.state);
+    cudaFree(L.coeff);
+    cudaFree(L.parent);
+  }
+  void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
+                  d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
+                  d->partials, d->counter, d->scal};
+  for (void* p : ptrs) cudaFree(p);
+  if (d->scal_host) cudaFreeHost(d->scal_host);
+  for (auto& q : d->prof.pending) {
+    cudaEventDestroy(q.a);
+    cudaEventDestroy(q.b);
+  }
+  for (cudaEvent_t e : d->prof.pool) cudaEventDestroy(e);
+  delete d;
+  h.dev = nullptr;
+}
+
+uint64_t device_bytes(const Hier& h) { return h.dev ? h.dev->bytes : 0; }
+
+static gmg_status ensure_scalars(DeviceState* d, int n) {
+  if (n <= d->max_scal) return GMG_OK;
+  cudaFree(d->scal);
+  if (d->scal_host) cudaFreeHost(d->scal_host);
+  d->scal = nullptr;
+  d->scal_host = nullptr;
+  int cap = std::max(n, 4096);
+  GMG_CUDA_TRY(cudaMalloc(&d->scal, sizeof(double) * cap));
+  GMG_CUDA_TRY(cudaMallocHost(&d->scal_host, sizeof(double) * cap));
+  GMG_CUDA_TRY(cudaMemset(d->scal, 0, sizeof(double) * cap));
+  d->max_scal = cap;
+  return GMG_OK;
+}
+
+static double host_dot(DeviceState* d, int64_t n, const double* a, const double* b) {
+  launch_dot(n, a, b, d->partials, d->counter, d->scal, d->stream);
+  cudaMemcpyAsync(d->scal_host, d->scal, sizeof(double), cudaMemcpyDeviceToHost, d->stream);
+  cudaStreamSynchronize(d->stream);
+  return d->scal_host[0];
+}
+
+// lambda_max of D^{-1} A_l^S: PCG from y0 = 0 on A^S y = b0 with Jacobi
+// preconditioning; Lanczos tridiagonal from the CG coefficients (Sec. 4.1).
+static gmg_status estimate_lambda(Hier& h, int l, double* r, double* z, double* p, double* Ap,
+                                  const double* dinv64, double* out) {
+  DeviceState* d = h.dev;
+  const LevelDev& L = d->lv[l];
+  const LevelHost& LH = h.levels[l];
+  const int64_t n = L.n_slots;
+  cudaStream_t s = d->stream;
+  // start vector on S slots: -5.5 + (rank mod 12), rank in canonical key order
+  std::vector<int64_t> sidx;
+  for (int64_t i = 0; i < n; ++i)
+    if (LH.slot_class[i] == 1) sidx.push_back(i);
+  std::sort(sidx.begin(), sidx.end(), [&](int64_t a, int64_t b) { return LH.slot_key[a] < LH.slot_key[b]; });
+  std::vector<double> b0(n, 0.0);
+  for (size_t i = 0; i < sidx.size(); ++i) b0[sidx[i]] = -5.5 + (double)(i % 12);
+  GMG_CUDA_TRY(cudaMemcpyAsync(r, b0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  GMG_CUDA_TRY(cudaMemsetAsync(Ap, 0, n * sizeof(double), s));
+  launch_mul(n, dinv64, r, z, s);
+  GMG_CUDA_TRY(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double rz = host_dot(d, n, r, z);
+  const double rz0 = rz;
+  const int iters = (int)std::min<int64_t>(h.params.eig_iters, (int64_t)sidx.size());
+  std::vector<double> alpha, beta;
+  LevelArgs a = level_args(h, l);
+  for (int j = 0; j < iters; ++j) {
+    GMG_CUDA_TRY(launch_level_cheb<double>(h.dim, h.k, a, p, nullptr, nullptr, nullptr, Ap, 0.0, 0.0, true, s));
+    double pAp = host_dot(d, n, p, Ap);
+    double al = rz / pAp;
+    alpha.push_back(al);
+    launch_axpy(n, -al, Ap, r, s);
+    launch_mul(n, dinv64, r, z, s);
+    double rz_new = host_dot(d, n, r, z);
+    if (j == iters - 1 || rz_new <= 1e-24 * rz0) break;
+    double be = rz_new / rz;
+    beta.push_back(be);
+    launch_xpay(n, z, be, p, s);
+    rz = rz_new;
+  }
+  GMG_CUDA_TRY(cudaGetLastError());
+  size_t m = alpha.size();
+  std::vector<double> diag(m), off(m > 0 ? m - 1 : 0);
+  for (size_t j = 0; j < m; ++j) {
+    diag[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+    if (j + 1 < m) off[j] = std::sqrt(beta[j]) / alpha[j];
+  }
+  *out = tridiag_max_eig(diag, off);
+  return GMG_OK;
+}
+
+gmg_status device_setup(Hier& h) {
+  auto t0 = std::chrono::steady_clock::now();
+  DeviceState* d = new DeviceState();
+  h.dev = d;
+  d->stream = (cudaStream_t)h.ctx->c.stream;
+  d->prec = h.params.vcycle_prec;
+  const int L = h.L, dim = h.dim, k = h.k;
+  const int NOWN = ipow_h(2 * k, dim);
+  d->lv.resize(L + 1);
+  for (int l = 0; l <= L; ++l) {
+    LevelDev& D = d->lv[l];
+    const LevelHost& H = h.levels[l];
+    D.offset = h.level_offset[l];
+    D.n_slots = h.level_offset[l + 1] - h.level_offset[l];
+    double hh[3];
+    level_scales(h, l, D.scale, hh);
+    D.n_S = (double)H.n_S;
+    D.n_I = (double)H.n_I;
+    if (l == 0) continue;
+    D.cheb_flops = (double)H.n_groups * cheb_group_flops(dim, k);
+    D.n_groups = H.n_groups;
+    GMG_TRY(upload(d, &D.nbr, H.nbr));
+    GMG_TRY(upload(d, &D.state, H.state));
+    GMG_TRY(upload(d, &D.coeff, H.coeff));
+    GMG_TRY(upload(d, &D.parent, H.parent));
+    if (D.n_slots != (H.n_groups + H.n_ghosts) * NOWN) {
+      set_error("level slot count mismatch");
+      return GMG_EINVAL;
+    }
+  }
+  for (int dd = 0; dd < 3; ++dd) d->coarse_lat[dd] = h.coarse_lattice[dd];
+  d->n_coarse = h.n_coarse;
+  GMG_TRY(upload(d, &d->coarse_inv, h.coarse_inverse));
+  // level vectors
+  const size_t esz = d->prec == GMG_PREC_FP32 ? sizeof(float) : sizeof(double);
+  const int64_t ns = h.total_slots;
+  {
+    unsigned char* p;
+    GMG_TRY(dev_alloc(d, &p, ns * esz)); d->uA = p;
+    GMG_TRY(dev_alloc(d, &p, ns * esz)); d->uB = p;
+    GMG_TRY(dev_alloc(d, &p, ns * esz)); d->g = p;
+    GMG_TRY(dev_alloc(d, &p, ns * esz)); d->dinv = p;
+  }
+  // active mesh
+  const ActiveHost& A = h.active;
+  d->n_unknowns = A.n_unknowns;
+  d->n_cells = A.n_cells;
+  GMG_TRY(upload(d, &d->cell_nodes, A.cell_nodes));
+  GMG_TRY(upload(d, &d->cell_coeff, A.cell_coeff));
+  GMG_TRY(upload(d, &d->cell_level, A.cell_level));
+  GMG_TRY(upload(d, &d->cell_coords, A.cell_coords));
+  GMG_TRY(upload(d, &d->hang_ptr, A.hang_ptr));
+  GMG_TRY(upload(d, &d->hang_col, A.hang_col));
+  GMG_TRY(upload(d, &d->hang_w, A.hang_w));
+  GMG_TRY(upload(d, &d->home, A.home_global));
+  for (int l = 0; l < GMG_MAX_LEVELS; ++l) level_scales(h, l, d->level_scale[l], d->cell_h[l]);
+  {
+    const double nc = ipow_d(k + 1, dim);
+    const double per_node = dim == 3 ? 8.0 * (k + 1) + 2.0 : 4.0 * (k + 1) + 2.0;  // FMA per cell node
+    d->active_flops = 2.0 * per_node * nc * (double)A.n_cells;
+    d->active_bytes = (double)A.n_cells * (4.0 * nc + 9.0) + 24.0 * (double)A.n_unknowns +
+                      12.0 * (double)A.hang_col.size();
+  }
+  GMG_CUDA_TRY(set_active_scales(d->level_scale, d->cell_h, h.lo));
+  GMG_TRY(dev_alloc(d, &d->r, A.n_unknowns));
+  GMG_TRY(dev_alloc(d, &d->p, A.n_unknowns));
+  GMG_TRY(dev_alloc(d, &d->Ap, A.n_unknowns));
+  GMG_TRY(dev_alloc(d, &d->z, A.n_unknowns));
+  GMG_TRY(dev_alloc(d, &d->partials, kMaxReduceBlocks));
+  GMG_TRY(dev_alloc(d, &d->counter, 1));
+  GMG_CUDA_TRY(cudaMemset(d->counter, 0, sizeof(unsigned)));
+  GMG_TRY(ensure_scalars(d, 4096));
+  cudaStream_t s = d->stream;
+  // inverse diagonals (FP64), eigenvalue estimates on each level l >= 1
+  double* dinv64 = nullptr;
+  if (d->prec == GMG_PREC_FP64) {
+    dinv64 = (double*)d->dinv;
+  } else {
+    GMG_CUDA_TRY(cudaMalloc(&dinv64, ns * sizeof(double)));
+  }
+  GMG_CUDA_TRY(cudaMemsetAsync(dinv64, 0, ns * sizeof(double), s));
+  for (int l = 1; l <= L; ++l)
+    GMG_CUDA_TRY(launch_level_diag(dim, k, level_args(h, l), dinv64 + d->lv[l].offset, s));
+  h.lambda.assign(L + 1, 0.0);
+  int64_t max_slots = 0;
+  for (int l = 1; l <= L; ++l) max_slots = std::max(max_slots, d->lv[l].n_slots);
+  gmg_status st = GMG_OK;
+  if (max_slots > 0) {
+    double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr;
+    bool need = h.fixed_lambda.empty();
+    if (need) {
+      GMG_CUDA_TRY(cudaMalloc(&r, max_slots * sizeof(double)));
+      GMG_CUDA_TRY(cudaMalloc(&z, max_slots * sizeof(double)));
+      GMG_CUDA_TRY(cudaMalloc(&p, max_slots * sizeof(double)));
+      GMG_CUDA_TRY(cudaMalloc(&Ap, max_slots * sizeof(double)));
+    }
+    for (int l = 1; l <= L && st == GMG_OK; ++l) {
+      if (need) st = estimate_lambda(h, l, r, z, p, Ap, dinv64 + d->lv[l].offset, &h.lambda[l]);
+      else h.lambda[l] = h.fixed_lambda[l];
+    }
+    cudaFree(r);
+    cudaFree(z);
+    cudaFree(p);
+    cudaFree(Ap);
+  }
+  if (st != GMG_OK) return st;
+  if (d->prec == GMG_PREC_FP32) {
+    GMG_CUDA_TRY(launch_convert_d2f(ns, dinv64, (float*)d->dinv, s));
+    GMG_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(dinv64);
+  }
+  for (int l = 1; l <= L; ++l) {
+    LevelDev& D = d->lv[l];
+    D.lambda = h.lambda[l];
+    double a = h.params.eig_lo * D.lambda, b = h.params.eig_hi * D.lambda;
+    D.theta = 0.5 * (a + b);
+    D.delta = 0.5 * (b - a);
+    D.sigma = D.theta / D.delta;
+  }
+  GMG_CUDA_TRY(cudaStreamSynchronize(s));
+  h.setup_device_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return GMG_OK;
+}
+
+// ------------------------------------------------------------- smoothing
+// m Chebyshev updates on level l: x_{j+1} = x_j + rho_j rho_{j-1} (x_j - x_{j-1})
+// + (2 rho_j / delta) D^{-1} (g - A x_j), x_1 = x_0 + D^{-1}(g - A x_0) / theta
+// (Saad, Alg. 12.1, written as a three-term recurrence).  `cur` holds x_0;
+// from_zero: x_0 = 0 and `other` must be zero on every slot.  Returns the
+// buffer that holds the result.
+template <typename T>
+static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cur, T* other, bool from_zero,
+                          T** result) {
+  const LevelDev& D = h.dev->lv[l];
+  cudaStream_t s = h.dev->stream;
+  LevelArgs a = level_args(h, l);
+  const int m = h.params.cheb_degree;
+  double rho = 1.0 / D.sigma;
+  cudaError_t e;
+  const double cheb_bytes = sizeof(T) * (5.0 * D.n_S + D.n_I);
+  if (from_zero) {
+    Track t(h.dev, GMG_K_SMOOTH_FIRST, 3.0 * sizeof(T) * D.n_slots, 2.0 * D.n_slots);
+    e = launch_scale_vec<T>(D.n_slots, dinv, g, (T)(1.0 / D.theta), cur, s);
+  } else {
+    Track t(h.dev, GMG_K_CHEB, cheb_bytes, D.cheb_flops);
+    e = launch_level_cheb<T>(h.dim, h.k, a, cur, nullptr, g, dinv, other, (T)0, (T)(1.0 / D.theta), false, s);
+    std::swap(cur, other);
+  }
+  if (e != cudaSuccess) return e;
+  for (int j = 1; j < m; ++j) {
+    double rho_new = 1.0 / (2.0 * D.sigma - rho);
+    T c1 = (T)(rho_new * rho), c2 = (T)(2.0 * rho_new / D.delta);
+    Track t(h.dev, GMG_K_CHEB, cheb_bytes, D.cheb_flops);
+    e = launch_level_cheb<T>(h.dim, h.k, a, cur, other, g, dinv, other, c1, c2, false, s);
+    if (e != cudaSuccess) return e;
+    std::swap(cur, other);
+    rho = rho_new;
+  }
+  *result = cur;
+  return cudaSuccess;
+}
+
+// z = B r (one V-cycle); rz_out (device) receives r.z.
+template <typename T>
+static gmg_status vcycle_impl(Hier& h, const double* r, double* z, double* rz_out) {
+  DeviceState* d = h.dev;
+  cudaStream_t s = d->stream;
+  const int L = h.L;
+  const size_t bytes = (size_t)h.total_slots * sizeof(T);
+  T* uA = (T*)d->uA;
+  T* uB = (T*)d->uB;
+  T* g = (T*)d->g;
+  const T* dinv = (const T*)d->dinv;
+  GMG_CUDA_TRY(cudaMemsetAsync(uA, 0, bytes, s));
+  GMG_CUDA_TRY(cudaMemsetAsync(uB, 0, bytes, s));
+  GMG_CUDA_TRY(cudaMemsetAsync(g, 0, bytes, s));
+  {
+    Track t(d, GMG_K_COPY_TO, (12.0 + sizeof(T)) * d->n_unknowns, 0.0);
+    GMG_CUDA_TRY(launch_copy_to_mg<T>(d->n_unknowns, r, d->home, g, s));
+  }
+  const double kd = ipow_d(h.k, h.dim);
+  // down-sweep: pre-smoothing on V^S from zero, residual on S u I, restriction
+  for (int l = L; l >= 1; --l) {
+    const LevelDev& D = d->lv[l];
+    T* res = nullptr;
+    GMG_CUDA_TRY(smooth<T>(h, l, g + D.offset, dinv + D.offset, uA + D.offset, uB + D.offset, true, &res));
+    Track t(d, GMG_K_RESTRICT, sizeof(T) * (2.0 * (D.n_S + D.n_I) + 2.0 * kd * D.n_groups), 0.0);
+    GMG_CUDA_TRY(launch_level_residual_restrict<T>(h.dim, h.k, level_args(h, l), res, g + D.offset,
+                                                   g + d->lv[l - 1].offset, s));
+  }
+  // The smoother alternates buffers so that every level's final result (after
+  // m pre- and m post-smoothing updates) ends in uB; the coarse solution goes
+  // there too.
+  {
+    const double nc = (double)d->n_coarse;
+    Track t(d, GMG_K_COARSE, 8.0 * nc * nc + 2.0 * sizeof(T) * nc, 2.0 * nc * nc);
+    GMG_CUDA_TRY(launch_coarse_solve<T>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv, g, uB, s));
+  }
+  for (int l = 1; l <= L; ++l) {
+    const LevelDev& D = d->lv[l];
+    const int m = h.params.cheb_degree;
+    T* pre = (m % 2 == 1) ? uA + D.offset : uB + D.offset;
+    T* oth = (m % 2 == 1) ? uB + D.offset : uA + D.offset;
+    {
+      Track t(d, GMG_K_PROLONG, sizeof(T) * (kd * D.n_groups + 2.0 * D.n_S + 2.0 * D.n_I), 0.0);
+      GMG_CUDA_TRY(launch_level_prolongate<T>(h.dim, h.k, level_args(h, l), uB + d->lv[l - 1].offset, pre, oth, s));
+    }
+    T* res = nullptr;
+    GMG_CUDA_TRY(smooth<T>(h, l, g + D.offset, dinv + D.offset, pre, oth, false, &res));
+    if (res != uB + D.offset) {
+      set_error("internal: V-cycle result not in the final buffer");
+      return GMG_EINVAL;
+    }
+  }
+  Track t(d, GMG_K_COPY_FROM, (20.0 + sizeof(T)) * d->n_unknowns, 2.0 * d->n_unknowns);
+  GMG_CUDA_TRY(launch_copy_from_mg<T>(d->n_unknowns, uB, d->home, r, z, d->partials, d->counter, rz_out, s));
+  return GMG_OK;
+}
+
+static gmg_status vcycle_any(Hier& h, const double* r, double* z, double* rz_out) {
+  if (h.dev->prec == GMG_PREC_FP32) return vcycle_impl<float>(h, r, z, rz_out);
+  return vcycle_impl<double>(h, r, z, rz_out);
+}
+
+gmg_status device_vcycle(Hier& h, const double* r, double* z) {
+  GMG_TRY(ensure_scalars(h.dev, 8));
+  return vcycle_any(h, r, z, h.dev->scal + 1);
+}
+
+gmg_status device_apply(Hier& h, const double* x, double* y) {
+  DeviceState* d = h.dev;
+  GMG_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * d->n_unknowns, d->stream));
+  Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
+  GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), x, y, d->partials, d->counter, nullptr, d->stream));
+  return GMG_OK;
+}
+
+gmg_status device_rhs(Hier& h, int kind, double* b) {
+  DeviceState* d = h.dev;
+  if (kind != 0) {
+    set_error("gmg_assemble_rhs: unknown kind");
+    return GMG_EINVAL;
+  }
+  GMG_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * d->n_unknowns, d->stream));
+  GMG_CUDA_TRY(launch_rhs_sine(h.dim, h.k, active_args(h), d->cell_coords, b, d->stream));
+  return GMG_OK;
+}
+
+// Preconditioned CG (x0 = 0).  Scalars live on the device: slot 0 = b.b,
+// slots 1+3i .. 3+3i = (r_i.z_i, p_i.A p_i, r_{i+1}.r_{i+1}) of iteration i.
+gmg_status device_solve(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
+                        gmg_stats* st) {
+  DeviceState* d = h.dev;
+  cudaStream_t s = d->stream;
+  const int64_t n = d->n_unknowns;
+  const int limit = fixed_iterations > 0 ? fixed_iterations : max_iter;
+  GMG_TRY(ensure_scalars(d, 3 * limit + 8));
+  double* S = d->scal;
+  double* H = d->scal_host;
+  GMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  GMG_CUDA_TRY(cudaMemcpyAsync(d->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  {
+    Track t(d, GMG_K_OTHER, 8.0 * n, 2.0 * n);
+    GMG_CUDA_TRY(launch_dot(n, b, b, d->partials, d->counter, S, s));
+  }
+  GMG_CUDA_TRY(cudaMemcpyAsync(H, S, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GMG_CUDA_TRY(cudaStreamSynchronize(s));
+  const double bb = H[0];
+  gmg_stats stats;
+  stats.iterations = 0;
+  stats.converged = 0;
+  stats.rel_residual = bb > 0 ? 1.0 : 0.0;
+  stats.norm_b = std::sqrt(bb);
+  if (!(bb > 0.0)) {
+    stats.converged = 1;
+    if (st) *st = stats;
+    if (std::isnan(bb)) {
+      set_error("right-hand side contains NaN");
+      return GMG_ENAN;
+    }
+    return GMG_OK;
+  }
+  GMG_TRY(vcycle_any(h, d->r, d->z, S + 1));
+  GMG_CUDA_TRY(cudaMemcpyAsync(d->p, d->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  gmg_status result = GMG_ENOTCONV;
+  for (int it = 0; it < limit; ++it) {
+    double* base = S + 1 + 3 * it;
+    GMG_CUDA_TRY(cudaMemsetAsync(d->Ap, 0, sizeof(double) * n, s));
+    {
+      Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
+      GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), d->p, d->Ap, d->partials, d->counter, base + 1, s));
+    }
+    {
+      Track t(d, GMG_K_CG_XR, 48.0 * n, 6.0 * n);
+      GMG_CUDA_TRY(launch_cg_update_xr(n, x, d->r, d->p, d->Ap, base, base + 1, d->partials, d->counter, base + 2, s));
+    }
+    GMG_CUDA_TRY(cudaMemcpyAsync(H + 1 + 3 * it, base, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GMG_CUDA_TRY(cudaStreamSynchronize(s));
+    const double rz = H[1 + 3 * it], pAp = H[2 + 3 * it], rr = H[3 + 3 * it];
+    stats.iterations = it + 1;
+    stats.rel_residual = std::sqrt(rr / bb);
+    if (std::isnan(rz) || std::isnan(pAp) || std::isnan(rr) || std::isinf(rr)) {
+      set_error("NaN/Inf in a CG scalar");
+      result = GMG_ENAN;
+      break;
+    }
+    if (!(pAp > 0.0)) {
+      set_error("CG breakdown: p.Ap <= 0");
+      result = GMG_EBREAKDOWN;
+      break;
+    }
+    if (fixed_iterations > 0) {
+      if (it + 1 == fixed_iterations) {
+        stats.converged = stats.rel_residual <= tol;
+        result = GMG_OK;
+        break;
+      }
+    } else if (stats.rel_residual <= tol) {
+      stats.converged = 1;
+      result = GMG_OK;
+      break;
+    }
+    if (it + 1 == limit) break;
+    GMG_TRY(vcycle_any(h, d->r, d->z, base + 3));
+    Track t(d, GMG_K_CG_P, 24.0 * n, 2.0 * n);
+    GMG_CUDA_TRY(launch_cg_update_p(n, d->p, d->z, base + 3, base, s));
+  }
+  if (result == GMG_ENOTCONV) set_error("CG did not converge within max_iter");
+  if (st) *st = stats;
+  return result;
+}
+
+// ------------------------------------------------- level operations (tests)
+template <typename T>
+static gmg_status level_apply_t(Hier& h, int l, const void* x, void* y) {
+  GMG_CUDA_TRY(launch_level_cheb<T>(h.dim, h.k, level_args(h, l), (const T*)x, nullptr, nullptr, nullptr, (T*)y,
+                                    (T)0, (T)0, true, h.dev->stream));
+  return GMG_OK;
+}
+gmg_status device_level_apply(Hier& h, int l, const void* x, void* y) {
+  return h.dev->prec == GMG_PREC_FP32 ? level_apply_t<float>(h, l, x, y) : level_apply_t<double>(h, l, x, y);
+}
+
+gmg_status device_level_residual_restrict(Hier& h, int l, const void* u, const void* g, void* gc) {
+  cudaError_t e = h.dev->prec == GMG_PREC_FP32
+                      ? launch_level_residual_restrict<float>(h.dim, h.k, level_args(h, l), (const float*)u,
+                                                              (const float*)g, (float*)gc, h.dev->stream)
+                      : launch_level_residual_restrict<double>(h.dim, h.k, level_args(h, l), (const double*)u,
+                                                               (const double*)g, (double*)gc, h.dev->stream);
+  GMG_CUDA_TRY(e);
+  return GMG_OK;
+}
+
+gmg_status device_level_prolongate(Hier& h, int l, const void* uc, void* u, void* u2) {
+  cudaError_t e = h.dev->prec == GMG_PREC_FP32
+                      ? launch_level_prolongate<float>(h.dim, h.k, level_args(h, l), (const float*)uc, (float*)u,
+                                                       (float*)u2, h.dev->stream)
+                      : launch_level_prolongate<double>(h.dim, h.k, level_args(h, l), (const double*)uc, (double*)u,
+                                                        (double*)u2, h.dev->stream);
+  GMG_CUDA_TRY(e);
+  return GMG_OK;
+}
+
+template <typename T>
+static gmg_status level_smooth_t(Hier& h, int l, const void* g, void* u, void* tmp, int from_zero) {
+  DeviceState* d = h.dev;
+  const LevelDev& D = d->lv[l];
+  const T* dinv = (const T*)d->dinv + D.offset;
+  T* res = nullptr;
+  if (from_zero) GMG_CUDA_TRY(cudaMemsetAsync(tmp, 0, D.n_slots * sizeof(T), d->stream));
+  else GMG_CUDA_TRY(cudaMemcpyAsync(tmp, u, D.n_slots * sizeof(T), cudaMemcpyDeviceToDevice, d->stream));
+  GMG_CUDA_TRY(smooth<T>(h, l, (const T*)g, dinv, (T*)u, (T*)tmp, from_zero != 0, &res));
+  if (res != (T*)u)
+    GMG_CUDA_TRY(cudaMemcpyAsync(u, res, D.n_slots * sizeof(T), cudaMemcpyDeviceToDevice, d->stream));
+  return GMG_OK;
+}
+gmg_status device_level_smooth(Hier& h, int l, const void* g, void* u, void* tmp, int from_zero) {
+  return h.dev->prec == GMG_PREC_FP32 ? level_smooth_t<float>(h, l, g, u, tmp, from_zero)
+                                      : level_smooth_t<double>(h, l, g, u, tmp, from_zero);
+}
+
+gmg_status device_level_inv_diag(Hier& h, int l, void* out) {
+  DeviceState* d = h.dev;
+  const LevelDev& D = d->lv[l];
+  size_t esz = d->prec == GMG_PREC_FP32 ? sizeof(float) : sizeof(double);
+  GMG_CUDA_TRY(cudaMemcpyAsync(out, (const unsigned char*)d->dinv + D.offset * esz, D.n_slots * esz,
+                               cudaMemcpyDeviceToDevice, d->stream));
+  return GMG_OK;
+}
+
+gmg_status device_coarse_solve(Hier& h, const void* g0, void* u0) {
+  DeviceState* d = h.dev;
+  cudaError_t e = d->prec == GMG_PREC_FP32
+                      ? launch_coarse_solve<float>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv,
+                                                   (const float*)g0, (float*)u0, d->stream)
+                      : launch_coarse_solve<double>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv,
+                                                    (const double*)g0, (double*)u0, d->stream);
+  GMG_CUDA_TRY(e);
+  return GMG_OK;
+}
+
+}  // namespace gmg

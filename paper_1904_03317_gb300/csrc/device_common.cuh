@@ -1,0 +1,168 @@
+// Device-side declarations shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "gmg_internal.h"
+
+namespace gmg {
+
+#define GMG_CUDA_TRY(expr)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_error(std::string("CUDA error: ") + cudaGetErrorString(e_) + " at " +    \
+                __FILE__ + ":" + std::to_string(__LINE__));                        \
+      return GMG_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+// Per-level device data (level l >= 1 is stored by sibling groups).
+struct LevelDev {
+  int64_t n_groups = 0;
+  int64_t n_slots = 0;
+  int64_t offset = 0;           // in the concatenated level vectors
+  int32_t* nbr = nullptr;       // n_groups x 3^d
+  uint64_t* state = nullptr;    // n_groups
+  double* coeff = nullptr;      // n_groups
+  int32_t* parent = nullptr;    // n_groups
+  double scale[3] = {0, 0, 0};  // K-term factor per direction: prod_{j!=i} h_j / h_i
+  // Chebyshev parameters (host)
+  double lambda = 0, theta = 0, delta = 0, sigma = 0;
+  // accounting: S and I nodes, FP operations of one smoothing launch
+  double n_S = 0, n_I = 0, cheb_flops = 0;
+};
+
+// Arguments of the level kernels, passed by value.
+struct LevelArgs {
+  int64_t n_groups;
+  const int32_t* nbr;
+  const uint64_t* state;
+  const double* coeff;
+  const int32_t* parent;
+  const int32_t* nbr_coarse;  // level l-1 neighbour table (l >= 2)
+  int64_t coarse_lat[3];      // coarse lattice extents (l == 1)
+  double scale[3];
+  int level;
+};
+
+// Launch accounting (gmg_profile_*).
+struct Profile {
+  uint64_t launches[GMG_NUM_KERNEL_KINDS] = {};
+  double ms[GMG_NUM_KERNEL_KINDS] = {};
+  double bytes[GMG_NUM_KERNEL_KINDS] = {};
+  double flops[GMG_NUM_KERNEL_KINDS] = {};
+  bool timing = false;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+};
+
+struct DeviceState {
+  cudaStream_t stream = nullptr;
+  Profile prof;
+  int prec = GMG_PREC_FP32;
+  size_t bytes = 0;
+  std::vector<LevelDev> lv;
+  // concatenated level vectors in the V-cycle precision
+  void* uA = nullptr;
+  void* uB = nullptr;
+  void* g = nullptr;
+  void* dinv = nullptr;
+  // coarse level
+  double* coarse_inv = nullptr;  // n_coarse^2
+  int64_t n_coarse = 0;
+  int64_t coarse_lat[3] = {1, 1, 1};
+  // active (leaf) mesh
+  int64_t n_unknowns = 0, n_cells = 0;
+  int32_t* cell_nodes = nullptr;
+  double* cell_coeff = nullptr;
+  uint8_t* cell_level = nullptr;
+  int32_t* cell_coords = nullptr;
+  int32_t* hang_ptr = nullptr;
+  int32_t* hang_col = nullptr;
+  double* hang_w = nullptr;
+  uint32_t* home = nullptr;
+  double level_scale[GMG_MAX_LEVELS][3];  // leaf-cell operator factors per level
+  double cell_h[GMG_MAX_LEVELS][3];       // cell sizes per level
+  // CG work vectors
+  double* r = nullptr;
+  double* p = nullptr;
+  double* Ap = nullptr;
+  double* z = nullptr;
+  // reductions
+  double* partials = nullptr;     // kMaxReduceBlocks
+  unsigned* counter = nullptr;
+  double* scal = nullptr;         // device scalars (see ScalarSlot)
+  double* scal_host = nullptr;    // pinned mirror
+  int max_scal = 0;
+  double active_flops = 0, active_bytes = 0;  // per leaf-operator launch
+};
+
+constexpr int kMaxReduceBlocks = 4096;
+
+// ------------------------------------------------------------ launchers
+// Level kernels (kernels_level.cu).  T = float or double; all pointers are
+// level-local (already offset to the level's first slot) unless noted.
+template <typename T>
+cudaError_t launch_level_cheb(int dim, int k, const LevelArgs& a, const T* x, const T* xprev,
+                              const T* g, const T* dinv, T* out, T c1, T c2, bool apply_only,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_level_residual_restrict(int dim, int k, const LevelArgs& a, const T* u,
+                                           const T* g, T* gc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_level_prolongate(int dim, int k, const LevelArgs& a, const T* uc, T* u, T* u2,
+                                    cudaStream_t s);
+cudaError_t launch_level_diag(int dim, int k, const LevelArgs& a, double* diag_inv,
+                              cudaStream_t s);
+
+// Active mesh and vector kernels (kernels_active.cu).
+struct ActiveArgs {
+  int64_t n_cells;
+  const int32_t* cell_nodes;
+  const double* cell_coeff;
+  const uint8_t* cell_level;
+  const int32_t* hang_ptr;
+  const int32_t* hang_col;
+  const double* hang_w;
+};
+cudaError_t launch_active_apply(int dim, int k, const ActiveArgs& a, const double* x, double* y,
+                                double* partials, unsigned* counter, double* energy_out,
+                                cudaStream_t s);
+cudaError_t set_active_scales(const double scale[GMG_MAX_LEVELS][3],
+                              const double h[GMG_MAX_LEVELS][3], const double lo[3]);
+cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* cell_coords,
+                            double* b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_to_mg(int64_t n, const double* r, const uint32_t* home, T* g,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_from_mg(int64_t n, const T* u, const uint32_t* home, const double* r,
+                                double* z, double* partials, unsigned* counter, double* rz_out,
+                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(int dim, int64_t n_coarse, const int64_t lat[3],
+                                const double* inv, const T* g0, T* u0, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, cudaStream_t s);
+cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials,
+                       unsigned* counter, double* out, cudaStream_t s);
+cudaError_t launch_cg_update_xr(int64_t n, double* x, double* r, const double* p,
+                                const double* Ap, const double* rz, const double* pAp,
+                                double* partials, unsigned* counter, double* rr_out,
+                                cudaStream_t s);
+cudaError_t launch_cg_update_p(int64_t n, double* p, const double* z, const double* rz_new,
+                               const double* rz_old, cudaStream_t s);
+cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_mul(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
+cudaError_t launch_xpay(int64_t n, const double* x, double beta, double* y, cudaStream_t s);
+cudaError_t launch_convert_d2f(int64_t n, const double* in, float* out, cudaStream_t s);
+
+}  // namespace gmg

@@ -1,0 +1,685 @@
+// Host construction of the multigrid hierarchy (setup; Sec. 2.3 and Sec. 1).
+//
+// Level l >= 1 consists of all cells of level l (leaves or not).  They come
+// in sibling groups -- the 2^d children of a refined cell of level l-1 --
+// and each group is stored as one block of (2k)^d nodes (see LevelHost).
+// A node of level l is
+//   D  if it lies on the boundary of the brick (value fixed to 0),
+//   I  if some level-l lattice cell inside the brick whose closure contains
+//      it does not exist (refinement edge, Sec. 2.3, Fig. 1),
+//   S  otherwise (strictly inside the level-l cells).
+// Because the level-l lattice cells touching a node are children of the
+// refined level-(l-1) positions touching it, the class follows from the
+// states of the 3^d parent positions around a group.
+//
+// The leaf mesh: its nodes are the nodes of the leaf cells; a node lying in
+// the closure of a coarser leaf without being one of its nodes is hanging
+// and takes the value of that leaf's interpolant (Sec. 1).  Unknowns are the
+// leaf nodes that are neither hanging nor on the boundary, in key order.
+// Each unknown is copied to one level only, its home level: the coarsest
+// level of the leaves that contain it, where it is an S node.
+#include <omp.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+#include <stdexcept>
+
+#include "gmg_internal.h"
+
+namespace gmg {
+
+// ------------------------------------------------------------- 1-D tables
+static void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  // Gauss-Legendre on [0, 1] for n = 1..3 (exact to degree 2n-1)
+  x.clear();
+  w.clear();
+  if (n == 1) {
+    x = {0.5};
+    w = {1.0};
+  } else if (n == 2) {
+    double a = 0.5 / std::sqrt(3.0);
+    x = {0.5 - a, 0.5 + a};
+    w = {0.5, 0.5};
+  } else if (n == 3) {
+    double a = 0.5 * std::sqrt(0.6);
+    x = {0.5 - a, 0.5, 0.5 + a};
+    w = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  } else {
+    throw std::runtime_error("gauss_rule: unsupported n");
+  }
+}
+
+static double lagrange(int k, int j, double t) {
+  double v = 1.0;
+  for (int m = 0; m <= k; ++m)
+    if (m != j) v *= (t - (double)m / k) / ((double)(j - m) / k);
+  return v;
+}
+
+static double lagrange_d(int k, int j, double t) {
+  double s = 0.0;
+  for (int i = 0; i <= k; ++i) {
+    if (i == j) continue;
+    double v = 1.0 / ((double)(j - i) / k);
+    for (int m = 0; m <= k; ++m)
+      if (m != j && m != i) v *= (t - (double)m / k) / ((double)(j - m) / k);
+    s += v;
+  }
+  return s;
+}
+
+void reference_1d(int k, std::vector<double>& M, std::vector<double>& K, std::vector<double>& E) {
+  int n = k + 1;
+  std::vector<double> xq, wq;
+  gauss_rule(n, xq, wq);
+  M.assign(n * n, 0.0);
+  K.assign(n * n, 0.0);
+  for (int q = 0; q < n; ++q)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        M[i * n + j] += wq[q] * lagrange(k, i, xq[q]) * lagrange(k, j, xq[q]);
+        K[i * n + j] += wq[q] * lagrange_d(k, i, xq[q]) * lagrange_d(k, j, xq[q]);
+      }
+  // parent basis at the 2k+1 child nodes of the parent interval
+  E.assign((2 * k + 1) * n, 0.0);
+  for (int r = 0; r <= 2 * k; ++r)
+    for (int j = 0; j < n; ++j) {
+      double v = lagrange(k, j, (double)r / (2 * k));
+      E[r * n + j] = std::fabs(v) < 1e-15 ? 0.0 : v;
+    }
+}
+
+bool spd_inverse(std::vector<double>& A, int64_t n) {
+  // Cholesky A = L L^T in place (lower), then A^{-1} = L^-T L^-1.
+  std::vector<double> Lm(A);
+  for (int64_t j = 0; j < n; ++j) {
+    double s = Lm[j * n + j];
+    for (int64_t p = 0; p < j; ++p) s -= Lm[j * n + p] * Lm[j * n + p];
+    if (!(s > 0.0)) return false;
+    double d = std::sqrt(s);
+    Lm[j * n + j] = d;
+#pragma omp parallel for if (n > 256)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double t = Lm[i * n + j];
+      for (int64_t p = 0; p < j; ++p) t -= Lm[i * n + p] * Lm[j * n + p];
+      Lm[i * n + j] = t / d;
+    }
+  }
+  // invert L (lower triangular) column by column
+  std::vector<double> Li(n * n, 0.0);
+#pragma omp parallel for if (n > 256)
+  for (int64_t c = 0; c < n; ++c) {
+    for (int64_t i = c; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int64_t p = c; p < i; ++p) t -= Lm[i * n + p] * Li[p * n + c];
+      Li[i * n + c] = t / Lm[i * n + i];
+    }
+  }
+  // A^{-1} = Li^T Li
+#pragma omp parallel for if (n > 256)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      double t = 0.0;
+      for (int64_t p = std::max(i, j); p < n; ++p) t += Li[p * n + i] * Li[p * n + j];
+      A[i * n + j] = t;
+    }
+  return true;
+}
+
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  // largest eigenvalue of the symmetric tridiagonal (diag a, off-diagonal b)
+  // by Sturm-sequence bisection on a Gershgorin interval
+  size_t m = a.size();
+  if (m == 0) return 0.0;
+  double lo = a[0], hi = a[0];
+  for (size_t i = 0; i < m; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // number of eigenvalues < x
+    int cnt = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < m; ++i) {
+      double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+      d = a[i] - x - (i > 0 ? bb / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0.0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= (int)m) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// ---------------------------------------------------------------- helpers
+static inline int ipow(int b, int e) {
+  int r = 1;
+  while (e--) r *= b;
+  return r;
+}
+
+static void parallel_sort_u64(std::vector<uint64_t>& v) {
+  // LSD radix sort, 16-bit digits, skipping digits above the largest key
+  if (v.empty()) return;
+  uint64_t mx = 0;
+#pragma omp parallel for reduction(max : mx)
+  for (size_t i = 0; i < v.size(); ++i) mx = std::max(mx, v[i]);
+  int bits = 0;
+  while (bits < 64 && (mx >> bits)) bits += 16;
+  std::vector<uint64_t> tmp(v.size());
+  int nt = omp_get_max_threads();
+  for (int shift = 0; shift < bits; shift += 16) {
+    std::vector<size_t> hist((size_t)nt * 65536, 0);
+    size_t n = v.size();
+#pragma omp parallel num_threads(nt)
+    {
+      int t = omp_get_thread_num();
+      size_t b = n * t / nt, e = n * (t + 1) / nt;
+      size_t* h = &hist[(size_t)t * 65536];
+      for (size_t i = b; i < e; ++i) ++h[(v[i] >> shift) & 0xFFFF];
+    }
+    size_t sum = 0;
+    for (int d = 0; d < 65536; ++d)
+      for (int t = 0; t < nt; ++t) {
+        size_t c = hist[(size_t)t * 65536 + d];
+        hist[(size_t)t * 65536 + d] = sum;
+        sum += c;
+      }
+#pragma omp parallel num_threads(nt)
+    {
+      int t = omp_get_thread_num();
+      size_t b = n * t / nt, e = n * (t + 1) / nt;
+      size_t* h = &hist[(size_t)t * 65536];
+      for (size_t i = b; i < e; ++i) tmp[h[(v[i] >> shift) & 0xFFFF]++] = v[i];
+    }
+    v.swap(tmp);
+  }
+}
+
+static inline int64_t lower_index(const std::vector<uint64_t>& keys, uint64_t k) {
+  auto it = std::lower_bound(keys.begin(), keys.end(), k);
+  if (it == keys.end() || *it != k) return -1;
+  return it - keys.begin();
+}
+
+// ------------------------------------------------------------------ build
+void build_host_hierarchy(Hier& h, const Forest& f) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int dim = f.dim, k = h.k;
+  h.dim = dim;
+  for (int d = 0; d < 3; ++d) {
+    h.n0[d] = f.n0[d];
+    h.lo[d] = f.lo[d];
+    h.hi[d] = d < dim ? f.hi[d] : f.lo[d] + 1.0;
+  }
+  const int L = f.num_levels() - 1;
+  h.L = L;
+  if (L > 20) throw std::runtime_error("more than 20 levels");
+  const int NO = 2 * k;                  // owned nodes per direction of a block
+  const int NOWN = ipow(NO, dim);        // nodes per block
+  const int NNB = ipow(3, dim);          // neighbour offsets incl. centre
+  const int NLOC = ipow(k + 1, dim);     // nodes per cell
+  std::vector<double> M1, K1, E1;
+  reference_1d(k, M1, K1, E1);
+
+  auto coarse_coeff_of = [&](int level, const int64_t* c) {
+    int64_t cc[3];
+    for (int d = 0; d < 3; ++d) cc[d] = d < dim ? c[d] >> level : 0;
+    return h.coarse_coeff[cc[0] + (int64_t)h.n0[0] * (cc[1] + (int64_t)h.n0[1] * cc[2])];
+  };
+  auto node_key = [&](int level, const int64_t* q) -> int64_t {
+    int s = L - level;
+    return (int64_t)pack3(q[0] << s, dim > 1 ? q[1] << s : 0, dim > 2 ? q[2] << s : 0);
+  };
+  int64_t node_ext[3];  // largest finest-lattice node coordinate per direction
+  for (int d = 0; d < 3; ++d) node_ext[d] = d < dim ? (int64_t)h.n0[d] * k << L : 0;
+  auto key_is_boundary = [&](uint64_t key) {
+    int64_t q[3];
+    unpack3(key, q);
+    for (int d = 0; d < dim; ++d)
+      if (q[d] == 0 || q[d] == node_ext[d]) return true;
+    return false;
+  };
+
+  h.levels.assign(L + 1, LevelHost());
+  h.level_offset.assign(L + 2, 0);
+
+  // ---------------------------------------------------- level 0: lattice
+  {
+    LevelHost& lv = h.levels[0];
+    lv.level = 0;
+    int64_t n = 1;
+    for (int d = 0; d < 3; ++d) {
+      h.coarse_lattice[d] = d < dim ? (int64_t)k * h.n0[d] + 1 : 1;
+      n *= h.coarse_lattice[d];
+    }
+    lv.slot_class.assign(n, 0);
+    lv.slot_key.assign(n, -1);
+    h.n_coarse = 0;
+    for (int64_t z = 0; z < h.coarse_lattice[2]; ++z)
+      for (int64_t y = 0; y < h.coarse_lattice[1]; ++y)
+        for (int64_t x = 0; x < h.coarse_lattice[0]; ++x) {
+          int64_t s = x + h.coarse_lattice[0] * (y + h.coarse_lattice[1] * z);
+          int64_t q[3] = {x, y, z};
+          lv.slot_key[s] = node_key(0, q);
+          bool bd = key_is_boundary((uint64_t)lv.slot_key[s]);
+          lv.slot_class[s] = bd ? 3 : 1;
+          if (!bd) ++h.n_coarse;
+        }
+    lv.n_cells = (uint64_t)h.n0[0] * h.n0[1] * h.n0[2];
+    lv.n_S = h.n_coarse;
+  }
+  h.level_offset[1] = (int64_t)h.levels[0].slot_class.size();
+
+  // ------------------------------------------------ levels l >= 1: blocks
+  std::vector<HashMap64> block_map(L + 1);  // parent position (level l-1) -> block index
+  for (int l = 1; l <= L; ++l) {
+    LevelHost& lv = h.levels[l];
+    lv.level = l;
+    // groups = refined cells of level l-1, in canonical (tree, Morton) order
+    struct G {
+      uint64_t tree, morton;
+      int64_t c[3];
+    };
+    std::vector<G> gs;
+    int Lp = l - 1;
+    f.cells[Lp].for_each([&](uint64_t key, int32_t v) {
+      if (!v) return;
+      G g;
+      unpack3(key, g.c);
+      int64_t t[3], loc[3];
+      for (int d = 0; d < 3; ++d) {
+        t[d] = g.c[d] >> Lp;
+        loc[d] = g.c[d] - (t[d] << Lp);
+      }
+      g.tree = (uint64_t)(t[0] + (int64_t)h.n0[0] * (t[1] + (int64_t)h.n0[1] * t[2]));
+      uint64_t m = 0;
+      for (int i = 0; i < 21; ++i)
+        for (int d = 0; d < dim; ++d) m |= (((uint64_t)loc[d] >> i) & 1ull) << (dim * i + d);
+      g.morton = m;
+      gs.push_back(g);
+    });
+    std::sort(gs.begin(), gs.end(), [](const G& a, const G& b) {
+      return a.tree != b.tree ? a.tree < b.tree : a.morton < b.morton;
+    });
+    lv.n_groups = (int64_t)gs.size();
+    HashMap64& bm = block_map[l];
+    bm.reserve(gs.size() * 2);
+    lv.block_pos.resize(3 * gs.size());
+    for (size_t i = 0; i < gs.size(); ++i) {
+      bm.insert(pack3(gs[i].c[0], gs[i].c[1], gs[i].c[2]), (int32_t)i);
+      for (int d = 0; d < 3; ++d) lv.block_pos[3 * i + d] = gs[i].c[d];
+    }
+    lv.nbr.assign((size_t)lv.n_groups * NNB, -1);
+    lv.state.assign(lv.n_groups, 0);
+    lv.coeff.resize(lv.n_groups);
+    lv.parent.resize(lv.n_groups);
+    int64_t next_ghost = lv.n_groups;
+    for (int64_t g = 0; g < lv.n_groups; ++g) {
+      const int64_t* p = gs[g].c;
+      uint64_t st = 0;
+      for (int nb = 0; nb < NNB; ++nb) {
+        int o[3] = {nb % 3 - 1, dim > 1 ? (nb / 3) % 3 - 1 : 0, dim > 2 ? nb / 9 - 1 : 0};
+        int64_t q[3] = {p[0] + o[0], p[1] + o[1], p[2] + o[2]};
+        int s;
+        int32_t slot;
+        if (!f.inside(Lp, q)) {
+          s = kStateOutside;
+          slot = -1;
+        } else if (f.refined(Lp, q)) {
+          s = kStateRefined;
+          slot = *bm.find(pack3(q[0], q[1], q[2]));
+        } else {
+          s = kStateGhost;
+          auto ins = bm.insert(pack3(q[0], q[1], q[2]), (int32_t)next_ghost);
+          if (ins.second) {
+            ++next_ghost;
+            for (int d = 0; d < 3; ++d) lv.block_pos.push_back(q[d]);
+          }
+          slot = *ins.first;
+        }
+        lv.nbr[(size_t)g * NNB + nb] = slot;
+        st |= (uint64_t)s << (2 * nb);
+      }
+      // child position of the parent cell inside its own sibling group
+      uint64_t cb = (p[0] & 1) | (dim > 1 ? (p[1] & 1) << 1 : 0) | (dim > 2 ? (p[2] & 1) << 2 : 0);
+      st |= cb << 60;
+      lv.state[g] = st;
+      lv.coeff[g] = coarse_coeff_of(Lp, p);
+      if (l == 1) {
+        lv.parent[g] = (int32_t)(p[0] + (int64_t)h.n0[0] * (p[1] + (int64_t)h.n0[1] * p[2]));
+      } else {
+        const int32_t* pp = block_map[l - 1].find(pack3(p[0] >> 1, dim > 1 ? p[1] >> 1 : 0,
+                                                        dim > 2 ? p[2] >> 1 : 0));
+        if (!pp || *pp >= h.levels[l - 1].n_groups)
+          throw std::runtime_error("parent of a refined cell is not a sibling group");
+        lv.parent[g] = *pp;
+      }
+    }
+    lv.n_ghosts = next_ghost - lv.n_groups;
+    int64_t nslots = (lv.n_groups + lv.n_ghosts) * NOWN;
+    h.level_offset[l + 1] = h.level_offset[l] + nslots;
+    // slot classes and keys, from every real group's (2k+1)^d node block
+    lv.slot_class.assign(nslots, 0);
+    lv.slot_key.assign(nslots, -1);
+    const int NG = 2 * k + 1;
+    const int NGRP = ipow(NG, dim);
+    bool bad = false;
+    // pass 0 writes every node's class and key; pass 1 re-derives them from
+    // every group that touches the node and checks that all groups agree
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < lv.n_groups; ++g) {
+      const int64_t* p = gs[g].c;
+      uint64_t st = lv.state[g];
+      for (int n = 0; n < NGRP; ++n) {
+        int loc[3] = {n % NG, dim > 1 ? (n / NG) % NG : 0, dim > 2 ? n / (NG * NG) : 0};
+        // touching parent positions and the block that stores the node
+        int lo_o[3], hi_o[3], own[3], ol[3];
+        for (int d = 0; d < 3; ++d) {
+          if (d >= dim) {
+            lo_o[d] = hi_o[d] = 0; own[d] = 0; ol[d] = 0;
+            continue;
+          }
+          lo_o[d] = loc[d] == 0 ? -1 : 0;
+          hi_o[d] = loc[d] == 2 * k ? 1 : 0;
+          own[d] = loc[d] == 2 * k ? 1 : 0;
+          ol[d] = loc[d] == 2 * k ? 0 : loc[d];
+        }
+        bool outside = false, ghost = false;
+        for (int oz = lo_o[2]; oz <= hi_o[2]; ++oz)
+          for (int oy = lo_o[1]; oy <= hi_o[1]; ++oy)
+            for (int ox = lo_o[0]; ox <= hi_o[0]; ++ox) {
+              int nb = (ox + 1) + 3 * (oy + 1) + (dim > 2 ? 9 * (oz + 1) : 0);
+              int s = (int)((st >> (2 * nb)) & 3);
+              if (s == kStateOutside) outside = true;
+              if (s == kStateGhost) ghost = true;
+            }
+        int cls = outside ? 3 : (ghost ? 2 : 1);
+        int nbo = (own[0] + 1) + 3 * (own[1] + 1) + (dim > 2 ? 9 * (own[2] + 1) : 0);
+        int32_t blk = lv.nbr[(size_t)g * NNB + nbo];
+        if (blk < 0) continue;  // stored outside the domain: Dirichlet, no slot
+        int64_t slot = (int64_t)blk * NOWN + ol[0] + NO * (ol[1] + NO * ol[2]);
+        int64_t q[3] = {2 * k * p[0] + loc[0], dim > 1 ? 2 * k * p[1] + loc[1] : 0,
+                        dim > 2 ? 2 * k * p[2] + loc[2] : 0};
+        int64_t key = node_key(l, q);
+        if (pass == 0) {
+          lv.slot_class[slot] = (int8_t)cls;
+          lv.slot_key[slot] = key;
+        } else if (lv.slot_class[slot] != cls || lv.slot_key[slot] != key) {
+          bad = true;
+        }
+      }
+    }
+    }
+    if (bad) throw std::runtime_error("inconsistent node classes between sibling groups");
+    for (int64_t s = 0; s < nslots; ++s) {
+      if (lv.slot_class[s] == 1) ++lv.n_S;
+      if (lv.slot_class[s] == 2) ++lv.n_I;
+    }
+    lv.n_cells = (uint64_t)lv.n_groups << dim;
+  }
+  h.total_slots = h.level_offset[L + 1];
+  if (h.total_slots >= (int64_t)1 << 32) throw std::runtime_error("level vectors exceed 2^32 slots");
+
+  // --------------------------------------------------------- leaf mesh
+  ActiveHost& A = h.active;
+  const int64_t nleaf = (int64_t)f.leaf_level.size();
+  A.n_cells = nleaf;
+  for (int l = 0; l <= L; ++l) h.levels[l].n_leaves = 0;
+  for (int64_t i = 0; i < nleaf; ++i) h.levels[f.leaf_level[i]].n_leaves++;
+  std::vector<uint64_t> keys((size_t)nleaf * NLOC);
+  auto cell_key = [&](int64_t i, int j) -> uint64_t {
+    int lvl = f.leaf_level[i];
+    int loc[3] = {j % (k + 1), dim > 1 ? (j / (k + 1)) % (k + 1) : 0,
+                  dim > 2 ? j / ((k + 1) * (k + 1)) : 0};
+    int64_t q[3];
+    for (int d = 0; d < 3; ++d) q[d] = d < dim ? f.leaf_coords[3 * i + d] * k + loc[d] : 0;
+    return (uint64_t)node_key(lvl, q);
+  };
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nleaf; ++i)
+    for (int j = 0; j < NLOC; ++j) keys[(size_t)i * NLOC + j] = cell_key(i, j);
+  std::vector<uint64_t> nodes(keys);
+  parallel_sort_u64(nodes);
+  nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+  const int64_t nn = (int64_t)nodes.size();
+  A.n_leaf_nodes = nn;
+  std::vector<int32_t> node_of((size_t)nleaf * NLOC);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < (int64_t)keys.size(); ++i) node_of[i] = (int32_t)lower_index(nodes, keys[i]);
+  std::vector<uint64_t>().swap(keys);
+  // coarsest leaf level having each node
+  std::vector<int8_t> lmin(nn, 127);
+  {
+    std::vector<std::vector<int64_t>> by_level(L + 1);
+    for (int64_t i = 0; i < nleaf; ++i) by_level[f.leaf_level[i]].push_back(i);
+    for (int l = L; l >= 0; --l) {
+      const auto& cl = by_level[l];
+#pragma omp parallel for schedule(static)
+      for (int64_t t = 0; t < (int64_t)cl.size(); ++t)
+        for (int j = 0; j < NLOC; ++j) lmin[node_of[(size_t)cl[t] * NLOC + j]] = (int8_t)l;
+    }
+  }
+  // classify: 0 unknown, 1 Dirichlet, 2 hanging
+  std::vector<int8_t> ncls(nn, 0);
+  std::vector<int32_t> hang_of(nn, -1);
+  struct HRow {
+    int64_t node;
+    int n;
+    int64_t mkey[9];
+    double w[9];
+  };
+  std::vector<std::vector<HRow>> hrows_t(omp_get_max_threads());
+  bool chain_or_bad = false;
+#pragma omp parallel for schedule(dynamic, 4096)
+  for (int64_t i = 0; i < nn; ++i) {
+    if (key_is_boundary(nodes[i])) {
+      ncls[i] = 1;
+      continue;
+    }
+    int lm = lmin[i];
+    if (lm == 0) continue;
+    int lc = lm - 1;
+    int64_t kq[3];
+    unpack3(nodes[i], kq);
+    int64_t q[3];  // node-lattice coordinates at level lm
+    for (int d = 0; d < 3; ++d) q[d] = d < dim ? kq[d] >> (L - lm) : 0;
+    // candidate level-lc cells containing the node
+    int64_t cand[3][2];
+    int nc[3];
+    for (int d = 0; d < 3; ++d) {
+      if (d >= dim) {
+        cand[d][0] = 0;
+        nc[d] = 1;
+        continue;
+      }
+      int64_t c = q[d] / (2 * k);
+      if (q[d] % (2 * k) == 0) {
+        cand[d][0] = c - 1;
+        cand[d][1] = c;
+        nc[d] = 2;
+      } else {
+        cand[d][0] = c;
+        nc[d] = 1;
+      }
+    }
+    for (int a = 0; a < nc[0]; ++a)
+      for (int b = 0; b < nc[1]; ++b)
+        for (int c2 = 0; c2 < nc[2]; ++c2) {
+          int64_t cc[3] = {cand[0][a], cand[1][b], cand[2][c2]};
+          if (!f.inside(lc, cc) || !f.exists(lc, cc) || f.refined(lc, cc)) continue;
+          if (ncls[i] == 2) continue;
+          // a coarser leaf contains the node, which is not one of its nodes
+          HRow row;
+          row.node = i;
+          row.n = 0;
+          int r[3];
+          for (int d = 0; d < 3; ++d) r[d] = d < dim ? (int)(q[d] - 2 * k * cc[d]) : 0;
+          for (int j = 0; j < NLOC; ++j) {
+            int jl[3] = {j % (k + 1), dim > 1 ? (j / (k + 1)) % (k + 1) : 0,
+                         dim > 2 ? j / ((k + 1) * (k + 1)) : 0};
+            double w = 1.0;
+            for (int d = 0; d < dim; ++d) w *= E1[r[d] * (k + 1) + jl[d]];
+            if (w == 0.0) continue;
+            int64_t mq[3];
+            for (int d = 0; d < 3; ++d) mq[d] = d < dim ? cc[d] * k + jl[d] : 0;
+            if (row.n >= 9) {
+              chain_or_bad = true;
+              break;
+            }
+            row.mkey[row.n] = node_key(lc, mq);
+            row.w[row.n] = w;
+            ++row.n;
+          }
+          ncls[i] = 2;
+          hrows_t[omp_get_thread_num()].push_back(row);
+        }
+  }
+  if (chain_or_bad) throw std::runtime_error("hanging node with too many masters");
+  std::vector<HRow> hrows;
+  for (auto& v : hrows_t) hrows.insert(hrows.end(), v.begin(), v.end());
+  std::sort(hrows.begin(), hrows.end(), [](const HRow& a, const HRow& b) { return a.node < b.node; });
+  // unknown numbering
+  std::vector<int64_t> unk_of(nn, -1);
+  int64_t nu = 0;
+  for (int64_t i = 0; i < nn; ++i)
+    if (ncls[i] == 0) unk_of[i] = nu++;
+  A.n_unknowns = nu;
+  A.unknown_keys.resize(nu);
+  A.home_level.resize(nu);
+  for (int64_t i = 0; i < nn; ++i)
+    if (ncls[i] == 0) {
+      A.unknown_keys[unk_of[i]] = (int64_t)nodes[i];
+      A.home_level[unk_of[i]] = lmin[i];
+    }
+  // hanging rows
+  A.hang_key.resize(hrows.size());
+  A.hang_ptr.assign(hrows.size() + 1, 0);
+  A.hang_col.clear();
+  A.hang_w.clear();
+  A.hang_master_key.clear();
+  for (size_t r = 0; r < hrows.size(); ++r) {
+    hang_of[hrows[r].node] = (int32_t)r;
+    A.hang_key[r] = (int64_t)nodes[hrows[r].node];
+    for (int m = 0; m < hrows[r].n; ++m) {
+      int64_t mi = lower_index(nodes, (uint64_t)hrows[r].mkey[m]);
+      if (mi < 0) throw std::runtime_error("master node of a hanging node is not a leaf node");
+      if (ncls[mi] == 2) throw std::runtime_error("constraint chain");
+      if (ncls[mi] == 1) continue;  // Dirichlet master carries 0
+      A.hang_col.push_back((int32_t)unk_of[mi]);
+      A.hang_w.push_back(hrows[r].w[m]);
+      A.hang_master_key.push_back(hrows[r].mkey[m]);
+    }
+    A.hang_ptr[r + 1] = (int32_t)A.hang_col.size();
+  }
+  // per leaf cell tables
+  A.cell_nodes.resize((size_t)nleaf * NLOC);
+  A.cell_coeff.resize(nleaf);
+  A.cell_level.resize(nleaf);
+  A.cell_coords.resize(3 * nleaf);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nleaf; ++i) {
+    int64_t c[3] = {f.leaf_coords[3 * i], f.leaf_coords[3 * i + 1], f.leaf_coords[3 * i + 2]};
+    A.cell_coeff[i] = coarse_coeff_of(f.leaf_level[i], c);
+    A.cell_level[i] = (uint8_t)f.leaf_level[i];
+    for (int d = 0; d < 3; ++d) A.cell_coords[3 * i + d] = (int32_t)c[d];
+    for (int j = 0; j < NLOC; ++j) {
+      int32_t n = node_of[(size_t)i * NLOC + j];
+      int32_t v;
+      if (ncls[n] == 0) v = (int32_t)unk_of[n];
+      else if (ncls[n] == 1) v = -1;
+      else v = -2 - hang_of[n];
+      A.cell_nodes[(size_t)i * NLOC + j] = v;
+    }
+  }
+  // home slots
+  A.home_slot.resize(nu);
+  A.home_global.resize(nu);
+  bool bad_home = false;
+#pragma omp parallel for schedule(static)
+  for (int64_t u = 0; u < nu; ++u) {
+    int lm = A.home_level[u];
+    int64_t kq[3];
+    unpack3((uint64_t)A.unknown_keys[u], kq);
+    int64_t q[3];
+    for (int d = 0; d < 3; ++d) q[d] = d < dim ? kq[d] >> (L - lm) : 0;
+    int64_t slot;
+    if (lm == 0) {
+      slot = q[0] + h.coarse_lattice[0] * (q[1] + h.coarse_lattice[1] * q[2]);
+    } else {
+      int64_t gp[3], ol[3];
+      for (int d = 0; d < 3; ++d) {
+        gp[d] = d < dim ? q[d] / (2 * k) : 0;
+        ol[d] = d < dim ? q[d] % (2 * k) : 0;
+      }
+      const int32_t* b = block_map[lm].find(pack3(gp[0], gp[1], gp[2]));
+      if (!b || *b >= h.levels[lm].n_groups) {
+        bad_home = true;
+        continue;
+      }
+      slot = (int64_t)(*b) * NOWN + ol[0] + NO * (ol[1] + NO * ol[2]);
+    }
+    if (h.levels[lm].slot_class[slot] != 1 || h.levels[lm].slot_key[slot] != A.unknown_keys[u])
+      bad_home = true;
+    A.home_slot[u] = slot;
+    A.home_global[u] = (uint32_t)(h.level_offset[lm] + slot);
+  }
+  if (bad_home) throw std::runtime_error("an unknown is not an S node of its home level");
+
+  // ------------------------------------------------- coarse matrix A_0
+  {
+    const int n1 = k + 1;
+    double hc[3];
+    for (int d = 0; d < 3; ++d) hc[d] = d < dim ? (h.hi[d] - h.lo[d]) / h.n0[d] : 1.0;
+    // element matrix: sum_i (prod_{j != i} h_j / h_i) K in direction i, M elsewhere
+    std::vector<double> Ae((size_t)NLOC * NLOC, 0.0);
+    for (int a = 0; a < NLOC; ++a)
+      for (int b = 0; b < NLOC; ++b) {
+        int ia[3] = {a % n1, (a / n1) % n1, a / (n1 * n1)};
+        int ib[3] = {b % n1, (b / n1) % n1, b / (n1 * n1)};
+        double s = 0.0;
+        for (int dir = 0; dir < dim; ++dir) {
+          double t = 1.0;
+          for (int e = 0; e < dim; ++e) {
+            if (e == dir) t *= K1[ia[e] * n1 + ib[e]] / hc[e];
+            else t *= M1[ia[e] * n1 + ib[e]] * hc[e];
+          }
+          s += t;
+        }
+        Ae[(size_t)a * NLOC + b] = s;
+      }
+    std::vector<int64_t> interior_index(h.levels[0].slot_class.size(), -1);
+    int64_t ni = 0;
+    for (size_t s = 0; s < interior_index.size(); ++s)
+      if (h.levels[0].slot_class[s] == 1) interior_index[s] = ni++;
+    std::vector<double> A0((size_t)ni * ni, 0.0);
+    for (int64_t cz = 0; cz < h.n0[2]; ++cz)
+      for (int64_t cy = 0; cy < h.n0[1]; ++cy)
+        for (int64_t cx = 0; cx < h.n0[0]; ++cx) {
+          int64_t cc[3] = {cx, cy, cz};
+          double a = coarse_coeff_of(0, cc);
+          int64_t id[64];
+          for (int j = 0; j < NLOC; ++j) {
+            int jl[3] = {j % n1, dim > 1 ? (j / n1) % n1 : 0, dim > 2 ? j / (n1 * n1) : 0};
+            int64_t q[3] = {cx * k + jl[0], dim > 1 ? cy * k + jl[1] : 0, dim > 2 ? cz * k + jl[2] : 0};
+            id[j] = interior_index[q[0] + h.coarse_lattice[0] * (q[1] + h.coarse_lattice[1] * q[2])];
+          }
+          for (int a1 = 0; a1 < NLOC; ++a1)
+            for (int b1 = 0; b1 < NLOC; ++b1)
+              if (id[a1] >= 0 && id[b1] >= 0) A0[id[a1] * ni + id[b1]] += a * Ae[(size_t)a1 * NLOC + b1];
+        }
+    if (ni > 0 && !spd_inverse(A0, ni)) throw std::runtime_error("coarse matrix is not SPD");
+    h.coarse_inverse.swap(A0);
+  }
+  h.setup_host_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace gmg

@@ -1,0 +1,522 @@
+// Leaf-mesh (active) operator, right-hand side, CG vector kernels, copy
+// maps between active and level vectors, and the coarse solve.
+//
+// Active operator (outer CG, FP64): y = C^T A_leaf C x.  Each leaf cell
+// gathers its (K+1)^d node values -- an unknown's value, 0 on the boundary,
+// or for a hanging node the interpolant of the coarser neighbour leaf (the
+// constraint row C, Sec. 1) -- applies the cell's Kronecker-sum Laplacian by
+// sum factorisation, and scatters the result back through C^T with FP64
+// atomics.  x^T A x is accumulated from the cells' local energies
+// x_K^T A_K x_K, which needs no second pass over y.
+//
+// Reductions are deterministic: each block writes its partial sum, and the
+// last block to finish (atomic ticket) sums the partials in index order.
+#include "device_common.cuh"
+
+namespace gmg {
+
+template <int K>
+__host__ __device__ constexpr double amass1(int i, int j) {
+  if constexpr (K == 1) {
+    return i == j ? 1.0 / 3.0 : 1.0 / 6.0;
+  } else {
+    return (i == 1 && j == 1) ? 16.0 / 30.0
+           : (i == 1 || j == 1) ? 2.0 / 30.0
+           : (i == j) ? 4.0 / 30.0 : -1.0 / 30.0;
+  }
+}
+
+template <int K>
+__host__ __device__ constexpr double astiff1(int i, int j) {
+  if constexpr (K == 1) {
+    return i == j ? 1.0 : -1.0;
+  } else {
+    return (i == 1 && j == 1) ? 16.0 / 3.0
+           : (i == 1 || j == 1) ? -8.0 / 3.0
+           : (i == j) ? 7.0 / 3.0 : 1.0 / 3.0;
+  }
+}
+
+template <int I, int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    sfor<I + 1, N>(f);
+  }
+}
+
+__constant__ double c_level_scale[GMG_MAX_LEVELS][3];
+__constant__ double c_cell_h[GMG_MAX_LEVELS][3];
+__constant__ double c_lo[3];
+
+cudaError_t set_active_scales(const double scale[GMG_MAX_LEVELS][3], const double h[GMG_MAX_LEVELS][3],
+                              const double lo[3]) {
+  cudaError_t e = cudaMemcpyToSymbol(c_level_scale, scale, sizeof(double) * GMG_MAX_LEVELS * 3);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_cell_h, h, sizeof(double) * GMG_MAX_LEVELS * 3);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_lo, lo, sizeof(double) * 3);
+}
+
+// ------------------------------------------------------------ reductions
+// Block sum in a fixed order; result valid in thread 0.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < BS / 32; ++i) s += sh[i];
+  }
+  __syncthreads();
+  return s;
+}
+
+// Write this block's partial; the last block sums all partials in order into *out.
+template <int BS>
+__device__ __forceinline__ void finish_reduction(double block_total, double* partials, unsigned* counter,
+                                                 double* out) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = block_total;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double sh[BS / 32];
+  double v = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += BS) v += ((volatile double*)partials)[i];
+  double s = block_sum<BS>(v, sh);
+  if (threadIdx.x == 0) {
+    *out = s;
+    *counter = 0;
+  }
+}
+
+static inline unsigned reduce_grid(int64_t n, int bs) {
+  int64_t b = (n + bs - 1) / bs;
+  if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// ------------------------------------------------------- active operator
+template <int DIM, int K>
+struct ActGeo {
+  static constexpr int N1 = K + 1;
+  static constexpr int NC = DIM == 3 ? N1 * N1 * N1 : N1 * N1;  // nodes per cell
+  static constexpr int CPB = NC == 4 ? 64 : 32;  // cells per block: CPB * NC is a multiple of 32
+  static constexpr int BS = CPB * NC;
+  static constexpr int MAX_GRID = 152 * 12;       // bounded grid-stride (reduction partials)
+};
+
+template <int DIM, int K>
+__device__ __forceinline__ double gather_node(int32_t id, const double* __restrict__ x, const int32_t* hp,
+                                              const int32_t* hc, const double* hw) {
+  if (id >= 0) return x[id];
+  if (id == -1) return 0.0;
+  int h = -2 - id;
+  double v = 0.0;
+  for (int m = hp[h]; m < hp[h + 1]; ++m) v += hw[m] * x[hc[m]];
+  return v;
+}
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(ActGeo<DIM, K>::BS)
+active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restrict__ y,
+                    double* partials, unsigned* counter, double* energy_out) {
+  using G = ActGeo<DIM, K>;
+  constexpr int N1 = G::N1, NC = G::NC;
+  __shared__ double X[G::CPB][NC];
+  __shared__ double T1M[G::CPB][NC], T1K[G::CPB][NC];
+  __shared__ double T2MM[G::CPB][NC], T2MK[G::CPB][NC], T2KM[G::CPB][NC];
+  __shared__ double red[G::BS / 32];
+  const int cl = threadIdx.x / NC;      // cell within block
+  const int n = threadIdx.x % NC;       // node within cell
+  const int ix = n % N1, iy = (n / N1) % N1, iz = DIM == 3 ? n / (N1 * N1) : 0;
+  const int64_t nbatch = (a.n_cells + G::CPB - 1) / G::CPB;
+  double e = 0.0;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const int64_t cell = batch * G::CPB + cl;
+    const bool active = cell < a.n_cells;
+    int32_t id = -1;
+    double coef = 0.0;
+    int lvl = 0;
+    if (active) {
+      id = a.cell_nodes[cell * NC + n];
+      coef = a.cell_coeff[cell];
+      lvl = a.cell_level[cell];
+    }
+    X[cl][n] = active ? gather_node<DIM, K>(id, x, a.hang_ptr, a.hang_col, a.hang_w) : 0.0;
+    __syncthreads();
+    double out = 0.0;
+    if constexpr (DIM == 3) {
+      double m = 0, k = 0;
+      sfor<0, N1>([&](auto c) {
+        double v = X[cl][c + N1 * (iy + N1 * iz)];
+        m += amass1<K>(ix, c) * v;
+        k += astiff1<K>(ix, c) * v;
+      });
+      T1M[cl][n] = m;
+      T1K[cl][n] = k;
+      __syncthreads();
+      double mm = 0, mk = 0, km = 0;
+      sfor<0, N1>([&](auto c) {
+        double vm = T1M[cl][ix + N1 * (c + N1 * iz)];
+        double vk = T1K[cl][ix + N1 * (c + N1 * iz)];
+        mm += amass1<K>(iy, c) * vm;
+        mk += astiff1<K>(iy, c) * vm;
+        km += amass1<K>(iy, c) * vk;
+      });
+      T2MM[cl][n] = mm;
+      T2MK[cl][n] = mk;
+      T2KM[cl][n] = km;
+      __syncthreads();
+      const double sx = c_level_scale[lvl][0], sy = c_level_scale[lvl][1], sz = c_level_scale[lvl][2];
+      sfor<0, N1>([&](auto c) {
+        int j = ix + N1 * (iy + N1 * c);
+        out += astiff1<K>(iz, c) * sz * T2MM[cl][j] + amass1<K>(iz, c) * (sy * T2MK[cl][j] + sx * T2KM[cl][j]);
+      });
+    } else {
+      double m = 0, k = 0;
+      sfor<0, N1>([&](auto c) {
+        double v = X[cl][c + N1 * iy];
+        m += amass1<K>(ix, c) * v;
+        k += astiff1<K>(ix, c) * v;
+      });
+      T1M[cl][n] = m;
+      T1K[cl][n] = k;
+      __syncthreads();
+      const double sx = c_level_scale[lvl][0], sy = c_level_scale[lvl][1];
+      sfor<0, N1>([&](auto c) {
+        int j = ix + N1 * c;
+        out += astiff1<K>(iy, c) * sy * T1M[cl][j] + amass1<K>(iy, c) * sx * T1K[cl][j];
+      });
+    }
+    out *= coef;
+    if (active) {
+      e += X[cl][n] * out;
+      if (id >= 0) {
+        atomicAdd(y + id, out);
+      } else if (id <= -2) {
+        int h = -2 - id;
+        for (int m = a.hang_ptr[h]; m < a.hang_ptr[h + 1]; ++m) atomicAdd(y + a.hang_col[m], a.hang_w[m] * out);
+      }
+    }
+    __syncthreads();  // X / T arrays are reused by the next batch
+  }
+  if (energy_out) {
+    double s = block_sum<G::BS>(e, red);
+    finish_reduction<G::BS>(s, partials, counter, energy_out);
+  }
+}
+
+template <int DIM, int K>
+static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double* y, double* partials,
+                                   unsigned* counter, double* energy, cudaStream_t s) {
+  using G = ActGeo<DIM, K>;
+  if (a.n_cells == 0) return cudaSuccess;
+  int64_t blocks = (a.n_cells + G::CPB - 1) / G::CPB;
+  if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
+  static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
+  active_apply_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_active_apply(int dim, int k, const ActiveArgs& a, const double* x, double* y,
+                                double* partials, unsigned* counter, double* energy_out,
+                                cudaStream_t s) {
+  if (dim == 3 && k == 2) return active_dispatch<3, 2>(a, x, y, partials, counter, energy_out, s);
+  if (dim == 3 && k == 1) return active_dispatch<3, 1>(a, x, y, partials, counter, energy_out, s);
+  if (dim == 2 && k == 2) return active_dispatch<2, 2>(a, x, y, partials, counter, energy_out, s);
+  if (dim == 2 && k == 1) return active_dispatch<2, 1>(a, x, y, partials, counter, energy_out, s);
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------ right-hand side
+// b_i += int_K f phi_i with f = d pi^2 prod sin(pi x_i), (K+1)^d Gauss points.
+template <int K>
+__device__ __forceinline__ void gauss_point(int q, double& x, double& w) {
+  if constexpr (K == 1) {
+    const double a = 0.28867513459481288225;  // 1 / (2 sqrt 3)
+    x = q == 0 ? 0.5 - a : 0.5 + a;
+    w = 0.5;
+  } else {
+    const double a = 0.38729833462074168852;  // sqrt(3/5) / 2
+    x = q == 0 ? 0.5 - a : (q == 1 ? 0.5 : 0.5 + a);
+    w = q == 1 ? 8.0 / 18.0 : 5.0 / 18.0;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ double lagr(int j, double t) {
+  double v = 1.0;
+  for (int m = 0; m <= K; ++m)
+    if (m != j) v *= (t - (double)m / K) / ((double)(j - m) / K);
+  return v;
+}
+
+template <int DIM, int K>
+__global__ void rhs_sine_kernel(ActiveArgs a, const int32_t* __restrict__ coords, double* __restrict__ b) {
+  using G = ActGeo<DIM, K>;
+  constexpr int N1 = G::N1, NC = G::NC;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cell = t / NC;
+  const int n = (int)(t % NC);
+  if (cell >= a.n_cells) return;
+  const int lvl = a.cell_level[cell];
+  const int i[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
+  double h[3], lo[3];
+  for (int d = 0; d < 3; ++d) {
+    h[d] = c_cell_h[lvl][d];
+    lo[d] = c_lo[d] + coords[3 * cell + d] * h[d];
+  }
+  const double PI = 3.14159265358979323846;
+  double acc = 0.0;
+  for (int qz = 0; qz < (DIM == 3 ? N1 : 1); ++qz)
+    for (int qy = 0; qy < N1; ++qy)
+      for (int qx = 0; qx < N1; ++qx) {
+        double px, wx, py, wy, pz = 0.5, wz = 1.0;
+        gauss_point<K>(qx, px, wx);
+        gauss_point<K>(qy, py, wy);
+        if (DIM == 3) gauss_point<K>(qz, pz, wz);
+        double f = DIM * PI * PI * sin(PI * (lo[0] + h[0] * px)) * sin(PI * (lo[1] + h[1] * py));
+        if (DIM == 3) f *= sin(PI * (lo[2] + h[2] * pz));
+        double phi = lagr<K>(i[0], px) * lagr<K>(i[1], py) * (DIM == 3 ? lagr<K>(i[2], pz) : 1.0);
+        acc += wx * wy * wz * f * phi;
+      }
+  acc *= h[0] * h[1] * (DIM == 3 ? h[2] : 1.0);
+  int32_t id = a.cell_nodes[cell * NC + n];
+  if (id >= 0) {
+    atomicAdd(b + id, acc);
+  } else if (id <= -2) {
+    int hh = -2 - id;
+    for (int m = a.hang_ptr[hh]; m < a.hang_ptr[hh + 1]; ++m) atomicAdd(b + a.hang_col[m], a.hang_w[m] * acc);
+  }
+}
+
+cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* coords, double* b,
+                            cudaStream_t s) {
+  int nc = (dim == 3 ? (k + 1) * (k + 1) * (k + 1) : (k + 1) * (k + 1));
+  int64_t n = a.n_cells * nc;
+  if (n == 0) return cudaSuccess;
+  unsigned grid = (unsigned)((n + 255) / 256);
+  if (dim == 3 && k == 2) rhs_sine_kernel<3, 2><<<grid, 256, 0, s>>>(a, coords, b);
+  else if (dim == 3 && k == 1) rhs_sine_kernel<3, 1><<<grid, 256, 0, s>>>(a, coords, b);
+  else if (dim == 2 && k == 2) rhs_sine_kernel<2, 2><<<grid, 256, 0, s>>>(a, coords, b);
+  else if (dim == 2 && k == 1) rhs_sine_kernel<2, 1><<<grid, 256, 0, s>>>(a, coords, b);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ copy maps
+template <typename T>
+__global__ void copy_to_mg_kernel(int64_t n, const double* __restrict__ r, const uint32_t* __restrict__ home,
+                                  T* __restrict__ g) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    g[home[i]] = (T)r[i];
+}
+
+template <typename T>
+cudaError_t launch_copy_to_mg(int64_t n, const double* r, const uint32_t* home, T* g, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t b = (n + 255) / 256;
+  copy_to_mg_kernel<T><<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, r, home, g);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) copy_from_mg_kernel(int64_t n, const T* __restrict__ u,
+                                                           const uint32_t* __restrict__ home,
+                                                           const double* __restrict__ r, double* __restrict__ z,
+                                                           double* partials, unsigned* counter, double* rz_out) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)u[home[i]];
+    z[i] = v;
+    acc += r[i] * v;
+  }
+  double s = block_sum<256>(acc, sh);
+  finish_reduction<256>(s, partials, counter, rz_out);
+}
+
+template <typename T>
+cudaError_t launch_copy_from_mg(int64_t n, const T* u, const uint32_t* home, const double* r, double* z,
+                                double* partials, unsigned* counter, double* rz_out, cudaStream_t s) {
+  copy_from_mg_kernel<T><<<reduce_grid(n, 256), 256, 0, s>>>(n, u, home, r, z, partials, counter, rz_out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ coarse solve
+// u0 = A0^{-1} g0 over the interior nodes of the coarse lattice (dense FP64 inverse).
+template <typename T>
+__global__ void coarse_solve_kernel(int dim, int64_t nc, int64_t lx, int64_t ly, int64_t lz,
+                                    const double* __restrict__ inv, const T* __restrict__ g0,
+                                    T* __restrict__ u0) {
+  extern __shared__ double gs[];
+  const int64_t ix = lx - 2, iy = dim > 1 ? ly - 2 : 1;
+  auto slot_of = [&](int64_t i) {
+    int64_t x = i % ix, y = (i / ix) % iy, z = i / (ix * iy);
+    return (x + 1) + lx * ((y + 1) + ly * (dim > 2 ? z + 1 : 0));
+  };
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) gs[i] = (double)g0[slot_of(i)];
+  __syncthreads();
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < nc; row += (int64_t)gridDim.x * blockDim.x) {
+    const double* a = inv + row * nc;
+    double acc = 0.0;
+    for (int64_t j = 0; j < nc; ++j) acc += a[j] * gs[j];
+    u0[slot_of(row)] = (T)acc;
+  }
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(int dim, int64_t nc, const int64_t lat[3], const double* inv, const T* g0,
+                                T* u0, cudaStream_t s) {
+  if (nc == 0) return cudaSuccess;
+  size_t sm = (size_t)nc * sizeof(double);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(coarse_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    init = true;
+  }
+  unsigned grid = (unsigned)((nc + 127) / 128);
+  coarse_solve_kernel<T><<<grid, 128, sm, s>>>(dim, nc, lat[0], lat[1], lat[2], inv, g0, u0);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- vector kernels
+template <typename T>
+__global__ void scale_vec_kernel(int64_t n, const T* __restrict__ dinv, const T* __restrict__ g, T c,
+                                 T* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = c * dinv[i] * g[i];
+}
+
+template <typename T>
+cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t b = (n + 255) / 256;
+  scale_vec_kernel<T><<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, dinv, g, c, out);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) dot_kernel(int64_t n, const double* __restrict__ a,
+                                                  const double* __restrict__ b, double* partials,
+                                                  unsigned* counter, double* out) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  double s = block_sum<256>(acc, sh);
+  finish_reduction<256>(s, partials, counter, out);
+}
+
+cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials, unsigned* counter,
+                       double* out, cudaStream_t s) {
+  dot_kernel<<<reduce_grid(n, 256), 256, 0, s>>>(n, a, b, partials, counter, out);
+  return cudaGetLastError();
+}
+
+// x += alpha p, r -= alpha Ap, rr = r.r   with alpha = rz / pAp read on the device
+__global__ void __launch_bounds__(256) cg_update_xr_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                           const double* __restrict__ p,
+                                                           const double* __restrict__ Ap, const double* rz,
+                                                           const double* pAp, double* partials,
+                                                           unsigned* counter, double* rr_out) {
+  __shared__ double sh[8];
+  const double alpha = *rz / *pAp;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * Ap[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double s = block_sum<256>(acc, sh);
+  finish_reduction<256>(s, partials, counter, rr_out);
+}
+
+cudaError_t launch_cg_update_xr(int64_t n, double* x, double* r, const double* p, const double* Ap,
+                                const double* rz, const double* pAp, double* partials, unsigned* counter,
+                                double* rr_out, cudaStream_t s) {
+  cg_update_xr_kernel<<<reduce_grid(n, 256), 256, 0, s>>>(n, x, r, p, Ap, rz, pAp, partials, counter, rr_out);
+  return cudaGetLastError();
+}
+
+// p = z + beta p, beta = rz_new / rz_old
+__global__ void cg_update_p_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                                   const double* rz_new, const double* rz_old) {
+  const double beta = *rz_new / *rz_old;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+cudaError_t launch_cg_update_p(int64_t n, double* p, const double* z, const double* rz_new,
+                               const double* rz_old, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t b = (n + 255) / 256;
+  cg_update_p_kernel<<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, p, z, rz_new, rz_old);
+  return cudaGetLastError();
+}
+
+__global__ void axpy_kernel(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+__global__ void mul_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i] * b[i];
+}
+__global__ void xpay_kernel(int64_t n, const double* __restrict__ x, double beta, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] + beta * y[i];
+}
+__global__ void d2f_kernel(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+static inline unsigned vgrid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (unsigned)(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
+}
+cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
+  axpy_kernel<<<vgrid(n), 256, 0, s>>>(n, a, x, y);
+  return cudaGetLastError();
+}
+cudaError_t launch_mul(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+  mul_kernel<<<vgrid(n), 256, 0, s>>>(n, a, b, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_xpay(int64_t n, const double* x, double beta, double* y, cudaStream_t s) {
+  xpay_kernel<<<vgrid(n), 256, 0, s>>>(n, x, beta, y);
+  return cudaGetLastError();
+}
+cudaError_t launch_convert_d2f(int64_t n, const double* in, float* out, cudaStream_t s) {
+  d2f_kernel<<<vgrid(n), 256, 0, s>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_copy_to_mg<float>(int64_t, const double*, const uint32_t*, float*, cudaStream_t);
+template cudaError_t launch_copy_to_mg<double>(int64_t, const double*, const uint32_t*, double*, cudaStream_t);
+template cudaError_t launch_copy_from_mg<float>(int64_t, const float*, const uint32_t*, const double*, double*,
+                                                double*, unsigned*, double*, cudaStream_t);
+template cudaError_t launch_copy_from_mg<double>(int64_t, const double*, const uint32_t*, const double*, double*,
+                                                 double*, unsigned*, double*, cudaStream_t);
+template cudaError_t launch_coarse_solve<float>(int, int64_t, const int64_t*, const double*, const float*, float*,
+                                                cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(int, int64_t, const int64_t*, const double*, const double*,
+                                                 double*, cudaStream_t);
+template cudaError_t launch_scale_vec<float>(int64_t, const float*, const float*, float, float*, cudaStream_t);
+template cudaError_t launch_scale_vec<double>(int64_t, const double*, const double*, double, double*,
+                                              cudaStream_t);
+
+}  // namespace gmg

@@ -1,0 +1,973 @@
+// Level kernels of the local-smoothing V-cycle (Sec. 2.3, Algorithm 2).
+//
+// Storage: level l >= 1 is a list of sibling groups (the 2^d children of a
+// refined level-(l-1) cell).  A group's node block is the (2K+1)^d lattice
+// of its cells' nodes; the group stores the (2K)^d nodes with local index
+// < 2K, and nodes with local index 2K live in the +1 neighbour's block.
+// nbr[g][o] (o in {-1,0,1}^d) is the block of the neighbour at offset o
+// (a real group, a ghost block holding refinement-edge nodes, or -1 outside
+// the brick); state[g] holds 2 bits per offset (refined / not refined
+// inside / outside) and, in bits 60..62, the parent's position inside its
+// own sibling group.
+//
+// The level operator on Cartesian cells is the Kronecker sum
+//   A_cell = a_cell * sum_i s_i (K (x) M (x) M  with K in direction i),
+// s_i = prod_{j != i} h_j / h_i, K and M the 1-D stiffness and mass
+// matrices of Q_K on [0,1], evaluated by sum factorisation (Sec. 3.2).
+//
+// Smoothing / apply kernel: one pass per group that reads the (3K+1)^d halo
+// [-K, 2K]^d around the group (cells of the group and of the 7 lower
+// neighbours touch the group's stored nodes) and writes the group's stored
+// nodes -- no atomics.  Rows of the 1-D matrices are "extended": rows
+// 0..2K-1 hold the group's own two cells, row 2K the lower neighbour's cell
+// at node 0; the extended result is combined with the coefficient of the
+// group each row combination belongs to, so coefficient jumps between
+// groups are exact.
+//
+// Residual + restriction kernel: per group, t = w g - A_G u on the group's
+// (2K+1)^d nodes (A_G = the group's own cells, w = 1 / number of refined
+// groups sharing the node), then R = P^T restricted to the parent cell's
+// (K+1)^d nodes and accumulated atomically.  Summed over groups this is
+// R (g - A u) exactly, without forming t.
+#include <type_traits>
+
+#include "device_common.cuh"
+
+namespace gmg {
+
+// ------------------------------------------------- 1-D closed-form tables
+template <int K>
+__host__ __device__ constexpr double mass1(int i, int j) {
+  if constexpr (K == 1) {
+    return i == j ? 1.0 / 3.0 : 1.0 / 6.0;
+  } else {
+    // (1/30) [[4, 2, -1], [2, 16, 2], [-1, 2, 4]]
+    return (i == 1 && j == 1) ? 16.0 / 30.0
+           : (i == 1 || j == 1) ? 2.0 / 30.0
+           : (i == j) ? 4.0 / 30.0 : -1.0 / 30.0;
+  }
+}
+
+template <int K>
+__host__ __device__ constexpr double stiff1(int i, int j) {
+  if constexpr (K == 1) {
+    return i == j ? 1.0 : -1.0;
+  } else {
+    // (1/3) [[7, -8, 1], [-8, 16, -8], [1, -8, 7]]
+    return (i == 1 && j == 1) ? 16.0 / 3.0
+           : (i == 1 || j == 1) ? -8.0 / 3.0
+           : (i == j) ? 7.0 / 3.0 : 1.0 / 3.0;
+  }
+}
+
+template <int K, bool STIFF>
+__host__ __device__ constexpr double elem1(int i, int j) {
+  return STIFF ? stiff1<K>(i, j) : mass1<K>(i, j);
+}
+
+// parent basis function j evaluated at child node r (r = 0..2K) of the parent interval
+template <int K>
+__host__ __device__ constexpr double embed1(int r, int j) {
+  if constexpr (K == 1) {
+    return r == 1 ? 0.5 : ((r == 0) == (j == 0) ? 1.0 : 0.0);
+  } else {
+    if (r == 0) return j == 0 ? 1.0 : 0.0;
+    if (r == 2) return j == 1 ? 1.0 : 0.0;
+    if (r == 4) return j == 2 ? 1.0 : 0.0;
+    if (r == 1) return j == 0 ? 0.375 : (j == 1 ? 0.75 : -0.125);
+    return j == 0 ? -0.125 : (j == 1 ? 0.75 : 0.375);  // r == 3
+  }
+}
+
+// extended halo matrix: rows e in [0, 2K], halo columns c in [0, 3K] (position c - K)
+template <int K, bool STIFF>
+__host__ __device__ constexpr double bext(int e, int c) {
+  int p = c - K;
+  double v = 0.0;
+  if (e < 2 * K) {
+    for (int cell = 0; cell < 2; ++cell) {
+      int lo = K * cell;
+      if (e >= lo && e <= lo + K && p >= lo && p <= lo + K) v += elem1<K, STIFF>(e - lo, p - lo);
+    }
+  } else if (p >= -K && p <= 0) {
+    v = elem1<K, STIFF>(K, p + K);
+  }
+  return v;
+}
+
+// group-local matrix over the group's two cells, (2K+1) x (2K+1)
+template <int K, bool STIFF>
+__host__ __device__ constexpr double bgrp(int a, int b) {
+  double v = 0.0;
+  for (int cell = 0; cell < 2; ++cell) {
+    int lo = K * cell;
+    if (a >= lo && a <= lo + K && b >= lo && b <= lo + K) v += elem1<K, STIFF>(a - lo, b - lo);
+  }
+  return v;
+}
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+__host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+
+template <int DIM, int K>
+struct Geo {
+  static constexpr int NH = 3 * K + 1;   // halo nodes per direction
+  static constexpr int NE = 2 * K + 1;   // extended rows per direction
+  static constexpr int NO = 2 * K;       // stored nodes per direction of a block
+  static constexpr int NG = 2 * K + 1;   // group nodes per direction
+  static constexpr int N1 = K + 1;       // cell nodes per direction
+  static constexpr int NOWN = ipow_c(NO, DIM);
+  static constexpr int NHALO = ipow_c(NH, DIM);
+  static constexpr int NGRP = ipow_c(NG, DIM);
+  static constexpr int NCELL = ipow_c(N1, DIM);
+  static constexpr int NNB = ipow_c(3, DIM);
+  static constexpr int TEAM = NOWN;      // threads per group
+  static constexpr int GPB = TEAM >= 256 ? 1 : 256 / TEAM;  // groups per block
+};
+
+// index of neighbour offset (ox, oy, oz) in a group's 3^DIM neighbour table
+template <int DIM>
+__device__ __forceinline__ int nbi(int ox, int oy, int oz) {
+  return DIM == 3 ? (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1) : (ox + 1) + 3 * (oy + 1);
+}
+
+__device__ __forceinline__ int state_of(uint64_t st, int nb) { return (int)((st >> (2 * nb)) & 3); }
+
+// class of a node from its touching-offset ranges: 1 S, 2 I, 3 D
+template <int DIM>
+__device__ __forceinline__ int node_class(uint64_t st, const int* lo_o, const int* hi_o) {
+  bool outside = false, ghost = false;
+  for (int oz = (DIM > 2 ? lo_o[2] : 0); oz <= (DIM > 2 ? hi_o[2] : 0); ++oz)
+    for (int oy = lo_o[1]; oy <= hi_o[1]; ++oy)
+      for (int ox = lo_o[0]; ox <= hi_o[0]; ++ox) {
+        int s = state_of(st, nbi<DIM>(ox, oy, oz));
+        outside |= (s == kStateOutside);
+        ghost |= (s == kStateGhost);
+      }
+  return outside ? 3 : (ghost ? 2 : 1);
+}
+
+// ------------------------------------------------------ smoothing kernel
+template <typename T, int DIM, int K>
+struct ChebSmem {
+  using G = Geo<DIM, K>;
+  static constexpr int X = G::NHALO;
+  static constexpr int T1 = (DIM == 3 ? G::NH * G::NH : G::NH) * G::NE;  // per array
+  static constexpr int T2 = DIM == 3 ? G::NH * G::NE * G::NE : 0;         // per array
+  static constexpr int Y = ipow_c(G::NE, DIM);
+  static constexpr int PER_GROUP = X + 2 * T1 + 3 * T2 + Y + (1 << DIM);
+  static constexpr size_t HEADER = ((size_t)G::GPB * (8 + 4 * G::NNB) + 15) / 16 * 16;
+  static constexpr size_t bytes() { return HEADER + (size_t)G::GPB * PER_GROUP * sizeof(T); }
+};
+
+// Sum-factorised extended operator: X (halo, NH^DIM) -> Y (NE^DIM, unscaled by coefficients).
+template <typename T, int DIM, int K>
+__device__ __forceinline__ void ext_operator(const T* X, T* T1M, T* T1K, T* T2MM, T* T2MK, T* T2KM,
+                                             T* Y, int lane, const double* scale) {
+  using G = Geo<DIM, K>;
+  constexpr int NH = G::NH, NE = G::NE;
+  const T sx = (T)scale[0], sy = (T)scale[1], sz = (T)scale[2];
+  if constexpr (DIM == 3) {
+    // stage x: lines (z, y)
+    for (int line = lane; line < NH * NH; line += G::TEAM) {
+      const T* in = X + line * NH;
+      T v[NH];
+      static_for<0, NH>([&](auto c) { v[c] = in[c]; });
+      static_for<0, NE>([&](auto e) {
+        T m = 0, kk = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bm != 0.0) m += (T)bm * v[c];
+          if constexpr (bk != 0.0) kk += (T)bk * v[c];
+        });
+        T1M[line * NE + e] = m;
+        T1K[line * NE + e] = kk;
+      });
+    }
+    __syncthreads();
+    // stage y: lines (z, ex); T1 layout [z][y][ex]
+    for (int line = lane; line < NH * NE; line += G::TEAM) {
+      int z = line / NE, ex = line % NE;
+      T vm[NH], vk[NH];
+      static_for<0, NH>([&](auto y) {
+        vm[y] = T1M[(z * NH + y) * NE + ex];
+        vk[y] = T1K[(z * NH + y) * NE + ex];
+      });
+      static_for<0, NE>([&](auto e) {
+        T mm = 0, mk = 0, km = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bm != 0.0) {
+            mm += (T)bm * vm[c];
+            km += (T)bm * vk[c];
+          }
+          if constexpr (bk != 0.0) mk += (T)bk * vm[c];
+        });
+        int o = (z * NE + e) * NE + ex;  // [z][ey][ex]
+        T2MM[o] = mm;
+        T2MK[o] = mk;
+        T2KM[o] = km;
+      });
+    }
+    __syncthreads();
+    // stage z: lines (ey, ex); T2 layout [z][ey][ex]
+    for (int line = lane; line < NE * NE; line += G::TEAM) {
+      T a[NH], b[NH];
+      static_for<0, NH>([&](auto z) {
+        a[z] = T2MM[z * NE * NE + line];
+        b[z] = sy * T2MK[z * NE * NE + line] + sx * T2KM[z * NE * NE + line];
+      });
+      static_for<0, NE>([&](auto e) {
+        T acc = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bk != 0.0) acc += (T)bk * sz * a[c];
+          if constexpr (bm != 0.0) acc += (T)bm * b[c];
+        });
+        Y[e * NE * NE + line] = acc;
+      });
+    }
+    __syncthreads();
+  } else {
+    // DIM == 2: stage x over lines y, then stage y
+    for (int line = lane; line < NH; line += G::TEAM) {
+      const T* in = X + line * NH;
+      T v[NH];
+      static_for<0, NH>([&](auto c) { v[c] = in[c]; });
+      static_for<0, NE>([&](auto e) {
+        T m = 0, kk = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bm != 0.0) m += (T)bm * v[c];
+          if constexpr (bk != 0.0) kk += (T)bk * v[c];
+        });
+        T1M[line * NE + e] = m;
+        T1K[line * NE + e] = kk;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; line < NE; line += G::TEAM) {
+      T vm[NH], vk[NH];
+      static_for<0, NH>([&](auto y) {
+        vm[y] = T1M[y * NE + line];
+        vk[y] = T1K[y * NE + line];
+      });
+      static_for<0, NE>([&](auto e) {
+        T acc = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bk != 0.0) acc += (T)bk * sy * vm[c];
+          if constexpr (bm != 0.0) acc += (T)bm * sx * vk[c];
+        });
+        Y[e * NE + line] = acc;
+      });
+    }
+    __syncthreads();
+  }
+}
+
+// Load the (3K+1)^d halo of group g into X.
+template <typename T, int DIM, int K>
+__device__ __forceinline__ void load_halo(const T* __restrict__ x, const int32_t* nb, T* X, int lane) {
+  using G = Geo<DIM, K>;
+  constexpr int NH = G::NH, NO = G::NO;
+  for (int h = lane; h < G::NHALO; h += G::TEAM) {
+    int c[3] = {h % NH, DIM > 1 ? (h / NH) % NH : K, DIM > 2 ? h / (NH * NH) : K};
+    int ni = 0, loc = 0, mul3 = 1, mulo = 1;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      int rel = c[d] - K;
+      int o = rel < 0 ? -1 : (rel < NO ? 0 : 1);
+      ni += (o + 1) * mul3;
+      loc += (rel - NO * o) * mulo;
+      mul3 *= 3;
+      mulo *= NO;
+    }
+    int32_t blk = nb[ni];
+    X[h] = blk < 0 ? T(0) : x[(int64_t)blk * G::NOWN + loc];
+  }
+}
+
+// mode: 0 = apply (out[S] = A x), 1 = Chebyshev step
+template <typename T, int DIM, int K, int MODE>
+__global__ void __launch_bounds__(Geo<DIM, K>::GPB * Geo<DIM, K>::TEAM)
+level_cheb_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev,
+                  const T* __restrict__ gvec, const T* __restrict__ dinv, T* out, T c1, T c2) {
+  using G = Geo<DIM, K>;
+  using S = ChebSmem<T, DIM, K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / G::TEAM;
+  const int lane = threadIdx.x % G::TEAM;
+  const int64_t g = (int64_t)blockIdx.x * G::GPB + team;
+  uint64_t* sts = reinterpret_cast<uint64_t*>(smem_raw);
+  int32_t* nbs = reinterpret_cast<int32_t*>(sts + G::GPB) + team * G::NNB;
+  T* base = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER_GROUP;
+  T* X = base;
+  T* T1M = X + S::X;
+  T* T1K = T1M + S::T1;
+  T* T2MM = T1K + S::T1;
+  T* T2MK = T2MM + S::T2;
+  T* T2KM = T2MK + S::T2;
+  T* Y = T2KM + S::T2;
+  T* coefs = Y + S::Y;
+  const bool active = g < a.n_groups;
+  if (active) {
+    for (int i = lane; i < G::NNB; i += G::TEAM) nbs[i] = a.nbr[g * G::NNB + i];
+    if (lane == 0) sts[team] = a.state[g];
+  }
+  __syncthreads();
+  uint64_t st = active ? sts[team] : 0;
+  if (active) {
+    load_halo<T, DIM, K>(x, nbs, X, lane);
+    // coefficients of the groups at offsets in {-1, 0}^d (0 if not refined)
+    if (lane < (1 << DIM)) {
+      int o[3] = {-(lane & 1), DIM > 1 ? -((lane >> 1) & 1) : 0, DIM > 2 ? -((lane >> 2) & 1) : 0};
+      int ni = nbi<DIM>(o[0], o[1], o[2]);
+      T c = 0;
+      if (state_of(st, ni) == kStateRefined) c = (T)a.coeff[nbs[ni]];
+      coefs[lane] = c;
+    }
+  }
+  __syncthreads();
+  ext_operator<T, DIM, K>(X, T1M, T1K, T2MM, T2MK, T2KM, Y, active ? lane : G::TEAM, a.scale);
+  if (!active) return;
+  // combine extended rows for the stored node `lane`
+  constexpr int NO = G::NO, NE = G::NE;
+  int i[3] = {lane % NO, DIM > 1 ? (lane / NO) % NO : 0, DIM > 2 ? lane / (NO * NO) : 0};
+  T y = 0;
+  const int ne_x = i[0] == 0 ? 2 : 1, ne_y = (DIM > 1 && i[1] == 0) ? 2 : 1,
+            ne_z = (DIM > 2 && i[2] == 0) ? 2 : 1;
+  for (int bz = 0; bz < ne_z; ++bz)
+    for (int by = 0; by < ne_y; ++by)
+      for (int bx = 0; bx < ne_x; ++bx) {
+        int ex = bx ? 2 * K : i[0], ey = by ? 2 * K : i[1], ez = bz ? 2 * K : i[2];
+        int yi = DIM == 3 ? (ez * NE + ey) * NE + ex : ey * NE + ex;
+        y += coefs[bx | (by << 1) | (bz << 2)] * Y[yi];
+      }
+  int lo_o[3] = {i[0] == 0 ? -1 : 0, i[1] == 0 && DIM > 1 ? -1 : 0, i[2] == 0 && DIM > 2 ? -1 : 0};
+  int hi_o[3] = {0, 0, 0};
+  int cls = node_class<DIM>(st, lo_o, hi_o);
+  if (cls != 1) return;
+  const int64_t slot = g * G::NOWN + lane;
+  if constexpr (MODE == 0) {
+    out[slot] = y;
+  } else {
+    int hx = (i[0] + K) + G::NH * ((DIM > 1 ? i[1] + K : 0) + G::NH * (DIM > 2 ? i[2] + K : 0));
+    T xv = X[hx];
+    T xp = xprev ? xprev[slot] : T(0);
+    out[slot] = xv + c1 * (xv - xp) + c2 * dinv[slot] * (gvec[slot] - y);
+  }
+}
+
+// ------------------------------------------------- residual + restriction
+template <typename T, int DIM, int K>
+struct ResSmem {
+  using G = Geo<DIM, K>;
+  static constexpr int N = G::NGRP;
+  static constexpr int PER_GROUP = 9 * N;  // U, G/t, T1M, T1K, T2MM, T2MK, T2KM, Y, R
+  static constexpr size_t HEADER = ((size_t)G::GPB * 4 * G::NNB + 15) / 16 * 16;
+  static constexpr size_t bytes() { return HEADER + (size_t)G::GPB * PER_GROUP * sizeof(T); }
+};
+
+// group-local operator on NG^DIM nodes: Y = sum_i s_i (Kx M M ...) U
+template <typename T, int DIM, int K>
+__device__ __forceinline__ void grp_operator(const T* U, T* T1M, T* T1K, T* T2MM, T* T2MK, T* T2KM,
+                                             T* Y, int lane, int nthreads, const double* scale) {
+  using G = Geo<DIM, K>;
+  constexpr int NG = G::NG;
+  const T sx = (T)scale[0], sy = (T)scale[1], sz = (T)scale[2];
+  if constexpr (DIM == 3) {
+    for (int line = lane; line < NG * NG; line += nthreads) {
+      T v[NG];
+      static_for<0, NG>([&](auto c) { v[c] = U[line * NG + c]; });
+      static_for<0, NG>([&](auto e) {
+        T m = 0, kk = 0;
+        static_for<0, NG>([&](auto c) {
+          constexpr double bm = bgrp<K, false>(e, c);
+          constexpr double bk = bgrp<K, true>(e, c);
+          if constexpr (bm != 0.0) m += (T)bm * v[c];
+          if constexpr (bk != 0.0) kk += (T)bk * v[c];
+        });
+        T1M[line * NG + e] = m;
+        T1K[line * NG + e] = kk;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; line < NG * NG; line += nthreads) {
+      int z = line / NG, ex = line % NG;
+      T vm[NG], vk[NG];
+      static_for<0, NG>([&](auto y) {
+        vm[y] = T1M[(z * NG + y) * NG + ex];
+        vk[y] = T1K[(z * NG + y) * NG + ex];
+      });
+      static_for<0, NG>([&](auto e) {
+        T mm = 0, mk = 0, km = 0;
+        static_for<0, NG>([&](auto c) {
+          constexpr double bm = bgrp<K, false>(e, c);
+          constexpr double bk = bgrp<K, true>(e, c);
+          if constexpr (bm != 0.0) {
+            mm += (T)bm * vm[c];
+            km += (T)bm * vk[c];
+          }
+          if constexpr (bk != 0.0) mk += (T)bk * vm[c];
+        });
+        int o = (z * NG + e) * NG + ex;
+        T2MM[o] = mm;
+        T2MK[o] = mk;
+        T2KM[o] = km;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; line < NG * NG; line += nthreads) {
+      T p[NG], q[NG];
+      static_for<0, NG>([&](auto z) {
+        p[z] = T2MM[z * NG * NG + line];
+        q[z] = sy * T2MK[z * NG * NG + line] + sx * T2KM[z * NG * NG + line];
+      });
+      static_for<0, NG>([&](auto e) {
+        T acc = 0;
+        static_for<0, NG>([&](auto c) {
+          constexpr double bm = bgrp<K, false>(e, c);
+          constexpr double bk = bgrp<K, true>(e, c);
+          if constexpr (bk != 0.0) acc += (T)bk * sz * p[c];
+          if constexpr (bm != 0.0) acc += (T)bm * q[c];
+        });
+        Y[e * NG * NG + line] = acc;
+      });
+    }
+    __syncthreads();
+  } else {
+    for (int line = lane; line < NG; line += nthreads) {
+      T v[NG];
+      static_for<0, NG>([&](auto c) { v[c] = U[line * NG + c]; });
+      static_for<0, NG>([&](auto e) {
+        T m = 0, kk = 0;
+        static_for<0, NG>([&](auto c) {
+          constexpr double bm = bgrp<K, false>(e, c);
+          constexpr double bk = bgrp<K, true>(e, c);
+          if constexpr (bm != 0.0) m += (T)bm * v[c];
+          if constexpr (bk != 0.0) kk += (T)bk * v[c];
+        });
+        T1M[line * NG + e] = m;
+        T1K[line * NG + e] = kk;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; line < NG; line += nthreads) {
+      T vm[NG], vk[NG];
+      static_for<0, NG>([&](auto y) {
+        vm[y] = T1M[y * NG + line];
+        vk[y] = T1K[y * NG + line];
+      });
+      static_for<0, NG>([&](auto e) {
+        T acc = 0;
+        static_for<0, NG>([&](auto c) {
+          constexpr double bm = bgrp<K, false>(e, c);
+          constexpr double bk = bgrp<K, true>(e, c);
+          if constexpr (bk != 0.0) acc += (T)bk * sy * vm[c];
+          if constexpr (bm != 0.0) acc += (T)bm * sx * vk[c];
+        });
+        Y[e * NG + line] = acc;
+      });
+    }
+    __syncthreads();
+  }
+}
+
+// per-dimension touching offsets and storing block of group node local index a
+template <int K>
+__device__ __forceinline__ void node_ranges(int a, int& lo_o, int& hi_o, int& own, int& loc) {
+  lo_o = a == 0 ? -1 : 0;
+  hi_o = a == 2 * K ? 1 : 0;
+  own = a == 2 * K ? 1 : 0;
+  loc = a == 2 * K ? 0 : a;
+}
+
+// block index and local index of the parent cell's node j (per-direction jd) at level l-1
+template <int DIM, int K>
+__device__ __forceinline__ int64_t parent_node_slot(const LevelArgs& a, int64_t parent, uint64_t st,
+                                                    const int* jd) {
+  using G = Geo<DIM, K>;
+  if (a.level == 1) {
+    // parent is coarse cell `parent` of the n0 brick; coarse lattice (K n0 + 1)^d
+    int64_t n0x = (a.coarse_lat[0] - 1) / K, n0y = (a.coarse_lat[1] - 1) / K;
+    int64_t c[3] = {parent % n0x, DIM > 1 ? (parent / n0x) % n0y : 0, DIM > 2 ? parent / (n0x * n0y) : 0};
+    int64_t q[3];
+    for (int d = 0; d < 3; ++d) q[d] = d < DIM ? K * c[d] + jd[d] : 0;
+    return q[0] + a.coarse_lat[0] * (q[1] + a.coarse_lat[1] * q[2]);
+  }
+  int cb[3] = {(int)((st >> 60) & 1), (int)((st >> 61) & 1), (int)((st >> 62) & 1)};
+  int ni = 0, loc = 0, mul3 = 1, mulo = 1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    int pl = cb[d] * K + jd[d];
+    int o = pl == 2 * K ? 1 : 0;
+    ni += (o + 1) * mul3;
+    loc += (pl - 2 * K * o) * mulo;
+    mul3 *= 3;
+    mulo *= G::NO;
+  }
+  int32_t blk = a.nbr_coarse[parent * G::NNB + ni];
+  if (blk < 0) return -1;
+  return (int64_t)blk * G::NOWN + loc;
+}
+
+template <typename T, int DIM, int K>
+__global__ void __launch_bounds__(Geo<DIM, K>::GPB * Geo<DIM, K>::TEAM)
+level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __restrict__ gvec,
+                               T* __restrict__ gc) {
+  using G = Geo<DIM, K>;
+  using S = ResSmem<T, DIM, K>;
+  constexpr int NG = G::NG, N1 = G::N1, N = G::NGRP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / G::TEAM;
+  const int lane = threadIdx.x % G::TEAM;
+  const int64_t g = (int64_t)blockIdx.x * G::GPB + team;
+  int32_t* nbs = reinterpret_cast<int32_t*>(smem_raw) + team * G::NNB;
+  T* base = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER_GROUP;
+  T* U = base;
+  T* Tt = U + N;
+  T* T1M = Tt + N;
+  T* T1K = T1M + N;
+  T* T2MM = T1K + N;
+  T* T2MK = T2MM + N;
+  T* T2KM = T2MK + N;
+  T* Y = T2KM + N;
+  T* R = Y + N;
+  const bool active = g < a.n_groups;
+  uint64_t st = active ? a.state[g] : 0;
+  if (active) {
+    for (int i = lane; i < G::NNB; i += G::TEAM) nbs[i] = a.nbr[g * G::NNB + i];
+  }
+  __syncthreads();
+  if (active) {
+    for (int n = lane; n < N; n += G::TEAM) {
+      int ad[3] = {n % NG, DIM > 1 ? (n / NG) % NG : 0, DIM > 2 ? n / (NG * NG) : 0};
+      int ni = 0, loc = 0, mul3 = 1, mulo = 1;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        int lo_o, hi_o, own, l;
+        node_ranges<K>(ad[d], lo_o, hi_o, own, l);
+        ni += (own + 1) * mul3;
+        loc += l * mulo;
+        mul3 *= 3;
+        mulo *= G::NO;
+      }
+      int32_t blk = nbs[ni];
+      T uv = 0, gv = 0;
+      if (blk >= 0) {
+        int64_t s = (int64_t)blk * G::NOWN + loc;
+        uv = u[s];
+        gv = gvec[s];
+      }
+      U[n] = uv;
+      Tt[n] = gv;
+    }
+  }
+  __syncthreads();
+  grp_operator<T, DIM, K>(U, T1M, T1K, T2MM, T2MK, T2KM, Y, active ? lane : G::TEAM, G::TEAM, a.scale);
+  const T coef = active ? (T)a.coeff[g] : T(0);
+  if (active) {
+    for (int n = lane; n < N; n += G::TEAM) {
+      int ad[3] = {n % NG, DIM > 1 ? (n / NG) % NG : 0, DIM > 2 ? n / (NG * NG) : 0};
+      int lo_o[3] = {0, 0, 0}, hi_o[3] = {0, 0, 0};
+      for (int d = 0; d < DIM; ++d) {
+        int own, l;
+        node_ranges<K>(ad[d], lo_o[d], hi_o[d], own, l);
+      }
+      // class and number of refined groups sharing the node
+      bool outside = false, ghost = false;
+      int mult = 0;
+      for (int oz = lo_o[2]; oz <= hi_o[2]; ++oz)
+        for (int oy = lo_o[1]; oy <= hi_o[1]; ++oy)
+          for (int ox = lo_o[0]; ox <= hi_o[0]; ++ox) {
+            int s = state_of(st, nbi<DIM>(ox, oy, oz));
+            outside |= s == kStateOutside;
+            ghost |= s == kStateGhost;
+            mult += s == kStateRefined;
+          }
+      (void)ghost;
+      T t = outside ? T(0) : Tt[n] / (T)mult - coef * Y[n];
+      Tt[n] = t;
+    }
+  }
+  __syncthreads();
+  // restriction R = P^T: contract each direction with E^T (NG -> N1)
+  if constexpr (DIM == 3) {
+    // stage x: [z][y][a] -> T1M as [z][y][j]
+    for (int line = lane; active && line < NG * NG; line += G::TEAM) {
+      T v[NG];
+      static_for<0, NG>([&](auto c) { v[c] = Tt[line * NG + c]; });
+      static_for<0, N1>([&](auto j) {
+        T acc = 0;
+        static_for<0, NG>([&](auto r) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[r];
+        });
+        T1M[line * N1 + j] = acc;
+      });
+    }
+    __syncthreads();
+    // stage y: [z][y][jx] -> T1K as [z][jy][jx]
+    for (int line = lane; active && line < NG * N1; line += G::TEAM) {
+      int z = line / N1, jx = line % N1;
+      T v[NG];
+      static_for<0, NG>([&](auto y) { v[y] = T1M[(z * NG + y) * N1 + jx]; });
+      static_for<0, N1>([&](auto j) {
+        T acc = 0;
+        static_for<0, NG>([&](auto r) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[r];
+        });
+        T1K[(z * N1 + j) * N1 + jx] = acc;
+      });
+    }
+    __syncthreads();
+    // stage z: [z][jy][jx] -> R as [jz][jy][jx]
+    for (int line = lane; active && line < N1 * N1; line += G::TEAM) {
+      T v[NG];
+      static_for<0, NG>([&](auto z) { v[z] = T1K[z * N1 * N1 + line]; });
+      static_for<0, N1>([&](auto j) {
+        T acc = 0;
+        static_for<0, NG>([&](auto r) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[r];
+        });
+        R[j * N1 * N1 + line] = acc;
+      });
+    }
+    __syncthreads();
+  } else {
+    for (int line = lane; active && line < NG; line += G::TEAM) {
+      T v[NG];
+      static_for<0, NG>([&](auto c) { v[c] = Tt[line * NG + c]; });
+      static_for<0, N1>([&](auto j) {
+        T acc = 0;
+        static_for<0, NG>([&](auto r) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[r];
+        });
+        T1M[line * N1 + j] = acc;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; active && line < N1; line += G::TEAM) {
+      T v[NG];
+      static_for<0, NG>([&](auto y) { v[y] = T1M[y * N1 + line]; });
+      static_for<0, N1>([&](auto j) {
+        T acc = 0;
+        static_for<0, NG>([&](auto r) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[r];
+        });
+        R[j * N1 + line] = acc;
+      });
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+  const int64_t parent = a.parent[g];
+  for (int n = lane; n < G::NCELL; n += G::TEAM) {
+    int jd[3] = {n % N1, DIM > 1 ? (n / N1) % N1 : 0, DIM > 2 ? n / (N1 * N1) : 0};
+    int64_t s = parent_node_slot<DIM, K>(a, parent, st, jd);
+    if (s >= 0) atomicAdd(gc + s, R[n]);
+  }
+}
+
+// ------------------------------------------------------------ prolongation
+template <typename T, int DIM, int K>
+__global__ void __launch_bounds__(Geo<DIM, K>::GPB * Geo<DIM, K>::TEAM)
+level_prolongate_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u, T* __restrict__ u2) {
+  using G = Geo<DIM, K>;
+  constexpr int NG = G::NG, N1 = G::N1, N = G::NGRP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / G::TEAM;
+  const int lane = threadIdx.x % G::TEAM;
+  const int64_t g = (int64_t)blockIdx.x * G::GPB + team;
+  constexpr int PER = G::NCELL + 2 * N;
+  T* C = reinterpret_cast<T*>(smem_raw) + (size_t)team * PER;
+  T* W1 = C + G::NCELL;
+  T* W2 = W1 + N;
+  const bool active = g < a.n_groups;
+  uint64_t st = active ? a.state[g] : 0;
+  if (active) {
+    const int64_t parent = a.parent[g];
+    for (int n = lane; n < G::NCELL; n += G::TEAM) {
+      int jd[3] = {n % N1, DIM > 1 ? (n / N1) % N1 : 0, DIM > 2 ? n / (N1 * N1) : 0};
+      int64_t s = parent_node_slot<DIM, K>(a, parent, st, jd);
+      C[n] = s >= 0 ? uc[s] : T(0);
+    }
+  }
+  __syncthreads();
+  // interpolate: C [jz][jy][jx] -> W [z][y][x] with E in each direction
+  if constexpr (DIM == 3) {
+    for (int line = lane; active && line < N1 * N1; line += G::TEAM) {  // x: [jz][jy][jx]->[jz][jy][x]
+      T v[N1];
+      static_for<0, N1>([&](auto j) { v[j] = C[line * N1 + j]; });
+      static_for<0, NG>([&](auto r) {
+        T acc = 0;
+        static_for<0, N1>([&](auto j) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[j];
+        });
+        W1[line * NG + r] = acc;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; active && line < N1 * NG; line += G::TEAM) {  // y: -> [jz][y][x]
+      int jz = line / NG, x = line % NG;
+      T v[N1];
+      static_for<0, N1>([&](auto j) { v[j] = W1[(jz * N1 + j) * NG + x]; });
+      static_for<0, NG>([&](auto r) {
+        T acc = 0;
+        static_for<0, N1>([&](auto j) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[j];
+        });
+        W2[(jz * NG + r) * NG + x] = acc;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; active && line < NG * NG; line += G::TEAM) {  // z: -> [z][y][x]
+      T v[N1];
+      static_for<0, N1>([&](auto j) { v[j] = W2[j * NG * NG + line]; });
+      static_for<0, NG>([&](auto r) {
+        T acc = 0;
+        static_for<0, N1>([&](auto j) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[j];
+        });
+        W1[r * NG * NG + line] = acc;
+      });
+    }
+    __syncthreads();
+  } else {
+    for (int line = lane; active && line < N1; line += G::TEAM) {
+      T v[N1];
+      static_for<0, N1>([&](auto j) { v[j] = C[line * N1 + j]; });
+      static_for<0, NG>([&](auto r) {
+        T acc = 0;
+        static_for<0, N1>([&](auto j) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[j];
+        });
+        W2[line * NG + r] = acc;
+      });
+    }
+    __syncthreads();
+    for (int line = lane; active && line < NG; line += G::TEAM) {
+      T v[N1];
+      static_for<0, N1>([&](auto j) { v[j] = W2[j * NG + line]; });
+      static_for<0, NG>([&](auto r) {
+        T acc = 0;
+        static_for<0, N1>([&](auto j) {
+          constexpr double e = embed1<K>(r, j);
+          if constexpr (e != 0.0) acc += (T)e * v[j];
+        });
+        W1[r * NG + line] = acc;
+      });
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+  const int32_t* nb = a.nbr + g * G::NNB;
+  for (int n = lane; n < N; n += G::TEAM) {
+    int ad[3] = {n % NG, DIM > 1 ? (n / NG) % NG : 0, DIM > 2 ? n / (NG * NG) : 0};
+    int lo_o[3] = {0, 0, 0}, hi_o[3] = {0, 0, 0}, own[3] = {0, 0, 0}, loc[3] = {0, 0, 0};
+    for (int d = 0; d < DIM; ++d) node_ranges<K>(ad[d], lo_o[d], hi_o[d], own[d], loc[d]);
+    bool outside = false, ghost = false, owner = true;
+    for (int oz = lo_o[2]; oz <= hi_o[2]; ++oz)
+      for (int oy = lo_o[1]; oy <= hi_o[1]; ++oy)
+        for (int ox = lo_o[0]; ox <= hi_o[0]; ++ox) {
+          int s = state_of(st, nbi<DIM>(ox, oy, oz));
+          outside |= s == kStateOutside;
+          ghost |= s == kStateGhost;
+          // a refined group at a lexicographically smaller offset owns the write
+          bool neg = oz < 0 || (oz == 0 && (oy < 0 || (oy == 0 && ox < 0)));
+          if (s == kStateRefined && neg) owner = false;
+        }
+    if (outside || !owner) continue;
+    int32_t blk = nb[nbi<DIM>(own[0], own[1], own[2])];
+    if (blk < 0) continue;
+    int64_t s = (int64_t)blk * G::NOWN + loc[0] + G::NO * (loc[1] + G::NO * loc[2]);
+    T v = W1[n];
+    if (ghost) {
+      u[s] = v;
+      u2[s] = v;
+    } else {
+      u[s] += v;
+    }
+  }
+}
+
+// ------------------------------------------------------------ diagonal
+template <int DIM, int K>
+__global__ void __launch_bounds__(256) level_diag_kernel(LevelArgs a, double* __restrict__ dinv) {
+  using G = Geo<DIM, K>;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t g = idx / G::NOWN;
+  const int lane = (int)(idx % G::NOWN);
+  if (g >= a.n_groups) return;
+  const uint64_t st = a.state[g];
+  constexpr int NO = G::NO;
+  int i[3] = {lane % NO, DIM > 1 ? (lane / NO) % NO : 0, DIM > 2 ? lane / (NO * NO) : 0};
+  int lo_o[3] = {i[0] == 0 ? -1 : 0, DIM > 1 && i[1] == 0 ? -1 : 0, DIM > 2 && i[2] == 0 ? -1 : 0};
+  int hi_o[3] = {0, 0, 0};
+  const int64_t slot = g * G::NOWN + lane;
+  if (node_class<DIM>(st, lo_o, hi_o) != 1) {
+    dinv[slot] = 0.0;
+    return;
+  }
+  double diag = 0.0;
+  for (int bz = 0; bz < (lo_o[2] ? 2 : 1); ++bz)
+    for (int by = 0; by < (lo_o[1] ? 2 : 1); ++by)
+      for (int bx = 0; bx < (lo_o[0] ? 2 : 1); ++bx) {
+        int ni = nbi<DIM>(-bx, -by, -bz);
+        if (state_of(st, ni) != kStateRefined) continue;
+        double c = a.coeff[a.nbr[g * G::NNB + ni]];
+        int e[3] = {bx ? 2 * K : i[0], by ? 2 * K : i[1], bz ? 2 * K : i[2]};
+        double md[3], kd[3];
+        for (int d = 0; d < 3; ++d) {
+          md[d] = bext<K, false>(e[d], K + i[d]);
+          kd[d] = bext<K, true>(e[d], K + i[d]);
+        }
+        double s = 0.0;
+        for (int dir = 0; dir < DIM; ++dir) {
+          double t = a.scale[dir];
+          for (int d = 0; d < DIM; ++d) t *= (d == dir) ? kd[d] : md[d];
+          s += t;
+        }
+        diag += c * s;
+      }
+  dinv[slot] = 1.0 / diag;
+}
+
+// ----------------------------------------------------------- launchers
+template <typename T, int DIM, int K>
+static cudaError_t cheb_dispatch(const LevelArgs& a, const T* x, const T* xprev, const T* g,
+                                 const T* dinv, T* out, T c1, T c2, bool apply_only,
+                                 cudaStream_t s) {
+  using G = Geo<DIM, K>;
+  if (a.n_groups == 0) return cudaSuccess;
+  size_t sm = ChebSmem<T, DIM, K>::bytes() + 16;
+  dim3 grid((unsigned)((a.n_groups + G::GPB - 1) / G::GPB));
+  dim3 block(G::GPB * G::TEAM);
+  if (apply_only) {
+    static bool init = false;
+    if (!init) {
+      cudaFuncSetAttribute(level_cheb_kernel<T, DIM, K, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      init = true;
+    }
+    level_cheb_kernel<T, DIM, K, 0><<<grid, block, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+  } else {
+    static bool init = false;
+    if (!init) {
+      cudaFuncSetAttribute(level_cheb_kernel<T, DIM, K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      init = true;
+    }
+    level_cheb_kernel<T, DIM, K, 1><<<grid, block, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_level_cheb(int dim, int k, const LevelArgs& a, const T* x, const T* xprev,
+                              const T* g, const T* dinv, T* out, T c1, T c2, bool apply_only,
+                              cudaStream_t s) {
+  if (dim == 3 && k == 2) return cheb_dispatch<T, 3, 2>(a, x, xprev, g, dinv, out, c1, c2, apply_only, s);
+  if (dim == 3 && k == 1) return cheb_dispatch<T, 3, 1>(a, x, xprev, g, dinv, out, c1, c2, apply_only, s);
+  if (dim == 2 && k == 2) return cheb_dispatch<T, 2, 2>(a, x, xprev, g, dinv, out, c1, c2, apply_only, s);
+  if (dim == 2 && k == 1) return cheb_dispatch<T, 2, 1>(a, x, xprev, g, dinv, out, c1, c2, apply_only, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int DIM, int K>
+static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* gc, cudaStream_t s) {
+  using G = Geo<DIM, K>;
+  if (a.n_groups == 0) return cudaSuccess;
+  size_t sm = ResSmem<T, DIM, K>::bytes() + 16;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(level_residual_restrict_kernel<T, DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    init = true;
+  }
+  dim3 grid((unsigned)((a.n_groups + G::GPB - 1) / G::GPB));
+  level_residual_restrict_kernel<T, DIM, K><<<grid, G::GPB * G::TEAM, sm, s>>>(a, u, g, gc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_level_residual_restrict(int dim, int k, const LevelArgs& a, const T* u,
+                                           const T* g, T* gc, cudaStream_t s) {
+  if (dim == 3 && k == 2) return res_dispatch<T, 3, 2>(a, u, g, gc, s);
+  if (dim == 3 && k == 1) return res_dispatch<T, 3, 1>(a, u, g, gc, s);
+  if (dim == 2 && k == 2) return res_dispatch<T, 2, 2>(a, u, g, gc, s);
+  if (dim == 2 && k == 1) return res_dispatch<T, 2, 1>(a, u, g, gc, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int DIM, int K>
+static cudaError_t pro_dispatch(const LevelArgs& a, const T* uc, T* u, T* u2, cudaStream_t s) {
+  using G = Geo<DIM, K>;
+  if (a.n_groups == 0) return cudaSuccess;
+  size_t sm = (size_t)G::GPB * (G::NCELL + 2 * G::NGRP) * sizeof(T) + 16;
+  dim3 grid((unsigned)((a.n_groups + G::GPB - 1) / G::GPB));
+  level_prolongate_kernel<T, DIM, K><<<grid, G::GPB * G::TEAM, sm, s>>>(a, uc, u, u2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_level_prolongate(int dim, int k, const LevelArgs& a, const T* uc, T* u, T* u2,
+                                    cudaStream_t s) {
+  if (dim == 3 && k == 2) return pro_dispatch<T, 3, 2>(a, uc, u, u2, s);
+  if (dim == 3 && k == 1) return pro_dispatch<T, 3, 1>(a, uc, u, u2, s);
+  if (dim == 2 && k == 2) return pro_dispatch<T, 2, 2>(a, uc, u, u2, s);
+  if (dim == 2 && k == 1) return pro_dispatch<T, 2, 1>(a, uc, u, u2, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int DIM, int K>
+static cudaError_t diag_dispatch(const LevelArgs& a, double* d, cudaStream_t s) {
+  using G = Geo<DIM, K>;
+  int64_t n = a.n_groups * G::NOWN;
+  if (n == 0) return cudaSuccess;
+  level_diag_kernel<DIM, K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_diag(int dim, int k, const LevelArgs& a, double* d, cudaStream_t s) {
+  if (dim == 3 && k == 2) return diag_dispatch<3, 2>(a, d, s);
+  if (dim == 3 && k == 1) return diag_dispatch<3, 1>(a, d, s);
+  if (dim == 2 && k == 2) return diag_dispatch<2, 2>(a, d, s);
+  if (dim == 2 && k == 1) return diag_dispatch<2, 1>(a, d, s);
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_level_cheb<float>(int, int, const LevelArgs&, const float*, const float*,
+                                              const float*, const float*, float*, float, float, bool,
+                                              cudaStream_t);
+template cudaError_t launch_level_cheb<double>(int, int, const LevelArgs&, const double*, const double*,
+                                               const double*, const double*, double*, double, double,
+                                               bool, cudaStream_t);
+template cudaError_t launch_level_residual_restrict<float>(int, int, const LevelArgs&, const float*,
+                                                           const float*, float*, cudaStream_t);
+template cudaError_t launch_level_residual_restrict<double>(int, int, const LevelArgs&, const double*,
+                                                            const double*, double*, cudaStream_t);
+template cudaError_t launch_level_prolongate<float>(int, int, const LevelArgs&, const float*, float*,
+                                                    float*, cudaStream_t);
+template cudaError_t launch_level_prolongate<double>(int, int, const LevelArgs&, const double*,
+                                                     double*, double*, cudaStream_t);
+
+}  // namespace gmg

@@ -1,0 +1,120 @@
+"""C-ABI library on the CPU: it loads, exports every declared symbol, builds
+hierarchies on a host-only context identical to the oracle's, and rejects
+invalid input with GMG_EINVAL.  No compute call runs here (no GPU)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fem
+from oracle.mesh import build_forest
+from paper_1904_03317_gb300 import gmg as G
+from paper_1904_03317_gb300 import inputs
+from tests.helpers import small_workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1904_03317_gb300 import build
+    build.build()
+    yield
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gmg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = G.load_library()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(G.EXPORTED) == names
+
+
+def test_build_info_reports_sm103a():
+    import ctypes as C
+    a, v = C.c_int(), C.c_int()
+    assert G.load_library().gmg_build_info(C.byref(a), C.byref(v)) == 0
+    assert a.value == 1 and v.value == 1
+
+
+@pytest.mark.parametrize("name", list(small_workloads()))
+def test_host_hierarchy_matches_oracle(name):
+    w = small_workloads()[name]
+    m = G.build_mesh(w)
+    H = G.Hierarchy(G.Context(-1), m, w.degree, w.coeff)
+    f = build_forest(w.coarse, w.rounds)
+    lv, co = m.leaves()
+    assert set((l, tuple(c)) for l, c in f.leaves()) == set(
+        (int(l), tuple(int(x) for x in c)) for l, c in zip(lv, co))
+    d = fem.Discretization(f, w.degree, w.coeff)
+    np.testing.assert_array_equal(H.export(G.EXPORT_UNKNOWN_KEYS), d.unknown_keys)
+    np.testing.assert_array_equal(H.export(G.EXPORT_HOME_LEVEL), d.home_level)
+    hang = H.export(G.EXPORT_HANGING)
+    got = sorted((int(r["key"]), int(r["master"]), round(float(r["w"]), 12)) for r in hang)
+    want = sorted((k, m_, round(w_, 12)) for k, row in d.hanging.items() for m_, w_ in row
+                  if not d.is_dirichlet(m_))
+    assert got == want
+    for l in range(d.L + 1):
+        keys, iface, _ = d.level_space(l)
+        lk = H.export(G.EXPORT_LEVEL_KEYS, l)
+        lc = H.export(G.EXPORT_LEVEL_CLASS, l)
+        np.testing.assert_array_equal(np.sort(lk[lc == 1]), keys[~iface])
+        np.testing.assert_array_equal(np.sort(lk[lc == 2]), keys[iface])
+    info = H.info
+    assert info.n_unknowns == d.n and info.n_levels == d.L + 1
+    assert sum(info.n_home[l] for l in range(info.n_levels)) == d.n
+
+
+def test_leaves_are_in_morton_order_within_coarse_cells():
+    cm = inputs.CoarseMesh(2, (2, 1, 1), (0, 0, 0), (2, 1, 1))
+    m = G.Mesh(cm)
+    m.refine(np.ones(2, dtype=np.uint8))
+    lv, co = m.leaves()
+    # coarse cell 0 first; children in z-order (x fastest, then y)
+    assert [tuple(c[:2]) for c in co[:4]] == [(0, 0), (1, 0), (0, 1), (1, 1)]
+    assert [tuple(c[:2]) for c in co[4:]] == [(2, 0), (3, 0), (2, 1), (3, 1)]
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(G.GmgError) as e:
+        G.Mesh(inputs.CoarseMesh(4, (1, 1, 1), (0, 0, 0), (1, 1, 1)))
+    assert e.value.status == G.EINVAL
+    with pytest.raises(G.GmgError) as e:
+        G.Mesh(inputs.CoarseMesh(2, (2, 2, 1), (0, 0, 0), (0.0, 1.0, 1.0)))
+    assert e.value.status == G.EINVAL
+    m = G.Mesh(inputs.CoarseMesh(2, (2, 2, 1), (0, 0, 0), (1, 1, 1)))
+    with pytest.raises(G.GmgError) as e:
+        m.refine(np.ones(3, dtype=np.uint8))  # wrong length
+    assert e.value.status == G.EINVAL
+    ctx = G.Context(-1)
+    with pytest.raises(G.GmgError) as e:
+        G.Hierarchy(ctx, m, 3)
+    assert e.value.status == G.EINVAL
+    with pytest.raises(G.GmgError) as e:
+        G.Hierarchy(ctx, m, 1, coarse_coeff=[1.0, -1.0, 1.0, 1.0])
+    assert e.value.status == G.EINVAL
+    H = G.Hierarchy(ctx, m, 1)
+    # device calls on a host-only hierarchy fail cleanly
+    x = np.zeros(max(1, H.n))
+    with pytest.raises(G.GmgError) as e:
+        H.apply(x, x.copy())
+    assert e.value.status == G.EINVAL
+
+
+def test_closure_after_deep_refinement_matches_oracle():
+    cm = inputs.CoarseMesh(3, (2, 2, 2), (0, 0, 0), (1, 1, 1))
+    rounds = [inputs.round_sphere_surface((0.4301, 0.3701, 0.5501), 0.003)] * 5
+    m = G.Mesh(cm)
+    m.apply_rounds(rounds)
+    f = build_forest(cm, rounds)
+    lv, co = m.leaves()
+    assert set((l, tuple(c)) for l, c in f.leaves()) == set(
+        (int(l), tuple(int(x) for x in c)) for l, c in zip(lv, co))

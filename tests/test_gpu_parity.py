@@ -1,0 +1,289 @@
+"""GPU parity: every step of the solve path, called through the C ABI, against
+the FP64 oracle on the same seeded inputs.
+
+FP64 path: element-wise agreement to 1e-11 relative (the two sides differ
+only in rounding order); full solve to 1e-10 relative at the oracle's
+iteration count and iteration counts within +-1.  FP32 V-cycle: level
+operators within FP32 rounding (1e-5 relative), and the outer FP64 CG still
+reaches the 1e-8 relative residual.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import gmg as ogmg
+from paper_1904_03317_gb300 import gmg as G
+from tests.helpers import from_slots, level_maps, oracle_hierarchy, small_workloads, to_slots
+
+pytestmark = pytest.mark.gpu
+
+NAMES = list(small_workloads())
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    if not T.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_03317_gb300 import build
+    build.build()
+    return T
+
+
+_cache = {}
+
+
+def gpu_hier(torch, name, prec=G.PREC_FP64, fixed=True):
+    key = (name, prec, fixed)
+    if key not in _cache:
+        O = oracle_hierarchy(name)
+        w = small_workloads()[name]
+        lam = [lev.lam for lev in O.levels] if fixed else None
+        ctx = G.Context(0)
+        m = G.build_mesh(w)
+        H = G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=O.cheb_degree, vcycle_prec=prec,
+                        fixed_lambda=lam)
+        _cache[key] = (O, H, ctx, m)
+    return _cache[key][:2]
+
+
+def dev(torch, a, prec=G.PREC_FP64):
+    dt = torch.float64 if prec == G.PREC_FP64 else torch.float32
+    return torch.tensor(np.asarray(a), dtype=dt, device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_level_apply(torch, name, prec):
+    O, H = gpu_hier(torch, name, prec)
+    rng = np.random.default_rng(11)
+    for l in range(1, len(O.levels)):
+        lev = O.levels[l]
+        idx, cls = level_maps(H, O, l)
+        x = rng.uniform(-1, 1, len(lev.keys))
+        want = np.zeros(len(lev.keys))
+        want[lev.S] = lev.A_S @ x[lev.S] + lev.A_SI @ x[lev.I]
+        xs = dev(torch, to_slots(x, idx, len(idx)), prec)
+        ys = torch.zeros_like(xs)
+        H.level_apply(l, xs, ys)
+        torch.cuda.synchronize()
+        got = host(ys)
+        assert np.all(got[cls != 1] == 0.0)  # only S slots written
+        tol = 1e-11 if prec == G.PREC_FP64 else 2e-5
+        assert rel_err(from_slots(got, idx, len(lev.keys))[lev.S], want[lev.S]) < tol
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_residual_restrict(torch, name, prec):
+    O, H = gpu_hier(torch, name, prec)
+    rng = np.random.default_rng(12)
+    for l in range(1, len(O.levels)):
+        lev, levc = O.levels[l], O.levels[l - 1]
+        idx, cls = level_maps(H, O, l)
+        u = np.zeros(len(lev.keys)); u[lev.S] = rng.uniform(-1, 1, len(lev.S))
+        g = np.zeros(len(lev.keys)); g[lev.S] = rng.uniform(-1, 1, len(lev.S))
+        t = np.zeros(len(lev.keys))
+        t[lev.S] = g[lev.S] - lev.A_S @ u[lev.S]
+        t[lev.I] = -lev.A_IS @ u[lev.S]
+        want = lev.P.T @ t
+        n_c = int(H.info.slots[l - 1])
+        gc = torch.zeros(n_c, dtype=torch.float64 if prec == G.PREC_FP64 else torch.float32, device="cuda")
+        H.level_residual_restrict(l, dev(torch, to_slots(u, idx, len(idx)), prec),
+                                  dev(torch, to_slots(g, idx, len(idx)), prec), gc)
+        torch.cuda.synchronize()
+        idc, clsc = level_maps(H, O, l - 1)
+        got = from_slots(host(gc), idc, len(levc.keys))
+        tol = 1e-11 if prec == G.PREC_FP64 else 2e-5
+        assert rel_err(got, want) < tol
+        assert not np.any(want[levc.I])  # complete layer: R lands on S nodes only
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_prolongate(torch, name):
+    O, H = gpu_hier(torch, name)
+    rng = np.random.default_rng(13)
+    for l in range(1, len(O.levels)):
+        lev, levc = O.levels[l], O.levels[l - 1]
+        idx, cls = level_maps(H, O, l)
+        idc, clsc = level_maps(H, O, l - 1)
+        uc = rng.uniform(-1, 1, len(levc.keys))
+        u = np.zeros(len(lev.keys)); u[lev.S] = rng.uniform(-1, 1, len(lev.S))
+        pu = lev.P @ uc
+        ud = dev(torch, to_slots(u, idx, len(idx)))
+        u2 = torch.zeros_like(ud)
+        H.level_prolongate(l, dev(torch, to_slots(uc, idc, len(idc))), ud, u2)
+        torch.cuda.synchronize()
+        got = from_slots(host(ud), idx, len(lev.keys))
+        got2 = from_slots(host(u2), idx, len(lev.keys))
+        want = u.copy(); want[lev.S] += pu[lev.S]; want[lev.I] = pu[lev.I]
+        assert rel_err(got, want) < 1e-13
+        assert rel_err(got2[lev.I], pu[lev.I]) < 1e-13 if len(lev.I) else True
+        assert np.all(got2[lev.S] == 0.0)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_inverse_diagonal(torch, name):
+    O, H = gpu_hier(torch, name)
+    for l in range(1, len(O.levels)):
+        lev = O.levels[l]
+        idx, cls = level_maps(H, O, l)
+        out = torch.zeros(len(idx), dtype=torch.float64, device="cuda")
+        H.level_inv_diag(l, out)
+        torch.cuda.synchronize()
+        got = host(out)
+        assert np.all(got[cls != 1] == 0.0)
+        assert rel_err(from_slots(got, idx, len(lev.keys))[lev.S], lev.dinv) < 1e-13
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_coarse_solve(torch, name):
+    O, H = gpu_hier(torch, name)
+    lev = O.levels[0]
+    idx, cls = level_maps(H, O, 0)
+    rng = np.random.default_rng(14)
+    g = rng.uniform(-1, 1, len(lev.keys))
+    want = sla.cho_solve(O.coarse_chol, g)
+    u0 = torch.zeros(len(idx), dtype=torch.float64, device="cuda")
+    H.coarse_solve(dev(torch, to_slots(g, idx, len(idx))), u0)
+    torch.cuda.synchronize()
+    got = host(u0)
+    assert np.all(got[cls == 3] == 0.0)
+    assert rel_err(from_slots(got, idx, len(lev.keys)), want) < 1e-12
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_chebyshev_smoother(torch, name):
+    O, H = gpu_hier(torch, name)
+    rng = np.random.default_rng(15)
+    m = O.cheb_degree
+    for l in range(1, len(O.levels)):
+        lev = O.levels[l]
+        idx, cls = level_maps(H, O, l)
+        g = np.zeros(len(lev.keys)); g[lev.S] = rng.uniform(-1, 1, len(lev.S))
+        # from zero
+        want = np.zeros(len(lev.keys))
+        want[lev.S] = ogmg.chebyshev(lev.A_S, lev.dinv, np.zeros(len(lev.S)), g[lev.S], lev.lam, m, x0_is_zero=True)
+        ud = torch.zeros(len(idx), dtype=torch.float64, device="cuda")
+        tmp = torch.zeros_like(ud)
+        gd = dev(torch, to_slots(g, idx, len(idx)))
+        H.level_smooth(l, gd, ud, tmp, True)
+        torch.cuda.synchronize()
+        assert rel_err(from_slots(host(ud), idx, len(lev.keys)), want) < 1e-11
+        # from a nonzero start with fixed interface values
+        u0 = rng.uniform(-1, 1, len(lev.keys))
+        want = u0.copy()
+        want[lev.S] = ogmg.chebyshev(lev.A_S, lev.dinv, u0[lev.S], g[lev.S] - lev.A_SI @ u0[lev.I], lev.lam, m)
+        ud = dev(torch, to_slots(u0, idx, len(idx)))
+        H.level_smooth(l, gd, ud, tmp, False)
+        torch.cuda.synchronize()
+        assert rel_err(from_slots(host(ud), idx, len(lev.keys)), want) < 1e-11
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_eigenvalue_estimates(torch, name):
+    O, H = gpu_hier(torch, name, fixed=False)
+    for l in range(1, len(O.levels)):
+        assert H.info.lambda_max[l] == pytest.approx(O.levels[l].lam, rel=1e-10)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_vcycle(torch, name):
+    O, H = gpu_hier(torch, name)
+    rng = np.random.default_rng(16)
+    r = rng.uniform(-1, 1, O.disc.n)
+    want = ogmg.vcycle(O, r)
+    z = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    H.vcycle(dev(torch, r), z)
+    torch.cuda.synchronize()
+    assert rel_err(host(z), want) < 1e-11
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_vcycle_fp32(torch, name):
+    O, H = gpu_hier(torch, name, G.PREC_FP32)
+    rng = np.random.default_rng(17)
+    r = rng.uniform(-1, 1, O.disc.n)
+    want = ogmg.vcycle(O, r)
+    z = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    H.vcycle(dev(torch, r), z)
+    torch.cuda.synchronize()
+    assert rel_err(host(z), want) < 1e-4
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_active_apply(torch, name):
+    O, H = gpu_hier(torch, name)
+    rng = np.random.default_rng(18)
+    x = rng.uniform(-1, 1, O.disc.n)
+    y = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    H.apply(dev(torch, x), y)
+    torch.cuda.synchronize()
+    assert rel_err(host(y), O.disc.A @ x) < 1e-12
+
+
+@pytest.mark.parametrize("name", [n for n in NAMES if small_workloads()[n].coeff is None])
+def test_rhs_sine(torch, name):
+    O, H = gpu_hier(torch, name)
+    b = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    H.assemble_rhs(b)
+    torch.cuda.synchronize()
+    assert rel_err(host(b), O.disc.rhs_sine()) < 1e-12
+
+
+def _rhs(O, w):
+    from paper_1904_03317_gb300 import inputs
+    return O.disc.rhs_sine() if w.rhs == "sine" else inputs.random_rhs(w.seed, O.disc.n)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_solve_fp64_matches_oracle(torch, name):
+    O, H = gpu_hier(torch, name)
+    w = small_workloads()[name]
+    b = _rhs(O, w)
+    ref = ogmg.solve(O, b, 1e-10)
+    x = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    st = H.solve(dev(torch, b), x, tol=1e-10)
+    assert abs(st.iterations - ref.iterations) <= 1
+    # same iteration count: the iterates agree to rounding
+    st = H.solve(dev(torch, b), x, fixed_iterations=ref.iterations)
+    assert st.iterations == ref.iterations
+    assert rel_err(host(x), ref.x) < 1e-10
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_solve_fp32_vcycle_reaches_tolerance(torch, name):
+    O, H = gpu_hier(torch, name, G.PREC_FP32)
+    w = small_workloads()[name]
+    b = _rhs(O, w)
+    x = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    st = H.solve(dev(torch, b), x, tol=1e-8)
+    assert st.converged and st.rel_residual <= 1e-8
+    xs = host(x)
+    true_res = np.linalg.norm(b - O.disc.A @ xs) / np.linalg.norm(b)
+    assert true_res < 2e-8
+    ref = ogmg.solve(O, b, 1e-12)
+    assert rel_err(xs, ref.x) < 1e-6
+
+
+def test_solve_error_paths(torch):
+    O, H = gpu_hier(torch, "3d_q2_sphere")
+    b = dev(torch, O.disc.rhs_sine())
+    x = torch.zeros_like(b)
+    st = H.solve(b, x, tol=1e-12, max_iter=2, raise_on_error=False)
+    assert H.last_status == G.ENOTCONV and st.iterations == 2 and not st.converged
+    bn = b.clone()
+    bn[3] = float("nan")
+    H.solve(bn, x, tol=1e-8, raise_on_error=False)
+    assert H.last_status == G.ENAN
+    z = torch.zeros_like(b)
+    st = H.solve(z, x, tol=1e-8)
+    assert st.iterations == 0 and torch.count_nonzero(x).item() == 0
