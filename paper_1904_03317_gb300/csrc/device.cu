@@ -179,6 +179,12 @@ static ActiveArgs active_args(const Hier& h) {
   a.hang_ptr = h.dev->hang_ptr;
   a.hang_col = h.dev->hang_col;
   a.hang_w = h.dev->hang_w;
+  for (int l = 0; l < GMG_MAX_LEVELS; ++l)
+    for (int d = 0; d < 3; ++d) {
+      a.scale[l][d] = h.dev->level_scale[l][d];
+      a.h[l][d] = h.dev->cell_h[l][d];
+    }
+  for (int d = 0; d < 3; ++d) a.lo[d] = h.lo[d];
   return a;
 }
 
@@ -356,7 +362,6 @@ gmg_status device_setup(Hier& h) {
     d->active_bytes = (double)A.n_cells * (4.0 * nc + 9.0) + 24.0 * (double)A.n_unknowns +
                       12.0 * (double)A.hang_col.size();
   }
-  GMG_CUDA_TRY(set_active_scales(d->level_scale, d->cell_h, h.lo));
   GMG_TRY(dev_alloc(d, &d->r, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->p, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->Ap, A.n_unknowns));

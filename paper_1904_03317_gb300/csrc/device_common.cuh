@@ -132,12 +132,15 @@ struct ActiveArgs {
   const int32_t* hang_ptr;
   const int32_t* hang_col;
   const double* hang_w;
+  // per-level factors of the hierarchy (kernel parameters, so hierarchies
+  // that live side by side never share them)
+  double scale[GMG_MAX_LEVELS][3];  // s_i = prod_{j != i} h_j / h_i
+  double h[GMG_MAX_LEVELS][3];      // cell sizes
+  double lo[3];                     // brick origin
 };
 cudaError_t launch_active_apply(int dim, int k, const ActiveArgs& a, const double* x, double* y,
                                 double* partials, unsigned* counter, double* energy_out,
                                 cudaStream_t s);
-cudaError_t set_active_scales(const double scale[GMG_MAX_LEVELS][3],
-                              const double h[GMG_MAX_LEVELS][3], const double lo[3]);
 cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* cell_coords,
                             double* b, cudaStream_t s);
 template <typename T>

@@ -45,19 +45,6 @@ __device__ __forceinline__ void sfor(F&& f) {
   }
 }
 
-__constant__ double c_level_scale[GMG_MAX_LEVELS][3];
-__constant__ double c_cell_h[GMG_MAX_LEVELS][3];
-__constant__ double c_lo[3];
-
-cudaError_t set_active_scales(const double scale[GMG_MAX_LEVELS][3], const double h[GMG_MAX_LEVELS][3],
-                              const double lo[3]) {
-  cudaError_t e = cudaMemcpyToSymbol(c_level_scale, scale, sizeof(double) * GMG_MAX_LEVELS * 3);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyToSymbol(c_cell_h, h, sizeof(double) * GMG_MAX_LEVELS * 3);
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_lo, lo, sizeof(double) * 3);
-}
-
 // ------------------------------------------------------------ reductions
 // Block sum in a fixed order; result valid in thread 0.
 template <int BS>
@@ -177,7 +164,7 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
       T2MK[cl][n] = mk;
       T2KM[cl][n] = km;
       __syncthreads();
-      const double sx = c_level_scale[lvl][0], sy = c_level_scale[lvl][1], sz = c_level_scale[lvl][2];
+      const double sx = a.scale[lvl][0], sy = a.scale[lvl][1], sz = a.scale[lvl][2];
       sfor<0, N1>([&](auto c) {
         int j = ix + N1 * (iy + N1 * c);
         out += astiff1<K>(iz, c) * sz * T2MM[cl][j] + amass1<K>(iz, c) * (sy * T2MK[cl][j] + sx * T2KM[cl][j]);
@@ -192,7 +179,7 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
       T1M[cl][n] = m;
       T1K[cl][n] = k;
       __syncthreads();
-      const double sx = c_level_scale[lvl][0], sy = c_level_scale[lvl][1];
+      const double sx = a.scale[lvl][0], sy = a.scale[lvl][1];
       sfor<0, N1>([&](auto c) {
         int j = ix + N1 * c;
         out += astiff1<K>(iy, c) * sy * T1M[cl][j] + amass1<K>(iy, c) * sx * T1K[cl][j];
@@ -273,8 +260,8 @@ __global__ void rhs_sine_kernel(ActiveArgs a, const int32_t* __restrict__ coords
   const int i[3] = {n % N1, (n / N1) % N1, DIM == 3 ? n / (N1 * N1) : 0};
   double h[3], lo[3];
   for (int d = 0; d < 3; ++d) {
-    h[d] = c_cell_h[lvl][d];
-    lo[d] = c_lo[d] + coords[3 * cell + d] * h[d];
+    h[d] = a.h[lvl][d];
+    lo[d] = a.lo[d] + coords[3 * cell + d] * h[d];
   }
   const double PI = 3.14159265358979323846;
   double acc = 0.0;
