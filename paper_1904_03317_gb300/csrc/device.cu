@@ -160,11 +160,20 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.nbr = L.nbr;
   a.state = L.state;
   a.coeff = L.coeff;
+  a.coeff32 = L.coeff32;
+  a.smask = L.smask;
+  a.lcoef64 = L.lcoef64;
+  a.lcoef32 = L.lcoef32;
   a.parent = L.parent;
+  a.list_uniform = L.list_uniform;
+  a.list_jump = L.list_jump;
+  a.n_uniform = L.n_uniform;
+  a.n_jump = L.n_jump;
   a.nbr_coarse = l >= 2 ? h.dev->lv[l - 1].nbr : nullptr;
   for (int d = 0; d < 3; ++d) {
     a.coarse_lat[d] = h.coarse_lattice[d];
     a.scale[d] = L.scale[d];
+    a.scale32[d] = (float)L.scale[d];
   }
   a.level = l;
   return a;
@@ -211,6 +220,12 @@ void device_free(Hier& h) {
     cudaFree(L.state);
     cudaFree(L.coeff);
     cudaFree(L.parent);
+    cudaFree(L.smask);
+    cudaFree(L.lcoef64);
+    cudaFree(L.lcoef32);
+    cudaFree(L.coeff32);
+    cudaFree(L.list_uniform);
+    cudaFree(L.list_jump);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
@@ -312,7 +327,7 @@ gmg_status device_setup(Hier& h) {
     LevelDev& D = d->lv[l];
     const LevelHost& H = h.levels[l];
     D.offset = h.level_offset[l];
-    D.n_slots = h.level_offset[l + 1] - h.level_offset[l];
+    D.n_slots = (int64_t)H.slot_class.size();
     double hh[3];
     level_scales(h, l, D.scale, hh);
     D.n_S = (double)H.n_S;
@@ -324,6 +339,14 @@ gmg_status device_setup(Hier& h) {
     GMG_TRY(upload(d, &D.state, H.state));
     GMG_TRY(upload(d, &D.coeff, H.coeff));
     GMG_TRY(upload(d, &D.parent, H.parent));
+    GMG_TRY(upload(d, &D.smask, H.smask));
+    GMG_TRY(upload(d, &D.lcoef64, H.lcoef));
+    GMG_TRY(upload(d, &D.lcoef32, std::vector<float>(H.lcoef.begin(), H.lcoef.end())));
+    GMG_TRY(upload(d, &D.coeff32, std::vector<float>(H.coeff.begin(), H.coeff.end())));
+    GMG_TRY(upload(d, &D.list_uniform, H.list_uniform));
+    GMG_TRY(upload(d, &D.list_jump, H.list_jump));
+    D.n_uniform = (int64_t)H.list_uniform.size();
+    D.n_jump = (int64_t)H.list_jump.size();
     if (D.n_slots != (H.n_groups + H.n_ghosts) * NOWN) {
       set_error("level slot count mismatch");
       return GMG_EINVAL;

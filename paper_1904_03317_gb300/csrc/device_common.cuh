@@ -29,6 +29,13 @@ struct LevelDev {
   uint64_t* state = nullptr;    // n_groups
   double* coeff = nullptr;      // n_groups
   int32_t* parent = nullptr;    // n_groups
+  uint64_t* smask = nullptr;    // n_groups
+  double* lcoef64 = nullptr;    // n_groups x 2^d
+  float* lcoef32 = nullptr;     // n_groups x 2^d
+  float* coeff32 = nullptr;     // n_groups
+  int32_t* list_uniform = nullptr;
+  int32_t* list_jump = nullptr;
+  int64_t n_uniform = 0, n_jump = 0;
   double scale[3] = {0, 0, 0};  // K-term factor per direction: prod_{j!=i} h_j / h_i
   // Chebyshev parameters (host)
   double lambda = 0, theta = 0, delta = 0, sigma = 0;
@@ -42,10 +49,18 @@ struct LevelArgs {
   const int32_t* nbr;
   const uint64_t* state;
   const double* coeff;
+  const float* coeff32;
+  const uint64_t* smask;
+  const double* lcoef64;
+  const float* lcoef32;
   const int32_t* parent;
+  const int32_t* list_uniform;
+  const int32_t* list_jump;
+  int64_t n_uniform, n_jump;
   const int32_t* nbr_coarse;  // level l-1 neighbour table (l >= 2)
   int64_t coarse_lat[3];      // coarse lattice extents (l == 1)
   double scale[3];
+  float scale32[3];
   int level;
 };
 

@@ -128,6 +128,11 @@ struct LevelHost {
   std::vector<int32_t> nbr;         // n_groups x 3^d slots of neighbour blocks (-1 outside)
   std::vector<uint64_t> state;      // n_groups: 2 bits per 3^d offset + child bits
   std::vector<double> coeff;        // n_groups: a of the group's cells
+  std::vector<uint64_t> smask;      // n_groups: bit i set if stored node i is an S node
+  std::vector<double> lcoef;        // n_groups x 2^d: a of the groups at offsets {-1,0}^d (0 if not refined)
+  // groups whose refined lower neighbours all share the group's coefficient
+  // (one merged tensor product suffices), and the rest
+  std::vector<int32_t> list_uniform, list_jump;
   std::vector<int32_t> parent;      // n_groups: parent's group at l-1 (or coarse cell at l=1)
   std::vector<int64_t> block_pos;   // (n_groups + n_ghosts) x 3: parent-lattice position
   std::vector<int8_t> slot_class;   // 0 unused, 1 S, 2 I, 3 D

@@ -276,7 +276,8 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     lv.n_cells = (uint64_t)h.n0[0] * h.n0[1] * h.n0[2];
     lv.n_S = h.n_coarse;
   }
-  h.level_offset[1] = (int64_t)h.levels[0].slot_class.size();
+  auto pad64 = [](int64_t v) { return (v + 63) / 64 * 64; };  // level starts 256-byte aligned
+  h.level_offset[1] = pad64((int64_t)h.levels[0].slot_class.size());
 
   // ------------------------------------------------ levels l >= 1: blocks
   std::vector<HashMap64> block_map(L + 1);  // parent position (level l-1) -> block index
@@ -365,7 +366,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     }
     lv.n_ghosts = next_ghost - lv.n_groups;
     int64_t nslots = (lv.n_groups + lv.n_ghosts) * NOWN;
-    h.level_offset[l + 1] = h.level_offset[l] + nslots;
+    h.level_offset[l + 1] = pad64(h.level_offset[l] + nslots);
     // slot classes and keys, from every real group's (2k+1)^d node block
     lv.slot_class.assign(nslots, 0);
     lv.slot_key.assign(nslots, -1);
@@ -420,6 +421,27 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     }
     }
     if (bad) throw std::runtime_error("inconsistent node classes between sibling groups");
+    // per-group S mask of the stored nodes and coefficients of the lower neighbours
+    lv.smask.assign(lv.n_groups, 0);
+    lv.lcoef.assign((size_t)lv.n_groups << dim, 0.0);
+    for (int64_t g = 0; g < lv.n_groups; ++g) {
+      uint64_t m = 0;
+      for (int i = 0; i < NOWN; ++i)
+        if (lv.slot_class[g * NOWN + i] == 1) m |= 1ull << i;
+      lv.smask[g] = m;
+      for (int b = 0; b < (1 << dim); ++b) {
+        int o[3] = {-(b & 1), dim > 1 ? -((b >> 1) & 1) : 0, dim > 2 ? -((b >> 2) & 1) : 0};
+        int nb = (o[0] + 1) + 3 * (o[1] + 1) + (dim > 2 ? 9 * (o[2] + 1) : 0);
+        if (((lv.state[g] >> (2 * nb)) & 3) == kStateRefined)
+          lv.lcoef[((size_t)g << dim) + b] = lv.coeff[lv.nbr[(size_t)g * NNB + nb]];
+      }
+      bool uniform = true;
+      for (int b = 1; b < (1 << dim); ++b) {
+        double c = lv.lcoef[((size_t)g << dim) + b];
+        if (c != 0.0 && c != lv.coeff[g]) uniform = false;
+      }
+      (uniform ? lv.list_uniform : lv.list_jump).push_back((int32_t)g);
+    }
     for (int64_t s = 0; s < nslots; ++s) {
       if (lv.slot_class[s] == 1) ++lv.n_S;
       if (lv.slot_class[s] == 2) ++lv.n_I;

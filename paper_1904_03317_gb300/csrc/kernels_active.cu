@@ -114,14 +114,14 @@ __device__ __forceinline__ double gather_node(int32_t id, const double* __restri
 }
 
 template <int DIM, int K>
-__global__ void __launch_bounds__(ActGeo<DIM, K>::BS)
+__global__ void __launch_bounds__(ActGeo<DIM, K>::BS, ActGeo<DIM, K>::BS <= 512 ? 4 : 1)
 active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restrict__ y,
                     double* partials, unsigned* counter, double* energy_out) {
   using G = ActGeo<DIM, K>;
   constexpr int N1 = G::N1, NC = G::NC;
   __shared__ double X[G::CPB][NC];
   __shared__ double T1M[G::CPB][NC], T1K[G::CPB][NC];
-  __shared__ double T2MM[G::CPB][NC], T2MK[G::CPB][NC], T2KM[G::CPB][NC];
+  __shared__ double T2C[G::CPB][NC], T2D[G::CPB][NC];
   __shared__ double red[G::BS / 32];
   const int cl = threadIdx.x / NC;      // cell within block
   const int n = threadIdx.x % NC;       // node within cell
@@ -141,51 +141,55 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
     }
     X[cl][n] = active ? gather_node<DIM, K>(id, x, a.hang_ptr, a.hang_col, a.hang_w) : 0.0;
     __syncthreads();
-    double out = 0.0;
+    // Kronecker sum  sx Kx My Mz + sy Mx Ky Mz + sz Mx My Kz  as
+    //   A = Mx X, B = Kx X;  C = My A, D = sx My B + sy Ky A;  out = a (Mz D + sz Kz C)
+    double out;
     if constexpr (DIM == 3) {
-      double m = 0, k = 0;
+      double A = 0, B = 0;
       sfor<0, N1>([&](auto c) {
-        double v = X[cl][c + N1 * (iy + N1 * iz)];
-        m += amass1<K>(ix, c) * v;
-        k += astiff1<K>(ix, c) * v;
+        const double v = X[cl][c + N1 * (iy + N1 * iz)];
+        A += amass1<K>(ix, c) * v;
+        B += astiff1<K>(ix, c) * v;
       });
-      T1M[cl][n] = m;
-      T1K[cl][n] = k;
+      T1M[cl][n] = A;
+      T1K[cl][n] = B;
       __syncthreads();
-      double mm = 0, mk = 0, km = 0;
+      double C = 0, t1 = 0, t2 = 0;
       sfor<0, N1>([&](auto c) {
-        double vm = T1M[cl][ix + N1 * (c + N1 * iz)];
-        double vk = T1K[cl][ix + N1 * (c + N1 * iz)];
-        mm += amass1<K>(iy, c) * vm;
-        mk += astiff1<K>(iy, c) * vm;
-        km += amass1<K>(iy, c) * vk;
+        const int j = ix + N1 * (c + N1 * iz);
+        const double va = T1M[cl][j], vb = T1K[cl][j];
+        C += amass1<K>(iy, c) * va;
+        t1 += amass1<K>(iy, c) * vb;
+        t2 += astiff1<K>(iy, c) * va;
       });
-      T2MM[cl][n] = mm;
-      T2MK[cl][n] = mk;
-      T2KM[cl][n] = km;
+      T2C[cl][n] = C;
+      T2D[cl][n] = a.scale[lvl][0] * t1 + a.scale[lvl][1] * t2;
       __syncthreads();
-      const double sx = a.scale[lvl][0], sy = a.scale[lvl][1], sz = a.scale[lvl][2];
+      double t3 = 0, t4 = 0;
       sfor<0, N1>([&](auto c) {
-        int j = ix + N1 * (iy + N1 * c);
-        out += astiff1<K>(iz, c) * sz * T2MM[cl][j] + amass1<K>(iz, c) * (sy * T2MK[cl][j] + sx * T2KM[cl][j]);
+        const int j = ix + N1 * (iy + N1 * c);
+        t3 += amass1<K>(iz, c) * T2D[cl][j];
+        t4 += astiff1<K>(iz, c) * T2C[cl][j];
       });
+      out = coef * (t3 + a.scale[lvl][2] * t4);
     } else {
-      double m = 0, k = 0;
+      double A = 0, B = 0;
       sfor<0, N1>([&](auto c) {
-        double v = X[cl][c + N1 * iy];
-        m += amass1<K>(ix, c) * v;
-        k += astiff1<K>(ix, c) * v;
+        const double v = X[cl][c + N1 * iy];
+        A += amass1<K>(ix, c) * v;
+        B += astiff1<K>(ix, c) * v;
       });
-      T1M[cl][n] = m;
-      T1K[cl][n] = k;
+      T1M[cl][n] = A;
+      T1K[cl][n] = B;
       __syncthreads();
-      const double sx = a.scale[lvl][0], sy = a.scale[lvl][1];
+      double t1 = 0, t2 = 0;
       sfor<0, N1>([&](auto c) {
-        int j = ix + N1 * c;
-        out += astiff1<K>(iy, c) * sy * T1M[cl][j] + amass1<K>(iy, c) * sx * T1K[cl][j];
+        const int j = ix + N1 * c;
+        t1 += amass1<K>(iy, c) * T1K[cl][j];
+        t2 += astiff1<K>(iy, c) * T1M[cl][j];
       });
+      out = coef * (a.scale[lvl][0] * t1 + a.scale[lvl][1] * t2);
     }
-    out *= coef;
     if (active) {
       e += X[cl][n] * out;
       if (id >= 0) {

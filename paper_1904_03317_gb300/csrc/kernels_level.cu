@@ -170,10 +170,10 @@ struct ChebSmem {
 // Sum-factorised extended operator: X (halo, NH^DIM) -> Y (NE^DIM, unscaled by coefficients).
 template <typename T, int DIM, int K>
 __device__ __forceinline__ void ext_operator(const T* X, T* T1M, T* T1K, T* T2MM, T* T2MK, T* T2KM,
-                                             T* Y, int lane, const double* scale) {
+                                             T* Y, int lane, const T* scale) {
   using G = Geo<DIM, K>;
   constexpr int NH = G::NH, NE = G::NE;
-  const T sx = (T)scale[0], sy = (T)scale[1], sz = (T)scale[2];
+  const T sx = scale[0], sy = scale[1], sz = scale[2];
   if constexpr (DIM == 3) {
     // stage x: lines (z, y)
     for (int line = lane; line < NH * NH; line += G::TEAM) {
@@ -278,41 +278,76 @@ __device__ __forceinline__ void ext_operator(const T* X, T* T1M, T* T1K, T* T2MM
   }
 }
 
-// Load the (3K+1)^d halo of group g into X.
+// Scale factors and coefficients in the kernel's precision (no FP64 work in
+// the FP32 kernels: FP64 throughput is a small fraction of FP32 on this GPU).
+template <typename T>
+__device__ __forceinline__ T level_scale(const LevelArgs& a, int d) {
+  if constexpr (std::is_same<T, float>::value) return a.scale32[d];
+  else return a.scale[d];
+}
+template <typename T>
+__device__ __forceinline__ const T* lower_coefs(const LevelArgs& a) {
+  if constexpr (std::is_same<T, float>::value) return a.lcoef32;
+  else return a.lcoef64;
+}
+template <typename T>
+__device__ __forceinline__ T group_coef(const LevelArgs& a, int64_t g) {
+  if constexpr (std::is_same<T, float>::value) return a.coeff32[g];
+  else return a.coeff[g];
+}
+
+// Load the (3K+1)^d halo of a group into X, one neighbour block at a time.
+// Along each direction the halo [-K, 2K] is three segments: positions
+// -K..-1 (stored nodes K..2K-1 of the -1 neighbour), 0..2K-1 (own block) and
+// 2K (node 0 of the +1 neighbour); the sub-box of every neighbour block has
+// compile-time extents, so decoding an element index is shifts and masks.
+template <int K>
+struct Seg {
+  __device__ static constexpr int len(int o) { return o < 0 ? K : (o == 0 ? 2 * K : 1); }
+  __device__ static constexpr int src(int o) { return o < 0 ? K : 0; }       // first stored index read
+  __device__ static constexpr int dst(int o) { return o < 0 ? 0 : (o == 0 ? K : 3 * K); }  // halo index
+};
+
 template <typename T, int DIM, int K>
 __device__ __forceinline__ void load_halo(const T* __restrict__ x, const int32_t* nb, T* X, int lane) {
   using G = Geo<DIM, K>;
   constexpr int NH = G::NH, NO = G::NO;
-  for (int h = lane; h < G::NHALO; h += G::TEAM) {
-    int c[3] = {h % NH, DIM > 1 ? (h / NH) % NH : K, DIM > 2 ? h / (NH * NH) : K};
-    int ni = 0, loc = 0, mul3 = 1, mulo = 1;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      int rel = c[d] - K;
-      int o = rel < 0 ? -1 : (rel < NO ? 0 : 1);
-      ni += (o + 1) * mul3;
-      loc += (rel - NO * o) * mulo;
-      mul3 *= 3;
-      mulo *= NO;
+  static_for<0, G::NNB>([&](auto ni) {
+    constexpr int ox = ni % 3 - 1;
+    constexpr int oy = DIM > 1 ? (ni / 3) % 3 - 1 : 0;
+    constexpr int oz = DIM > 2 ? ni / 9 - 1 : 0;
+    constexpr int LX = Seg<K>::len(ox), LY = DIM > 1 ? Seg<K>::len(oy) : 1, LZ = DIM > 2 ? Seg<K>::len(oz) : 1;
+    constexpr int COUNT = LX * LY * LZ;
+    const int32_t blk = nb[ni];
+    const T* src = x + (int64_t)(blk < 0 ? 0 : blk) * G::NOWN;
+    for (int e = lane; e < COUNT; e += G::TEAM) {
+      const int a = e % LX, b = (e / LX) % LY, c = e / (LX * LY);
+      const int s = (Seg<K>::src(ox) + a) + NO * ((DIM > 1 ? Seg<K>::src(oy) + b : 0) +
+                                                   NO * (DIM > 2 ? Seg<K>::src(oz) + c : 0));
+      const int h = (Seg<K>::dst(ox) + a) + NH * ((DIM > 1 ? Seg<K>::dst(oy) + b : 0) +
+                                                   NH * (DIM > 2 ? Seg<K>::dst(oz) + c : 0));
+      X[h] = blk < 0 ? T(0) : src[s];
     }
-    int32_t blk = nb[ni];
-    X[h] = blk < 0 ? T(0) : x[(int64_t)blk * G::NOWN + loc];
-  }
+  });
 }
 
 // mode: 0 = apply (out[S] = A x), 1 = Chebyshev step
+//   out[S] = x + c1 (x - xprev) + c2 dinv (g - A x)
 template <typename T, int DIM, int K, int MODE>
 __global__ void __launch_bounds__(Geo<DIM, K>::GPB * Geo<DIM, K>::TEAM)
 level_cheb_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev,
                   const T* __restrict__ gvec, const T* __restrict__ dinv, T* out, T c1, T c2) {
   using G = Geo<DIM, K>;
   using S = ChebSmem<T, DIM, K>;
+  constexpr int NO = G::NO, NE = G::NE, ND = 1 << DIM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int team = threadIdx.x / G::TEAM;
   const int lane = threadIdx.x % G::TEAM;
-  const int64_t g = (int64_t)blockIdx.x * G::GPB + team;
-  uint64_t* sts = reinterpret_cast<uint64_t*>(smem_raw);
-  int32_t* nbs = reinterpret_cast<int32_t*>(sts + G::GPB) + team * G::NNB;
+  const int64_t t = (int64_t)blockIdx.x * G::GPB + team;
+  const bool active = t < a.n_jump;
+  const int64_t g = active ? a.list_jump[t] : 0;
+  uint64_t* masks = reinterpret_cast<uint64_t*>(smem_raw);
+  int32_t* nbs = reinterpret_cast<int32_t*>(masks + G::GPB) + team * G::NNB;
   T* base = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER_GROUP;
   T* X = base;
   T* T1M = X + S::X;
@@ -322,52 +357,249 @@ level_cheb_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev,
   T* T2KM = T2MK + S::T2;
   T* Y = T2KM + S::T2;
   T* coefs = Y + S::Y;
-  const bool active = g < a.n_groups;
   if (active) {
     for (int i = lane; i < G::NNB; i += G::TEAM) nbs[i] = a.nbr[g * G::NNB + i];
-    if (lane == 0) sts[team] = a.state[g];
+    if (lane < ND) coefs[lane] = lower_coefs<T>(a)[g * ND + lane];
+    if (lane == 0) masks[team] = a.smask[g];
   }
   __syncthreads();
-  uint64_t st = active ? sts[team] : 0;
-  if (active) {
-    load_halo<T, DIM, K>(x, nbs, X, lane);
-    // coefficients of the groups at offsets in {-1, 0}^d (0 if not refined)
-    if (lane < (1 << DIM)) {
-      int o[3] = {-(lane & 1), DIM > 1 ? -((lane >> 1) & 1) : 0, DIM > 2 ? -((lane >> 2) & 1) : 0};
-      int ni = nbi<DIM>(o[0], o[1], o[2]);
-      T c = 0;
-      if (state_of(st, ni) == kStateRefined) c = (T)a.coeff[nbs[ni]];
-      coefs[lane] = c;
-    }
-  }
+  if (active) load_halo<T, DIM, K>(x, nbs, X, lane);
   __syncthreads();
-  ext_operator<T, DIM, K>(X, T1M, T1K, T2MM, T2MK, T2KM, Y, active ? lane : G::TEAM, a.scale);
-  if (!active) return;
-  // combine extended rows for the stored node `lane`
-  constexpr int NO = G::NO, NE = G::NE;
-  int i[3] = {lane % NO, DIM > 1 ? (lane / NO) % NO : 0, DIM > 2 ? lane / (NO * NO) : 0};
+  const T sc[3] = {level_scale<T>(a, 0), level_scale<T>(a, 1), level_scale<T>(a, 2)};
+  ext_operator<T, DIM, K>(X, T1M, T1K, T2MM, T2MK, T2KM, Y, active ? lane : G::TEAM, sc);
+  if (!active || !((masks[team] >> lane) & 1ull)) return;  // only S nodes are written
+  // combine extended rows: rows 2K stand for the lower neighbour's cell at node 0
+  const int i0 = lane % NO, i1 = DIM > 1 ? (lane / NO) % NO : 0, i2 = DIM > 2 ? lane / (NO * NO) : 0;
   T y = 0;
-  const int ne_x = i[0] == 0 ? 2 : 1, ne_y = (DIM > 1 && i[1] == 0) ? 2 : 1,
-            ne_z = (DIM > 2 && i[2] == 0) ? 2 : 1;
-  for (int bz = 0; bz < ne_z; ++bz)
-    for (int by = 0; by < ne_y; ++by)
-      for (int bx = 0; bx < ne_x; ++bx) {
-        int ex = bx ? 2 * K : i[0], ey = by ? 2 * K : i[1], ez = bz ? 2 * K : i[2];
-        int yi = DIM == 3 ? (ez * NE + ey) * NE + ex : ey * NE + ex;
+  const int nbx = i0 == 0 ? 2 : 1, nby = (DIM > 1 && i1 == 0) ? 2 : 1, nbz = (DIM > 2 && i2 == 0) ? 2 : 1;
+  for (int bz = 0; bz < nbz; ++bz)
+    for (int by = 0; by < nby; ++by)
+      for (int bx = 0; bx < nbx; ++bx) {
+        const int ex = bx ? 2 * K : i0, ey = by ? 2 * K : i1, ez = bz ? 2 * K : i2;
+        const int yi = DIM == 3 ? (ez * NE + ey) * NE + ex : ey * NE + ex;
         y += coefs[bx | (by << 1) | (bz << 2)] * Y[yi];
       }
-  int lo_o[3] = {i[0] == 0 ? -1 : 0, i[1] == 0 && DIM > 1 ? -1 : 0, i[2] == 0 && DIM > 2 ? -1 : 0};
-  int hi_o[3] = {0, 0, 0};
-  int cls = node_class<DIM>(st, lo_o, hi_o);
-  if (cls != 1) return;
   const int64_t slot = g * G::NOWN + lane;
   if constexpr (MODE == 0) {
     out[slot] = y;
   } else {
-    int hx = (i[0] + K) + G::NH * ((DIM > 1 ? i[1] + K : 0) + G::NH * (DIM > 2 ? i[2] + K : 0));
-    T xv = X[hx];
-    T xp = xprev ? xprev[slot] : T(0);
+    const int hx = (i0 + K) + G::NH * ((DIM > 1 ? i1 + K : 0) + G::NH * (DIM > 2 ? i2 + K : 0));
+    const T xv = X[hx];
+    const T xp = xprev ? xprev[slot] : T(0);
     out[slot] = xv + c1 * (xv - xp) + c2 * dinv[slot] * (gvec[slot] - y);
+  }
+}
+
+// ------------------------------------------- smoothing kernel, uniform groups
+// Groups whose refined lower neighbours all share the group's coefficient:
+// the lower neighbour's cell at node 0 merges into row 0 of the 1-D matrices,
+// and one tensor product with (2K) x (3K+1) matrices gives the operator on
+// the stored nodes.  (Rows of nodes next to a missing neighbour pick up terms
+// of cells that do not exist, but those nodes are I or Dirichlet nodes and
+// are never written.)  A team of TW threads (within one warp) handles one
+// group, synchronising with __syncwarp only:
+//   stage 1: each thread loads one halo row along x (three vector loads: the
+//            -1, own and +1 blocks) and contracts it in registers;
+//   stage 2: y-contraction on shared memory;
+//   stage 3: z-contraction fused with the Chebyshev update of its nodes.
+template <int K, bool STIFF>
+__host__ __device__ constexpr double bmerged(int r, int c) {
+  return bext<K, STIFF>(r, c) + (r == 0 ? bext<K, STIFF>(2 * K, c) : 0.0);
+}
+
+template <int DIM, int K>
+struct Fast {
+  static constexpr int NH = 3 * K + 1, NO = 2 * K;
+  static constexpr int NOWN = ipow_c(NO, DIM), NNB = ipow_c(3, DIM);
+  static constexpr int L1 = DIM == 3 ? NH * NH : NH;  // stage-1 lines
+  static constexpr int TW = DIM == 3 ? (K == 2 ? 32 : 16) : (K == 2 ? 8 : 4);
+  static constexpr int TPB = 256 / TW;               // teams per block
+};
+
+template <typename T, int DIM, int K>
+struct FastSmem {
+  using F = Fast<DIM, K>;
+  static constexpr int T1 = F::L1 * F::NO;
+  static constexpr int T2 = DIM == 3 ? F::NH * F::NO * F::NO : 0;
+  static constexpr int PER = 2 * T1 + 3 * T2 + F::NOWN;
+  static constexpr size_t HEADER = ((size_t)F::TPB * (8 + sizeof(T) + 4 * F::NNB) + 15) / 16 * 16;
+  static constexpr size_t bytes() { return HEADER + (size_t)F::TPB * PER * sizeof(T); }
+};
+
+// N consecutive values from an address aligned to N * sizeof(T) (N = 1, 2, 4)
+template <typename T, int N>
+__device__ __forceinline__ void load_run(const T* __restrict__ p, T* v) {
+  if constexpr (N == 4 && sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (N == 2 && sizeof(T) == 4) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else if constexpr (N == 4 && sizeof(T) == 8) {
+    const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  } else if constexpr (N == 2 && sizeof(T) == 8) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
+}
+
+// halo index h in [0, 3K] -> neighbour offset and stored index in that block
+template <int K>
+__device__ __forceinline__ void halo_seg(int h, int& o, int& l) {
+  o = h < K ? -1 : (h < 3 * K ? 0 : 1);
+  l = h < K ? h + K : (h < 3 * K ? h - K : 0);
+}
+
+template <typename T, int DIM, int K, int MODE>
+__global__ void __launch_bounds__(256)
+level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, const T* __restrict__ gvec,
+                       const T* __restrict__ dinv, T* out, T c1, T c2) {
+  using F = Fast<DIM, K>;
+  using S = FastSmem<T, DIM, K>;
+  constexpr int NH = F::NH, NO = F::NO, TW = F::TW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / TW;
+  const int lane = threadIdx.x % TW;
+  const int64_t t = (int64_t)blockIdx.x * F::TPB + team;
+  const bool active = t < a.n_uniform;
+  const int64_t g = active ? a.list_uniform[t] : 0;
+  uint64_t* masks = reinterpret_cast<uint64_t*>(smem_raw);
+  T* coefs = reinterpret_cast<T*>(masks + F::TPB);
+  int32_t* nb = reinterpret_cast<int32_t*>(coefs + F::TPB) + team * F::NNB;
+  T* T1M = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
+  T* T1K = T1M + S::T1;
+  T* T2MM = T1K + S::T1;
+  T* T2MK = T2MM + S::T2;
+  T* T2KM = T2MK + S::T2;
+  T* Xown = T2KM + S::T2;
+  if (active) {
+    for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
+    if (lane == 0) {
+      masks[team] = a.smask[g];
+      coefs[team] = group_coef<T>(a, g);
+    }
+  }
+  __syncwarp();
+  // stage 1: halo rows along x, contracted with the merged 1-D matrices
+  if (active) {
+    for (int line = lane; line < F::L1; line += TW) {
+      int oy = 0, ly = 0, oz = 0, lz = 0;
+      halo_seg<K>(DIM == 3 ? line % NH : line, oy, ly);
+      if constexpr (DIM == 3) halo_seg<K>(line / NH, oz, lz);
+      const int row = NO * (ly + NO * lz);
+      T v[NH];
+      const int32_t b0 = nb[nbi<DIM>(-1, oy, oz)], b1 = nb[nbi<DIM>(0, oy, oz)], b2 = nb[nbi<DIM>(1, oy, oz)];
+      if (b0 >= 0) load_run<T, K>(x + (int64_t)b0 * F::NOWN + row + K, v);
+      else for (int i = 0; i < K; ++i) v[i] = T(0);
+      if (b1 >= 0) load_run<T, 2 * K>(x + (int64_t)b1 * F::NOWN + row, v + K);
+      else for (int i = 0; i < 2 * K; ++i) v[K + i] = T(0);
+      v[3 * K] = b2 >= 0 ? x[(int64_t)b2 * F::NOWN + row] : T(0);
+      if (oy == 0 && oz == 0) {
+#pragma unroll
+        for (int i = 0; i < NO; ++i) Xown[row + i] = v[K + i];
+      }
+      static_for<0, NO>([&](auto r) {
+        T m = 0, k = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bmerged<K, false>(r, c);
+          constexpr double bk = bmerged<K, true>(r, c);
+          if constexpr (bm != 0.0) m += (T)bm * v[c];
+          if constexpr (bk != 0.0) k += (T)bk * v[c];
+        });
+        T1M[line * NO + r] = m;
+        T1K[line * NO + r] = k;
+      });
+    }
+  }
+  __syncwarp();
+  const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
+  const uint64_t smask = masks[team];
+  const T coef = coefs[team];
+  auto update = [&](int node, T y) {
+    if (!((smask >> node) & 1ull)) return;
+    const int64_t slot = g * F::NOWN + node;
+    y *= coef;
+    if constexpr (MODE == 0) {
+      out[slot] = y;
+    } else {
+      const T xv = Xown[node];
+      const T xp = xprev ? xprev[slot] : T(0);
+      out[slot] = xv + c1 * (xv - xp) + c2 * dinv[slot] * (gvec[slot] - y);
+    }
+  };
+  if constexpr (DIM == 3) {
+    // stage 2: y direction; T1 layout [z][y][i] -> T2 layout [z][j][i]
+    if (active) {
+      for (int line = lane; line < NH * NO; line += TW) {
+        const int z = line / NO, i = line % NO;
+        T vm[NH], vk[NH];
+        static_for<0, NH>([&](auto y) {
+          vm[y] = T1M[(z * NH + y) * NO + i];
+          vk[y] = T1K[(z * NH + y) * NO + i];
+        });
+        static_for<0, NO>([&](auto j) {
+          T mm = 0, mk = 0, km = 0;
+          static_for<0, NH>([&](auto c) {
+            constexpr double bm = bmerged<K, false>(j, c);
+            constexpr double bk = bmerged<K, true>(j, c);
+            if constexpr (bm != 0.0) {
+              mm += (T)bm * vm[c];
+              km += (T)bm * vk[c];
+            }
+            if constexpr (bk != 0.0) mk += (T)bk * vm[c];
+          });
+          const int o = (z * NO + j) * NO + i;
+          T2MM[o] = mm;
+          T2MK[o] = mk;
+          T2KM[o] = km;
+        });
+      }
+    }
+    __syncwarp();
+    // stage 3: z direction, then the update of the line's nodes
+    if (active) {
+      for (int line = lane; line < NO * NO; line += TW) {
+        T p[NH], q[NH];
+        static_for<0, NH>([&](auto z) {
+          p[z] = sz * T2MM[z * NO * NO + line];
+          q[z] = sy * T2MK[z * NO * NO + line] + sx * T2KM[z * NO * NO + line];
+        });
+        static_for<0, NO>([&](auto kk) {
+          T y = 0;
+          static_for<0, NH>([&](auto c) {
+            constexpr double bm = bmerged<K, false>(kk, c);
+            constexpr double bk = bmerged<K, true>(kk, c);
+            if constexpr (bk != 0.0) y += (T)bk * p[c];
+            if constexpr (bm != 0.0) y += (T)bm * q[c];
+          });
+          update(line + NO * NO * kk, y);
+        });
+      }
+    }
+  } else {
+    if (active) {
+      for (int i = lane; i < NO; i += TW) {
+        T vm[NH], vk[NH];
+        static_for<0, NH>([&](auto y) {
+          vm[y] = sy * T1M[y * NO + i];
+          vk[y] = sx * T1K[y * NO + i];
+        });
+        static_for<0, NO>([&](auto j) {
+          T y = 0;
+          static_for<0, NH>([&](auto c) {
+            constexpr double bm = bmerged<K, false>(j, c);
+            constexpr double bk = bmerged<K, true>(j, c);
+            if constexpr (bk != 0.0) y += (T)bk * vm[c];
+            if constexpr (bm != 0.0) y += (T)bm * vk[c];
+          });
+          update(i + NO * j, y);
+        });
+      }
+    }
   }
 }
 
@@ -855,31 +1087,41 @@ __global__ void __launch_bounds__(256) level_diag_kernel(LevelArgs a, double* __
 }
 
 // ----------------------------------------------------------- launchers
+template <typename T, int DIM, int K, int MODE>
+static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, const T* g, const T* dinv,
+                               T* out, T c1, T c2, cudaStream_t s) {
+  if (a.n_uniform > 0) {
+    using F = Fast<DIM, K>;
+    const size_t sm = FastSmem<T, DIM, K>::bytes();
+    static bool init = false;
+    if (!init) {
+      cudaFuncSetAttribute(level_cheb_fast_kernel<T, DIM, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      init = true;
+    }
+    dim3 grid((unsigned)((a.n_uniform + F::TPB - 1) / F::TPB));
+    level_cheb_fast_kernel<T, DIM, K, MODE><<<grid, 256, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+  }
+  if (a.n_jump > 0) {
+    using G = Geo<DIM, K>;
+    const size_t sm = ChebSmem<T, DIM, K>::bytes() + 16;
+    static bool init = false;
+    if (!init) {
+      cudaFuncSetAttribute(level_cheb_kernel<T, DIM, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      init = true;
+    }
+    dim3 grid((unsigned)((a.n_jump + G::GPB - 1) / G::GPB));
+    level_cheb_kernel<T, DIM, K, MODE><<<grid, G::GPB * G::TEAM, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T, int DIM, int K>
 static cudaError_t cheb_dispatch(const LevelArgs& a, const T* x, const T* xprev, const T* g,
                                  const T* dinv, T* out, T c1, T c2, bool apply_only,
                                  cudaStream_t s) {
-  using G = Geo<DIM, K>;
   if (a.n_groups == 0) return cudaSuccess;
-  size_t sm = ChebSmem<T, DIM, K>::bytes() + 16;
-  dim3 grid((unsigned)((a.n_groups + G::GPB - 1) / G::GPB));
-  dim3 block(G::GPB * G::TEAM);
-  if (apply_only) {
-    static bool init = false;
-    if (!init) {
-      cudaFuncSetAttribute(level_cheb_kernel<T, DIM, K, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      init = true;
-    }
-    level_cheb_kernel<T, DIM, K, 0><<<grid, block, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
-  } else {
-    static bool init = false;
-    if (!init) {
-      cudaFuncSetAttribute(level_cheb_kernel<T, DIM, K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      init = true;
-    }
-    level_cheb_kernel<T, DIM, K, 1><<<grid, block, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
-  }
-  return cudaGetLastError();
+  return apply_only ? cheb_launch<T, DIM, K, 0>(a, x, xprev, g, dinv, out, c1, c2, s)
+                    : cheb_launch<T, DIM, K, 1>(a, x, xprev, g, dinv, out, c1, c2, s);
 }
 
 template <typename T>

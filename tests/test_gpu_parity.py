@@ -95,12 +95,11 @@ def test_residual_restrict(torch, name, prec):
         t[lev.S] = g[lev.S] - lev.A_S @ u[lev.S]
         t[lev.I] = -lev.A_IS @ u[lev.S]
         want = lev.P.T @ t
-        n_c = int(H.info.slots[l - 1])
-        gc = torch.zeros(n_c, dtype=torch.float64 if prec == G.PREC_FP64 else torch.float32, device="cuda")
+        idc, clsc = level_maps(H, O, l - 1)
+        gc = torch.zeros(len(idc), dtype=torch.float64 if prec == G.PREC_FP64 else torch.float32, device="cuda")
         H.level_residual_restrict(l, dev(torch, to_slots(u, idx, len(idx)), prec),
                                   dev(torch, to_slots(g, idx, len(idx)), prec), gc)
         torch.cuda.synchronize()
-        idc, clsc = level_maps(H, O, l - 1)
         got = from_slots(host(gc), idc, len(levc.keys))
         tol = 1e-11 if prec == G.PREC_FP64 else 2e-5
         assert rel_err(got, want) < tol
