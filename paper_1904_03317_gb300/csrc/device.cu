@@ -182,6 +182,12 @@ static LevelArgs level_args(const Hier& h, int l) {
 static ActiveArgs active_args(const Hier& h) {
   ActiveArgs a;
   a.n_cells = h.dev->n_cells;
+  a.cell_list = h.dev->loose;
+  a.n_list = h.dev->n_loose;
+  a.n_groups = h.dev->n_grp;
+  a.grp_nodes = h.dev->grp_nodes;
+  a.grp_coeff = h.dev->grp_coeff;
+  a.grp_level = h.dev->grp_level;
   a.cell_nodes = h.dev->cell_nodes;
   a.cell_coeff = h.dev->cell_coeff;
   a.cell_level = h.dev->cell_level;
@@ -229,7 +235,7 @@ void device_free(Hier& h) {
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
-                  d->partials, d->counter, d->scal};
+                  d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level};
   for (void* p : ptrs) cudaFree(p);
   if (d->scal_host) cudaFreeHost(d->scal_host);
   for (auto& q : d->prof.pending) {
@@ -377,12 +383,31 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->hang_col, A.hang_col));
   GMG_TRY(upload(d, &d->hang_w, A.hang_w));
   GMG_TRY(upload(d, &d->home, A.home_global));
+  GMG_TRY(upload(d, &d->loose, A.loose_cells));
+  GMG_TRY(upload(d, &d->grp_nodes, A.grp_nodes));
+  GMG_TRY(upload(d, &d->grp_coeff, A.grp_coeff));
+  GMG_TRY(upload(d, &d->grp_level, A.grp_level));
+  d->n_loose = (int64_t)A.loose_cells.size();
+  d->n_grp = A.n_groups;
   for (int l = 0; l < GMG_MAX_LEVELS; ++l) level_scales(h, l, d->level_scale[l], d->cell_h[l]);
   {
-    const double nc = ipow_d(k + 1, dim);
-    const double per_node = dim == 3 ? 8.0 * (k + 1) + 2.0 : 4.0 * (k + 1) + 2.0;  // FMA per cell node
-    d->active_flops = 2.0 * per_node * nc * (double)A.n_cells;
-    d->active_bytes = (double)A.n_cells * (4.0 * nc + 9.0) + 24.0 * (double)A.n_unknowns +
+    // floating-point operations (FMA = 2) of one leaf-operator application
+    const int n1 = k + 1, ng = 2 * k + 1;
+    const double nc = ipow_d(n1, dim), ngn = ipow_d(ng, dim), lines = ipow_d(ng, dim - 1);
+    const double nnz1 = n1 * n1;                       // dense (K+1)^2 element rows
+    const double nnzg = 2.0 * n1 * n1 - 1.0;           // assembled two-cell rows
+    double cell_flops, grp_flops;
+    if (dim == 3) {
+      cell_flops = nc * (2.0 * (2 * n1 + 3 * n1 + 1 + 2 * n1 + 1 + 1) + 2.0);
+      grp_flops = lines * 2.0 * (2 * nnzg + 3 * nnzg + 2 * nnzg) + ngn * (2.0 * 3 + 2.0);
+    } else {
+      cell_flops = nc * (2.0 * (2 * n1 + 2 * n1 + 1 + 1) + 2.0);
+      grp_flops = lines * 2.0 * (2 * nnzg + 2 * nnzg) + ngn * (2.0 * 2 + 2.0);
+    }
+    (void)nnz1;
+    d->active_flops = cell_flops * (double)A.loose_cells.size() + grp_flops * (double)A.n_groups;
+    d->active_bytes = 4.0 * (nc * (double)A.loose_cells.size() + ngn * (double)A.n_groups) +
+                      9.0 * (double)(A.loose_cells.size() + A.n_groups) + 24.0 * (double)A.n_unknowns +
                       12.0 * (double)A.hang_col.size();
   }
   GMG_TRY(dev_alloc(d, &d->r, A.n_unknowns));

@@ -100,6 +100,11 @@ struct DeviceState {
   double* cell_coeff = nullptr;
   uint8_t* cell_level = nullptr;
   int32_t* cell_coords = nullptr;
+  int32_t* loose = nullptr;
+  int64_t n_loose = 0, n_grp = 0;
+  int32_t* grp_nodes = nullptr;
+  double* grp_coeff = nullptr;
+  uint8_t* grp_level = nullptr;
   int32_t* hang_ptr = nullptr;
   int32_t* hang_col = nullptr;
   double* hang_w = nullptr;
@@ -141,6 +146,12 @@ cudaError_t launch_level_diag(int dim, int k, const LevelArgs& a, double* diag_i
 // Active mesh and vector kernels (kernels_active.cu).
 struct ActiveArgs {
   int64_t n_cells;
+  const int32_t* cell_list;  // optional: process only these cells (n_list of them)
+  int64_t n_list;
+  int64_t n_groups;          // full leaf sibling groups
+  const int32_t* grp_nodes;
+  const double* grp_coeff;
+  const uint8_t* grp_level;
   const int32_t* cell_nodes;
   const double* cell_coeff;
   const uint8_t* cell_level;

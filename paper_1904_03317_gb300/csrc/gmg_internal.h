@@ -161,6 +161,13 @@ struct ActiveHost {
   std::vector<double> hang_w;
   std::vector<int64_t> hang_master_key;  // for export (Dirichlet masters dropped)
   int64_t n_leaf_nodes = 0;
+  // leaf sibling groups: refined parents whose 2^d children are all leaves;
+  // node table over the group's (2k+1)^d nodes, same encoding as cell_nodes
+  int64_t n_groups = 0;
+  std::vector<int32_t> grp_nodes;
+  std::vector<double> grp_coeff;
+  std::vector<uint8_t> grp_level;
+  std::vector<int32_t> loose_cells;  // leaf cells not in a full group
 };
 
 struct DeviceState;  // defined in the CUDA translation units

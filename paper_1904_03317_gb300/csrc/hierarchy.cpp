@@ -622,6 +622,52 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       A.cell_nodes[(size_t)i * NLOC + j] = v;
     }
   }
+  // full leaf sibling groups: in canonical (Morton) order the 2^d children of
+  // a parent are consecutive, first child has all coordinate bits 0
+  {
+    const int nch = 1 << dim, NG = 2 * k + 1;
+    const int NGN = ipow(NG, dim);
+    A.grp_nodes.clear();
+    A.grp_coeff.clear();
+    A.grp_level.clear();
+    A.loose_cells.clear();
+    int64_t i = 0;
+    while (i < nleaf) {
+      const int lvl = f.leaf_level[i];
+      bool full = lvl > 0 && i + nch <= nleaf;
+      if (full) {
+        for (int d = 0; d < dim; ++d)
+          if (f.leaf_coords[3 * i + d] & 1) full = false;
+      }
+      if (full) {
+        for (int b = 1; b < nch && full; ++b) {
+          if (f.leaf_level[i + b] != lvl) full = false;
+          for (int d = 0; d < dim && full; ++d)
+            if (f.leaf_coords[3 * (i + b) + d] != f.leaf_coords[3 * i + d] + ((b >> d) & 1)) full = false;
+        }
+      }
+      if (!full) {
+        A.loose_cells.push_back((int32_t)i);
+        ++i;
+        continue;
+      }
+      const size_t base = A.grp_nodes.size();
+      A.grp_nodes.resize(base + NGN);
+      for (int b = 0; b < nch; ++b) {
+        const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
+        for (int j = 0; j < NLOC; ++j) {
+          const int lx = j % (k + 1), ly = dim > 1 ? (j / (k + 1)) % (k + 1) : 0,
+                    lz = dim > 2 ? j / ((k + 1) * (k + 1)) : 0;
+          const int gx = bx * k + lx, gy = by * k + ly, gz = bz * k + lz;
+          A.grp_nodes[base + gx + NG * (gy + NG * gz)] = A.cell_nodes[(size_t)(i + b) * NLOC + j];
+        }
+      }
+      A.grp_coeff.push_back(A.cell_coeff[i]);
+      A.grp_level.push_back((uint8_t)lvl);
+      i += nch;
+    }
+    A.n_groups = (int64_t)A.grp_coeff.size();
+  }
   // home slots
   A.home_slot.resize(nu);
   A.home_global.resize(nu);

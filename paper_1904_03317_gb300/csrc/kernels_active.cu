@@ -64,7 +64,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // Write this block's partial; the last block sums all partials in order into *out.
 template <int BS>
 __device__ __forceinline__ void finish_reduction(double block_total, double* partials, unsigned* counter,
-                                                 double* out) {
+                                                 double* out, bool accumulate = false) {
   __shared__ bool last;
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = block_total;
@@ -80,7 +80,7 @@ __device__ __forceinline__ void finish_reduction(double block_total, double* par
   for (unsigned i = threadIdx.x; i < gridDim.x; i += BS) v += ((volatile double*)partials)[i];
   double s = block_sum<BS>(v, sh);
   if (threadIdx.x == 0) {
-    *out = s;
+    *out = accumulate ? *out + s : s;
     *counter = 0;
   }
 }
@@ -116,7 +116,7 @@ __device__ __forceinline__ double gather_node(int32_t id, const double* __restri
 template <int DIM, int K>
 __global__ void __launch_bounds__(ActGeo<DIM, K>::BS, ActGeo<DIM, K>::BS <= 512 ? 4 : 1)
 active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restrict__ y,
-                    double* partials, unsigned* counter, double* energy_out) {
+                    double* partials, unsigned* counter, double* energy_out, bool accumulate) {
   using G = ActGeo<DIM, K>;
   constexpr int N1 = G::N1, NC = G::NC;
   __shared__ double X[G::CPB][NC];
@@ -126,11 +126,13 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
   const int cl = threadIdx.x / NC;      // cell within block
   const int n = threadIdx.x % NC;       // node within cell
   const int ix = n % N1, iy = (n / N1) % N1, iz = DIM == 3 ? n / (N1 * N1) : 0;
-  const int64_t nbatch = (a.n_cells + G::CPB - 1) / G::CPB;
+  const int64_t ncell = a.cell_list ? a.n_list : a.n_cells;
+  const int64_t nbatch = (ncell + G::CPB - 1) / G::CPB;
   double e = 0.0;
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const int64_t cell = batch * G::CPB + cl;
-    const bool active = cell < a.n_cells;
+    const int64_t ci = batch * G::CPB + cl;
+    const bool active = ci < ncell;
+    const int64_t cell = active ? (a.cell_list ? (int64_t)a.cell_list[ci] : ci) : 0;
     int32_t id = -1;
     double coef = 0.0;
     int lvl = 0;
@@ -203,19 +205,207 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
   }
   if (energy_out) {
     double s = block_sum<G::BS>(e, red);
-    finish_reduction<G::BS>(s, partials, counter, energy_out);
+    finish_reduction<G::BS>(s, partials, counter, energy_out, accumulate);
+  }
+}
+
+// ----------------------------------------- active operator, leaf sibling groups
+// Q groups of 2^d leaf cells per block; one thread per line of a group's
+// (2K+1)^d node lattice.  With all 2^d cells sharing one coefficient the
+// group operator is the Kronecker sum of (2K+1) x (2K+1) assembled 1-D
+// matrices, so shared nodes between the group's cells are computed once.
+template <int K, bool STIFF>
+__host__ __device__ constexpr double agrp(int a, int b) {
+  double v = 0.0;
+  for (int cell = 0; cell < 2; ++cell) {
+    int lo = K * cell;
+    if (a >= lo && a <= lo + K && b >= lo && b <= lo + K)
+      v += STIFF ? astiff1<K>(a - lo, b - lo) : amass1<K>(a - lo, b - lo);
+  }
+  return v;
+}
+
+template <int DIM, int K>
+struct AGrp {
+  static constexpr int NG = 2 * K + 1;
+  static constexpr int NN = DIM == 3 ? NG * NG * NG : NG * NG;
+  static constexpr int LINES = DIM == 3 ? NG * NG : NG;
+  static constexpr int Q = DIM == 3 ? (K == 2 ? 5 : 7) : (K == 2 ? 6 : 10);  // groups per block
+  static constexpr int BS = (Q * LINES + 31) / 32 * 32;
+  static constexpr int MAX_GRID = 152 * 16;
+};
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(AGrp<DIM, K>::BS)
+active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restrict__ y, double* partials,
+                    unsigned* counter, double* energy_out) {
+  using G = AGrp<DIM, K>;
+  constexpr int NG = G::NG, NN = G::NN, Q = G::Q;
+  __shared__ double X[Q][NN], A[Q][NN], B[Q][NN], C[Q][NN], D[Q][NN];
+  __shared__ double coef[Q], sc[Q][3];
+  __shared__ double red[G::BS / 32];
+  const int tid = threadIdx.x;
+  const int64_t nbatch = (a.n_groups + Q - 1) / Q;
+  double e = 0.0;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    for (int idx = tid; idx < Q * NN; idx += G::BS) {
+      const int q = idx / NN, n = idx % NN;
+      const int64_t grp = batch * Q + q;
+      X[q][n] = grp < a.n_groups ? gather_node<DIM, K>(a.grp_nodes[grp * NN + n], x, a.hang_ptr, a.hang_col, a.hang_w)
+                                 : 0.0;
+    }
+    if (tid < Q) {
+      const int64_t grp = batch * Q + tid;
+      const bool ok = grp < a.n_groups;
+      const int lvl = ok ? a.grp_level[grp] : 0;
+      coef[tid] = ok ? a.grp_coeff[grp] : 0.0;
+      sc[tid][0] = a.scale[lvl][0];
+      sc[tid][1] = a.scale[lvl][1];
+      sc[tid][2] = a.scale[lvl][2];
+    }
+    __syncthreads();
+    const int q = tid / G::LINES, line = tid % G::LINES;
+    const bool act = tid < Q * G::LINES;
+    // x direction: rows are contiguous
+    if (act) {
+      double v[NG];
+      sfor<0, NG>([&](auto c) { v[c] = X[q][c + NG * line]; });
+      sfor<0, NG>([&](auto r) {
+        double am = 0, bk = 0;
+        sfor<0, NG>([&](auto c) {
+          constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+          if constexpr (m != 0.0) am += m * v[c];
+          if constexpr (kk != 0.0) bk += kk * v[c];
+        });
+        A[q][r + NG * line] = am;
+        B[q][r + NG * line] = bk;
+      });
+    }
+    __syncthreads();
+    if constexpr (DIM == 3) {
+      // y direction: line = (ix, iz)
+      if (act) {
+        const int ix = line % NG, iz = line / NG;
+        double va[NG], vb[NG];
+        sfor<0, NG>([&](auto c) {
+          va[c] = A[q][ix + NG * (c + NG * iz)];
+          vb[c] = B[q][ix + NG * (c + NG * iz)];
+        });
+        const double sx = sc[q][0], sy = sc[q][1];
+        sfor<0, NG>([&](auto r) {
+          double cc = 0, t1 = 0, t2 = 0;
+          sfor<0, NG>([&](auto c) {
+            constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+            if constexpr (m != 0.0) {
+              cc += m * va[c];
+              t1 += m * vb[c];
+            }
+            if constexpr (kk != 0.0) t2 += kk * va[c];
+          });
+          C[q][ix + NG * (r + NG * iz)] = cc;
+          D[q][ix + NG * (r + NG * iz)] = sx * t1 + sy * t2;
+        });
+      }
+      __syncthreads();
+      // z direction: line = (ix, iy), then scatter
+      if (act) {
+        const int64_t grp = batch * Q + q;
+        const int ix = line % NG, iy = line / NG;
+        double vc[NG], vd[NG];
+        sfor<0, NG>([&](auto c) {
+          vc[c] = C[q][ix + NG * (iy + NG * c)];
+          vd[c] = D[q][ix + NG * (iy + NG * c)];
+        });
+        const double cf = coef[q], sz = sc[q][2];
+        if (grp < a.n_groups) {
+          sfor<0, NG>([&](auto r) {
+            double t3 = 0, t4 = 0;
+            sfor<0, NG>([&](auto c) {
+              constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+              if constexpr (m != 0.0) t3 += m * vd[c];
+              if constexpr (kk != 0.0) t4 += kk * vc[c];
+            });
+            const double out = cf * (t3 + sz * t4);
+            const int n = ix + NG * (iy + NG * r);
+            e += X[q][n] * out;
+            const int32_t id = a.grp_nodes[grp * NN + n];
+            const bool interior = ix > 0 && ix < NG - 1 && iy > 0 && iy < NG - 1 && r > 0 && r < NG - 1;
+            if (interior && id >= 0) {
+              y[id] = out;  // interior nodes belong to this group's cells only
+            } else if (id >= 0) {
+              atomicAdd(y + id, out);
+            } else if (id <= -2) {
+              const int h = -2 - id;
+              for (int m = a.hang_ptr[h]; m < a.hang_ptr[h + 1]; ++m) atomicAdd(y + a.hang_col[m], a.hang_w[m] * out);
+            }
+          });
+        }
+      }
+    } else {
+      if (act) {
+        const int64_t grp = batch * Q + q;
+        const int ix = line;
+        double va[NG], vb[NG];
+        sfor<0, NG>([&](auto c) {
+          va[c] = A[q][ix + NG * c];
+          vb[c] = B[q][ix + NG * c];
+        });
+        const double cf = coef[q], sx = sc[q][0], sy = sc[q][1];
+        if (grp < a.n_groups) {
+          sfor<0, NG>([&](auto r) {
+            double t1 = 0, t2 = 0;
+            sfor<0, NG>([&](auto c) {
+              constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+              if constexpr (m != 0.0) t1 += m * vb[c];
+              if constexpr (kk != 0.0) t2 += kk * va[c];
+            });
+            const double out = cf * (sx * t1 + sy * t2);
+            const int n = ix + NG * r;
+            e += X[q][n] * out;
+            const int32_t id = a.grp_nodes[grp * NN + n];
+            const bool interior = ix > 0 && ix < NG - 1 && r > 0 && r < NG - 1;
+            if (interior && id >= 0) {
+              y[id] = out;
+            } else if (id >= 0) {
+              atomicAdd(y + id, out);
+            } else if (id <= -2) {
+              const int h = -2 - id;
+              for (int m = a.hang_ptr[h]; m < a.hang_ptr[h + 1]; ++m) atomicAdd(y + a.hang_col[m], a.hang_w[m] * out);
+            }
+          });
+        }
+      }
+    }
+    __syncthreads();  // the next batch overwrites the shared arrays
+  }
+  if (energy_out) {
+    double s = block_sum<G::BS>(e, red);
+    finish_reduction<G::BS>(s, partials, counter, energy_out, false);
   }
 }
 
 template <int DIM, int K>
 static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double* y, double* partials,
                                    unsigned* counter, double* energy, cudaStream_t s) {
-  using G = ActGeo<DIM, K>;
-  if (a.n_cells == 0) return cudaSuccess;
-  int64_t blocks = (a.n_cells + G::CPB - 1) / G::CPB;
-  if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
-  static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
-  active_apply_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
+  bool wrote = false;
+  if (a.n_groups > 0) {
+    using G = AGrp<DIM, K>;
+    int64_t blocks = (a.n_groups + G::Q - 1) / G::Q;
+    if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
+    static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
+    active_group_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
+    wrote = true;
+  }
+  const int64_t ncell = a.cell_list ? a.n_list : a.n_cells;
+  if (ncell > 0) {
+    using G = ActGeo<DIM, K>;
+    int64_t blocks = (ncell + G::CPB - 1) / G::CPB;
+    if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
+    static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
+    active_apply_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy, wrote);
+    wrote = true;
+  }
+  if (!wrote && energy) cudaMemsetAsync(energy, 0, sizeof(double), s);
   return cudaGetLastError();
 }
 
