@@ -166,6 +166,7 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.lcoef32 = L.lcoef32;
   a.parent = L.parent;
   a.list_uniform = L.list_uniform;
+  a.pmask = L.pmask;
   a.list_jump = L.list_jump;
   a.n_uniform = L.n_uniform;
   a.n_jump = L.n_jump;
@@ -231,6 +232,7 @@ void device_free(Hier& h) {
     cudaFree(L.lcoef32);
     cudaFree(L.coeff32);
     cudaFree(L.list_uniform);
+    cudaFree(L.pmask);
     cudaFree(L.list_jump);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
@@ -350,6 +352,7 @@ gmg_status device_setup(Hier& h) {
     GMG_TRY(upload(d, &D.lcoef32, std::vector<float>(H.lcoef.begin(), H.lcoef.end())));
     GMG_TRY(upload(d, &D.coeff32, std::vector<float>(H.coeff.begin(), H.coeff.end())));
     GMG_TRY(upload(d, &D.list_uniform, H.list_uniform));
+    GMG_TRY(upload(d, &D.pmask, H.pmask));
     GMG_TRY(upload(d, &D.list_jump, H.list_jump));
     D.n_uniform = (int64_t)H.list_uniform.size();
     D.n_jump = (int64_t)H.list_jump.size();

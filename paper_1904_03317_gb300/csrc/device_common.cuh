@@ -35,6 +35,7 @@ struct LevelDev {
   float* coeff32 = nullptr;     // n_groups
   int32_t* list_uniform = nullptr;
   int32_t* list_jump = nullptr;
+  uint64_t* pmask = nullptr;    // n_groups x 4
   int64_t n_uniform = 0, n_jump = 0;
   double scale[3] = {0, 0, 0};  // K-term factor per direction: prod_{j!=i} h_j / h_i
   // Chebyshev parameters (host)
@@ -56,6 +57,7 @@ struct LevelArgs {
   const int32_t* parent;
   const int32_t* list_uniform;
   const int32_t* list_jump;
+  const uint64_t* pmask;
   int64_t n_uniform, n_jump;
   const int32_t* nbr_coarse;  // level l-1 neighbour table (l >= 2)
   int64_t coarse_lat[3];      // coarse lattice extents (l == 1)

@@ -133,6 +133,9 @@ struct LevelHost {
   // groups whose refined lower neighbours all share the group's coefficient
   // (one merged tensor product suffices), and the rest
   std::vector<int32_t> list_uniform, list_jump;
+  // prolongation write masks over the group's (2k+1)^d nodes (2 x 64 bits):
+  // add = stored S nodes (u += P uc), set = I nodes this group writes
+  std::vector<uint64_t> pmask;      // n_groups x 4: add[0], add[1], set[0], set[1]
   std::vector<int32_t> parent;      // n_groups: parent's group at l-1 (or coarse cell at l=1)
   std::vector<int64_t> block_pos;   // (n_groups + n_ghosts) x 3: parent-lattice position
   std::vector<int8_t> slot_class;   // 0 unused, 1 S, 2 I, 3 D

@@ -421,6 +421,29 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     }
     }
     if (bad) throw std::runtime_error("inconsistent node classes between sibling groups");
+    // prolongation masks: each stored S node is updated by its own group; an I
+    // node is written by its own group, or -- when its block is a ghost -- by
+    // every group that touches it (the same value)
+    lv.pmask.assign((size_t)lv.n_groups * 4, 0);
+    for (int64_t g = 0; g < lv.n_groups; ++g) {
+      for (int n = 0; n < NGRP; ++n) {
+        int loc[3] = {n % NG, dim > 1 ? (n / NG) % NG : 0, dim > 2 ? n / (NG * NG) : 0};
+        int own[3] = {0, 0, 0}, ol[3] = {0, 0, 0};
+        bool in_own = true;
+        for (int d = 0; d < dim; ++d) {
+          own[d] = loc[d] == 2 * k ? 1 : 0;
+          ol[d] = loc[d] == 2 * k ? 0 : loc[d];
+          if (own[d]) in_own = false;
+        }
+        int nbo = (own[0] + 1) + 3 * (own[1] + 1) + (dim > 2 ? 9 * (own[2] + 1) : 0);
+        int32_t blk = lv.nbr[(size_t)g * NNB + nbo];
+        if (blk < 0) continue;
+        int8_t cls = lv.slot_class[(int64_t)blk * NOWN + ol[0] + NO * (ol[1] + NO * ol[2])];
+        uint64_t bit = 1ull << (n & 63);
+        if (cls == 1 && in_own) lv.pmask[(size_t)g * 4 + (n >> 6)] |= bit;
+        if (cls == 2 && (in_own || blk >= lv.n_groups)) lv.pmask[(size_t)g * 4 + 2 + (n >> 6)] |= bit;
+      }
+    }
     // per-group S mask of the stored nodes and coefficients of the lower neighbours
     lv.smask.assign(lv.n_groups, 0);
     lv.lcoef.assign((size_t)lv.n_groups << dim, 0.0);

@@ -603,443 +603,353 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   }
 }
 
-// ------------------------------------------------- residual + restriction
-template <typename T, int DIM, int K>
-struct ResSmem {
-  using G = Geo<DIM, K>;
-  static constexpr int N = G::NGRP;
-  static constexpr int PER_GROUP = 9 * N;  // U, G/t, T1M, T1K, T2MM, T2MK, T2KM, Y, R
-  static constexpr size_t HEADER = ((size_t)G::GPB * 4 * G::NNB + 15) / 16 * 16;
-  static constexpr size_t bytes() { return HEADER + (size_t)G::GPB * PER_GROUP * sizeof(T); }
-};
-
-// group-local operator on NG^DIM nodes: Y = sum_i s_i (Kx M M ...) U
-template <typename T, int DIM, int K>
-__device__ __forceinline__ void grp_operator(const T* U, T* T1M, T* T1K, T* T2MM, T* T2MK, T* T2KM,
-                                             T* Y, int lane, int nthreads, const double* scale) {
-  using G = Geo<DIM, K>;
-  constexpr int NG = G::NG;
-  const T sx = (T)scale[0], sy = (T)scale[1], sz = (T)scale[2];
-  if constexpr (DIM == 3) {
-    for (int line = lane; line < NG * NG; line += nthreads) {
-      T v[NG];
-      static_for<0, NG>([&](auto c) { v[c] = U[line * NG + c]; });
-      static_for<0, NG>([&](auto e) {
-        T m = 0, kk = 0;
-        static_for<0, NG>([&](auto c) {
-          constexpr double bm = bgrp<K, false>(e, c);
-          constexpr double bk = bgrp<K, true>(e, c);
-          if constexpr (bm != 0.0) m += (T)bm * v[c];
-          if constexpr (bk != 0.0) kk += (T)bk * v[c];
-        });
-        T1M[line * NG + e] = m;
-        T1K[line * NG + e] = kk;
-      });
-    }
-    __syncthreads();
-    for (int line = lane; line < NG * NG; line += nthreads) {
-      int z = line / NG, ex = line % NG;
-      T vm[NG], vk[NG];
-      static_for<0, NG>([&](auto y) {
-        vm[y] = T1M[(z * NG + y) * NG + ex];
-        vk[y] = T1K[(z * NG + y) * NG + ex];
-      });
-      static_for<0, NG>([&](auto e) {
-        T mm = 0, mk = 0, km = 0;
-        static_for<0, NG>([&](auto c) {
-          constexpr double bm = bgrp<K, false>(e, c);
-          constexpr double bk = bgrp<K, true>(e, c);
-          if constexpr (bm != 0.0) {
-            mm += (T)bm * vm[c];
-            km += (T)bm * vk[c];
-          }
-          if constexpr (bk != 0.0) mk += (T)bk * vm[c];
-        });
-        int o = (z * NG + e) * NG + ex;
-        T2MM[o] = mm;
-        T2MK[o] = mk;
-        T2KM[o] = km;
-      });
-    }
-    __syncthreads();
-    for (int line = lane; line < NG * NG; line += nthreads) {
-      T p[NG], q[NG];
-      static_for<0, NG>([&](auto z) {
-        p[z] = T2MM[z * NG * NG + line];
-        q[z] = sy * T2MK[z * NG * NG + line] + sx * T2KM[z * NG * NG + line];
-      });
-      static_for<0, NG>([&](auto e) {
-        T acc = 0;
-        static_for<0, NG>([&](auto c) {
-          constexpr double bm = bgrp<K, false>(e, c);
-          constexpr double bk = bgrp<K, true>(e, c);
-          if constexpr (bk != 0.0) acc += (T)bk * sz * p[c];
-          if constexpr (bm != 0.0) acc += (T)bm * q[c];
-        });
-        Y[e * NG * NG + line] = acc;
-      });
-    }
-    __syncthreads();
-  } else {
-    for (int line = lane; line < NG; line += nthreads) {
-      T v[NG];
-      static_for<0, NG>([&](auto c) { v[c] = U[line * NG + c]; });
-      static_for<0, NG>([&](auto e) {
-        T m = 0, kk = 0;
-        static_for<0, NG>([&](auto c) {
-          constexpr double bm = bgrp<K, false>(e, c);
-          constexpr double bk = bgrp<K, true>(e, c);
-          if constexpr (bm != 0.0) m += (T)bm * v[c];
-          if constexpr (bk != 0.0) kk += (T)bk * v[c];
-        });
-        T1M[line * NG + e] = m;
-        T1K[line * NG + e] = kk;
-      });
-    }
-    __syncthreads();
-    for (int line = lane; line < NG; line += nthreads) {
-      T vm[NG], vk[NG];
-      static_for<0, NG>([&](auto y) {
-        vm[y] = T1M[y * NG + line];
-        vk[y] = T1K[y * NG + line];
-      });
-      static_for<0, NG>([&](auto e) {
-        T acc = 0;
-        static_for<0, NG>([&](auto c) {
-          constexpr double bm = bgrp<K, false>(e, c);
-          constexpr double bk = bgrp<K, true>(e, c);
-          if constexpr (bk != 0.0) acc += (T)bk * sy * vm[c];
-          if constexpr (bm != 0.0) acc += (T)bm * sx * vk[c];
-        });
-        Y[e * NG + line] = acc;
-      });
-    }
-    __syncthreads();
-  }
-}
-
-// per-dimension touching offsets and storing block of group node local index a
-template <int K>
-__device__ __forceinline__ void node_ranges(int a, int& lo_o, int& hi_o, int& own, int& loc) {
-  lo_o = a == 0 ? -1 : 0;
-  hi_o = a == 2 * K ? 1 : 0;
-  own = a == 2 * K ? 1 : 0;
-  loc = a == 2 * K ? 0 : a;
-}
-
-// block index and local index of the parent cell's node j (per-direction jd) at level l-1
+// Slot (in the level l-1 vector) of node jd of the parent cell of group g
+// at level l: level 1 parents are coarse cells on the (K n0 + 1)^d lattice;
+// otherwise the parent is child cb of its own group, whose node block and
+// +1 neighbours hold the parent's nodes at local index cb*K + jd.
 template <int DIM, int K>
 __device__ __forceinline__ int64_t parent_node_slot(const LevelArgs& a, int64_t parent, uint64_t st,
                                                     const int* jd) {
   using G = Geo<DIM, K>;
   if (a.level == 1) {
-    // parent is coarse cell `parent` of the n0 brick; coarse lattice (K n0 + 1)^d
-    int64_t n0x = (a.coarse_lat[0] - 1) / K, n0y = (a.coarse_lat[1] - 1) / K;
-    int64_t c[3] = {parent % n0x, DIM > 1 ? (parent / n0x) % n0y : 0, DIM > 2 ? parent / (n0x * n0y) : 0};
+    const int64_t n0x = (a.coarse_lat[0] - 1) / K, n0y = (a.coarse_lat[1] - 1) / K;
+    const int64_t c[3] = {parent % n0x, DIM > 1 ? (parent / n0x) % n0y : 0, DIM > 2 ? parent / (n0x * n0y) : 0};
     int64_t q[3];
     for (int d = 0; d < 3; ++d) q[d] = d < DIM ? K * c[d] + jd[d] : 0;
     return q[0] + a.coarse_lat[0] * (q[1] + a.coarse_lat[1] * q[2]);
   }
-  int cb[3] = {(int)((st >> 60) & 1), (int)((st >> 61) & 1), (int)((st >> 62) & 1)};
+  const int cb[3] = {(int)((st >> 60) & 1), (int)((st >> 61) & 1), (int)((st >> 62) & 1)};
   int ni = 0, loc = 0, mul3 = 1, mulo = 1;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    int pl = cb[d] * K + jd[d];
-    int o = pl == 2 * K ? 1 : 0;
+    const int pl = cb[d] * K + jd[d];
+    const int o = pl == 2 * K ? 1 : 0;
     ni += (o + 1) * mul3;
     loc += (pl - 2 * K * o) * mulo;
     mul3 *= 3;
     mulo *= G::NO;
   }
-  int32_t blk = a.nbr_coarse[parent * G::NNB + ni];
+  const int32_t blk = a.nbr_coarse[parent * G::NNB + ni];
   if (blk < 0) return -1;
   return (int64_t)blk * G::NOWN + loc;
 }
 
+// ------------------------------------------------- residual + restriction
+// Per group: g_{l-1} += R (w g) - a R A_G u on the parent cell's (K+1)^d nodes.
+// R A_G is again a Kronecker sum, of the (K+1) x (2K+1) products E^T K and
+// E^T M, so the restricted residual is one sum factorisation of u (and of
+// w g with E^T).  w = 1 / (number of groups sharing the node) is only needed
+// where g can be nonzero -- on S nodes, which every touching group refines --
+// so it is 2^-(number of directions in which the node is on the group's
+// boundary), a separable factor of E^T.  Dirichlet fine nodes interpolate
+// from Dirichlet coarse nodes only, so their garbage lands on coarse slots
+// that are never read.  u^I = 0 and g^I = 0 here (down-sweep).
+template <int K, int WHICH>  // WHICH: 0 = E^T M, 1 = E^T K, 2 = E^T diag(w)
+__host__ __device__ constexpr double rmat(int j, int a) {
+  if (WHICH == 2) return embed1<K>(a, j) * ((a == 0 || a == 2 * K) ? 0.5 : 1.0);
+  double v = 0.0;
+  for (int r = 0; r <= 2 * K; ++r) v += embed1<K>(r, j) * bgrp<K, WHICH == 1>(r, a);
+  return v;
+}
+
 template <typename T, int DIM, int K>
-__global__ void __launch_bounds__(Geo<DIM, K>::GPB * Geo<DIM, K>::TEAM)
+struct RestrictSmem {
+  using F = Fast<DIM, K>;
+  static constexpr int NG = 2 * K + 1, N1 = K + 1;
+  static constexpr int LX = DIM == 3 ? NG * NG : NG;      // stage-x lines
+  static constexpr int SX = LX * N1;                       // per array
+  static constexpr int SY = DIM == 3 ? NG * N1 * N1 : 0;   // per array
+  static constexpr int PER = 3 * SX + 4 * SY;
+  static constexpr size_t HEADER = ((size_t)F::TPB * (8 + sizeof(T) + 4 * F::NNB) + 15) / 16 * 16;
+  static constexpr size_t bytes() { return HEADER + (size_t)F::TPB * PER * sizeof(T); }
+};
+
+template <typename T, int DIM, int K>
+__global__ void __launch_bounds__(256)
 level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __restrict__ gvec,
                                T* __restrict__ gc) {
-  using G = Geo<DIM, K>;
-  using S = ResSmem<T, DIM, K>;
-  constexpr int NG = G::NG, N1 = G::N1, N = G::NGRP;
+  using F = Fast<DIM, K>;
+  using S = RestrictSmem<T, DIM, K>;
+  constexpr int NG = S::NG, N1 = S::N1, NO = F::NO, TW = F::TW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int team = threadIdx.x / G::TEAM;
-  const int lane = threadIdx.x % G::TEAM;
-  const int64_t g = (int64_t)blockIdx.x * G::GPB + team;
-  int32_t* nbs = reinterpret_cast<int32_t*>(smem_raw) + team * G::NNB;
-  T* base = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER_GROUP;
-  T* U = base;
-  T* Tt = U + N;
-  T* T1M = Tt + N;
-  T* T1K = T1M + N;
-  T* T2MM = T1K + N;
-  T* T2MK = T2MM + N;
-  T* T2KM = T2MK + N;
-  T* Y = T2KM + N;
-  T* R = Y + N;
+  const int team = threadIdx.x / TW;
+  const int lane = threadIdx.x % TW;
+  const int64_t g = (int64_t)blockIdx.x * F::TPB + team;
   const bool active = g < a.n_groups;
-  uint64_t st = active ? a.state[g] : 0;
+  uint64_t* states = reinterpret_cast<uint64_t*>(smem_raw);
+  T* coefs = reinterpret_cast<T*>(states + F::TPB);
+  int32_t* nb = reinterpret_cast<int32_t*>(coefs + F::TPB) + team * F::NNB;
+  T* XM = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
+  T* XK = XM + S::SX;
+  T* XG = XK + S::SX;
+  T* YMM = XG + S::SX;
+  T* YMK = YMM + S::SY;
+  T* YKM = YMK + S::SY;
+  T* YG = YKM + S::SY;
   if (active) {
-    for (int i = lane; i < G::NNB; i += G::TEAM) nbs[i] = a.nbr[g * G::NNB + i];
-  }
-  __syncthreads();
-  if (active) {
-    for (int n = lane; n < N; n += G::TEAM) {
-      int ad[3] = {n % NG, DIM > 1 ? (n / NG) % NG : 0, DIM > 2 ? n / (NG * NG) : 0};
-      int ni = 0, loc = 0, mul3 = 1, mulo = 1;
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        int lo_o, hi_o, own, l;
-        node_ranges<K>(ad[d], lo_o, hi_o, own, l);
-        ni += (own + 1) * mul3;
-        loc += l * mulo;
-        mul3 *= 3;
-        mulo *= G::NO;
-      }
-      int32_t blk = nbs[ni];
-      T uv = 0, gv = 0;
-      if (blk >= 0) {
-        int64_t s = (int64_t)blk * G::NOWN + loc;
-        uv = u[s];
-        gv = gvec[s];
-      }
-      U[n] = uv;
-      Tt[n] = gv;
+    for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
+    if (lane == 0) {
+      states[team] = a.state[g];
+      coefs[team] = group_coef<T>(a, g);
     }
   }
-  __syncthreads();
-  grp_operator<T, DIM, K>(U, T1M, T1K, T2MM, T2MK, T2KM, Y, active ? lane : G::TEAM, G::TEAM, a.scale);
-  const T coef = active ? (T)a.coeff[g] : T(0);
+  __syncwarp();
+  // stage x: rows (y, z) of the group's node lattice; u and g from the own
+  // block (2K values) and the +x neighbour (1 value)
   if (active) {
-    for (int n = lane; n < N; n += G::TEAM) {
-      int ad[3] = {n % NG, DIM > 1 ? (n / NG) % NG : 0, DIM > 2 ? n / (NG * NG) : 0};
-      int lo_o[3] = {0, 0, 0}, hi_o[3] = {0, 0, 0};
-      for (int d = 0; d < DIM; ++d) {
-        int own, l;
-        node_ranges<K>(ad[d], lo_o[d], hi_o[d], own, l);
+    for (int line = lane; line < S::LX; line += TW) {
+      const int y = DIM > 1 ? line % NG : 0, z = DIM > 2 ? line / NG : 0;
+      const int oy = y == 2 * K ? 1 : 0, oz = z == 2 * K ? 1 : 0;
+      const int row = NO * ((oy ? 0 : y) + NO * (oz ? 0 : z));
+      T uv[NG], gv[NG];
+      const int32_t b1 = nb[nbi<DIM>(0, oy, oz)], b2 = nb[nbi<DIM>(1, oy, oz)];
+      if (b1 >= 0) {
+        load_run<T, 2 * K>(u + (int64_t)b1 * F::NOWN + row, uv);
+        load_run<T, 2 * K>(gvec + (int64_t)b1 * F::NOWN + row, gv);
+      } else {
+        for (int i = 0; i < 2 * K; ++i) uv[i] = gv[i] = T(0);
       }
-      // class and number of refined groups sharing the node
-      bool outside = false, ghost = false;
-      int mult = 0;
-      for (int oz = lo_o[2]; oz <= hi_o[2]; ++oz)
-        for (int oy = lo_o[1]; oy <= hi_o[1]; ++oy)
-          for (int ox = lo_o[0]; ox <= hi_o[0]; ++ox) {
-            int s = state_of(st, nbi<DIM>(ox, oy, oz));
-            outside |= s == kStateOutside;
-            ghost |= s == kStateGhost;
-            mult += s == kStateRefined;
-          }
-      (void)ghost;
-      T t = outside ? T(0) : Tt[n] / (T)mult - coef * Y[n];
-      Tt[n] = t;
+      uv[2 * K] = b2 >= 0 ? u[(int64_t)b2 * F::NOWN + row] : T(0);
+      gv[2 * K] = b2 >= 0 ? gvec[(int64_t)b2 * F::NOWN + row] : T(0);
+      static_for<0, N1>([&](auto j) {
+        T m = 0, kk = 0, w = 0;
+        static_for<0, NG>([&](auto c) {
+          constexpr double em = rmat<K, 0>(j, c), ek = rmat<K, 1>(j, c), ew = rmat<K, 2>(j, c);
+          if constexpr (em != 0.0) m += (T)em * uv[c];
+          if constexpr (ek != 0.0) kk += (T)ek * uv[c];
+          if constexpr (ew != 0.0) w += (T)ew * gv[c];
+        });
+        XM[line * N1 + j] = m;
+        XK[line * N1 + j] = kk;
+        XG[line * N1 + j] = w;
+      });
     }
   }
-  __syncthreads();
-  // restriction R = P^T: contract each direction with E^T (NG -> N1)
+  __syncwarp();
+  const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
+  const T coef = coefs[team];
+  const uint64_t st = states[team];
+  const int64_t parent = active ? a.parent[g] : 0;
   if constexpr (DIM == 3) {
-    // stage x: [z][y][a] -> T1M as [z][y][j]
-    for (int line = lane; active && line < NG * NG; line += G::TEAM) {
-      T v[NG];
-      static_for<0, NG>([&](auto c) { v[c] = Tt[line * NG + c]; });
-      static_for<0, N1>([&](auto j) {
-        T acc = 0;
-        static_for<0, NG>([&](auto r) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[r];
+    // stage y: lines (z, jx); X layout [z][y][jx] -> Y layout [z][jy][jx]
+    if (active) {
+      for (int line = lane; line < NG * N1; line += TW) {
+        const int z = line / N1, jx = line % N1;
+        T vm[NG], vk[NG], vg[NG];
+        static_for<0, NG>([&](auto y) {
+          vm[y] = XM[(z * NG + y) * N1 + jx];
+          vk[y] = XK[(z * NG + y) * N1 + jx];
+          vg[y] = XG[(z * NG + y) * N1 + jx];
         });
-        T1M[line * N1 + j] = acc;
-      });
-    }
-    __syncthreads();
-    // stage y: [z][y][jx] -> T1K as [z][jy][jx]
-    for (int line = lane; active && line < NG * N1; line += G::TEAM) {
-      int z = line / N1, jx = line % N1;
-      T v[NG];
-      static_for<0, NG>([&](auto y) { v[y] = T1M[(z * NG + y) * N1 + jx]; });
-      static_for<0, N1>([&](auto j) {
-        T acc = 0;
-        static_for<0, NG>([&](auto r) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[r];
+        static_for<0, N1>([&](auto j) {
+          T mm = 0, mk = 0, km = 0, gg = 0;
+          static_for<0, NG>([&](auto c) {
+            constexpr double em = rmat<K, 0>(j, c), ek = rmat<K, 1>(j, c), ew = rmat<K, 2>(j, c);
+            if constexpr (em != 0.0) {
+              mm += (T)em * vm[c];
+              km += (T)em * vk[c];
+            }
+            if constexpr (ek != 0.0) mk += (T)ek * vm[c];
+            if constexpr (ew != 0.0) gg += (T)ew * vg[c];
+          });
+          const int o = (z * N1 + j) * N1 + jx;
+          YMM[o] = mm;
+          YMK[o] = mk;
+          YKM[o] = km;
+          YG[o] = gg;
         });
-        T1K[(z * N1 + j) * N1 + jx] = acc;
-      });
+      }
     }
-    __syncthreads();
-    // stage z: [z][jy][jx] -> R as [jz][jy][jx]
-    for (int line = lane; active && line < N1 * N1; line += G::TEAM) {
-      T v[NG];
-      static_for<0, NG>([&](auto z) { v[z] = T1K[z * N1 * N1 + line]; });
-      static_for<0, N1>([&](auto j) {
-        T acc = 0;
-        static_for<0, NG>([&](auto r) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[r];
+    __syncwarp();
+    // stage z: lines (jy, jx), scatter into the parent's nodes
+    if (active) {
+      for (int line = lane; line < N1 * N1; line += TW) {
+        T pm[NG], pq[NG], pg[NG];
+        static_for<0, NG>([&](auto z) {
+          pm[z] = sz * YMM[z * N1 * N1 + line];
+          pq[z] = sy * YMK[z * N1 * N1 + line] + sx * YKM[z * N1 * N1 + line];
+          pg[z] = YG[z * N1 * N1 + line];
         });
-        R[j * N1 * N1 + line] = acc;
-      });
+        static_for<0, N1>([&](auto j) {
+          T op = 0, rg = 0;
+          static_for<0, NG>([&](auto c) {
+            constexpr double em = rmat<K, 0>(j, c), ek = rmat<K, 1>(j, c), ew = rmat<K, 2>(j, c);
+            if constexpr (ek != 0.0) op += (T)ek * pm[c];
+            if constexpr (em != 0.0) op += (T)em * pq[c];
+            if constexpr (ew != 0.0) rg += (T)ew * pg[c];
+          });
+          const int jd[3] = {line % N1, line / N1, j};
+          const int64_t slot = parent_node_slot<DIM, K>(a, parent, st, jd);
+          if (slot >= 0) atomicAdd(gc + slot, rg - coef * op);
+        });
+      }
     }
-    __syncthreads();
   } else {
-    for (int line = lane; active && line < NG; line += G::TEAM) {
-      T v[NG];
-      static_for<0, NG>([&](auto c) { v[c] = Tt[line * NG + c]; });
-      static_for<0, N1>([&](auto j) {
-        T acc = 0;
-        static_for<0, NG>([&](auto r) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[r];
+    if (active) {
+      for (int jx = lane; jx < N1; jx += TW) {
+        T vm[NG], vk[NG], vg[NG];
+        static_for<0, NG>([&](auto y) {
+          vm[y] = sy * XM[y * N1 + jx];
+          vk[y] = sx * XK[y * N1 + jx];
+          vg[y] = XG[y * N1 + jx];
         });
-        T1M[line * N1 + j] = acc;
-      });
-    }
-    __syncthreads();
-    for (int line = lane; active && line < N1; line += G::TEAM) {
-      T v[NG];
-      static_for<0, NG>([&](auto y) { v[y] = T1M[y * N1 + line]; });
-      static_for<0, N1>([&](auto j) {
-        T acc = 0;
-        static_for<0, NG>([&](auto r) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[r];
+        static_for<0, N1>([&](auto j) {
+          T op = 0, rg = 0;
+          static_for<0, NG>([&](auto c) {
+            constexpr double em = rmat<K, 0>(j, c), ek = rmat<K, 1>(j, c), ew = rmat<K, 2>(j, c);
+            if constexpr (ek != 0.0) op += (T)ek * vm[c];
+            if constexpr (em != 0.0) op += (T)em * vk[c];
+            if constexpr (ew != 0.0) rg += (T)ew * vg[c];
+          });
+          const int jd[3] = {jx, j, 0};
+          const int64_t slot = parent_node_slot<DIM, K>(a, parent, st, jd);
+          if (slot >= 0) atomicAdd(gc + slot, rg - coef * op);
         });
-        R[j * N1 + line] = acc;
-      });
+      }
     }
-    __syncthreads();
-  }
-  if (!active) return;
-  const int64_t parent = a.parent[g];
-  for (int n = lane; n < G::NCELL; n += G::TEAM) {
-    int jd[3] = {n % N1, DIM > 1 ? (n / N1) % N1 : 0, DIM > 2 ? n / (N1 * N1) : 0};
-    int64_t s = parent_node_slot<DIM, K>(a, parent, st, jd);
-    if (s >= 0) atomicAdd(gc + s, R[n]);
   }
 }
 
 // ------------------------------------------------------------ prolongation
+// Per group: the parent's (K+1)^d values interpolated to the group's
+// (2K+1)^d nodes with E in each direction; stored S nodes get u += P uc, I
+// nodes u = u2 = P uc (masks prepared on the host).
 template <typename T, int DIM, int K>
-__global__ void __launch_bounds__(Geo<DIM, K>::GPB * Geo<DIM, K>::TEAM)
+struct ProlongSmem {
+  using F = Fast<DIM, K>;
+  static constexpr int NG = 2 * K + 1, N1 = K + 1;
+  static constexpr int NC = ipow_c(N1, DIM);
+  static constexpr int PX = (DIM == 3 ? N1 * N1 : N1) * NG;
+  static constexpr int PY = DIM == 3 ? N1 * NG * NG : 0;
+  static constexpr int PER = NC + PX + PY;
+  static constexpr size_t HEADER = ((size_t)F::TPB * (8 * 5 + 4 * F::NNB) + 15) / 16 * 16;
+  static constexpr size_t bytes() { return HEADER + (size_t)F::TPB * PER * sizeof(T); }
+};
+
+template <typename T, int DIM, int K>
+__global__ void __launch_bounds__(256)
 level_prolongate_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u, T* __restrict__ u2) {
-  using G = Geo<DIM, K>;
-  constexpr int NG = G::NG, N1 = G::N1, N = G::NGRP;
+  using F = Fast<DIM, K>;
+  using S = ProlongSmem<T, DIM, K>;
+  constexpr int NG = S::NG, N1 = S::N1, NO = F::NO, TW = F::TW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int team = threadIdx.x / G::TEAM;
-  const int lane = threadIdx.x % G::TEAM;
-  const int64_t g = (int64_t)blockIdx.x * G::GPB + team;
-  constexpr int PER = G::NCELL + 2 * N;
-  T* C = reinterpret_cast<T*>(smem_raw) + (size_t)team * PER;
-  T* W1 = C + G::NCELL;
-  T* W2 = W1 + N;
+  const int team = threadIdx.x / TW;
+  const int lane = threadIdx.x % TW;
+  const int64_t g = (int64_t)blockIdx.x * F::TPB + team;
   const bool active = g < a.n_groups;
-  uint64_t st = active ? a.state[g] : 0;
+  uint64_t* hdr = reinterpret_cast<uint64_t*>(smem_raw) + team * 5;  // state, add[2], set[2]
+  int32_t* nb = reinterpret_cast<int32_t*>(reinterpret_cast<uint64_t*>(smem_raw) + F::TPB * 5) + team * F::NNB;
+  T* C = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
+  T* PXa = C + S::NC;
+  T* PYa = PXa + S::PX;
+  if (active) {
+    for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
+    if (lane == 0) hdr[0] = a.state[g];
+    if (lane < 4) hdr[1 + lane] = a.pmask[g * 4 + lane];
+  }
+  __syncwarp();
   if (active) {
     const int64_t parent = a.parent[g];
-    for (int n = lane; n < G::NCELL; n += G::TEAM) {
-      int jd[3] = {n % N1, DIM > 1 ? (n / N1) % N1 : 0, DIM > 2 ? n / (N1 * N1) : 0};
-      int64_t s = parent_node_slot<DIM, K>(a, parent, st, jd);
+    const uint64_t st = hdr[0];
+    for (int n = lane; n < S::NC; n += TW) {
+      const int jd[3] = {n % N1, DIM > 1 ? (n / N1) % N1 : 0, DIM > 2 ? n / (N1 * N1) : 0};
+      const int64_t s = parent_node_slot<DIM, K>(a, parent, st, jd);
       C[n] = s >= 0 ? uc[s] : T(0);
     }
   }
-  __syncthreads();
-  // interpolate: C [jz][jy][jx] -> W [z][y][x] with E in each direction
-  if constexpr (DIM == 3) {
-    for (int line = lane; active && line < N1 * N1; line += G::TEAM) {  // x: [jz][jy][jx]->[jz][jy][x]
-      T v[N1];
-      static_for<0, N1>([&](auto j) { v[j] = C[line * N1 + j]; });
-      static_for<0, NG>([&](auto r) {
-        T acc = 0;
-        static_for<0, N1>([&](auto j) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[j];
-        });
-        W1[line * NG + r] = acc;
-      });
-    }
-    __syncthreads();
-    for (int line = lane; active && line < N1 * NG; line += G::TEAM) {  // y: -> [jz][y][x]
-      int jz = line / NG, x = line % NG;
-      T v[N1];
-      static_for<0, N1>([&](auto j) { v[j] = W1[(jz * N1 + j) * NG + x]; });
-      static_for<0, NG>([&](auto r) {
-        T acc = 0;
-        static_for<0, N1>([&](auto j) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[j];
-        });
-        W2[(jz * NG + r) * NG + x] = acc;
-      });
-    }
-    __syncthreads();
-    for (int line = lane; active && line < NG * NG; line += G::TEAM) {  // z: -> [z][y][x]
-      T v[N1];
-      static_for<0, N1>([&](auto j) { v[j] = W2[j * NG * NG + line]; });
-      static_for<0, NG>([&](auto r) {
-        T acc = 0;
-        static_for<0, N1>([&](auto j) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[j];
-        });
-        W1[r * NG * NG + line] = acc;
-      });
-    }
-    __syncthreads();
-  } else {
-    for (int line = lane; active && line < N1; line += G::TEAM) {
-      T v[N1];
-      static_for<0, N1>([&](auto j) { v[j] = C[line * N1 + j]; });
-      static_for<0, NG>([&](auto r) {
-        T acc = 0;
-        static_for<0, N1>([&](auto j) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[j];
-        });
-        W2[line * NG + r] = acc;
-      });
-    }
-    __syncthreads();
-    for (int line = lane; active && line < NG; line += G::TEAM) {
-      T v[N1];
-      static_for<0, N1>([&](auto j) { v[j] = W2[j * NG + line]; });
-      static_for<0, NG>([&](auto r) {
-        T acc = 0;
-        static_for<0, N1>([&](auto j) {
-          constexpr double e = embed1<K>(r, j);
-          if constexpr (e != 0.0) acc += (T)e * v[j];
-        });
-        W1[r * NG + line] = acc;
-      });
-    }
-    __syncthreads();
-  }
-  if (!active) return;
-  const int32_t* nb = a.nbr + g * G::NNB;
-  for (int n = lane; n < N; n += G::TEAM) {
-    int ad[3] = {n % NG, DIM > 1 ? (n / NG) % NG : 0, DIM > 2 ? n / (NG * NG) : 0};
-    int lo_o[3] = {0, 0, 0}, hi_o[3] = {0, 0, 0}, own[3] = {0, 0, 0}, loc[3] = {0, 0, 0};
-    for (int d = 0; d < DIM; ++d) node_ranges<K>(ad[d], lo_o[d], hi_o[d], own[d], loc[d]);
-    bool outside = false, ghost = false, owner = true;
-    for (int oz = lo_o[2]; oz <= hi_o[2]; ++oz)
-      for (int oy = lo_o[1]; oy <= hi_o[1]; ++oy)
-        for (int ox = lo_o[0]; ox <= hi_o[0]; ++ox) {
-          int s = state_of(st, nbi<DIM>(ox, oy, oz));
-          outside |= s == kStateOutside;
-          ghost |= s == kStateGhost;
-          // a refined group at a lexicographically smaller offset owns the write
-          bool neg = oz < 0 || (oz == 0 && (oy < 0 || (oy == 0 && ox < 0)));
-          if (s == kStateRefined && neg) owner = false;
-        }
-    if (outside || !owner) continue;
-    int32_t blk = nb[nbi<DIM>(own[0], own[1], own[2])];
-    if (blk < 0) continue;
-    int64_t s = (int64_t)blk * G::NOWN + loc[0] + G::NO * (loc[1] + G::NO * loc[2]);
-    T v = W1[n];
-    if (ghost) {
+  __syncwarp();
+  auto write = [&](int n, T v) {
+    const uint64_t add = hdr[1 + (n >> 6)], set = hdr[3 + (n >> 6)];
+    const uint64_t bit = 1ull << (n & 63);
+    const int x = n % NG, y = DIM > 1 ? (n / NG) % NG : 0, z = DIM > 2 ? n / (NG * NG) : 0;
+    if (add & bit) {
+      u[g * F::NOWN + x + NO * (y + NO * z)] += v;
+    } else if (set & bit) {
+      const int ox = x == 2 * K, oy = y == 2 * K, oz = z == 2 * K;
+      const int32_t blk = nb[nbi<DIM>(ox, oy, oz)];
+      const int64_t s = (int64_t)blk * F::NOWN + (ox ? 0 : x) + NO * ((oy ? 0 : y) + NO * (oz ? 0 : z));
       u[s] = v;
       u2[s] = v;
-    } else {
-      u[s] += v;
+    }
+  };
+  if constexpr (DIM == 3) {
+    // x: lines (jy, jz)
+    if (active) {
+      for (int line = lane; line < N1 * N1; line += TW) {
+        T c[N1];
+        static_for<0, N1>([&](auto j) { c[j] = C[line * N1 + j]; });
+        static_for<0, NG>([&](auto r) {
+          T v = 0;
+          static_for<0, N1>([&](auto j) {
+            constexpr double e = embed1<K>(r, j);
+            if constexpr (e != 0.0) v += (T)e * c[j];
+          });
+          PXa[line * NG + r] = v;
+        });
+      }
+    }
+    __syncwarp();
+    // y: lines (jz, x); PX layout [jz][jy][x] -> PY layout [jz][y][x]
+    if (active) {
+      for (int line = lane; line < N1 * NG; line += TW) {
+        const int jz = line / NG, x = line % NG;
+        T c[N1];
+        static_for<0, N1>([&](auto j) { c[j] = PXa[(jz * N1 + j) * NG + x]; });
+        static_for<0, NG>([&](auto r) {
+          T v = 0;
+          static_for<0, N1>([&](auto j) {
+            constexpr double e = embed1<K>(r, j);
+            if constexpr (e != 0.0) v += (T)e * c[j];
+          });
+          PYa[(jz * NG + r) * NG + x] = v;
+        });
+      }
+    }
+    __syncwarp();
+    // z: lines (y, x), write
+    if (active) {
+      for (int line = lane; line < NG * NG; line += TW) {
+        T c[N1];
+        static_for<0, N1>([&](auto j) { c[j] = PYa[j * NG * NG + line]; });
+        static_for<0, NG>([&](auto r) {
+          T v = 0;
+          static_for<0, N1>([&](auto j) {
+            constexpr double e = embed1<K>(r, j);
+            if constexpr (e != 0.0) v += (T)e * c[j];
+          });
+          write(line + NG * NG * r, v);
+        });
+      }
+    }
+  } else {
+    if (active) {
+      for (int line = lane; line < N1; line += TW) {
+        T c[N1];
+        static_for<0, N1>([&](auto j) { c[j] = C[line * N1 + j]; });
+        static_for<0, NG>([&](auto r) {
+          T v = 0;
+          static_for<0, N1>([&](auto j) {
+            constexpr double e = embed1<K>(r, j);
+            if constexpr (e != 0.0) v += (T)e * c[j];
+          });
+          PXa[line * NG + r] = v;
+        });
+      }
+    }
+    __syncwarp();
+    if (active) {
+      for (int x = lane; x < NG; x += TW) {
+        T c[N1];
+        static_for<0, N1>([&](auto j) { c[j] = PXa[j * NG + x]; });
+        static_for<0, NG>([&](auto r) {
+          T v = 0;
+          static_for<0, N1>([&](auto j) {
+            constexpr double e = embed1<K>(r, j);
+            if constexpr (e != 0.0) v += (T)e * c[j];
+          });
+          write(x + NG * r, v);
+        });
+      }
     }
   }
 }
@@ -1137,16 +1047,16 @@ cudaError_t launch_level_cheb(int dim, int k, const LevelArgs& a, const T* x, co
 
 template <typename T, int DIM, int K>
 static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* gc, cudaStream_t s) {
-  using G = Geo<DIM, K>;
+  using F = Fast<DIM, K>;
   if (a.n_groups == 0) return cudaSuccess;
-  size_t sm = ResSmem<T, DIM, K>::bytes() + 16;
+  const size_t sm = RestrictSmem<T, DIM, K>::bytes();
   static bool init = false;
   if (!init) {
     cudaFuncSetAttribute(level_residual_restrict_kernel<T, DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     init = true;
   }
-  dim3 grid((unsigned)((a.n_groups + G::GPB - 1) / G::GPB));
-  level_residual_restrict_kernel<T, DIM, K><<<grid, G::GPB * G::TEAM, sm, s>>>(a, u, g, gc);
+  dim3 grid((unsigned)((a.n_groups + F::TPB - 1) / F::TPB));
+  level_residual_restrict_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, u, g, gc);
   return cudaGetLastError();
 }
 
@@ -1162,11 +1072,16 @@ cudaError_t launch_level_residual_restrict(int dim, int k, const LevelArgs& a, c
 
 template <typename T, int DIM, int K>
 static cudaError_t pro_dispatch(const LevelArgs& a, const T* uc, T* u, T* u2, cudaStream_t s) {
-  using G = Geo<DIM, K>;
+  using F = Fast<DIM, K>;
   if (a.n_groups == 0) return cudaSuccess;
-  size_t sm = (size_t)G::GPB * (G::NCELL + 2 * G::NGRP) * sizeof(T) + 16;
-  dim3 grid((unsigned)((a.n_groups + G::GPB - 1) / G::GPB));
-  level_prolongate_kernel<T, DIM, K><<<grid, G::GPB * G::TEAM, sm, s>>>(a, uc, u, u2);
+  const size_t sm = ProlongSmem<T, DIM, K>::bytes();
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(level_prolongate_kernel<T, DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    init = true;
+  }
+  dim3 grid((unsigned)((a.n_groups + F::TPB - 1) / F::TPB));
+  level_prolongate_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, uc, u, u2);
   return cudaGetLastError();
 }
 
