@@ -236,6 +236,22 @@ gmg_status gmg_level_prolongate(gmg_hier* h, int level, const void* d_uc, void* 
  * The result ends in d_u. */
 gmg_status gmg_level_smooth(gmg_hier* h, int level, const void* d_g, void* d_u, void* d_tmp,
                             int from_zero);
+/* Same smoothing as gmg_level_smooth, but the recurrence's second level
+ * vector is kept in a static device array inside the library, so this call
+ * allocates no memory and needs no d_tmp.  For callers that cannot call
+ * cudaMalloc while they run: processes whose device memory belongs to another
+ * allocator (a framework's caching allocator or a fixed memory budget), and
+ * latency-critical loops that cannot pay the device-wide synchronisation of
+ * cudaMalloc/cudaFree.  The paper has no counterpart to this entry point.
+ * Limit: the level vector (its slot count times 4 bytes for an FP32 V-cycle,
+ * 8 for FP64) must fit in the 8 MiB array, else GMG_EINVAL.  The array is
+ * held by every GPU that loads the library until the process exits, and is
+ * shared by all calls: calls whose work overlaps on the GPU (other streams,
+ * other hierarchies on the same device) race on it.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  The contents of d_u are as
+ * after gmg_level_smooth; the array's contents afterwards are unspecified. */
+gmg_status gmg_level_smooth_noalloc(gmg_hier* h, int level, const void* d_g, void* d_u, int from_zero);
 /* Inverse diagonal of A_l^S on S slots, 0 elsewhere (level >= 1). */
 gmg_status gmg_level_inv_diag(gmg_hier* h, int level, void* d_out);
 /* u_0 = A_0^{-1} g_0 on the coarse lattice (interior slots; boundary slots 0). */

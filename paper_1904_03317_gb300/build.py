@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgmg.so")
 
-SOURCES = ["kernels_level.cu", "kernels_active.cu", "device.cu", "hierarchy.cpp", "mesh.cpp", "api.cpp"]
+SOURCES = ["kernels_level.cu", "kernels_active.cu", "device.cu", "hierarchy.cpp", "mesh.cpp", "api.cpp",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-DGMG_BUILT_FOR_SM103A",
           "-Xcompiler", "-fPIC,-fopenmp,-O3", "-I" + os.path.join(ROOT, "include")]

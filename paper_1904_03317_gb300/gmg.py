@@ -37,6 +37,7 @@ EXPORTED = [
     "gmg_assemble_rhs", "gmg_apply", "gmg_vcycle", "gmg_solve",
     "gmg_level_apply", "gmg_level_residual_restrict", "gmg_level_prolongate", "gmg_level_smooth",
     "gmg_level_inv_diag", "gmg_coarse_solve", "gmg_profile_reset", "gmg_profile_read",
+    "gmg_level_smooth_noalloc",
 ]
 
 KERNEL_KINDS = ["cheb", "smooth_first", "residual_restrict", "prolongate", "coarse", "copy_to_mg",
@@ -118,6 +119,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "gmg_level_residual_restrict": [vp, i32, vp, vp, vp],
         "gmg_level_prolongate": [vp, i32, vp, vp, vp],
         "gmg_level_smooth": [vp, i32, vp, vp, vp, i32],
+        "gmg_level_smooth_noalloc": [vp, i32, vp, vp, i32],
         "gmg_level_inv_diag": [vp, i32, vp],
         "gmg_coarse_solve": [vp, vp, vp],
         "gmg_profile_reset": [vp, i32],
@@ -306,6 +308,11 @@ class Hierarchy:
     def level_smooth(self, level, g, u, tmp, from_zero: bool):
         _check(load_library().gmg_level_smooth(self.handle, level, _ptr(g), _ptr(u), _ptr(tmp), int(from_zero)),
                "gmg_level_smooth")
+
+    def level_smooth_noalloc(self, level, g, u, from_zero: bool):
+        """gmg_level_smooth with the library's static scratch instead of a caller buffer."""
+        _check(load_library().gmg_level_smooth_noalloc(self.handle, level, _ptr(g), _ptr(u), int(from_zero)),
+               "gmg_level_smooth_noalloc")
 
     def level_inv_diag(self, level, out):
         _check(load_library().gmg_level_inv_diag(self.handle, level, _ptr(out)), "gmg_level_inv_diag")
