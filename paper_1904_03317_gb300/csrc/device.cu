@@ -167,6 +167,8 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.parent = L.parent;
   a.list_uniform = L.list_uniform;
   a.pmask = L.pmask;
+  a.bricks = L.bricks;
+  a.n_bricks = L.n_bricks;
   a.list_jump = L.list_jump;
   a.n_uniform = L.n_uniform;
   a.n_jump = L.n_jump;
@@ -233,6 +235,7 @@ void device_free(Hier& h) {
     cudaFree(L.coeff32);
     cudaFree(L.list_uniform);
     cudaFree(L.pmask);
+    cudaFree(L.bricks);
     cudaFree(L.list_jump);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
@@ -340,6 +343,7 @@ gmg_status device_setup(Hier& h) {
     level_scales(h, l, D.scale, hh);
     D.n_S = (double)H.n_S;
     D.n_I = (double)H.n_I;
+    D.n_S_jump = (double)H.n_S_jump;
     if (l == 0) continue;
     D.cheb_flops = (double)H.n_groups * cheb_group_flops(dim, k);
     D.n_groups = H.n_groups;
@@ -353,6 +357,8 @@ gmg_status device_setup(Hier& h) {
     GMG_TRY(upload(d, &D.coeff32, std::vector<float>(H.coeff.begin(), H.coeff.end())));
     GMG_TRY(upload(d, &D.list_uniform, H.list_uniform));
     GMG_TRY(upload(d, &D.pmask, H.pmask));
+    GMG_TRY(upload(d, &D.bricks, H.bricks));
+    D.n_bricks = (int64_t)H.bricks.size() / 64;
     GMG_TRY(upload(d, &D.list_jump, H.list_jump));
     D.n_uniform = (int64_t)H.list_uniform.size();
     D.n_jump = (int64_t)H.list_jump.size();
@@ -488,7 +494,9 @@ static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cu
   const int m = h.params.cheb_degree;
   double rho = 1.0 / D.sigma;
   cudaError_t e;
-  const double cheb_bytes = sizeof(T) * (5.0 * D.n_S + D.n_I);
+  // x (S and I), x_prev, g and the new x on S nodes; D^-1 is read only by
+  // groups at coefficient jumps (the others recompute it)
+  const double cheb_bytes = sizeof(T) * (4.0 * D.n_S + D.n_S_jump + D.n_I);
   if (from_zero) {
     Track t(h.dev, GMG_K_SMOOTH_FIRST, 3.0 * sizeof(T) * D.n_slots, 2.0 * D.n_slots);
     e = launch_scale_vec<T>(D.n_slots, dinv, g, (T)(1.0 / D.theta), cur, s);

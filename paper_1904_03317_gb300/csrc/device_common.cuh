@@ -36,12 +36,14 @@ struct LevelDev {
   int32_t* list_uniform = nullptr;
   int32_t* list_jump = nullptr;
   uint64_t* pmask = nullptr;    // n_groups x 4
+  int32_t* bricks = nullptr;    // n_bricks x 64
+  int64_t n_bricks = 0;
   int64_t n_uniform = 0, n_jump = 0;
   double scale[3] = {0, 0, 0};  // K-term factor per direction: prod_{j!=i} h_j / h_i
   // Chebyshev parameters (host)
   double lambda = 0, theta = 0, delta = 0, sigma = 0;
   // accounting: S and I nodes, FP operations of one smoothing launch
-  double n_S = 0, n_I = 0, cheb_flops = 0;
+  double n_S = 0, n_I = 0, n_S_jump = 0, cheb_flops = 0;
 };
 
 // Arguments of the level kernels, passed by value.
@@ -58,6 +60,8 @@ struct LevelArgs {
   const int32_t* list_uniform;
   const int32_t* list_jump;
   const uint64_t* pmask;
+  const int32_t* bricks;
+  int64_t n_bricks;
   int64_t n_uniform, n_jump;
   const int32_t* nbr_coarse;  // level l-1 neighbour table (l >= 2)
   int64_t coarse_lat[3];      // coarse lattice extents (l == 1)

@@ -133,6 +133,10 @@ struct LevelHost {
   // groups whose refined lower neighbours all share the group's coefficient
   // (one merged tensor product suffices), and the rest
   std::vector<int32_t> list_uniform, list_jump;
+  // 2x2x2 bricks of uniform groups sharing one coefficient (3D): per brick the
+  // 4^3 block indices of positions -1..2 around it (own groups at 0..1);
+  // list_uniform then holds only the uniform groups outside bricks
+  std::vector<int32_t> bricks;
   // prolongation write masks over the group's (2k+1)^d nodes (2 x 64 bits):
   // add = stored S nodes (u += P uc), set = I nodes this group writes
   std::vector<uint64_t> pmask;      // n_groups x 4: add[0], add[1], set[0], set[1]
@@ -140,7 +144,7 @@ struct LevelHost {
   std::vector<int64_t> block_pos;   // (n_groups + n_ghosts) x 3: parent-lattice position
   std::vector<int8_t> slot_class;   // 0 unused, 1 S, 2 I, 3 D
   std::vector<int64_t> slot_key;    // node key per slot (-1 unused)
-  uint64_t n_cells = 0, n_leaves = 0, n_S = 0, n_I = 0;
+  uint64_t n_cells = 0, n_leaves = 0, n_S = 0, n_I = 0, n_S_jump = 0;
 };
 
 enum : int { kStateRefined = 0, kStateGhost = 1, kStateOutside = 2 };

@@ -464,6 +464,45 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
         if (c != 0.0 && c != lv.coeff[g]) uniform = false;
       }
       (uniform ? lv.list_uniform : lv.list_jump).push_back((int32_t)g);
+      if (!uniform) lv.n_S_jump += (uint64_t)__builtin_popcountll(m);
+    }
+    // bricks: 8 uniform groups at positions p + {0,1}^3 with p even, one coefficient
+    if (dim == 3) {
+      std::vector<char> is_uniform(lv.n_groups, 0), taken(lv.n_groups, 0);
+      for (int32_t g : lv.list_uniform) is_uniform[g] = 1;
+      auto slot_at = [&](int64_t x, int64_t y, int64_t z) -> int32_t {
+        int64_t q[3] = {x, y, z};
+        if (!f.inside(Lp, q)) return -1;
+        const int32_t* b = bm.find(pack3(x, y, z));
+        return b ? *b : -2;
+      };
+      for (int64_t g = 0; g < lv.n_groups; ++g) {
+        const int64_t* p = gs[g].c;
+        if ((p[0] | p[1] | p[2]) & 1) continue;
+        bool ok = true;
+        int32_t own[8];
+        for (int b = 0; b < 8 && ok; ++b) {
+          int32_t s = slot_at(p[0] + (b & 1), p[1] + ((b >> 1) & 1), p[2] + ((b >> 2) & 1));
+          if (s < 0 || s >= lv.n_groups || !is_uniform[s] || lv.coeff[s] != lv.coeff[g]) ok = false;
+          else own[b] = s;
+        }
+        if (!ok) continue;
+        std::vector<int32_t> tab(64);
+        for (int z = 0; z < 4 && ok; ++z)
+          for (int y = 0; y < 4 && ok; ++y)
+            for (int x = 0; x < 4 && ok; ++x) {
+              int32_t s = slot_at(p[0] + x - 1, p[1] + y - 1, p[2] + z - 1);
+              if (s == -2) ok = false;  // a position without a block cannot occur next to a group
+              tab[x + 4 * (y + 4 * z)] = s;
+            }
+        if (!ok) continue;
+        lv.bricks.insert(lv.bricks.end(), tab.begin(), tab.end());
+        for (int b = 0; b < 8; ++b) taken[own[b]] = 1;
+      }
+      std::vector<int32_t> rest;
+      for (int32_t g : lv.list_uniform)
+        if (!taken[g]) rest.push_back(g);
+      lv.list_uniform.swap(rest);
     }
     for (int64_t s = 0; s < nslots; ++s) {
       if (lv.slot_class[s] == 1) ++lv.n_S;

@@ -454,6 +454,34 @@ __device__ __forceinline__ void halo_seg(int h, int& o, int& l) {
   l = h < K ? h + K : (h < 3 * K ? h - K : 0);
 }
 
+// store N consecutive values to shared memory (vector stores where aligned)
+template <typename T, int N>
+__device__ __forceinline__ void store_run(T* p, const T* v) {
+  if constexpr (N == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (N == 2 && sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (N == 4 && sizeof(T) == 8) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  } else if constexpr (N == 2 && sizeof(T) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = v[i];
+  }
+}
+
+// diagonal entry of the merged 1-D matrix at stored node i
+template <int K, bool STIFF>
+__device__ __forceinline__ double merged_diag(int i) {
+  double v = 0.0;
+  static_for<0, 2 * K>([&](auto r) {
+    if (i == r) v = bmerged<K, STIFF>(r, K + r);
+  });
+  return v;
+}
+
 template <typename T, int DIM, int K, int MODE>
 __global__ void __launch_bounds__(256)
 level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, const T* __restrict__ gvec,
@@ -461,6 +489,10 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   using F = Fast<DIM, K>;
   using S = FastSmem<T, DIM, K>;
   constexpr int NH = F::NH, NO = F::NO, TW = F::TW;
+  // last stage: L3 lines of NO outputs, R threads per line
+  constexpr int L3 = DIM == 3 ? NO * NO : NO;
+  constexpr int R = TW / L3 > 0 ? TW / L3 : 1;
+  constexpr int OPT = (NO + R - 1) / R;  // outputs per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int team = threadIdx.x / TW;
   const int lane = threadIdx.x % TW;
@@ -476,6 +508,24 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   T* T2MK = T2MM + S::T2;
   T* T2KM = T2MK + S::T2;
   T* Xown = T2KM + S::T2;
+  // this thread's output nodes: line `ol`, outputs k = part + R * o
+  const int ol = lane % L3, part = lane / L3;
+  const bool has_out = lane < L3 * R;
+  // prefetch the update's operands; they are used only after the contractions
+  T pre_xp[OPT], pre_g[OPT];
+  if constexpr (MODE == 1) {
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+      const int kk = part + R * o;
+      pre_xp[o] = T(0);
+      pre_g[o] = T(0);
+      if (active && has_out && kk < NO) {
+        const int64_t slot = g * F::NOWN + ol + L3 * kk;
+        pre_g[o] = gvec[slot];
+        if (xprev) pre_xp[o] = xprev[slot];
+      }
+    }
+  }
   if (active) {
     for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
     if (lane == 0) {
@@ -498,37 +548,49 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
       if (b1 >= 0) load_run<T, 2 * K>(x + (int64_t)b1 * F::NOWN + row, v + K);
       else for (int i = 0; i < 2 * K; ++i) v[K + i] = T(0);
       v[3 * K] = b2 >= 0 ? x[(int64_t)b2 * F::NOWN + row] : T(0);
-      if (oy == 0 && oz == 0) {
-#pragma unroll
-        for (int i = 0; i < NO; ++i) Xown[row + i] = v[K + i];
-      }
+      if (oy == 0 && oz == 0) store_run<T, NO>(Xown + row, v + K);
+      T m[NO], k[NO];
       static_for<0, NO>([&](auto r) {
-        T m = 0, k = 0;
+        T sm = 0, sk = 0;
         static_for<0, NH>([&](auto c) {
           constexpr double bm = bmerged<K, false>(r, c);
           constexpr double bk = bmerged<K, true>(r, c);
-          if constexpr (bm != 0.0) m += (T)bm * v[c];
-          if constexpr (bk != 0.0) k += (T)bk * v[c];
+          if constexpr (bm != 0.0) sm += (T)bm * v[c];
+          if constexpr (bk != 0.0) sk += (T)bk * v[c];
         });
-        T1M[line * NO + r] = m;
-        T1K[line * NO + r] = k;
+        m[r] = sm;
+        k[r] = sk;
       });
+      store_run<T, NO>(T1M + line * NO, m);
+      store_run<T, NO>(T1K + line * NO, k);
     }
   }
   __syncwarp();
   const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
   const uint64_t smask = masks[team];
   const T coef = coefs[team];
-  auto update = [&](int node, T y) {
+  // Chebyshev update of stored node `node`; D^{-1} of an S node of a uniform
+  // group is the inverse of coef * sum_d s_d prod_e (diagonal of the merged
+  // 1-D matrices), the same value the setup stores
+  auto update = [&](int node, T y, int o) {
     if (!((smask >> node) & 1ull)) return;
     const int64_t slot = g * F::NOWN + node;
     y *= coef;
     if constexpr (MODE == 0) {
       out[slot] = y;
     } else {
+      const int i0 = node % NO, i1 = DIM > 1 ? (node / NO) % NO : 0, i2 = DIM > 2 ? node / (NO * NO) : 0;
+      const T mx = (T)merged_diag<K, false>(i0), kx = (T)merged_diag<K, true>(i0);
+      const T my = (T)merged_diag<K, false>(i1), ky = (T)merged_diag<K, true>(i1);
+      T diag;
+      if constexpr (DIM == 3) {
+        const T mz = (T)merged_diag<K, false>(i2), kz = (T)merged_diag<K, true>(i2);
+        diag = coef * (sx * kx * my * mz + sy * mx * ky * mz + sz * mx * my * kz);
+      } else {
+        diag = coef * (sx * kx * my + sy * mx * ky);
+      }
       const T xv = Xown[node];
-      const T xp = xprev ? xprev[slot] : T(0);
-      out[slot] = xv + c1 * (xv - xp) + c2 * dinv[slot] * (gvec[slot] - y);
+      out[slot] = xv + c1 * (xv - pre_xp[o]) + c2 * (pre_g[o] - y) / diag;
     }
   };
   if constexpr (DIM == 3) {
@@ -560,45 +622,254 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
       }
     }
     __syncwarp();
-    // stage 3: z direction, then the update of the line's nodes
-    if (active) {
-      for (int line = lane; line < NO * NO; line += TW) {
-        T p[NH], q[NH];
-        static_for<0, NH>([&](auto z) {
-          p[z] = sz * T2MM[z * NO * NO + line];
-          q[z] = sy * T2MK[z * NO * NO + line] + sx * T2KM[z * NO * NO + line];
+    // stage 3: z direction for this thread's outputs, then the update
+    if (active && has_out) {
+      T p[NH], q[NH];
+      static_for<0, NH>([&](auto z) {
+        p[z] = sz * T2MM[z * L3 + ol];
+        q[z] = sy * T2MK[z * L3 + ol] + sx * T2KM[z * L3 + ol];
+      });
+#pragma unroll
+      for (int o = 0; o < OPT; ++o) {
+        const int kk = part + R * o;
+        if (kk >= NO) break;
+        T y = 0;
+        static_for<0, NO>([&](auto r) {
+          if (kk == r) {
+            static_for<0, NH>([&](auto c) {
+              constexpr double bm = bmerged<K, false>(r, c);
+              constexpr double bk = bmerged<K, true>(r, c);
+              if constexpr (bk != 0.0) y += (T)bk * p[c];
+              if constexpr (bm != 0.0) y += (T)bm * q[c];
+            });
+          }
         });
-        static_for<0, NO>([&](auto kk) {
-          T y = 0;
-          static_for<0, NH>([&](auto c) {
-            constexpr double bm = bmerged<K, false>(kk, c);
-            constexpr double bk = bmerged<K, true>(kk, c);
-            if constexpr (bk != 0.0) y += (T)bk * p[c];
-            if constexpr (bm != 0.0) y += (T)bm * q[c];
-          });
-          update(line + NO * NO * kk, y);
-        });
+        update(ol + L3 * kk, y, o);
       }
     }
   } else {
-    if (active) {
-      for (int i = lane; i < NO; i += TW) {
-        T vm[NH], vk[NH];
-        static_for<0, NH>([&](auto y) {
-          vm[y] = sy * T1M[y * NO + i];
-          vk[y] = sx * T1K[y * NO + i];
+    if (active && has_out) {
+      T vm[NH], vk[NH];
+      static_for<0, NH>([&](auto y) {
+        vm[y] = sy * T1M[y * NO + ol];
+        vk[y] = sx * T1K[y * NO + ol];
+      });
+#pragma unroll
+      for (int o = 0; o < OPT; ++o) {
+        const int kk = part + R * o;
+        if (kk >= NO) break;
+        T y = 0;
+        static_for<0, NO>([&](auto r) {
+          if (kk == r) {
+            static_for<0, NH>([&](auto c) {
+              constexpr double bm = bmerged<K, false>(r, c);
+              constexpr double bk = bmerged<K, true>(r, c);
+              if constexpr (bk != 0.0) y += (T)bk * vm[c];
+              if constexpr (bm != 0.0) y += (T)bm * vk[c];
+            });
+          }
         });
-        static_for<0, NO>([&](auto j) {
-          T y = 0;
-          static_for<0, NH>([&](auto c) {
-            constexpr double bm = bmerged<K, false>(j, c);
-            constexpr double bk = bmerged<K, true>(j, c);
-            if constexpr (bk != 0.0) y += (T)bk * vm[c];
-            if constexpr (bm != 0.0) y += (T)bm * vk[c];
-          });
-          update(i + NO * j, y);
+        update(ol + L3 * kk, y, o);
+      }
+    }
+  }
+}
+
+// --------------------------------------------- smoothing kernel, 2x2x2 bricks
+// Eight uniform sibling groups at positions p + {0,1}^3 (one coefficient)
+// form a brick of (4K)^3 stored nodes whose halo is (5K+1)^3: the halo rows
+// per stored node drop by about 2x against single groups.  A 128-thread
+// team handles one brick with the same three contractions; the rows of the
+// 1-D matrices cover the brick's four cells per direction plus the lower
+// neighbour's cell.
+template <int K, bool STIFF>
+__host__ __device__ constexpr double bbrick(int r, int c) {
+  const int p = c - K;
+  double v = 0.0;
+  for (int cell = -1; cell < 4; ++cell) {
+    const int lo = K * cell;
+    if (r >= lo && r <= lo + K && p >= lo && p <= lo + K) v += elem1<K, STIFF>(r - lo, p - lo);
+  }
+  return v;
+}
+
+template <int K>
+struct BrickG {
+  static constexpr int NO = 2 * K, OB = 4 * K, HB = 5 * K + 1;
+  static constexpr int NOWN = NO * NO * NO;
+  static constexpr int TB = K == 2 ? 128 : 64;  // threads per brick (= block)
+  static constexpr int L3 = OB * OB;            // last-stage lines
+  static constexpr int R = TB / L3 > 0 ? TB / L3 : 1;
+  static constexpr int OPT = (OB + R - 1) / R;
+};
+
+template <typename T, int K>
+struct BrickSmem {
+  using B = BrickG<K>;
+  static constexpr int T1 = B::HB * B::HB * B::OB;
+  static constexpr int T2 = B::HB * B::OB * B::OB;
+  static constexpr int XO = B::OB * B::OB * B::OB;
+  static constexpr size_t bytes() { return (size_t)(2 * T1 + 3 * T2 + XO) * sizeof(T) + 64 * 4 + 8 * 8 + 16; }
+};
+
+// halo index h in [0, 5K] -> group index (-1..2) along the direction and stored index
+template <int K>
+__device__ __forceinline__ void brick_seg(int h, int& gidx, int& l) {
+  const int p = h - K;
+  gidx = p < 0 ? -1 : (p < 2 * K ? 0 : (p < 4 * K ? 1 : 2));
+  l = p - 2 * K * gidx;
+}
+
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(BrickG<K>::TB)
+level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, const T* __restrict__ gvec, T* out,
+                        T c1, T c2) {
+  using B = BrickG<K>;
+  using S = BrickSmem<T, K>;
+  constexpr int NO = B::NO, OB = B::OB, HB = B::HB, TB = B::TB, L3 = B::L3, R = B::R, OPT = B::OPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* T1M = reinterpret_cast<T*>(smem_raw);
+  T* T1K = T1M + S::T1;
+  T* T2MM = T1K + S::T1;
+  T* T2MK = T2MM + S::T2;
+  T* T2KM = T2MK + S::T2;
+  T* Xown = T2KM + S::T2;
+  int32_t* tab = reinterpret_cast<int32_t*>(Xown + S::XO);
+  uint64_t* smask = reinterpret_cast<uint64_t*>(tab + 64);
+  const int tid = threadIdx.x;
+  const int64_t br = blockIdx.x;
+  if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
+  __syncthreads();
+  // own groups sit at table positions (1..2)^3
+  auto own_group = [&](int bx, int by, int bz) { return tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))]; };
+  if (tid < 8) smask[tid] = a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)];
+  const T coef = group_coef<T>(a, own_group(0, 0, 0));
+  // this thread's outputs: line ol = (i, j), k = part + R * o
+  const int ol = tid % L3, part = tid / L3;
+  const bool has_out = tid < L3 * R;
+  const int oi = ol % OB, oj = ol / OB;
+  T pre_xp[OPT], pre_g[OPT];
+  int64_t slots[OPT];
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    slots[o] = -1;
+    pre_xp[o] = pre_g[o] = T(0);
+    if (has_out && kk < OB) {
+      const int32_t gid = own_group(oi / NO, oj / NO, kk / NO);
+      slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
+      if constexpr (MODE == 1) {
+        pre_g[o] = gvec[slots[o]];
+        if (xprev) pre_xp[o] = xprev[slots[o]];
+      }
+    }
+  }
+  // stage 1: halo rows along x (four segments: groups -1, 0, 1, 2)
+  for (int line = tid; line < HB * HB; line += TB) {
+    int gy, ly, gz, lz;
+    brick_seg<K>(line % HB, gy, ly);
+    brick_seg<K>(line / HB, gz, lz);
+    const int row = NO * (ly + NO * lz);
+    const int tb = 4 * ((gy + 1) + 4 * (gz + 1));
+    T v[HB];
+    const int32_t b0 = tab[tb + 0], b1 = tab[tb + 1], b2 = tab[tb + 2], b3 = tab[tb + 3];
+    if (b0 >= 0) load_run<T, K>(x + (int64_t)b0 * B::NOWN + row + K, v);
+    else for (int i = 0; i < K; ++i) v[i] = T(0);
+    if (b1 >= 0) load_run<T, 2 * K>(x + (int64_t)b1 * B::NOWN + row, v + K);
+    else for (int i = 0; i < 2 * K; ++i) v[K + i] = T(0);
+    if (b2 >= 0) load_run<T, 2 * K>(x + (int64_t)b2 * B::NOWN + row, v + 3 * K);
+    else for (int i = 0; i < 2 * K; ++i) v[3 * K + i] = T(0);
+    v[5 * K] = b3 >= 0 ? x[(int64_t)b3 * B::NOWN + row] : T(0);
+    if (gy >= 0 && gy <= 1 && gz >= 0 && gz <= 1) {
+      const int by = gy * NO + ly, bz = gz * NO + lz;
+      store_run<T, OB>(Xown + OB * (by + OB * bz), v + K);
+    }
+    T m[OB], k[OB];
+    static_for<0, OB>([&](auto r) {
+      T sm = 0, sk = 0;
+      static_for<0, HB>([&](auto c) {
+        constexpr double bm = bbrick<K, false>(r, c);
+        constexpr double bk = bbrick<K, true>(r, c);
+        if constexpr (bm != 0.0) sm += (T)bm * v[c];
+        if constexpr (bk != 0.0) sk += (T)bk * v[c];
+      });
+      m[r] = sm;
+      k[r] = sk;
+    });
+    store_run<T, 4>(T1M + line * OB, m);
+    store_run<T, 4>(T1K + line * OB, k);
+    if constexpr (OB == 8) {
+      store_run<T, 4>(T1M + line * OB + 4, m + 4);
+      store_run<T, 4>(T1K + line * OB + 4, k + 4);
+    }
+  }
+  __syncthreads();
+  // stage 2: y direction, lines (z, i)
+  for (int line = tid; line < HB * OB; line += TB) {
+    const int z = line / OB, i = line % OB;
+    T vm[HB], vk[HB];
+    static_for<0, HB>([&](auto y) {
+      vm[y] = T1M[(z * HB + y) * OB + i];
+      vk[y] = T1K[(z * HB + y) * OB + i];
+    });
+    static_for<0, OB>([&](auto j) {
+      T mm = 0, mk = 0, km = 0;
+      static_for<0, HB>([&](auto c) {
+        constexpr double bm = bbrick<K, false>(j, c);
+        constexpr double bk = bbrick<K, true>(j, c);
+        if constexpr (bm != 0.0) {
+          mm += (T)bm * vm[c];
+          km += (T)bm * vk[c];
+        }
+        if constexpr (bk != 0.0) mk += (T)bk * vm[c];
+      });
+      const int o = (z * OB + j) * OB + i;
+      T2MM[o] = mm;
+      T2MK[o] = mk;
+      T2KM[o] = km;
+    });
+  }
+  __syncthreads();
+  // stage 3: z direction and the update
+  if (!has_out) return;
+  const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
+  T p[HB], q[HB];
+  static_for<0, HB>([&](auto z) {
+    p[z] = sz * T2MM[z * L3 + ol];
+    q[z] = sy * T2MK[z * L3 + ol] + sx * T2KM[z * L3 + ol];
+  });
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    if (kk >= OB) break;
+    T y = 0;
+    static_for<0, OB>([&](auto r) {
+      if (kk == r) {
+        static_for<0, HB>([&](auto c) {
+          constexpr double bm = bbrick<K, false>(r, c);
+          constexpr double bk = bbrick<K, true>(r, c);
+          if constexpr (bk != 0.0) y += (T)bk * p[c];
+          if constexpr (bm != 0.0) y += (T)bm * q[c];
         });
       }
+    });
+    const int gsel = (oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO));
+    const int node = (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
+    if (!((smask[gsel] >> node) & 1ull)) continue;
+    y *= coef;
+    if constexpr (MODE == 0) {
+      out[slots[o]] = y;
+    } else {
+      T mdx = 0, kdx = 0, mdy = 0, kdy = 0, mdz = 0, kdz = 0;
+      static_for<0, OB>([&](auto r) {
+        constexpr T md = (T)bbrick<K, false>(r, K + r), kd = (T)bbrick<K, true>(r, K + r);
+        if (oi == r) { mdx = md; kdx = kd; }
+        if (oj == r) { mdy = md; kdy = kd; }
+        if (kk == r) { mdz = md; kdz = kd; }
+      });
+      const T diag = coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz);
+      const T xv = Xown[oi + OB * (oj + OB * kk)];
+      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2 * (pre_g[o] - y) / diag;
     }
   }
 }
@@ -1000,6 +1271,17 @@ __global__ void __launch_bounds__(256) level_diag_kernel(LevelArgs a, double* __
 template <typename T, int DIM, int K, int MODE>
 static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, const T* g, const T* dinv,
                                T* out, T c1, T c2, cudaStream_t s) {
+  if constexpr (DIM == 3) {
+    if (a.n_bricks > 0) {
+      const size_t sm = BrickSmem<T, K>::bytes();
+      static bool init = false;
+      if (!init) {
+        cudaFuncSetAttribute(level_cheb_brick_kernel<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        init = true;
+      }
+      level_cheb_brick_kernel<T, K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1, c2);
+    }
+  }
   if (a.n_uniform > 0) {
     using F = Fast<DIM, K>;
     const size_t sm = FastSmem<T, DIM, K>::bytes();
