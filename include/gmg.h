@@ -98,6 +98,8 @@ typedef struct gmg_info {
   uint64_t n_S[GMG_MAX_LEVELS];         /* S nodes of each level (Sec. 2.3) */
   uint64_t n_I[GMG_MAX_LEVELS];         /* I (refinement-edge) nodes of each level */
   uint64_t n_home[GMG_MAX_LEVELS];      /* unknowns whose home level is l */
+  uint64_t bricks[GMG_MAX_LEVELS];      /* 2x2x2 bricks of uniform groups (3D smoother tiles) */
+  uint64_t groups_jump[GMG_MAX_LEVELS]; /* groups next to a coefficient jump (general kernel) */
   double lambda_max[GMG_MAX_LEVELS];    /* estimated (or fixed) lambda_max of D^-1 A_l^S */
   uint64_t device_bytes;                /* device memory held by the hierarchy */
   double setup_host_s, setup_device_s;  /* wall time of the two setup phases */

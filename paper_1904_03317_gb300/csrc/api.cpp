@@ -276,6 +276,8 @@ gmg_status gmg_hier_info(const gmg_hier* hh, gmg_info* info) {
     info->slots[l] = h.level_offset[l + 1] - h.level_offset[l];
     info->n_S[l] = L.n_S;
     info->n_I[l] = L.n_I;
+    info->bricks[l] = L.bricks.size() / 64;
+    info->groups_jump[l] = L.list_jump.size();
     info->lambda_max[l] = l < (int)h.lambda.size() ? h.lambda[l] : 0.0;
   }
   for (int32_t lv : h.active.home_level) info->n_home[lv]++;

@@ -68,6 +68,7 @@ class InfoC(C.Structure):
                 ("groups", C.c_uint64 * MAX_LEVELS), ("ghosts", C.c_uint64 * MAX_LEVELS),
                 ("slots", C.c_uint64 * MAX_LEVELS), ("n_S", C.c_uint64 * MAX_LEVELS),
                 ("n_I", C.c_uint64 * MAX_LEVELS), ("n_home", C.c_uint64 * MAX_LEVELS),
+                ("bricks", C.c_uint64 * MAX_LEVELS), ("groups_jump", C.c_uint64 * MAX_LEVELS),
                 ("lambda_max", C.c_double * MAX_LEVELS), ("device_bytes", C.c_uint64),
                 ("setup_host_s", C.c_double), ("setup_device_s", C.c_double)]
 
