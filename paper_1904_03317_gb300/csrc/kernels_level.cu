@@ -569,9 +569,28 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
   const uint64_t smask = masks[team];
   const T coef = coefs[team];
-  // Chebyshev update of stored node `node`; D^{-1} of an S node of a uniform
+  // Chebyshev update of stored node `node`.  D^{-1} of an S node of a uniform
   // group is the inverse of coef * sum_d s_d prod_e (diagonal of the merged
-  // 1-D matrices), the same value the setup stores
+  // 1-D matrices); that diagonal depends on an index only through its parity,
+  // and all outputs of this thread share one parity pattern (R is even or the
+  // thread has one output), so one reciprocal serves them.
+  T c2d = T(0);
+  if constexpr (MODE == 1) {
+    const T md0 = (T)bmerged<K, false>(0, K), kd0 = (T)bmerged<K, true>(0, K);
+    const T md1 = (T)bmerged<K, false>(1, K + 1), kd1 = (T)bmerged<K, true>(1, K + 1);
+    const int p0 = (DIM == 3 ? ol % NO : ol) & 1, p1 = (DIM == 3 ? ol / NO : part) & 1, p2 = part & 1;
+    const T mdx = p0 ? md1 : md0, kdx = p0 ? kd1 : kd0;
+    const T mdy = p1 ? md1 : md0, kdy = p1 ? kd1 : kd0;
+    T diag;
+    if constexpr (DIM == 3) {
+      const T mdz = p2 ? md1 : md0, kdz = p2 ? kd1 : kd0;
+      diag = coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz);
+    } else {
+      diag = coef * (sx * kdx * mdy + sy * mdx * kdy);
+    }
+    c2d = c2 / diag;
+  }
+  static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share one parity pattern");
   auto update = [&](int node, T y, int o) {
     if (!((smask >> node) & 1ull)) return;
     const int64_t slot = g * F::NOWN + node;
@@ -579,18 +598,8 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
     if constexpr (MODE == 0) {
       out[slot] = y;
     } else {
-      const int i0 = node % NO, i1 = DIM > 1 ? (node / NO) % NO : 0, i2 = DIM > 2 ? node / (NO * NO) : 0;
-      const T mx = (T)merged_diag<K, false>(i0), kx = (T)merged_diag<K, true>(i0);
-      const T my = (T)merged_diag<K, false>(i1), ky = (T)merged_diag<K, true>(i1);
-      T diag;
-      if constexpr (DIM == 3) {
-        const T mz = (T)merged_diag<K, false>(i2), kz = (T)merged_diag<K, true>(i2);
-        diag = coef * (sx * kx * my * mz + sy * mx * ky * mz + sz * mx * my * kz);
-      } else {
-        diag = coef * (sx * kx * my + sy * mx * ky);
-      }
       const T xv = Xown[node];
-      out[slot] = xv + c1 * (xv - pre_xp[o]) + c2 * (pre_g[o] - y) / diag;
+      out[slot] = xv + c1 * (xv - pre_xp[o]) + c2d * (pre_g[o] - y);
     }
   };
   if constexpr (DIM == 3) {
@@ -707,7 +716,8 @@ template <typename T, int K>
 struct BrickSmem {
   using B = BrickG<K>;
   static constexpr int T1 = B::HB * B::HB * B::OB;
-  static constexpr int T2 = B::HB * B::OB * B::OB;
+  static constexpr int ZS = B::OB * B::OB + (B::OB == 8 ? 8 : 4);  // padded z stride of the stage-2 arrays
+  static constexpr int T2 = B::HB * ZS;
   static constexpr int XO = B::OB * B::OB * B::OB;
   static constexpr size_t bytes() { return (size_t)(2 * T1 + 3 * T2 + XO) * sizeof(T) + 64 * 4 + 8 * 8 + 16; }
 };
@@ -823,7 +833,7 @@ level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, co
         }
         if constexpr (bk != 0.0) mk += (T)bk * vm[c];
       });
-      const int o = (z * OB + j) * OB + i;
+      const int o = z * S::ZS + j * OB + i;
       T2MM[o] = mm;
       T2MK[o] = mk;
       T2KM[o] = km;
@@ -835,9 +845,22 @@ level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, co
   const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
   T p[HB], q[HB];
   static_for<0, HB>([&](auto z) {
-    p[z] = sz * T2MM[z * L3 + ol];
-    q[z] = sy * T2MK[z * L3 + ol] + sx * T2KM[z * L3 + ol];
+    p[z] = sz * T2MM[z * S::ZS + ol];
+    q[z] = sy * T2MK[z * S::ZS + ol] + sx * T2KM[z * S::ZS + ol];
   });
+  // The diagonal of the merged brick matrices depends on the index only
+  // through its parity (vertex or interior node of a cell), and all outputs
+  // of this thread share one parity pattern, so one reciprocal serves them.
+  T c2d = T(0);
+  if constexpr (MODE == 1) {
+    const T md0 = (T)bbrick<K, false>(0, K), kd0 = (T)bbrick<K, true>(0, K);
+    const T md1 = (T)bbrick<K, false>(1, K + 1), kd1 = (T)bbrick<K, true>(1, K + 1);
+    const T mdx = (oi & 1) ? md1 : md0, kdx = (oi & 1) ? kd1 : kd0;
+    const T mdy = (oj & 1) ? md1 : md0, kdy = (oj & 1) ? kd1 : kd0;
+    const T mdz = (part & 1) ? md1 : md0, kdz = (part & 1) ? kd1 : kd0;
+    c2d = c2 / (coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz));
+  }
+  static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share the parity of k");
 #pragma unroll
   for (int o = 0; o < OPT; ++o) {
     const int kk = part + R * o;
@@ -860,16 +883,8 @@ level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, co
     if constexpr (MODE == 0) {
       out[slots[o]] = y;
     } else {
-      T mdx = 0, kdx = 0, mdy = 0, kdy = 0, mdz = 0, kdz = 0;
-      static_for<0, OB>([&](auto r) {
-        constexpr T md = (T)bbrick<K, false>(r, K + r), kd = (T)bbrick<K, true>(r, K + r);
-        if (oi == r) { mdx = md; kdx = kd; }
-        if (oj == r) { mdy = md; kdy = kd; }
-        if (kk == r) { mdz = md; kdz = kd; }
-      });
-      const T diag = coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz);
       const T xv = Xown[oi + OB * (oj + OB * kk)];
-      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2 * (pre_g[o] - y) / diag;
+      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2d * (pre_g[o] - y);
     }
   }
 }
