@@ -79,6 +79,14 @@ typedef struct gmg_params {
   const double* fixed_lambda; /* optional host array, one value per level (index 0
                                  unused): use these lambda_max instead of estimating.
                                  NULL = estimate. Copied during gmg_hier_build. */
+  int solve_graph;            /* 1 (default): gmg_solve runs the whole CG loop as one CUDA
+                                 graph whose loop is controlled on the device (a conditional
+                                 WHILE node): one launch and one synchronisation per solve.
+                                 The graph is captured by the first such solve, which also
+                                 allocates its iterate (n_unknowns doubles).  0, or profile
+                                 timing on (gmg_profile_reset): one stream launch per kernel
+                                 and one host check per iteration.  Both modes perform the
+                                 same operations in the same order (identical results). */
 } gmg_params;
 
 #define GMG_MAX_LEVELS 24
@@ -205,8 +213,12 @@ gmg_status gmg_vcycle(gmg_hier* h, const double* d_r, double* d_z);
 
 /* Preconditioned CG from x = 0 (Sec. 4.1): stop when ||r||_2 <= tol ||b||_2
  * or after max_iter updates; if fixed_iterations > 0, run exactly that many
- * updates and ignore tol.  d_b, d_x: device FP64 active vectors.  Reads one
- * residual norm per iteration back to the host (synchronises the stream).
+ * updates and ignore tol.  d_b, d_x: device FP64 active vectors.  The
+ * stopping test runs on the device in graph mode (gmg_params.solve_graph) and
+ * on the host in stream mode; either way the call returns after the stream
+ * has been synchronised.  The first graph-mode solve captures the graph on a
+ * private stream: it must not itself be called while a stream capture of
+ * the calling thread is in progress.
  * Returns GMG_ENOTCONV when max_iter is hit without convergence (x holds the
  * last iterate), GMG_EBREAKDOWN / GMG_ENAN on a bad CG scalar. */
 gmg_status gmg_solve(gmg_hier* h, const double* d_b, double* d_x, double tol, int max_iter,

@@ -172,6 +172,7 @@ void gmg_params_default(gmg_params* p) {
   p->eig_iters = 10;
   p->vcycle_prec = GMG_PREC_FP32;
   p->fixed_lambda = nullptr;
+  p->solve_graph = 1;
 }
 
 gmg_status gmg_hier_build(gmg_ctx* ctx, const gmg_mesh* mesh, int degree, const double* coarse_coeff,

@@ -79,6 +79,12 @@ struct Track {
   int kind;
   cudaEvent_t a = nullptr;
   Track(DeviceState* dd, int k, double bytes, double flops) : d(dd), kind(k) {
+    if (d->cap) {  // captured into a graph: counted per execution of the graph
+      d->cap->launches[k] += 1;
+      d->cap->bytes[k] += bytes;
+      d->cap->flops[k] += flops;
+      return;
+    }
     Profile& p = d->prof;
     p.launches[k] += 1;
     p.bytes[k] += bytes;
@@ -243,6 +249,12 @@ void device_free(Hier& h) {
                   d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level};
   for (void* p : ptrs) cudaFree(p);
   if (d->scal_host) cudaFreeHost(d->scal_host);
+  if (d->cg_exec) cudaGraphExecDestroy(d->cg_exec);
+  if (d->cg_graph) cudaGraphDestroy(d->cg_graph);
+  cudaFree(d->x_iter);
+  cudaFree(d->ctl);
+  if (d->ctl_host) cudaFreeHost(d->ctl_host);
+  if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
   for (auto& q : d->prof.pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -406,9 +418,13 @@ gmg_status device_setup(Hier& h) {
     const double nnz1 = n1 * n1;                       // dense (K+1)^2 element rows
     const double nnzg = 2.0 * n1 * n1 - 1.0;           // assembled two-cell rows
     double cell_flops, grp_flops;
+    double s0[3], h0[3];
+    level_scales(h, 0, s0, h0);
+    const bool iso = s0[0] == s0[1] && (dim == 2 || s0[1] == s0[2]);
     if (dim == 3) {
       cell_flops = nc * (2.0 * (2 * n1 + 3 * n1 + 1 + 2 * n1 + 1 + 1) + 2.0);
-      grp_flops = lines * 2.0 * (2 * nnzg + 3 * nnzg + 2 * nnzg) + ngn * (2.0 * 3 + 2.0);
+      // isotropic group kernel: no per-direction scaling (one multiply per node)
+      grp_flops = lines * 2.0 * (2 * nnzg + 3 * nnzg + 2 * nnzg) + ngn * (iso ? 2.0 + 1.0 : 2.0 * 3 + 2.0);
     } else {
       cell_flops = nc * (2.0 * (2 * n1 + 2 * n1 + 1 + 1) + 2.0);
       grp_flops = lines * 2.0 * (2 * nnzg + 2 * nnzg) + ngn * (2.0 * 2 + 2.0);
@@ -605,10 +621,12 @@ gmg_status device_rhs(Hier& h, int kind, double* b) {
   return GMG_OK;
 }
 
-// Preconditioned CG (x0 = 0).  Scalars live on the device: slot 0 = b.b,
-// slots 1+3i .. 3+3i = (r_i.z_i, p_i.A p_i, r_{i+1}.r_{i+1}) of iteration i.
-gmg_status device_solve(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
-                        gmg_stats* st) {
+// Preconditioned CG (x0 = 0), stream mode: the host reads the scalars of
+// every iteration and decides whether to go on.  Scalars live on the device:
+// slot 0 = b.b, slots 1+3i .. 3+3i = (r_i.z_i, p_i.A p_i, r_{i+1}.r_{i+1}) of
+// iteration i.
+static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
+                               gmg_stats* st) {
   DeviceState* d = h.dev;
   cudaStream_t s = d->stream;
   const int64_t n = d->n_unknowns;
@@ -687,6 +705,214 @@ gmg_status device_solve(Hier& h, const double* b, double* x, double tol, int max
   if (result == GMG_ENOTCONV) set_error("CG did not converge within max_iter");
   if (st) *st = stats;
   return result;
+}
+
+// ------------------------------------------------------ graph-mode CG
+// The same iteration as solve_stream, reordered so that the loop body starts
+// with the preconditioner: with p_{-1} = 0 and r_{-1}.z_{-1} = 1, pass i is
+//   z = B r, rz = r.z, p = z + (rz / rz_old) p, Ap = A p, pAp = p.Ap,
+//   x += (rz/pAp) p, r -= (rz/pAp) Ap, rr = r.r, check,
+// which performs exactly the stream-mode operations.  The loop is a
+// conditional WHILE node whose condition the check kernel sets, so a solve is
+// one graph launch and one host synchronisation.
+
+// Ends a capture that failed and passes its status on.
+static gmg_status abandon_capture(cudaStream_t s, gmg_status st) {
+  cudaGraph_t g = nullptr;
+  cudaStreamEndCapture(s, &g);
+  cudaGetLastError();
+  return st;
+}
+
+static gmg_status capture_prelude(Hier& h, cudaGraph_t g, cudaGraphConditionalHandle* loop, cudaGraph_t* body) {
+  DeviceState* d = h.dev;
+  cudaStream_t s = d->stream;
+  const int64_t n = d->n_unknowns;
+  GMG_CUDA_TRY(cudaMemsetAsync(d->x_iter, 0, sizeof(double) * n, s));
+  GMG_CUDA_TRY(cudaMemsetAsync(d->p, 0, sizeof(double) * n, s));
+  {
+    Track t(d, GMG_K_OTHER, 8.0 * n, 2.0 * n);
+    GMG_CUDA_TRY(launch_dot(n, d->r, d->r, d->partials, d->counter, &d->ctl->bb, s));
+  }
+  GMG_CUDA_TRY(cudaGraphConditionalHandleCreate(loop, g, 0, cudaGraphCondAssignDefault));
+  {
+    Track t(d, GMG_K_OTHER, 0.0, 0.0);
+    GMG_CUDA_TRY(launch_cg_graph_init(d->ctl, *loop, s));
+  }
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  GMG_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = *loop;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  GMG_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  GMG_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return GMG_OK;
+}
+
+static gmg_status capture_body(Hier& h, cudaGraphConditionalHandle loop) {
+  DeviceState* d = h.dev;
+  cudaStream_t s = d->stream;
+  const int64_t n = d->n_unknowns;
+  GraphCtl* c = d->ctl;
+  GMG_TRY(vcycle_any(h, d->r, d->z, &c->rz));
+  {
+    Track t(d, GMG_K_CG_P, 24.0 * n, 2.0 * n);
+    GMG_CUDA_TRY(launch_cg_update_p(n, d->p, d->z, &c->rz, &c->rz_old, s));
+  }
+  GMG_CUDA_TRY(cudaMemsetAsync(d->Ap, 0, sizeof(double) * n, s));
+  {
+    Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
+    GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), d->p, d->Ap, d->partials, d->counter, &c->pAp, s));
+  }
+  {
+    Track t(d, GMG_K_CG_XR, 48.0 * n, 6.0 * n);
+    GMG_CUDA_TRY(launch_cg_update_xr(n, d->x_iter, d->r, d->p, d->Ap, &c->rz, &c->pAp, d->partials, d->counter,
+                                     &c->rr, s));
+  }
+  Track t(d, GMG_K_OTHER, 0.0, 0.0);
+  GMG_CUDA_TRY(launch_cg_graph_check(c, loop, s));
+  return GMG_OK;
+}
+
+static gmg_status build_solve_graph(Hier& h) {
+  DeviceState* d = h.dev;
+  if (!d->x_iter) GMG_TRY(dev_alloc(d, &d->x_iter, (size_t)d->n_unknowns));
+  if (!d->ctl) GMG_TRY(dev_alloc(d, &d->ctl, 1));
+  if (!d->ctl_host) GMG_CUDA_TRY(cudaMallocHost(&d->ctl_host, sizeof(GraphCtl)));
+  // capture on a private stream: the context's stream may be the legacy
+  // default stream, which cannot be captured
+  if (!d->cap_stream) GMG_CUDA_TRY(cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  GMG_CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaStream_t user = d->stream;
+  d->stream = d->cap_stream;
+  d->cg_pre = Tally();
+  d->cg_body = Tally();
+  cudaGraphConditionalHandle loop = 0;
+  cudaGraph_t body = nullptr;
+  gmg_status st = GMG_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(d->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+    st = GMG_ECUDA;
+  }
+  if (st == GMG_OK) {
+    d->cap = &d->cg_pre;
+    st = capture_prelude(h, g, &loop, &body);
+    if (st != GMG_OK) {
+      st = abandon_capture(d->stream, st);
+    } else {
+      cudaGraph_t out = nullptr;
+      e = cudaStreamEndCapture(d->stream, &out);
+      if (e != cudaSuccess) {
+        set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+        st = GMG_ECUDA;
+      }
+    }
+  }
+  if (st == GMG_OK) {
+    e = cudaStreamBeginCaptureToGraph(d->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+      st = GMG_ECUDA;
+    } else {
+      d->cap = &d->cg_body;
+      st = capture_body(h, loop);
+      if (st != GMG_OK) {
+        st = abandon_capture(d->stream, st);
+      } else {
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(d->stream, &out);
+        if (e != cudaSuccess) {
+          set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+          st = GMG_ECUDA;
+        }
+      }
+    }
+  }
+  d->cap = nullptr;
+  d->stream = user;
+  cudaGraphExec_t ex = nullptr;
+  if (st == GMG_OK) {
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+      set_error(std::string("graph instantiation: ") + cudaGetErrorString(e));
+      st = GMG_ECUDA;
+    }
+  }
+  if (st != GMG_OK) {
+    cudaGraphDestroy(g);
+    return st;
+  }
+  d->cg_graph = g;
+  d->cg_exec = ex;
+  return GMG_OK;
+}
+
+static void add_tally(Profile& p, const Tally& t, uint64_t times) {
+  for (int k = 0; k < GMG_NUM_KERNEL_KINDS; ++k) {
+    p.launches[k] += t.launches[k] * times;
+    p.bytes[k] += t.bytes[k] * (double)times;
+    p.flops[k] += t.flops[k] * (double)times;
+  }
+}
+
+static gmg_status solve_graph(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
+                              gmg_stats* st) {
+  DeviceState* d = h.dev;
+  if (!d->cg_exec) GMG_TRY(build_solve_graph(h));
+  cudaStream_t s = d->stream;
+  const int64_t n = d->n_unknowns;
+  GraphCtl* c = d->ctl_host;
+  *c = GraphCtl();
+  c->tol = tol;
+  c->limit = fixed_iterations > 0 ? fixed_iterations : max_iter;
+  c->fixed = fixed_iterations > 0 ? fixed_iterations : 0;
+  c->status = GS_RUNNING;
+  GMG_CUDA_TRY(cudaMemcpyAsync(d->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GMG_CUDA_TRY(cudaMemcpyAsync(d->ctl, c, sizeof(GraphCtl), cudaMemcpyHostToDevice, s));
+  GMG_CUDA_TRY(cudaGraphLaunch(d->cg_exec, s));
+  GMG_CUDA_TRY(cudaMemcpyAsync(x, d->x_iter, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GMG_CUDA_TRY(cudaMemcpyAsync(c, d->ctl, sizeof(GraphCtl), cudaMemcpyDeviceToHost, s));
+  GMG_CUDA_TRY(cudaStreamSynchronize(s));
+  add_tally(d->prof, d->cg_pre, 1);
+  add_tally(d->prof, d->cg_body, (uint64_t)std::max(c->it, 0));
+  gmg_stats stats;
+  stats.iterations = c->it;
+  stats.norm_b = std::sqrt(c->bb);
+  stats.rel_residual = c->it > 0 ? std::sqrt(c->rr / c->bb) : (c->bb > 0 ? 1.0 : 0.0);
+  stats.converged = c->status == GS_DONE && (c->it == 0 || stats.rel_residual <= tol);
+  if (st) *st = stats;
+  switch (c->status) {
+    case GS_DONE:
+      return GMG_OK;
+    case GS_NOTCONV:
+      set_error("CG did not converge within max_iter");
+      return GMG_ENOTCONV;
+    case GS_NAN:
+      set_error(c->it == 0 ? "right-hand side contains NaN" : "NaN/Inf in a CG scalar");
+      return GMG_ENAN;
+    case GS_BREAKDOWN:
+      set_error("CG breakdown: p.Ap <= 0");
+      return GMG_EBREAKDOWN;
+    default:
+      set_error("internal: graph-mode CG ended without a status");
+      return GMG_ECUDA;
+  }
+}
+
+// Graph mode unless it is switched off or per-kernel timing is on (the
+// events that time single launches exist only in stream mode).
+gmg_status device_solve(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
+                        gmg_stats* st) {
+  if (h.params.solve_graph && !h.dev->prof.timing) return solve_graph(h, b, x, tol, max_iter, fixed_iterations, st);
+  return solve_stream(h, b, x, tol, max_iter, fixed_iterations, st);
 }
 
 // ------------------------------------------------- level operations (tests)

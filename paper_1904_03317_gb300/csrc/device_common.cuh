@@ -85,6 +85,28 @@ struct Profile {
   std::vector<cudaEvent_t> pool;
 };
 
+// Launch counts of a captured graph section, added to Profile per execution.
+struct Tally {
+  uint64_t launches[GMG_NUM_KERNEL_KINDS] = {};
+  double bytes[GMG_NUM_KERNEL_KINDS] = {};
+  double flops[GMG_NUM_KERNEL_KINDS] = {};
+};
+
+// Scalars and loop control of the graph-mode CG, in device memory.
+struct GraphCtl {
+  double bb;      // b.b
+  double rz_old;  // r_{i-1}.z_{i-1} (1 before the first iteration, where p = 0)
+  double rz;      // r_i.z_i
+  double pAp;     // p_i.A p_i
+  double rr;      // r_{i+1}.r_{i+1}
+  double tol;     // relative tolerance
+  int it;         // completed iterations
+  int limit;      // iteration limit
+  int fixed;      // > 0: run exactly this many iterations
+  int status;     // GraphStatus
+};
+enum GraphStatus { GS_RUNNING = 0, GS_DONE = 1, GS_NOTCONV = 2, GS_NAN = 3, GS_BREAKDOWN = 4 };
+
 struct DeviceState {
   cudaStream_t stream = nullptr;
   Profile prof;
@@ -129,6 +151,15 @@ struct DeviceState {
   double* scal_host = nullptr;    // pinned mirror
   int max_scal = 0;
   double active_flops = 0, active_bytes = 0;  // per leaf-operator launch
+  // graph-mode CG, built by the first graph-mode solve
+  Tally* cap = nullptr;            // non-null while a graph section is captured
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t cg_graph = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  Tally cg_pre, cg_body;           // launches before the loop and per loop pass
+  double* x_iter = nullptr;        // iterate of the graph-mode CG
+  GraphCtl* ctl = nullptr;
+  GraphCtl* ctl_host = nullptr;    // pinned mirror
 };
 
 constexpr int kMaxReduceBlocks = 4096;
@@ -195,6 +226,11 @@ cudaError_t launch_cg_update_xr(int64_t n, double* x, double* r, const double* p
                                 cudaStream_t s);
 cudaError_t launch_cg_update_p(int64_t n, double* p, const double* z, const double* rz_new,
                                const double* rz_old, cudaStream_t s);
+// Loop control of the graph-mode CG: `init` starts the loop when b.b > 0,
+// `check` counts an iteration, applies the stopping rules and sets the loop
+// condition.
+cudaError_t launch_cg_graph_init(GraphCtl* c, cudaGraphConditionalHandle loop, cudaStream_t s);
+cudaError_t launch_cg_graph_check(GraphCtl* c, cudaGraphConditionalHandle loop, cudaStream_t s);
 cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_mul(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
 cudaError_t launch_xpay(int64_t n, const double* x, double beta, double* y, cudaStream_t s);

@@ -235,7 +235,7 @@ struct AGrp {
   static constexpr int MAX_GRID = 152 * 16;
 };
 
-template <int DIM, int K>
+template <int DIM, int K, bool ISO>
 __global__ void __launch_bounds__(AGrp<DIM, K>::BS)
 active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restrict__ y, double* partials,
                     unsigned* counter, double* energy_out) {
@@ -283,6 +283,9 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
     }
     __syncthreads();
     if constexpr (DIM == 3) {
+      // cubic cells (s_x = s_y = s_z = s): D = My B + Ky A and out = a s (Mz D + Kz C)
+      // need no per-direction scaling
+      constexpr bool iso = ISO;
       // y direction: line = (ix, iz)
       if (act) {
         const int ix = line % NG, iz = line / NG;
@@ -300,10 +303,13 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
               cc += m * va[c];
               t1 += m * vb[c];
             }
-            if constexpr (kk != 0.0) t2 += kk * va[c];
+            if constexpr (kk != 0.0) {
+              if constexpr (iso) t1 += kk * va[c];
+              else t2 += kk * va[c];
+            }
           });
           C[q][ix + NG * (r + NG * iz)] = cc;
-          D[q][ix + NG * (r + NG * iz)] = sx * t1 + sy * t2;
+          D[q][ix + NG * (r + NG * iz)] = iso ? t1 : sx * t1 + sy * t2;
         });
       }
       __syncthreads();
@@ -317,15 +323,19 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
           vd[c] = D[q][ix + NG * (iy + NG * c)];
         });
         const double cf = coef[q], sz = sc[q][2];
+        const double cfs = cf * sz;
         if (grp < a.n_groups) {
           sfor<0, NG>([&](auto r) {
             double t3 = 0, t4 = 0;
             sfor<0, NG>([&](auto c) {
               constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
               if constexpr (m != 0.0) t3 += m * vd[c];
-              if constexpr (kk != 0.0) t4 += kk * vc[c];
+              if constexpr (kk != 0.0) {
+                if constexpr (iso) t3 += kk * vc[c];
+                else t4 += kk * vc[c];
+              }
             });
-            const double out = cf * (t3 + sz * t4);
+            const double out = iso ? cfs * t3 : cf * (t3 + sz * t4);
             const int n = ix + NG * (iy + NG * r);
             e += X[q][n] * out;
             const int32_t id = a.grp_nodes[grp * NN + n];
@@ -393,7 +403,10 @@ static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double*
     int64_t blocks = (a.n_groups + G::Q - 1) / G::Q;
     if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
     static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
-    active_group_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
+    // cubic cells on every level (the ratios of the sides are those of the coarse cells)
+    const bool iso = a.scale[0][0] == a.scale[0][1] && (DIM == 2 || a.scale[0][1] == a.scale[0][2]);
+    if (iso) active_group_kernel<DIM, K, true><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
+    else active_group_kernel<DIM, K, false><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
     wrote = true;
   }
   const int64_t ncell = a.cell_list ? a.n_list : a.n_cells;
@@ -644,6 +657,46 @@ cudaError_t launch_cg_update_p(int64_t n, double* p, const double* z, const doub
   if (n == 0) return cudaSuccess;
   int64_t b = (n + 255) / 256;
   cg_update_p_kernel<<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, p, z, rz_new, rz_old);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------- graph-mode CG control
+// Single-thread kernels; the stopping rules are those of the stream-mode loop
+// (NaN/Inf scalar, p.Ap <= 0, fixed count, ||r|| <= tol ||b||, limit).
+__global__ void cg_graph_init_kernel(GraphCtl* c, cudaGraphConditionalHandle loop) {
+  const double bb = c->bb;
+  c->rz_old = 1.0;
+  const bool go = bb > 0.0;
+  if (!go) c->status = isnan(bb) ? GS_NAN : GS_DONE;
+  cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
+__global__ void cg_graph_check_kernel(GraphCtl* c, cudaGraphConditionalHandle loop) {
+  const int it = c->it + 1;
+  c->it = it;
+  const double rz = c->rz, pAp = c->pAp, rr = c->rr;
+  int status = GS_RUNNING;
+  if (isnan(rz) || isnan(pAp) || isnan(rr) || isinf(rr))
+    status = GS_NAN;
+  else if (!(pAp > 0.0))
+    status = GS_BREAKDOWN;
+  else if (c->fixed > 0) {
+    if (it == c->fixed) status = GS_DONE;
+  } else if (sqrt(rr / c->bb) <= c->tol)
+    status = GS_DONE;
+  if (status == GS_RUNNING && it >= c->limit) status = GS_NOTCONV;
+  c->status = status;
+  c->rz_old = rz;
+  cudaGraphSetConditional(loop, status == GS_RUNNING ? 1u : 0u);
+}
+
+cudaError_t launch_cg_graph_init(GraphCtl* c, cudaGraphConditionalHandle loop, cudaStream_t s) {
+  cg_graph_init_kernel<<<1, 1, 0, s>>>(c, loop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_graph_check(GraphCtl* c, cudaGraphConditionalHandle loop, cudaStream_t s) {
+  cg_graph_check_kernel<<<1, 1, 0, s>>>(c, loop);
   return cudaGetLastError();
 }
 

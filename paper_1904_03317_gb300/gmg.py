@@ -57,7 +57,7 @@ class CoarseMeshC(C.Structure):
 class ParamsC(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("eig_lo", C.c_double), ("eig_hi", C.c_double),
                 ("eig_iters", C.c_int), ("vcycle_prec", C.c_int),
-                ("fixed_lambda", C.POINTER(C.c_double))]
+                ("fixed_lambda", C.POINTER(C.c_double)), ("solve_graph", C.c_int)]
 
 
 class InfoC(C.Structure):
@@ -235,11 +235,12 @@ class Hierarchy:
 
     def __init__(self, ctx: Context, mesh: Mesh, degree: int, coarse_coeff=None, cheb_degree: int = 5,
                  vcycle_prec: int = PREC_FP32, eig_lo: float = 0.08, eig_hi: float = 1.2, eig_iters: int = 10,
-                 fixed_lambda: Optional[Sequence[float]] = None):
+                 fixed_lambda: Optional[Sequence[float]] = None, solve_graph: bool = True):
         lib = load_library()
         p = ParamsC()
         lib.gmg_params_default(C.byref(p))
         p.cheb_degree, p.eig_lo, p.eig_hi, p.eig_iters, p.vcycle_prec = cheb_degree, eig_lo, eig_hi, eig_iters, vcycle_prec
+        p.solve_graph = int(solve_graph)
         self._lam = None
         if fixed_lambda is not None:
             self._lam = np.ascontiguousarray(np.asarray(fixed_lambda, dtype=np.float64))

@@ -12,7 +12,8 @@ from paper_1904_03317_gb300 import inputs
 def small_workloads():
     """Workloads the oracle finishes in seconds that still span many groups,
     ghost blocks, hanging nodes and a ragged last block of cells."""
-    cm3 = inputs.CoarseMesh(3, (3, 2, 2), (0.0, 0.0, 0.0), (1.5, 1.0, 1.0))
+    # anisotropic cells (0.5 x 0.5 x 0.4) keep the general-scale kernels covered
+    cm3 = inputs.CoarseMesh(3, (3, 2, 2), (0.0, 0.0, 0.0), (1.5, 1.0, 0.8))
     return {
         "2d_q1_circle": inputs.poisson2d_circle(3, 3),
         "2d_q2_circle": inputs.Workload("2d_q2", inputs.CoarseMesh(2, (4, 3, 1), (0, 0, 0), (1.0, 0.75, 1)), 2,
@@ -21,8 +22,8 @@ def small_workloads():
         "3d_q2_sphere": inputs.poisson3d_sphere(1, 2),
         "3d_q1_sphere": inputs.poisson3d_sphere(2, 2, degree=1),
         "3d_q2_checker": inputs.Workload("3d_q2_checker", cm3, 2,
-                                         [inputs.round_uniform(), inputs.round_sphere_surface((0.7, 0.5, 0.5), 0.3),
-                                          inputs.round_sphere_surface((0.7, 0.5, 0.5), 0.3)],
+                                         [inputs.round_uniform(), inputs.round_sphere_surface((0.7, 0.5, 0.4), 0.3),
+                                          inputs.round_sphere_surface((0.7, 0.5, 0.4), 0.3)],
                                          np.array([1.0, 100.0, 3.0, 1.0, 50.0, 1.0, 7.0, 1.0, 1.0, 100.0, 2.0, 1.0]),
                                          "random", 4, seed=7),
     }

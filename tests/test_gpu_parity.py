@@ -33,8 +33,8 @@ def torch():
 _cache = {}
 
 
-def gpu_hier(torch, name, prec=G.PREC_FP64, fixed=True):
-    key = (name, prec, fixed)
+def gpu_hier(torch, name, prec=G.PREC_FP64, fixed=True, solve_graph=True):
+    key = (name, prec, fixed, solve_graph)
     if key not in _cache:
         O = oracle_hierarchy(name)
         w = small_workloads()[name]
@@ -42,7 +42,7 @@ def gpu_hier(torch, name, prec=G.PREC_FP64, fixed=True):
         ctx = G.Context(0)
         m = G.build_mesh(w)
         H = G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=O.cheb_degree, vcycle_prec=prec,
-                        fixed_lambda=lam)
+                        fixed_lambda=lam, solve_graph=solve_graph)
         _cache[key] = (O, H, ctx, m)
     return _cache[key][:2]
 
@@ -273,8 +273,53 @@ def test_solve_fp32_vcycle_reaches_tolerance(torch, name):
     assert rel_err(xs, ref.x) < 1e-6
 
 
-def test_solve_error_paths(torch):
-    O, H = gpu_hier(torch, "3d_q2_sphere")
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_solve_graph_equals_stream(torch, name, prec):
+    """The graph-mode loop performs the stream-mode operations in the same
+    order, so iterates and statistics agree to rounding (the leaf operator
+    and the restriction scatter with atomics, whose order varies from run to
+    run: FP64 rounding for an FP64 V-cycle, FP32 rounding of the
+    preconditioner for an FP32 one); the launch accounting agrees too."""
+    O, Hg = gpu_hier(torch, name, prec)
+    _, Hs = gpu_hier(torch, name, prec, solve_graph=False)
+    w = small_workloads()[name]
+    b = dev(torch, _rhs(O, w))
+    xtol = 1e-10 if prec == G.PREC_FP64 else 1e-4
+    for kw in (dict(tol=1e-9), dict(fixed_iterations=3)):
+        xg = torch.full_like(b, 7.0)
+        xs = torch.full_like(b, -7.0)
+        Hg.profile_reset()
+        sg = Hg.solve(b, xg, **kw)
+        pg = Hg.profile_read()
+        Hs.profile_reset()
+        ss = Hs.solve(b, xs, **kw)
+        ps = Hs.profile_read()
+        assert sg.norm_b == ss.norm_b
+        if prec == G.PREC_FP32 and "tol" in kw and sg.iterations != ss.iterations:
+            # a residual within rounding of the tolerance may stop one pass apart
+            assert abs(sg.iterations - ss.iterations) == 1 and sg.converged and ss.converged
+            continue
+        assert (sg.iterations, sg.converged) == (ss.iterations, ss.converged)
+        assert abs(sg.rel_residual - ss.rel_residual) <= xtol * ss.rel_residual
+        assert rel_err(host(xg), host(xs)) < xtol
+        lg = {k: v["launches"] for k, v in pg.items()}
+        ls = {k: v["launches"] for k, v in ps.items()}
+        it = sg.iterations
+        # graph mode forms p_0 with the p update (stream mode copies z) and
+        # adds one loop-control kernel before the loop and one per pass
+        assert lg.pop("cg_update_p") == ls.pop("cg_update_p") + 1
+        assert lg.pop("other") == ls.pop("other") + 1 + it
+        assert lg == ls
+    # a second graph solve reuses the graph and starts from scratch again
+    xg2 = torch.zeros_like(b)
+    sg2 = Hg.solve(b, xg2, fixed_iterations=3)
+    assert sg2.iterations == 3 and rel_err(host(xg2), host(xs)) < xtol
+
+
+@pytest.mark.parametrize("solve_graph", [True, False])
+def test_solve_error_paths(torch, solve_graph):
+    O, H = gpu_hier(torch, "3d_q2_sphere", solve_graph=solve_graph)
     b = dev(torch, O.disc.rhs_sine())
     x = torch.zeros_like(b)
     st = H.solve(b, x, tol=1e-12, max_iter=2, raise_on_error=False)
