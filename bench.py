@@ -167,6 +167,8 @@ def main():
     ap.add_argument("--adaptive-ref", type=int, default=ADAPTIVE_REF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--solve-mode", default="graph", choices=["graph", "stream"],
+                    help="graph: each solve is one CUDA-graph launch; stream: one launch per kernel")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -214,7 +216,8 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = G.Context(local, stream.cuda_stream)
     t0 = time.perf_counter()
-    H = G.Hierarchy(ctx, mesh, w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32)
+    H = G.Hierarchy(ctx, mesh, w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32,
+                    solve_graph=args.solve_mode == "graph")
     t_setup = time.perf_counter() - t0
     info = H.info
     n = H.n
@@ -225,7 +228,8 @@ def main():
         H.solve(b, x, tol=TOL)
 
     # ---- timed region: K solves, each one CUDA-graph launch whose CG loop
-    # runs on the device (launches counted by the library's accounting)
+    # runs on the device (--solve-mode graph; launches counted by the
+    # library's accounting)
     sampler = ClockSampler(local)
     sampler.start()
     H.profile_reset(timing=False)
@@ -319,7 +323,7 @@ def main():
             "config": {"workload": f"poisson3d_q2_sphere_g{args.global_ref}_a{args.adaptive_ref}",
                        "unknowns": n, "leaves": int(info.n_leaves), "levels": int(info.n_levels),
                        "tol": TOL, "cheb_degree": w.cheb_degree, "cg_iterations": iters,
-                       "parallelism": f"replicas x{world}",
+                       "parallelism": f"replicas x{world}", "solve_mode": args.solve_mode,
                        "l2": f"inputs larger than L2 (active vector {8 * n / 1e6:.0f} MB)",
                        "setup_s": {"mesh": round(t_mesh, 3), "hierarchy_host": round(info.setup_host_s, 3),
                                    "hierarchy_device": round(info.setup_device_s, 3),

@@ -111,6 +111,10 @@ typedef struct gmg_info {
   double lambda_max[GMG_MAX_LEVELS];    /* estimated (or fixed) lambda_max of D^-1 A_l^S */
   uint64_t device_bytes;                /* device memory held by the hierarchy */
   double setup_host_s, setup_device_s;  /* wall time of the two setup phases */
+  /* how the leaf-mesh operator covers the leaf cells: patches of 4^d cells
+   * (the grandchildren of one cell, all leaves), full sibling groups of 2^d
+   * leaf cells, and single cells */
+  uint64_t leaf_patches, leaf_groups, leaf_single_cells;
 } gmg_info;
 
 typedef struct gmg_stats {

@@ -285,6 +285,9 @@ gmg_status gmg_hier_info(const gmg_hier* hh, gmg_info* info) {
   info->device_bytes = device_bytes(h);
   info->setup_host_s = h.setup_host_s;
   info->setup_device_s = h.setup_device_s;
+  info->leaf_patches = (uint64_t)h.active.n_patches;
+  info->leaf_groups = (uint64_t)h.active.n_groups;
+  info->leaf_single_cells = h.active.loose_cells.size();
   return GMG_OK;
 }
 

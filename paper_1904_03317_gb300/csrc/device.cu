@@ -10,6 +10,8 @@
 
 namespace gmg {
 
+thread_local uint64_t g_kernel_launches = 0;
+
 namespace {
 
 template <typename T>
@@ -73,20 +75,24 @@ static void drain(DeviceState* d) {
   p.pending.clear();
 }
 
-// Counts one launch of `kind`; with timing on, brackets it with events.
+// Accounts the kernels launched in its scope (one step of the path) to
+// `kind`, with the step's algorithmic bytes and flops; with timing on,
+// brackets the step with events.
 struct Track {
   DeviceState* d;
   int kind;
+  uint64_t first;
+  uint64_t* launches;
   cudaEvent_t a = nullptr;
-  Track(DeviceState* dd, int k, double bytes, double flops) : d(dd), kind(k) {
+  Track(DeviceState* dd, int k, double bytes, double flops) : d(dd), kind(k), first(g_kernel_launches) {
     if (d->cap) {  // captured into a graph: counted per execution of the graph
-      d->cap->launches[k] += 1;
+      launches = &d->cap->launches[k];
       d->cap->bytes[k] += bytes;
       d->cap->flops[k] += flops;
       return;
     }
     Profile& p = d->prof;
-    p.launches[k] += 1;
+    launches = &p.launches[k];
     p.bytes[k] += bytes;
     p.flops[k] += flops;
     if (p.timing) {
@@ -96,6 +102,7 @@ struct Track {
     }
   }
   ~Track() {
+    *launches += g_kernel_launches - first;
     if (!a) return;
     cudaEvent_t b = take_event(d->prof);
     cudaEventRecord(b, d->stream);
@@ -197,12 +204,24 @@ static ActiveArgs active_args(const Hier& h) {
   a.grp_nodes = h.dev->grp_nodes;
   a.grp_coeff = h.dev->grp_coeff;
   a.grp_level = h.dev->grp_level;
+  a.n_patches = h.dev->n_pat;
+  a.pat_nodes = h.dev->pat_nodes;
+  a.pat_coeff = h.dev->pat_coeff;
+  a.pat_level = h.dev->pat_level;
   a.cell_nodes = h.dev->cell_nodes;
   a.cell_coeff = h.dev->cell_coeff;
   a.cell_level = h.dev->cell_level;
   a.hang_ptr = h.dev->hang_ptr;
   a.hang_col = h.dev->hang_col;
   a.hang_w = h.dev->hang_w;
+  a.n_hang = h.dev->n_hang;
+  a.xh = h.dev->xh;
+  a.yh = h.dev->yh;
+  a.n_masters = h.dev->n_masters;
+  a.hm_node = h.dev->hm_node;
+  a.hm_ptr = h.dev->hm_ptr;
+  a.hm_hang = h.dev->hm_hang;
+  a.hm_w = h.dev->hm_w;
   for (int l = 0; l < GMG_MAX_LEVELS; ++l)
     for (int d = 0; d < 3; ++d) {
       a.scale[l][d] = h.dev->level_scale[l][d];
@@ -246,7 +265,9 @@ void device_free(Hier& h) {
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
-                  d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level};
+                  d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level,
+                  d->pat_nodes, d->pat_coeff, d->pat_level, d->xh, d->yh, d->hm_node, d->hm_ptr,
+                  d->hm_hang, d->hm_w};
   for (void* p : ptrs) cudaFree(p);
   if (d->scal_host) cudaFreeHost(d->scal_host);
   if (d->cg_exec) cudaGraphExecDestroy(d->cg_exec);
@@ -403,37 +424,52 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->hang_ptr, A.hang_ptr));
   GMG_TRY(upload(d, &d->hang_col, A.hang_col));
   GMG_TRY(upload(d, &d->hang_w, A.hang_w));
+  d->n_hang = (int64_t)A.hang_key.size();
+  d->n_masters = (int64_t)A.hm_node.size();
+  GMG_TRY(dev_alloc(d, &d->xh, (size_t)d->n_hang));
+  GMG_TRY(dev_alloc(d, &d->yh, (size_t)d->n_hang));
+  GMG_TRY(upload(d, &d->hm_node, A.hm_node));
+  GMG_TRY(upload(d, &d->hm_ptr, A.hm_ptr));
+  GMG_TRY(upload(d, &d->hm_hang, A.hm_hang));
+  GMG_TRY(upload(d, &d->hm_w, A.hm_w));
   GMG_TRY(upload(d, &d->home, A.home_global));
   GMG_TRY(upload(d, &d->loose, A.loose_cells));
   GMG_TRY(upload(d, &d->grp_nodes, A.grp_nodes));
   GMG_TRY(upload(d, &d->grp_coeff, A.grp_coeff));
   GMG_TRY(upload(d, &d->grp_level, A.grp_level));
+  GMG_TRY(upload(d, &d->pat_nodes, A.pat_nodes));
+  GMG_TRY(upload(d, &d->pat_coeff, A.pat_coeff));
+  GMG_TRY(upload(d, &d->pat_level, A.pat_level));
   d->n_loose = (int64_t)A.loose_cells.size();
   d->n_grp = A.n_groups;
+  d->n_pat = A.n_patches;
   for (int l = 0; l < GMG_MAX_LEVELS; ++l) level_scales(h, l, d->level_scale[l], d->cell_h[l]);
   {
     // floating-point operations (FMA = 2) of one leaf-operator application
-    const int n1 = k + 1, ng = 2 * k + 1;
-    const double nc = ipow_d(n1, dim), ngn = ipow_d(ng, dim), lines = ipow_d(ng, dim - 1);
-    const double nnz1 = n1 * n1;                       // dense (K+1)^2 element rows
-    const double nnzg = 2.0 * n1 * n1 - 1.0;           // assembled two-cell rows
-    double cell_flops, grp_flops;
+    const int n1 = k + 1;
+    const double nc = ipow_d(n1, dim);
     double s0[3], h0[3];
     level_scales(h, 0, s0, h0);
     const bool iso = s0[0] == s0[1] && (dim == 2 || s0[1] == s0[2]);
-    if (dim == 3) {
-      cell_flops = nc * (2.0 * (2 * n1 + 3 * n1 + 1 + 2 * n1 + 1 + 1) + 2.0);
-      // isotropic group kernel: no per-direction scaling (one multiply per node)
-      grp_flops = lines * 2.0 * (2 * nnzg + 3 * nnzg + 2 * nnzg) + ngn * (iso ? 2.0 + 1.0 : 2.0 * 3 + 2.0);
-    } else {
-      cell_flops = nc * (2.0 * (2 * n1 + 2 * n1 + 1 + 1) + 2.0);
-      grp_flops = lines * 2.0 * (2 * nnzg + 2 * nnzg) + ngn * (2.0 * 2 + 2.0);
-    }
-    (void)nnz1;
-    d->active_flops = cell_flops * (double)A.loose_cells.size() + grp_flops * (double)A.n_groups;
-    d->active_bytes = 4.0 * (nc * (double)A.loose_cells.size() + ngn * (double)A.n_groups) +
-                      9.0 * (double)(A.loose_cells.size() + A.n_groups) + 24.0 * (double)A.n_unknowns +
-                      12.0 * (double)A.hang_col.size();
+    // a group of P^d cells: 1-D passes over (Pk+1)^(d-1) lines with the
+    // P n1^2 - (P - 1) nonzeros of the assembled 1-D matrices
+    auto group_flops = [&](int P) {
+      const double ng = P * k + 1.0, ngn = std::pow(ng, dim), lines = std::pow(ng, dim - 1);
+      const double nnz = P * n1 * n1 - (P - 1.0);
+      if (dim == 3)  // isotropic: no per-direction scaling (one multiply per node)
+        return lines * 2.0 * (2 * nnz + 3 * nnz + 2 * nnz) + ngn * (iso ? 2.0 + 1.0 : 2.0 * 3 + 2.0);
+      return lines * 2.0 * (2 * nnz + 2 * nnz) + ngn * (2.0 * 2 + 2.0);
+    };
+    const double cell_flops = dim == 3 ? nc * (2.0 * (2 * n1 + 3 * n1 + 1 + 2 * n1 + 1 + 1) + 2.0)
+                                       : nc * (2.0 * (2 * n1 + 2 * n1 + 1 + 1) + 2.0);
+    const double ngn2 = ipow_d(2 * k + 1, dim), ngn4 = ipow_d(4 * k + 1, dim);
+    const double nl = (double)A.loose_cells.size(), ng2 = (double)A.n_groups, ng4 = (double)A.n_patches;
+    // hanging nodes: x_h = C_h x before, y += C_h^T y_h after (one FMA per entry each)
+    const double nnzc = (double)A.hang_col.size();
+    d->active_flops = cell_flops * nl + group_flops(2) * ng2 + group_flops(4) * ng4 + 4.0 * nnzc;
+    d->active_bytes = 4.0 * (nc * nl + ngn2 * ng2 + ngn4 * ng4) + 9.0 * (nl + ng2 + ng4) +
+                      24.0 * (double)A.n_unknowns + 2.0 * 12.0 * nnzc + 32.0 * (double)A.hang_key.size() +
+                      16.0 * (double)A.hm_node.size();
   }
   GMG_TRY(dev_alloc(d, &d->r, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->p, A.n_unknowns));

@@ -20,6 +20,12 @@ namespace gmg {
     }                                                                              \
   } while (0)
 
+// Kernels launched by this thread: every launch site counts itself, and the
+// launch accounting attributes the launches made inside one accounting scope
+// to that scope's kind.
+extern thread_local uint64_t g_kernel_launches;
+#define GMG_COUNT_LAUNCH() (++::gmg::g_kernel_launches)
+
 // Per-level device data (level l >= 1 is stored by sibling groups).
 struct LevelDev {
   int64_t n_groups = 0;
@@ -133,9 +139,20 @@ struct DeviceState {
   int32_t* grp_nodes = nullptr;
   double* grp_coeff = nullptr;
   uint8_t* grp_level = nullptr;
+  int64_t n_pat = 0;
+  int32_t* pat_nodes = nullptr;
+  double* pat_coeff = nullptr;
+  uint8_t* pat_level = nullptr;
   int32_t* hang_ptr = nullptr;
   int32_t* hang_col = nullptr;
   double* hang_w = nullptr;
+  int64_t n_hang = 0, n_masters = 0;
+  double* xh = nullptr;
+  double* yh = nullptr;
+  int32_t* hm_node = nullptr;
+  int32_t* hm_ptr = nullptr;
+  int32_t* hm_hang = nullptr;
+  double* hm_w = nullptr;
   uint32_t* home = nullptr;
   double level_scale[GMG_MAX_LEVELS][3];  // leaf-cell operator factors per level
   double cell_h[GMG_MAX_LEVELS][3];       // cell sizes per level
@@ -189,12 +206,24 @@ struct ActiveArgs {
   const int32_t* grp_nodes;
   const double* grp_coeff;
   const uint8_t* grp_level;
+  int64_t n_patches;         // leaf patches (4^d cells)
+  const int32_t* pat_nodes;
+  const double* pat_coeff;
+  const uint8_t* pat_level;
   const int32_t* cell_nodes;
   const double* cell_coeff;
   const uint8_t* cell_level;
   const int32_t* hang_ptr;
   const int32_t* hang_col;
   const double* hang_w;
+  int64_t n_hang;
+  double* xh;                // hanging-node values of the operand
+  double* yh;                // contributions to hanging nodes
+  int64_t n_masters;         // unknowns that are masters of hanging nodes
+  const int32_t* hm_node;    // their unknown indices
+  const int32_t* hm_ptr;     // n_masters + 1
+  const int32_t* hm_hang;    // hanging node of each entry
+  const double* hm_w;        // its weight
   // per-level factors of the hierarchy (kernel parameters, so hierarchies
   // that live side by side never share them)
   double scale[GMG_MAX_LEVELS][3];  // s_i = prod_{j != i} h_j / h_i

@@ -167,6 +167,10 @@ struct ActiveHost {
   std::vector<int32_t> hang_col;
   std::vector<double> hang_w;
   std::vector<int64_t> hang_master_key;  // for export (Dirichlet masters dropped)
+  // the same constraints by master: unknown hm_node[i] is a master of the
+  // hanging rows hm_hang[hm_ptr[i] .. hm_ptr[i+1]) with weights hm_w
+  std::vector<int32_t> hm_node, hm_ptr, hm_hang;
+  std::vector<double> hm_w;
   int64_t n_leaf_nodes = 0;
   // leaf sibling groups: refined parents whose 2^d children are all leaves;
   // node table over the group's (2k+1)^d nodes, same encoding as cell_nodes
@@ -174,7 +178,13 @@ struct ActiveHost {
   std::vector<int32_t> grp_nodes;
   std::vector<double> grp_coeff;
   std::vector<uint8_t> grp_level;
-  std::vector<int32_t> loose_cells;  // leaf cells not in a full group
+  // leaf patches: cells whose 4^d grandchildren are all leaves, node table
+  // over the patch's (4k+1)^d nodes; their cells are in no group
+  int64_t n_patches = 0;
+  std::vector<int32_t> pat_nodes;
+  std::vector<double> pat_coeff;
+  std::vector<uint8_t> pat_level;
+  std::vector<int32_t> loose_cells;  // leaf cells in neither a patch nor a full group
 };
 
 struct DeviceState;  // defined in the CUDA translation units

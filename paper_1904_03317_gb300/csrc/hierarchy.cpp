@@ -664,6 +664,29 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     }
     A.hang_ptr[r + 1] = (int32_t)A.hang_col.size();
   }
+  {
+    // transposed constraints, masters in increasing unknown order
+    const size_t nnz = A.hang_col.size();
+    std::vector<int32_t> cnt(nu + 1, 0);
+    for (int32_t c : A.hang_col) cnt[c + 1]++;
+    for (int64_t u = 0; u < nu; ++u) cnt[u + 1] += cnt[u];
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+    A.hm_hang.assign(nnz, 0);
+    A.hm_w.assign(nnz, 0.0);
+    for (size_t r = 0; r + 1 < A.hang_ptr.size(); ++r)
+      for (int32_t m = A.hang_ptr[r]; m < A.hang_ptr[r + 1]; ++m) {
+        const int32_t at = fill[A.hang_col[m]]++;
+        A.hm_hang[at] = (int32_t)r;
+        A.hm_w[at] = A.hang_w[m];
+      }
+    A.hm_node.clear();
+    A.hm_ptr.assign(1, 0);
+    for (int64_t u = 0; u < nu; ++u)
+      if (cnt[u + 1] > cnt[u]) {
+        A.hm_node.push_back((int32_t)u);
+        A.hm_ptr.push_back(cnt[u + 1]);
+      }
+  }
   // per leaf cell tables
   A.cell_nodes.resize((size_t)nleaf * NLOC);
   A.cell_coeff.resize(nleaf);
@@ -684,18 +707,53 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       A.cell_nodes[(size_t)i * NLOC + j] = v;
     }
   }
-  // full leaf sibling groups: in canonical (Morton) order the 2^d children of
-  // a parent are consecutive, first child has all coordinate bits 0
+  // leaf patches and full leaf sibling groups: in canonical (Morton) order
+  // the 2^d children of a parent (and the 4^d grandchildren of a grandparent)
+  // are consecutive, the first one with the low coordinate bits 0
   {
     const int nch = 1 << dim, NG = 2 * k + 1;
     const int NGN = ipow(NG, dim);
+    const int npc = nch * nch, NP = 4 * k + 1;
+    const int NPN = ipow(NP, dim);
     A.grp_nodes.clear();
     A.grp_coeff.clear();
     A.grp_level.clear();
+    A.pat_nodes.clear();
+    A.pat_coeff.clear();
+    A.pat_level.clear();
     A.loose_cells.clear();
     int64_t i = 0;
     while (i < nleaf) {
       const int lvl = f.leaf_level[i];
+      bool patch = lvl > 1 && i + npc <= nleaf;
+      for (int d = 0; d < dim && patch; ++d)
+        if (f.leaf_coords[3 * i + d] & 3) patch = false;
+      for (int b = 1; b < npc && patch; ++b) {
+        if (f.leaf_level[i + b] != lvl) patch = false;
+        const int hi = b >> dim, lo = b & (nch - 1);
+        for (int d = 0; d < dim && patch; ++d)
+          if (f.leaf_coords[3 * (i + b) + d] != f.leaf_coords[3 * i + d] + 2 * ((hi >> d) & 1) + ((lo >> d) & 1))
+            patch = false;
+      }
+      if (patch) {
+        const size_t base = A.pat_nodes.size();
+        A.pat_nodes.resize(base + NPN);
+        for (int b = 0; b < npc; ++b) {
+          const int hi = b >> dim, lo = b & (nch - 1);
+          int pc[3] = {0, 0, 0};
+          for (int d = 0; d < dim; ++d) pc[d] = 2 * ((hi >> d) & 1) + ((lo >> d) & 1);
+          for (int j = 0; j < NLOC; ++j) {
+            const int lx = j % (k + 1), ly = dim > 1 ? (j / (k + 1)) % (k + 1) : 0,
+                      lz = dim > 2 ? j / ((k + 1) * (k + 1)) : 0;
+            const int gx = pc[0] * k + lx, gy = pc[1] * k + ly, gz = pc[2] * k + lz;
+            A.pat_nodes[base + gx + NP * (gy + NP * gz)] = A.cell_nodes[(size_t)(i + b) * NLOC + j];
+          }
+        }
+        A.pat_coeff.push_back(A.cell_coeff[i]);
+        A.pat_level.push_back((uint8_t)lvl);
+        i += npc;
+        continue;
+      }
       bool full = lvl > 0 && i + nch <= nleaf;
       if (full) {
         for (int d = 0; d < dim; ++d)
@@ -729,6 +787,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       i += nch;
     }
     A.n_groups = (int64_t)A.grp_coeff.size();
+    A.n_patches = (int64_t)A.pat_coeff.size();
   }
   // home slots
   A.home_slot.resize(nu);

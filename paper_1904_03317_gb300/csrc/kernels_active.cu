@@ -102,15 +102,51 @@ struct ActGeo {
   static constexpr int MAX_GRID = 152 * 12;       // bounded grid-stride (reduction partials)
 };
 
-template <int DIM, int K>
-__device__ __forceinline__ double gather_node(int32_t id, const double* __restrict__ x, const int32_t* hp,
-                                              const int32_t* hc, const double* hw) {
+// Value of a cell node: an unknown, 0 at a Dirichlet node, or the value of a
+// hanging node, which hang_gather_kernel has formed beforehand.
+__device__ __forceinline__ double gather_node(int32_t id, const double* __restrict__ x,
+                                              const double* __restrict__ xh) {
   if (id >= 0) return x[id];
   if (id == -1) return 0.0;
-  int h = -2 - id;
-  double v = 0.0;
-  for (int m = hp[h]; m < hp[h + 1]; ++m) v += hw[m] * x[hc[m]];
-  return v;
+  return xh[-2 - id];
+}
+
+// Adds a cell contribution to node `id`; contributions to a hanging node are
+// summed per hanging node and passed on to its masters by hang_scatter_kernel.
+__device__ __forceinline__ void scatter_node(int32_t id, double v, double* __restrict__ y, double* __restrict__ yh) {
+  if (id >= 0)
+    atomicAdd(y + id, v);
+  else if (id <= -2)
+    atomicAdd(yh + (-2 - id), v);
+}
+
+// Hanging-node values x_h = sum_m w_hm x_m (the rows of C), and zeroed
+// accumulators for their contributions.
+__global__ void __launch_bounds__(256) hang_gather_kernel(int64_t nh, const int32_t* __restrict__ hp,
+                                                          const int32_t* __restrict__ hc,
+                                                          const double* __restrict__ hw,
+                                                          const double* __restrict__ x, double* __restrict__ xh,
+                                                          double* __restrict__ yh) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int m = hp[h]; m < hp[h + 1]; ++m) v += hw[m] * x[hc[m]];
+    xh[h] = v;
+    yh[h] = 0.0;
+  }
+}
+
+// y_m += sum_h w_hm y_h for every master unknown m (C^T applied to the
+// hanging-node sums); one thread per master, so no atomics.
+__global__ void __launch_bounds__(256) hang_scatter_kernel(int64_t nm, const int32_t* __restrict__ node,
+                                                           const int32_t* __restrict__ mp,
+                                                           const int32_t* __restrict__ mh,
+                                                           const double* __restrict__ mw,
+                                                           const double* __restrict__ yh, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = mp[i]; j < mp[i + 1]; ++j) s += mw[j] * yh[mh[j]];
+    y[node[i]] += s;
+  }
 }
 
 template <int DIM, int K>
@@ -141,7 +177,7 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
       coef = a.cell_coeff[cell];
       lvl = a.cell_level[cell];
     }
-    X[cl][n] = active ? gather_node<DIM, K>(id, x, a.hang_ptr, a.hang_col, a.hang_w) : 0.0;
+    X[cl][n] = active ? gather_node(id, x, a.xh) : 0.0;
     __syncthreads();
     // Kronecker sum  sx Kx My Mz + sy Mx Ky Mz + sz Mx My Kz  as
     //   A = Mx X, B = Kx X;  C = My A, D = sx My B + sy Ky A;  out = a (Mz D + sz Kz C)
@@ -194,12 +230,7 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
     }
     if (active) {
       e += X[cl][n] * out;
-      if (id >= 0) {
-        atomicAdd(y + id, out);
-      } else if (id <= -2) {
-        int h = -2 - id;
-        for (int m = a.hang_ptr[h]; m < a.hang_ptr[h + 1]; ++m) atomicAdd(y + a.hang_col[m], a.hang_w[m] * out);
-      }
+      scatter_node(id, out, y, a.yh);
     }
     __syncthreads();  // X / T arrays are reused by the next batch
   }
@@ -209,15 +240,17 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
   }
 }
 
-// ----------------------------------------- active operator, leaf sibling groups
-// Q groups of 2^d leaf cells per block; one thread per line of a group's
-// (2K+1)^d node lattice.  With all 2^d cells sharing one coefficient the
-// group operator is the Kronecker sum of (2K+1) x (2K+1) assembled 1-D
-// matrices, so shared nodes between the group's cells are computed once.
-template <int K, bool STIFF>
+// ------------------------------- active operator, leaf groups and leaf patches
+// A group (P = 2) is a refined cell whose 2^d children are all leaves, a patch
+// (P = 4) a cell whose 4^d grandchildren are.  All P^d cells share one
+// coefficient, so the operator of the group is the Kronecker sum of
+// (PK+1) x (PK+1) assembled 1-D matrices and nodes shared between its cells
+// are computed once.  Q groups per block, one thread per line of a group's
+// (PK+1)^d node lattice.
+template <int K, int P, bool STIFF>
 __host__ __device__ constexpr double agrp(int a, int b) {
   double v = 0.0;
-  for (int cell = 0; cell < 2; ++cell) {
+  for (int cell = 0; cell < P; ++cell) {
     int lo = K * cell;
     if (a >= lo && a <= lo + K && b >= lo && b <= lo + K)
       v += STIFF ? astiff1<K>(a - lo, b - lo) : amass1<K>(a - lo, b - lo);
@@ -225,40 +258,49 @@ __host__ __device__ constexpr double agrp(int a, int b) {
   return v;
 }
 
-template <int DIM, int K>
+template <int DIM, int K, int P>
 struct AGrp {
-  static constexpr int NG = 2 * K + 1;
+  static constexpr int NG = P * K + 1;
   static constexpr int NN = DIM == 3 ? NG * NG * NG : NG * NG;
   static constexpr int LINES = DIM == 3 ? NG * NG : NG;
-  static constexpr int Q = DIM == 3 ? (K == 2 ? 5 : 7) : (K == 2 ? 6 : 10);  // groups per block
+  // groups per block: as many lines as fit 128 threads (256 for Q2 3D patches)
+  static constexpr int TARGET = (DIM == 3 && P == 4 && K == 2) ? 256 : 128;
+  static constexpr int Q = TARGET / LINES > 0 ? TARGET / LINES : 1;
   static constexpr int BS = (Q * LINES + 31) / 32 * 32;
   static constexpr int MAX_GRID = 152 * 16;
+  // dynamic shared memory: X, A (later C) and B (later D) per group
+  static constexpr size_t SMEM = sizeof(double) * (3 * Q * NN + 4 * Q + BS / 32);
 };
 
-template <int DIM, int K, bool ISO>
-__global__ void __launch_bounds__(AGrp<DIM, K>::BS)
-active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restrict__ y, double* partials,
-                    unsigned* counter, double* energy_out) {
-  using G = AGrp<DIM, K>;
+template <int DIM, int K, int P, bool ISO>
+__global__ void __launch_bounds__(AGrp<DIM, K, P>::BS)
+active_group_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__ grp_nodes,
+                    const double* __restrict__ grp_coeff, const uint8_t* __restrict__ grp_level,
+                    const double* __restrict__ x, double* __restrict__ y, double* partials, unsigned* counter,
+                    double* energy_out, bool accumulate) {
+  using G = AGrp<DIM, K, P>;
   constexpr int NG = G::NG, NN = G::NN, Q = G::Q;
-  __shared__ double X[Q][NN], A[Q][NN], B[Q][NN], C[Q][NN], D[Q][NN];
-  __shared__ double coef[Q], sc[Q][3];
-  __shared__ double red[G::BS / 32];
+  extern __shared__ double smem_g[];
+  double (*X)[NN] = reinterpret_cast<double (*)[NN]>(smem_g);
+  double (*A)[NN] = reinterpret_cast<double (*)[NN]>(smem_g + Q * NN);
+  double (*B)[NN] = reinterpret_cast<double (*)[NN]>(smem_g + 2 * Q * NN);
+  double* coef = smem_g + 3 * Q * NN;
+  double (*sc)[3] = reinterpret_cast<double (*)[3]>(coef + Q);
+  double* red = coef + 4 * Q;
   const int tid = threadIdx.x;
-  const int64_t nbatch = (a.n_groups + Q - 1) / Q;
+  const int64_t nbatch = (n_grp + Q - 1) / Q;
   double e = 0.0;
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     for (int idx = tid; idx < Q * NN; idx += G::BS) {
       const int q = idx / NN, n = idx % NN;
       const int64_t grp = batch * Q + q;
-      X[q][n] = grp < a.n_groups ? gather_node<DIM, K>(a.grp_nodes[grp * NN + n], x, a.hang_ptr, a.hang_col, a.hang_w)
-                                 : 0.0;
+      X[q][n] = grp < n_grp ? gather_node(grp_nodes[grp * NN + n], x, a.xh) : 0.0;
     }
     if (tid < Q) {
       const int64_t grp = batch * Q + tid;
-      const bool ok = grp < a.n_groups;
-      const int lvl = ok ? a.grp_level[grp] : 0;
-      coef[tid] = ok ? a.grp_coeff[grp] : 0.0;
+      const bool ok = grp < n_grp;
+      const int lvl = ok ? grp_level[grp] : 0;
+      coef[tid] = ok ? grp_coeff[grp] : 0.0;
       sc[tid][0] = a.scale[lvl][0];
       sc[tid][1] = a.scale[lvl][1];
       sc[tid][2] = a.scale[lvl][2];
@@ -273,7 +315,7 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
       sfor<0, NG>([&](auto r) {
         double am = 0, bk = 0;
         sfor<0, NG>([&](auto c) {
-          constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+          constexpr double m = agrp<K, P, false>(r, c), kk = agrp<K, P, true>(r, c);
           if constexpr (m != 0.0) am += m * v[c];
           if constexpr (kk != 0.0) bk += kk * v[c];
         });
@@ -286,7 +328,8 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
       // cubic cells (s_x = s_y = s_z = s): D = My B + Ky A and out = a s (Mz D + Kz C)
       // need no per-direction scaling
       constexpr bool iso = ISO;
-      // y direction: line = (ix, iz)
+      // y direction: line = (ix, iz); a thread reads its whole line before it
+      // overwrites it, so C and D take the places of A and B
       if (act) {
         const int ix = line % NG, iz = line / NG;
         double va[NG], vb[NG];
@@ -298,7 +341,7 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
         sfor<0, NG>([&](auto r) {
           double cc = 0, t1 = 0, t2 = 0;
           sfor<0, NG>([&](auto c) {
-            constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+            constexpr double m = agrp<K, P, false>(r, c), kk = agrp<K, P, true>(r, c);
             if constexpr (m != 0.0) {
               cc += m * va[c];
               t1 += m * vb[c];
@@ -308,8 +351,8 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
               else t2 += kk * va[c];
             }
           });
-          C[q][ix + NG * (r + NG * iz)] = cc;
-          D[q][ix + NG * (r + NG * iz)] = iso ? t1 : sx * t1 + sy * t2;
+          A[q][ix + NG * (r + NG * iz)] = cc;
+          B[q][ix + NG * (r + NG * iz)] = iso ? t1 : sx * t1 + sy * t2;
         });
       }
       __syncthreads();
@@ -319,16 +362,16 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
         const int ix = line % NG, iy = line / NG;
         double vc[NG], vd[NG];
         sfor<0, NG>([&](auto c) {
-          vc[c] = C[q][ix + NG * (iy + NG * c)];
-          vd[c] = D[q][ix + NG * (iy + NG * c)];
+          vc[c] = A[q][ix + NG * (iy + NG * c)];
+          vd[c] = B[q][ix + NG * (iy + NG * c)];
         });
         const double cf = coef[q], sz = sc[q][2];
         const double cfs = cf * sz;
-        if (grp < a.n_groups) {
+        if (grp < n_grp) {
           sfor<0, NG>([&](auto r) {
             double t3 = 0, t4 = 0;
             sfor<0, NG>([&](auto c) {
-              constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+              constexpr double m = agrp<K, P, false>(r, c), kk = agrp<K, P, true>(r, c);
               if constexpr (m != 0.0) t3 += m * vd[c];
               if constexpr (kk != 0.0) {
                 if constexpr (iso) t3 += kk * vc[c];
@@ -338,16 +381,12 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
             const double out = iso ? cfs * t3 : cf * (t3 + sz * t4);
             const int n = ix + NG * (iy + NG * r);
             e += X[q][n] * out;
-            const int32_t id = a.grp_nodes[grp * NN + n];
+            const int32_t id = grp_nodes[grp * NN + n];
             const bool interior = ix > 0 && ix < NG - 1 && iy > 0 && iy < NG - 1 && r > 0 && r < NG - 1;
-            if (interior && id >= 0) {
+            if (interior && id >= 0)
               y[id] = out;  // interior nodes belong to this group's cells only
-            } else if (id >= 0) {
-              atomicAdd(y + id, out);
-            } else if (id <= -2) {
-              const int h = -2 - id;
-              for (int m = a.hang_ptr[h]; m < a.hang_ptr[h + 1]; ++m) atomicAdd(y + a.hang_col[m], a.hang_w[m] * out);
-            }
+            else
+              scatter_node(id, out, y, a.yh);
           });
         }
       }
@@ -361,27 +400,23 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
           vb[c] = B[q][ix + NG * c];
         });
         const double cf = coef[q], sx = sc[q][0], sy = sc[q][1];
-        if (grp < a.n_groups) {
+        if (grp < n_grp) {
           sfor<0, NG>([&](auto r) {
             double t1 = 0, t2 = 0;
             sfor<0, NG>([&](auto c) {
-              constexpr double m = agrp<K, false>(r, c), kk = agrp<K, true>(r, c);
+              constexpr double m = agrp<K, P, false>(r, c), kk = agrp<K, P, true>(r, c);
               if constexpr (m != 0.0) t1 += m * vb[c];
               if constexpr (kk != 0.0) t2 += kk * va[c];
             });
             const double out = cf * (sx * t1 + sy * t2);
             const int n = ix + NG * r;
             e += X[q][n] * out;
-            const int32_t id = a.grp_nodes[grp * NN + n];
+            const int32_t id = grp_nodes[grp * NN + n];
             const bool interior = ix > 0 && ix < NG - 1 && r > 0 && r < NG - 1;
-            if (interior && id >= 0) {
+            if (interior && id >= 0)
               y[id] = out;
-            } else if (id >= 0) {
-              atomicAdd(y + id, out);
-            } else if (id <= -2) {
-              const int h = -2 - id;
-              for (int m = a.hang_ptr[h]; m < a.hang_ptr[h + 1]; ++m) atomicAdd(y + a.hang_col[m], a.hang_w[m] * out);
-            }
+            else
+              scatter_node(id, out, y, a.yh);
           });
         }
       }
@@ -390,23 +425,55 @@ active_group_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
   }
   if (energy_out) {
     double s = block_sum<G::BS>(e, red);
-    finish_reduction<G::BS>(s, partials, counter, energy_out, false);
+    finish_reduction<G::BS>(s, partials, counter, energy_out, accumulate);
   }
+}
+
+template <int DIM, int K, int P>
+static void group_launch(const ActiveArgs& a, int64_t n, const int32_t* nodes, const double* coeff,
+                         const uint8_t* level, const double* x, double* y, double* partials, unsigned* counter,
+                         double* energy, bool accumulate, cudaStream_t s) {
+  using G = AGrp<DIM, K, P>;
+  static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
+  static const bool init = [] {
+    cudaFuncSetAttribute(active_group_kernel<DIM, K, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)G::SMEM);
+    cudaFuncSetAttribute(active_group_kernel<DIM, K, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)G::SMEM);
+    return true;
+  }();
+  (void)init;
+  int64_t blocks = (n + G::Q - 1) / G::Q;
+  if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
+  // cubic cells on every level (the ratios of the sides are those of the coarse cells)
+  const bool iso = a.scale[0][0] == a.scale[0][1] && (DIM == 2 || a.scale[0][1] == a.scale[0][2]);
+  if (iso)
+    active_group_kernel<DIM, K, P, true><<<(unsigned)blocks, G::BS, G::SMEM, s>>>(
+        a, n, nodes, coeff, level, x, y, partials, counter, energy, accumulate);
+  else
+    active_group_kernel<DIM, K, P, false><<<(unsigned)blocks, G::BS, G::SMEM, s>>>(
+        a, n, nodes, coeff, level, x, y, partials, counter, energy, accumulate);
+  GMG_COUNT_LAUNCH();
 }
 
 template <int DIM, int K>
 static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double* y, double* partials,
                                    unsigned* counter, double* energy, cudaStream_t s) {
   bool wrote = false;
+  if (a.n_hang > 0) {
+    const int64_t b = (a.n_hang + 255) / 256;
+    hang_gather_kernel<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(a.n_hang, a.hang_ptr, a.hang_col,
+                                                                                a.hang_w, x, a.xh, a.yh);
+    GMG_COUNT_LAUNCH();
+  }
+  if (a.n_patches > 0) {
+    group_launch<DIM, K, 4>(a, a.n_patches, a.pat_nodes, a.pat_coeff, a.pat_level, x, y, partials, counter,
+                            energy, false, s);
+    wrote = true;
+  }
   if (a.n_groups > 0) {
-    using G = AGrp<DIM, K>;
-    int64_t blocks = (a.n_groups + G::Q - 1) / G::Q;
-    if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
-    static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
-    // cubic cells on every level (the ratios of the sides are those of the coarse cells)
-    const bool iso = a.scale[0][0] == a.scale[0][1] && (DIM == 2 || a.scale[0][1] == a.scale[0][2]);
-    if (iso) active_group_kernel<DIM, K, true><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
-    else active_group_kernel<DIM, K, false><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy);
+    group_launch<DIM, K, 2>(a, a.n_groups, a.grp_nodes, a.grp_coeff, a.grp_level, x, y, partials, counter,
+                            energy, wrote, s);
     wrote = true;
   }
   const int64_t ncell = a.cell_list ? a.n_list : a.n_cells;
@@ -416,7 +483,14 @@ static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double*
     if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
     static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
     active_apply_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy, wrote);
+    GMG_COUNT_LAUNCH();
     wrote = true;
+  }
+  if (a.n_masters > 0) {
+    const int64_t b = (a.n_masters + 255) / 256;
+    hang_scatter_kernel<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(a.n_masters, a.hm_node, a.hm_ptr,
+                                                                                 a.hm_hang, a.hm_w, a.yh, y);
+    GMG_COUNT_LAUNCH();
   }
   if (!wrote && energy) cudaMemsetAsync(energy, 0, sizeof(double), s);
   return cudaGetLastError();
@@ -505,6 +579,7 @@ cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* 
   else if (dim == 2 && k == 2) rhs_sine_kernel<2, 2><<<grid, 256, 0, s>>>(a, coords, b);
   else if (dim == 2 && k == 1) rhs_sine_kernel<2, 1><<<grid, 256, 0, s>>>(a, coords, b);
   else return cudaErrorInvalidValue;
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -521,6 +596,7 @@ cudaError_t launch_copy_to_mg(int64_t n, const double* r, const uint32_t* home, 
   if (n == 0) return cudaSuccess;
   int64_t b = (n + 255) / 256;
   copy_to_mg_kernel<T><<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, r, home, g);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -544,6 +620,7 @@ template <typename T>
 cudaError_t launch_copy_from_mg(int64_t n, const T* u, const uint32_t* home, const double* r, double* z,
                                 double* partials, unsigned* counter, double* rz_out, cudaStream_t s) {
   copy_from_mg_kernel<T><<<reduce_grid(n, 256), 256, 0, s>>>(n, u, home, r, z, partials, counter, rz_out);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -582,6 +659,7 @@ cudaError_t launch_coarse_solve(int dim, int64_t nc, const int64_t lat[3], const
   }
   unsigned grid = (unsigned)((nc + 127) / 128);
   coarse_solve_kernel<T><<<grid, 128, sm, s>>>(dim, nc, lat[0], lat[1], lat[2], inv, g0, u0);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -598,6 +676,7 @@ cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, 
   if (n == 0) return cudaSuccess;
   int64_t b = (n + 255) / 256;
   scale_vec_kernel<T><<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, dinv, g, c, out);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -615,6 +694,7 @@ __global__ void __launch_bounds__(256) dot_kernel(int64_t n, const double* __res
 cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials, unsigned* counter,
                        double* out, cudaStream_t s) {
   dot_kernel<<<reduce_grid(n, 256), 256, 0, s>>>(n, a, b, partials, counter, out);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -641,6 +721,7 @@ cudaError_t launch_cg_update_xr(int64_t n, double* x, double* r, const double* p
                                 const double* rz, const double* pAp, double* partials, unsigned* counter,
                                 double* rr_out, cudaStream_t s) {
   cg_update_xr_kernel<<<reduce_grid(n, 256), 256, 0, s>>>(n, x, r, p, Ap, rz, pAp, partials, counter, rr_out);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -657,6 +738,7 @@ cudaError_t launch_cg_update_p(int64_t n, double* p, const double* z, const doub
   if (n == 0) return cudaSuccess;
   int64_t b = (n + 255) / 256;
   cg_update_p_kernel<<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, p, z, rz_new, rz_old);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -692,11 +774,13 @@ __global__ void cg_graph_check_kernel(GraphCtl* c, cudaGraphConditionalHandle lo
 
 cudaError_t launch_cg_graph_init(GraphCtl* c, cudaGraphConditionalHandle loop, cudaStream_t s) {
   cg_graph_init_kernel<<<1, 1, 0, s>>>(c, loop);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_graph_check(GraphCtl* c, cudaGraphConditionalHandle loop, cudaStream_t s) {
   cg_graph_check_kernel<<<1, 1, 0, s>>>(c, loop);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -724,18 +808,22 @@ static inline unsigned vgrid(int64_t n) {
 }
 cudaError_t launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
   axpy_kernel<<<vgrid(n), 256, 0, s>>>(n, a, x, y);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t launch_mul(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
   mul_kernel<<<vgrid(n), 256, 0, s>>>(n, a, b, out);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t launch_xpay(int64_t n, const double* x, double beta, double* y, cudaStream_t s) {
   xpay_kernel<<<vgrid(n), 256, 0, s>>>(n, x, beta, y);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t launch_convert_d2f(int64_t n, const double* in, float* out, cudaStream_t s) {
   d2f_kernel<<<vgrid(n), 256, 0, s>>>(n, in, out);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

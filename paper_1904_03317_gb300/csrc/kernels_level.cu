@@ -1295,6 +1295,7 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
         init = true;
       }
       level_cheb_brick_kernel<T, K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1, c2);
+      GMG_COUNT_LAUNCH();
     }
   }
   if (a.n_uniform > 0) {
@@ -1307,6 +1308,7 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
     }
     dim3 grid((unsigned)((a.n_uniform + F::TPB - 1) / F::TPB));
     level_cheb_fast_kernel<T, DIM, K, MODE><<<grid, 256, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+    GMG_COUNT_LAUNCH();
   }
   if (a.n_jump > 0) {
     using G = Geo<DIM, K>;
@@ -1318,6 +1320,7 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
     }
     dim3 grid((unsigned)((a.n_jump + G::GPB - 1) / G::GPB));
     level_cheb_kernel<T, DIM, K, MODE><<<grid, G::GPB * G::TEAM, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+    GMG_COUNT_LAUNCH();
   }
   return cudaGetLastError();
 }
@@ -1354,6 +1357,7 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
   }
   dim3 grid((unsigned)((a.n_groups + F::TPB - 1) / F::TPB));
   level_residual_restrict_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, u, g, gc);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1379,6 +1383,7 @@ static cudaError_t pro_dispatch(const LevelArgs& a, const T* uc, T* u, T* u2, cu
   }
   dim3 grid((unsigned)((a.n_groups + F::TPB - 1) / F::TPB));
   level_prolongate_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, uc, u, u2);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1398,6 +1403,7 @@ static cudaError_t diag_dispatch(const LevelArgs& a, double* d, cudaStream_t s) 
   int64_t n = a.n_groups * G::NOWN;
   if (n == 0) return cudaSuccess;
   level_diag_kernel<DIM, K><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, d);
+  GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

@@ -70,7 +70,8 @@ class InfoC(C.Structure):
                 ("n_I", C.c_uint64 * MAX_LEVELS), ("n_home", C.c_uint64 * MAX_LEVELS),
                 ("bricks", C.c_uint64 * MAX_LEVELS), ("groups_jump", C.c_uint64 * MAX_LEVELS),
                 ("lambda_max", C.c_double * MAX_LEVELS), ("device_bytes", C.c_uint64),
-                ("setup_host_s", C.c_double), ("setup_device_s", C.c_double)]
+                ("setup_host_s", C.c_double), ("setup_device_s", C.c_double),
+                ("leaf_patches", C.c_uint64), ("leaf_groups", C.c_uint64), ("leaf_single_cells", C.c_uint64)]
 
 
 class KernelStatsC(C.Structure):

@@ -21,8 +21,14 @@ def small_workloads():
                                         None, "sine", 3),
         "3d_q2_sphere": inputs.poisson3d_sphere(1, 2),
         "3d_q1_sphere": inputs.poisson3d_sphere(2, 2, degree=1),
+        # leaf patches (4x4x4 cells), groups and single cells side by side
+        "3d_q2_patches": inputs.Workload("3d_q2_patches",
+                                         inputs.CoarseMesh(3, (3, 2, 2), (0.0, 0.0, 0.0), (1.5, 1.0, 1.0)), 2,
+                                         [inputs.round_uniform()] * 2
+                                         + [inputs.round_sphere_surface((0.3, 0.3, 0.3), 0.12)],
+                                         None, "sine", 4),
         "3d_q2_checker": inputs.Workload("3d_q2_checker", cm3, 2,
-                                         [inputs.round_uniform(), inputs.round_sphere_surface((0.7, 0.5, 0.4), 0.3),
+                                         [inputs.round_uniform(), inputs.round_uniform(),
                                           inputs.round_sphere_surface((0.7, 0.5, 0.4), 0.3)],
                                          np.array([1.0, 100.0, 3.0, 1.0, 50.0, 1.0, 7.0, 1.0, 1.0, 100.0, 2.0, 1.0]),
                                          "random", 4, seed=7),

@@ -45,6 +45,23 @@ def test_build_info_reports_sm103a():
     assert a.value == 1 and v.value == 1
 
 
+def test_leaf_cells_partitioned_into_patches_groups_and_single_cells():
+    """Every leaf cell is in exactly one patch, group or single-cell list,
+    and the parity workloads exercise all three forms of the leaf operator
+    (Q2 3D with cubic and with stretched cells, Q1 3D, Q1 2D)."""
+    seen = {}
+    for name, w in small_workloads().items():
+        m = G.build_mesh(w)
+        i = G.Hierarchy(G.Context(-1), m, w.degree, w.coeff).info
+        nch = 2 ** w.coarse.dim
+        assert i.leaf_patches * nch * nch + i.leaf_groups * nch + i.leaf_single_cells == i.n_leaves
+        seen[name] = (i.leaf_patches, i.leaf_groups, i.leaf_single_cells)
+    for name in ("3d_q2_patches", "3d_q2_checker", "3d_q1_sphere", "2d_q1_circle"):
+        assert min(seen[name]) > 0, (name, seen[name])
+    # a ragged last block of the Q2 3D patch kernel (3 patches per block)
+    assert seen["3d_q2_patches"][0] % 3 != 0
+
+
 @pytest.mark.parametrize("name", list(small_workloads()))
 def test_host_hierarchy_matches_oracle(name):
     w = small_workloads()[name]
