@@ -889,6 +889,159 @@ level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, co
   }
 }
 
+// FP32 brick kernel with packed two-wide FMAs (fma.rn.f32x2): stage 1 forms
+// the mass and stiffness rows of a halo line as one pair, stage 2 pairs the
+// two stage-1 results and stores the two stage-3 operands (p, q) as a pair,
+// stage 3 contracts (bk, bm) against (p, q).  Per component the arithmetic is
+// that of the scalar kernel; the shared arrays hold float2 and are padded so
+// that consecutive z planes fall on opposite halves of the banks.
+template <int K>
+struct Brick2S {
+  using B = BrickG<K>;
+  static constexpr int S1 = B::OB + 1;                          // stage-1 row stride (float2)
+  static constexpr int PZ1 = ((B::HB * S1 + 7) / 16) * 16 + 8;  // stage-1 z-plane stride, = 8 (mod 16)
+  static constexpr int T1 = B::HB * PZ1;
+  static constexpr int ZS = B::OB * B::OB + 8;                  // stage-2 z-plane stride, = 8 (mod 16)
+  static constexpr int T2 = B::HB * ZS;
+  static constexpr int XO = B::OB * B::OB * B::OB;
+  static constexpr size_t bytes() { return (size_t)(T1 + T2) * sizeof(float2) + XO * sizeof(float) + 64 * 4 + 8 * 8 + 16; }
+};
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(BrickG<K>::TB)
+level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float* xprev,
+                           const float* __restrict__ gvec, float* out, float c1, float c2) {
+  using B = BrickG<K>;
+  using S = Brick2S<K>;
+  constexpr int NO = B::NO, OB = B::OB, HB = B::HB, TB = B::TB, L3 = B::L3, R = B::R, OPT = B::OPT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* T1 = reinterpret_cast<float2*>(smem_raw);
+  float2* T2 = T1 + S::T1;
+  float* Xown = reinterpret_cast<float*>(T2 + S::T2);
+  int32_t* tab = reinterpret_cast<int32_t*>(Xown + S::XO);
+  uint64_t* smask = reinterpret_cast<uint64_t*>(tab + 64);
+  const int tid = threadIdx.x;
+  const int64_t br = blockIdx.x;
+  if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
+  __syncthreads();
+  auto own_group = [&](int bx, int by, int bz) { return tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))]; };
+  if (tid < 8) smask[tid] = a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)];
+  const float coef = a.coeff32[own_group(0, 0, 0)];
+  const int ol = tid % L3, part = tid / L3;
+  const bool has_out = tid < L3 * R;
+  const int oi = ol % OB, oj = ol / OB;
+  float pre_xp[OPT], pre_g[OPT];
+  int64_t slots[OPT];
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    slots[o] = -1;
+    pre_xp[o] = pre_g[o] = 0.f;
+    if (has_out && kk < OB) {
+      const int32_t gid = own_group(oi / NO, oj / NO, kk / NO);
+      slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
+      if constexpr (MODE == 1) {
+        pre_g[o] = gvec[slots[o]];
+        if (xprev) pre_xp[o] = xprev[slots[o]];
+      }
+    }
+  }
+  // stage 1: halo rows along x -> (mass, stiffness) pairs
+  for (int line = tid; line < HB * HB; line += TB) {
+    const int hy = line % HB, hz = line / HB;
+    int gy, ly, gz, lz;
+    brick_seg<K>(hy, gy, ly);
+    brick_seg<K>(hz, gz, lz);
+    const int row = NO * (ly + NO * lz);
+    const int tb = 4 * ((gy + 1) + 4 * (gz + 1));
+    float v[HB];
+    const int32_t b0 = tab[tb + 0], b1 = tab[tb + 1], b2 = tab[tb + 2], b3 = tab[tb + 3];
+    if (b0 >= 0) load_run<float, K>(x + (int64_t)b0 * B::NOWN + row + K, v);
+    else for (int i = 0; i < K; ++i) v[i] = 0.f;
+    if (b1 >= 0) load_run<float, 2 * K>(x + (int64_t)b1 * B::NOWN + row, v + K);
+    else for (int i = 0; i < 2 * K; ++i) v[K + i] = 0.f;
+    if (b2 >= 0) load_run<float, 2 * K>(x + (int64_t)b2 * B::NOWN + row, v + 3 * K);
+    else for (int i = 0; i < 2 * K; ++i) v[3 * K + i] = 0.f;
+    v[5 * K] = b3 >= 0 ? x[(int64_t)b3 * B::NOWN + row] : 0.f;
+    if (gy >= 0 && gy <= 1 && gz >= 0 && gz <= 1) {
+      const int by = gy * NO + ly, bz = gz * NO + lz;
+      store_run<float, OB>(Xown + OB * (by + OB * bz), v + K);
+    }
+    float2 vv[HB];
+    static_for<0, HB>([&](auto c) { vv[c] = make_float2(v[c], v[c]); });
+    float2* dst = T1 + hz * S::PZ1 + hy * S::S1;
+    static_for<0, OB>([&](auto r) {
+      float2 acc = make_float2(0.f, 0.f);
+      static_for<0, HB>([&](auto c) {
+        constexpr double bm = bbrick<K, false>(r, c);
+        constexpr double bk = bbrick<K, true>(r, c);
+        if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bm, (float)bk), vv[c], acc);
+      });
+      dst[r] = acc;
+    });
+  }
+  __syncthreads();
+  const float sx = a.scale32[0], sy = a.scale32[1], sz = a.scale32[2];
+  // stage 2: y direction, lines (z, i); stores p = sz MM and q = sy MK + sx KM
+  for (int line = tid; line < HB * OB; line += TB) {
+    const int z = line / OB, i = line % OB;
+    float2 w[HB];
+    static_for<0, HB>([&](auto y) { w[y] = T1[z * S::PZ1 + y * S::S1 + i]; });
+    static_for<0, OB>([&](auto j) {
+      float2 mmkm = make_float2(0.f, 0.f);
+      float mk = 0.f;
+      static_for<0, HB>([&](auto c) {
+        constexpr double bm = bbrick<K, false>(j, c);
+        constexpr double bk = bbrick<K, true>(j, c);
+        if constexpr (bm != 0.0) mmkm = __ffma2_rn(make_float2((float)bm, (float)bm), w[c], mmkm);
+        if constexpr (bk != 0.0) mk += (float)bk * w[c].x;
+      });
+      T2[z * S::ZS + j * OB + i] = make_float2(sz * mmkm.x, sy * mk + sx * mmkm.y);
+    });
+  }
+  __syncthreads();
+  // stage 3: z direction and the update
+  if (!has_out) return;
+  float2 pq[HB];
+  static_for<0, HB>([&](auto z) { pq[z] = T2[z * S::ZS + ol]; });
+  float c2d = 0.f;
+  if constexpr (MODE == 1) {
+    const float md0 = (float)bbrick<K, false>(0, K), kd0 = (float)bbrick<K, true>(0, K);
+    const float md1 = (float)bbrick<K, false>(1, K + 1), kd1 = (float)bbrick<K, true>(1, K + 1);
+    const float mdx = (oi & 1) ? md1 : md0, kdx = (oi & 1) ? kd1 : kd0;
+    const float mdy = (oj & 1) ? md1 : md0, kdy = (oj & 1) ? kd1 : kd0;
+    const float mdz = (part & 1) ? md1 : md0, kdz = (part & 1) ? kd1 : kd0;
+    c2d = c2 / (coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz));
+  }
+  static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share the parity of k");
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    if (kk >= OB) break;
+    float2 acc = make_float2(0.f, 0.f);
+    static_for<0, OB>([&](auto r) {
+      if (kk == r) {
+        static_for<0, HB>([&](auto c) {
+          constexpr double bm = bbrick<K, false>(r, c);
+          constexpr double bk = bbrick<K, true>(r, c);
+          if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bk, (float)bm), pq[c], acc);
+        });
+      }
+    });
+    float y = acc.x + acc.y;
+    const int gsel = (oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO));
+    const int node = (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
+    if (!((smask[gsel] >> node) & 1ull)) continue;
+    y *= coef;
+    if constexpr (MODE == 0) {
+      out[slots[o]] = y;
+    } else {
+      const float xv = Xown[oi + OB * (oj + OB * kk)];
+      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2d * (pre_g[o] - y);
+    }
+  }
+}
+
 // Slot (in the level l-1 vector) of node jd of the parent cell of group g
 // at level l: level 1 parents are coarse cells on the (K n0 + 1)^d lattice;
 // otherwise the parent is child cb of its own group, whose node block and
@@ -1288,14 +1441,29 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
                                T* out, T c1, T c2, cudaStream_t s) {
   if constexpr (DIM == 3) {
     if (a.n_bricks > 0) {
-      const size_t sm = BrickSmem<T, K>::bytes();
-      static bool init = false;
-      if (!init) {
-        cudaFuncSetAttribute(level_cheb_brick_kernel<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        init = true;
+      if constexpr (std::is_same<T, float>::value) {
+        const size_t sm = Brick2S<K>::bytes();
+        static bool init = false;
+        if (!init) {
+          cudaFuncSetAttribute(level_cheb_brick_f2_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+          init = true;
+        }
+        level_cheb_brick_f2_kernel<K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1,
+                                                                                            c2);
+        GMG_COUNT_LAUNCH();
+      } else {
+        const size_t sm = BrickSmem<T, K>::bytes();
+        static bool init = false;
+        if (!init) {
+          cudaFuncSetAttribute(level_cheb_brick_kernel<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+          init = true;
+        }
+        level_cheb_brick_kernel<T, K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1,
+                                                                                           c2);
+        GMG_COUNT_LAUNCH();
       }
-      level_cheb_brick_kernel<T, K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1, c2);
-      GMG_COUNT_LAUNCH();
     }
   }
   if (a.n_uniform > 0) {
