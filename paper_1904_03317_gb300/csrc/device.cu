@@ -182,6 +182,8 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.pmask = L.pmask;
   a.bricks = L.bricks;
   a.n_bricks = L.n_bricks;
+  a.list_rest = L.list_rest;
+  a.n_rest = L.n_rest;
   a.list_jump = L.list_jump;
   a.n_uniform = L.n_uniform;
   a.n_jump = L.n_jump;
@@ -262,6 +264,7 @@ void device_free(Hier& h) {
     cudaFree(L.pmask);
     cudaFree(L.bricks);
     cudaFree(L.list_jump);
+    cudaFree(L.list_rest);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
@@ -392,6 +395,8 @@ gmg_status device_setup(Hier& h) {
     GMG_TRY(upload(d, &D.pmask, H.pmask));
     GMG_TRY(upload(d, &D.bricks, H.bricks));
     D.n_bricks = (int64_t)H.bricks.size() / 64;
+    GMG_TRY(upload(d, &D.list_rest, H.list_rest));
+    D.n_rest = (int64_t)H.list_rest.size();
     GMG_TRY(upload(d, &D.list_jump, H.list_jump));
     D.n_uniform = (int64_t)H.list_uniform.size();
     D.n_jump = (int64_t)H.list_jump.size();

@@ -44,6 +44,8 @@ struct LevelDev {
   uint64_t* pmask = nullptr;    // n_groups x 4
   int32_t* bricks = nullptr;    // n_bricks x 64
   int64_t n_bricks = 0;
+  int32_t* list_rest = nullptr; // groups outside bricks
+  int64_t n_rest = 0;
   int64_t n_uniform = 0, n_jump = 0;
   double scale[3] = {0, 0, 0};  // K-term factor per direction: prod_{j!=i} h_j / h_i
   // Chebyshev parameters (host)
@@ -68,6 +70,8 @@ struct LevelArgs {
   const uint64_t* pmask;
   const int32_t* bricks;
   int64_t n_bricks;
+  const int32_t* list_rest;
+  int64_t n_rest;
   int64_t n_uniform, n_jump;
   const int32_t* nbr_coarse;  // level l-1 neighbour table (l >= 2)
   int64_t coarse_lat[3];      // coarse lattice extents (l == 1)

@@ -137,6 +137,8 @@ struct LevelHost {
   // 4^3 block indices of positions -1..2 around it (own groups at 0..1);
   // list_uniform then holds only the uniform groups outside bricks
   std::vector<int32_t> bricks;
+  // groups outside bricks (all groups when there are none), increasing
+  std::vector<int32_t> list_rest;
   // prolongation write masks over the group's (2k+1)^d nodes (2 x 64 bits):
   // add = stored S nodes (u += P uc), set = I nodes this group writes
   std::vector<uint64_t> pmask;      // n_groups x 4: add[0], add[1], set[0], set[1]

@@ -504,6 +504,9 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
         if (!taken[g]) rest.push_back(g);
       lv.list_uniform.swap(rest);
     }
+    lv.list_rest = lv.list_uniform;
+    lv.list_rest.insert(lv.list_rest.end(), lv.list_jump.begin(), lv.list_jump.end());
+    std::sort(lv.list_rest.begin(), lv.list_rest.end());
     for (int64_t s = 0; s < nslots; ++s) {
       if (lv.slot_class[s] == 1) ++lv.n_S;
       if (lv.slot_class[s] == 2) ++lv.n_I;

@@ -268,12 +268,14 @@ struct AGrp {
   static constexpr int Q = TARGET / LINES > 0 ? TARGET / LINES : 1;
   static constexpr int BS = (Q * LINES + 31) / 32 * 32;
   static constexpr int MAX_GRID = 152 * 16;
+  // resident blocks per SM the register budget is sized for
+  static constexpr int MIN_BLOCKS = BS >= 256 ? 3 : 8;
   // dynamic shared memory: X, A (later C) and B (later D) per group
   static constexpr size_t SMEM = sizeof(double) * (3 * Q * NN + 4 * Q + BS / 32);
 };
 
 template <int DIM, int K, int P, bool ISO>
-__global__ void __launch_bounds__(AGrp<DIM, K, P>::BS)
+__global__ void __launch_bounds__(AGrp<DIM, K, P>::BS, AGrp<DIM, K, P>::MIN_BLOCKS)
 active_group_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__ grp_nodes,
                     const double* __restrict__ grp_coeff, const uint8_t* __restrict__ grp_level,
                     const double* __restrict__ x, double* __restrict__ y, double* partials, unsigned* counter,
@@ -638,12 +640,16 @@ __global__ void coarse_solve_kernel(int dim, int64_t nc, int64_t lx, int64_t ly,
   };
   for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) gs[i] = (double)g0[slot_of(i)];
   __syncthreads();
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < nc; row += (int64_t)gridDim.x * blockDim.x) {
-    const double* a = inv + row * nc;
-    double acc = 0.0;
-    for (int64_t j = 0; j < nc; ++j) acc += a[j] * gs[j];
-    u0[slot_of(row)] = (T)acc;
-  }
+  // one warp per row: coalesced reads of the row, fixed-order reduction
+  const int lane = threadIdx.x % 32;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (row >= nc) return;
+  const double* a = inv + row * nc;
+  double acc = 0.0;
+  for (int64_t j = lane; j < nc; j += 32) acc += a[j] * gs[j];
+#pragma unroll
+  for (int o = 16; o > 0; o /= 2) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) u0[slot_of(row)] = (T)acc;
 }
 
 template <typename T>
@@ -657,8 +663,8 @@ cudaError_t launch_coarse_solve(int dim, int64_t nc, const int64_t lat[3], const
     cudaFuncSetAttribute(coarse_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     init = true;
   }
-  unsigned grid = (unsigned)((nc + 127) / 128);
-  coarse_solve_kernel<T><<<grid, 128, sm, s>>>(dim, nc, lat[0], lat[1], lat[2], inv, g0, u0);
+  unsigned grid = (unsigned)((nc + 7) / 8);  // 8 rows (warps) per block
+  coarse_solve_kernel<T><<<grid, 256, sm, s>>>(dim, nc, lat[0], lat[1], lat[2], inv, g0, u0);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }

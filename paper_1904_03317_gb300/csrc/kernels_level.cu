@@ -1267,15 +1267,17 @@ struct ProlongSmem {
 
 template <typename T, int DIM, int K>
 __global__ void __launch_bounds__(256)
-level_prolongate_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u, T* __restrict__ u2) {
+level_prolongate_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u, T* __restrict__ u2,
+                        const int32_t* __restrict__ list, int64_t n_list) {
   using F = Fast<DIM, K>;
   using S = ProlongSmem<T, DIM, K>;
   constexpr int NG = S::NG, N1 = S::N1, NO = F::NO, TW = F::TW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int team = threadIdx.x / TW;
   const int lane = threadIdx.x % TW;
-  const int64_t g = (int64_t)blockIdx.x * F::TPB + team;
-  const bool active = g < a.n_groups;
+  const int64_t gi = (int64_t)blockIdx.x * F::TPB + team;
+  const bool active = gi < n_list;
+  const int64_t g = active ? (list ? (int64_t)list[gi] : gi) : 0;
   uint64_t* hdr = reinterpret_cast<uint64_t*>(smem_raw) + team * 5;  // state, add[2], set[2]
   int32_t* nb = reinterpret_cast<int32_t*>(reinterpret_cast<uint64_t*>(smem_raw) + F::TPB * 5) + team * F::NNB;
   T* C = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
@@ -1539,18 +1541,149 @@ cudaError_t launch_level_residual_restrict(int dim, int k, const LevelArgs& a, c
   return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------- prolongation, 2x2x2 bricks
+// The eight groups of a brick at level l >= 2 are the children of the eight
+// cells of one sibling group at level l-1, so the brick's (4K+1)^3 fine nodes
+// are the tensor-product embedding of that group's (2K+1)^3 coarse nodes:
+// three 1-D passes shared by the eight groups.  Each fine node is written by
+// the brick group whose lattice holds it with the smallest offset, with that
+// group's add / set masks, exactly as the per-group kernel would.
+template <int K>
+__host__ __device__ constexpr double ebrick(int f, int c) {
+  const int cell = f / (2 * K) > 1 ? 1 : f / (2 * K);
+  const int r = f - 2 * K * cell, j = c - K * cell;
+  return (j >= 0 && j <= K) ? embed1<K>(r, j) : 0.0;
+}
+
+template <typename T, int K>
+struct ProBrick {
+  static constexpr int NO = 2 * K, NC = 2 * K + 1, NF = 4 * K + 1, NG = 2 * K + 1;
+  static constexpr int NOWN = NO * NO * NO;
+  static constexpr int TB = 128;
+  static constexpr int C = NC * NC * NC, PX = NC * NC * NF, PY = NC * NF * NF;
+  static constexpr size_t HEAD = 1024;  // masks (256 B), brick table (256 B), coarse neighbours (108 B)
+  static constexpr size_t bytes() { return HEAD + (size_t)(C + PX + PY) * sizeof(T); }
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(ProBrick<T, K>::TB)
+level_prolongate_brick_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u, T* __restrict__ u2) {
+  using P = ProBrick<T, K>;
+  constexpr int NO = P::NO, NC = P::NC, NF = P::NF, NG = P::NG, TB = P::TB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* masks = reinterpret_cast<uint64_t*>(smem_raw);     // 8 groups x (add0, add1, set0, set1)
+  int32_t* tab = reinterpret_cast<int32_t*>(masks + 32);
+  int32_t* cnb = tab + 64;                                       // 27 neighbours of the coarse group
+  T* C = reinterpret_cast<T*>(smem_raw + P::HEAD);
+  T* PXa = C + P::C;
+  T* PYa = PXa + P::PX;
+  const int tid = threadIdx.x;
+  const int64_t br = blockIdx.x;
+  if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
+  __syncthreads();
+  auto own = [&](int gx, int gy, int gz) { return tab[(gx + 1) + 4 * ((gy + 1) + 4 * (gz + 1))]; };
+  if (tid < 32) masks[tid] = a.pmask[(int64_t)own((tid >> 2) & 1, (tid >> 3) & 1, (tid >> 4) & 1) * 4 + (tid & 3)];
+  if (tid < 27) cnb[tid] = a.nbr_coarse[(int64_t)a.parent[own(0, 0, 0)] * 27 + tid];
+  __syncthreads();
+  // coarse nodes of the parent group (its +1 faces from the neighbours)
+  for (int i = tid; i < P::C; i += TB) {
+    const int cx = i % NC, cy = (i / NC) % NC, cz = i / (NC * NC);
+    const int ox = cx == 2 * K, oy = cy == 2 * K, oz = cz == 2 * K;
+    const int32_t blk = cnb[(ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1))];
+    C[i] = blk >= 0 ? uc[(int64_t)blk * NO * NO * NO + (cx - 2 * K * ox) + NO * ((cy - 2 * K * oy) + NO * (cz - 2 * K * oz))]
+                    : T(0);
+  }
+  __syncthreads();
+  // x: lines (cy, cz)
+  for (int line = tid; line < NC * NC; line += TB) {
+    T c[NC];
+    static_for<0, NC>([&](auto j) { c[j] = C[line * NC + j]; });
+    static_for<0, NF>([&](auto r) {
+      T v = 0;
+      static_for<0, NC>([&](auto j) {
+        constexpr double e = ebrick<K>(r, j);
+        if constexpr (e != 0.0) v += (T)e * c[j];
+      });
+      PXa[line * NF + r] = v;
+    });
+  }
+  __syncthreads();
+  // y: lines (cz, fx); PX [cz][cy][fx] -> PY [cz][fy][fx]
+  for (int line = tid; line < NC * NF; line += TB) {
+    const int cz = line / NF, fx = line % NF;
+    T c[NC];
+    static_for<0, NC>([&](auto j) { c[j] = PXa[(cz * NC + j) * NF + fx]; });
+    static_for<0, NF>([&](auto r) {
+      T v = 0;
+      static_for<0, NC>([&](auto j) {
+        constexpr double e = ebrick<K>(r, j);
+        if constexpr (e != 0.0) v += (T)e * c[j];
+      });
+      PYa[(cz * NF + r) * NF + fx] = v;
+    });
+  }
+  __syncthreads();
+  // z: lines (fx, fy), then write
+  for (int line = tid; line < NF * NF; line += TB) {
+    const int fx = line % NF, fy = line / NF;
+    T c[NC];
+    static_for<0, NC>([&](auto j) { c[j] = PYa[(j * NF + fy) * NF + fx]; });
+    const int bx = fx / NO, by = fy / NO;                 // storage block offsets 0..2
+    const int gx = bx > 1 ? 1 : bx, gy = by > 1 ? 1 : by;  // writing group
+    const int lx = fx - NO * gx, ly = fy - NO * gy;        // its lattice position 0..2K
+    static_for<0, NF>([&](auto r) {
+      T v = 0;
+      static_for<0, NC>([&](auto j) {
+        constexpr double e = ebrick<K>(r, j);
+        if constexpr (e != 0.0) v += (T)e * c[j];
+      });
+      constexpr int bz = r / NO, gz = bz > 1 ? 1 : bz, lz = r - NO * gz;
+      const int gsel = gx + 2 * (gy + 2 * gz);
+      const int n = lx + NG * (ly + NG * lz);
+      const uint64_t bit = 1ull << (n & 63);
+      if (masks[gsel * 4 + (n >> 6)] & bit) {
+        u[(int64_t)own(gx, gy, gz) * P::NOWN + lx + NO * (ly + NO * lz)] += v;
+      } else if (masks[gsel * 4 + 2 + (n >> 6)] & bit) {
+        const int32_t blk = tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))];
+        const int64_t s = (int64_t)blk * P::NOWN + (fx - NO * bx) + NO * ((fy - NO * by) + NO * (r - NO * bz));
+        u[s] = v;
+        u2[s] = v;
+      }
+    });
+  }
+}
+
 template <typename T, int DIM, int K>
 static cudaError_t pro_dispatch(const LevelArgs& a, const T* uc, T* u, T* u2, cudaStream_t s) {
   using F = Fast<DIM, K>;
   if (a.n_groups == 0) return cudaSuccess;
+  // bricks above level 1 (whose parents form one coarse group) take the brick
+  // kernel, the other groups the per-group kernel
+  const bool bricks = DIM == 3 && a.level >= 2 && a.n_bricks > 0;
+  if constexpr (DIM == 3) {
+    if (bricks) {
+      const size_t sm = ProBrick<T, K>::bytes();
+      static bool init = false;
+      if (!init) {
+        cudaFuncSetAttribute(level_prolongate_brick_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+        init = true;
+      }
+      level_prolongate_brick_kernel<T, K><<<(unsigned)a.n_bricks, ProBrick<T, K>::TB, sm, s>>>(a, uc, u, u2);
+      GMG_COUNT_LAUNCH();
+    }
+  }
+  const int32_t* list = bricks ? a.list_rest : nullptr;
+  const int64_t n = bricks ? a.n_rest : a.n_groups;
+  if (n == 0) return cudaGetLastError();
   const size_t sm = ProlongSmem<T, DIM, K>::bytes();
   static bool init = false;
   if (!init) {
     cudaFuncSetAttribute(level_prolongate_kernel<T, DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     init = true;
   }
-  dim3 grid((unsigned)((a.n_groups + F::TPB - 1) / F::TPB));
-  level_prolongate_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, uc, u, u2);
+  dim3 grid((unsigned)((n + F::TPB - 1) / F::TPB));
+  level_prolongate_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, uc, u, u2, list, n);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
