@@ -431,15 +431,304 @@ active_group_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__ grp
   }
 }
 
+// ------------------------ active operator, exact split-integer evaluation
+// For cubic cells the 1-D element matrices are integer matrices over common
+// denominators: M = M~ / DM, K = K~ / DK with DM = 30, DK = 3 for Q2 and
+// DM = 6, DK = 1 for Q1.  The operator of a group is then
+//   y = a s / (DM^(d-1) DK) * (integer Kronecker sum) x,
+// and the integer Kronecker sum applied to integers is exact.  Relative to a
+// power of two q = 2^eq set by the group's largest |x| (|x| < 2^15 q), each
+// value is split exactly into x / q = P1 + 2^-15 (P2 + r) with integers
+// |P1|, |P2| < 2^15 and r in [0, 1) rounded to 24 bits.  P1 and P2 go
+// through the int32 sum factorisation (the bound of the integer Kronecker sum
+// keeps every partial sum below 2^31), r through an FP32 one, and only the
+// recombination 2^15 y(P1) + y(P2) + y(r) and the scaling are FP64: four FP64
+// operations per node instead of about thirty.  The result is exact up to
+// the 24-bit rounding of r, which is below 2^-38 of the largest input, and
+// the final FP64 rounding.
+template <int K>
+struct IntElem {
+  static constexpr int DM = K == 1 ? 6 : 30, DK = K == 1 ? 1 : 3;
+};
+
+template <int K, bool STIFF>
+__host__ __device__ constexpr int ielem1(int i, int j) {
+  if constexpr (K == 1) {
+    return STIFF ? (i == j ? 1 : -1) : (i == j ? 2 : 1);
+  } else {
+    if constexpr (STIFF) return (i == 1 && j == 1) ? 16 : (i == 1 || j == 1) ? -8 : (i == j) ? 7 : 1;
+    else return (i == 1 && j == 1) ? 16 : (i == 1 || j == 1) ? 2 : (i == j) ? 4 : -1;
+  }
+}
+
+template <int K, int P, bool STIFF>
+__host__ __device__ constexpr int igrp(int a, int b) {
+  int v = 0;
+  for (int cell = 0; cell < P; ++cell) {
+    int lo = K * cell;
+    if (a >= lo && a <= lo + K && b >= lo && b <= lo + K) v += ielem1<K, STIFF>(a - lo, b - lo);
+  }
+  return v;
+}
+
+// the integer matrices are the FP64 ones times their denominators
+template <int K>
+constexpr bool int_elems_match() {
+  for (int i = 0; i <= K; ++i)
+    for (int j = 0; j <= K; ++j) {
+      const double dm = amass1<K>(i, j) * IntElem<K>::DM - ielem1<K, false>(i, j);
+      const double dk = astiff1<K>(i, j) * IntElem<K>::DK - ielem1<K, true>(i, j);
+      if (dm > 1e-12 || dm < -1e-12 || dk > 1e-12 || dk < -1e-12) return false;
+    }
+  return true;
+}
+static_assert(int_elems_match<1>() && int_elems_match<2>(), "integer element matrices");
+
+// largest sum of |entries| of a row of the assembled integer matrices
+template <int K, int P, bool STIFF>
+constexpr long long igrp_rowsum() {
+  long long best = 0;
+  for (int r = 0; r <= P * K; ++r) {
+    long long t = 0;
+    for (int c = 0; c <= P * K; ++c) t += igrp<K, P, STIFF>(r, c) < 0 ? -igrp<K, P, STIFF>(r, c) : igrp<K, P, STIFF>(r, c);
+    best = t > best ? t : best;
+  }
+  return best;
+}
+
+// bound on |integer Kronecker sum| per unit input
+template <int DIM, int K, int P>
+constexpr long long ikron_bound() {
+  constexpr long long m = igrp_rowsum<K, P, false>(), k = igrp_rowsum<K, P, true>();
+  return DIM == 3 ? 3 * m * m * k : 2 * m * k;
+}
+
+// |x| = m 2^e split against q = 2^eq (|x| < 2^15 q): x / q = p1 + 2^-15 (p2 + r)
+__device__ __forceinline__ void split_exact(double x, int eq, int& p1, int& p2, float& r) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (E) m |= 1ull << 52;
+  const int e = (E ? E : 1) - 1075;
+  const int s = eq - e;                 // |x| / q = m 2^-s, s >= 38
+  const unsigned long long hi = s < 64 ? (m >> s) : 0ull;
+  const unsigned long long rem1 = s < 64 ? (m & ((1ull << s) - 1ull)) : m;
+  const int s2 = s - 15;                // >= 23
+  const unsigned long long mid = s2 < 64 ? (rem1 >> s2) : 0ull;
+  const unsigned long long rem2 = s2 < 64 ? (rem1 & ((1ull << s2) - 1ull)) : rem1;
+  float rf = 0.f;
+  if (rem2) {  // rem2 2^-s2 in [0, 1): its leading 24 bits as a float
+    const int nb = 64 - __clzll((long long)rem2);
+    const unsigned mant = nb > 24 ? (unsigned)(rem2 >> (nb - 24)) : (unsigned)(rem2 << (24 - nb));
+    const int fexp = nb - 1 - s2;
+    if (fexp >= -126) rf = __int_as_float(((fexp + 127) << 23) | (int)(mant & 0x7FFFFFu));
+  }
+  const bool neg = (b >> 63) != 0;
+  p1 = neg ? -(int)hi : (int)hi;
+  p2 = neg ? -(int)mid : (int)mid;
+  r = neg ? -rf : rf;
+}
+
+// exact conversions without the FP64 conversion unit
+__device__ __forceinline__ double i64_to_double(long long v) {  // |v| < 2^51
+  return __longlong_as_double(0x4338000000000000LL + v) - 6755399441055744.0;
+}
+__device__ __forceinline__ double f32_to_double(float f) {  // normal or zero (subnormals flushed)
+  const unsigned u = (unsigned)__float_as_int(f);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  if (ex == 0) return 0.0;
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+template <int DIM, int K, int P>
+struct AGrpI {
+  using G = AGrp<DIM, K, P>;
+  static constexpr int NN = G::NN, Q = G::Q, BS = G::BS;
+  // X (FP64) and, per component (P1, P2, r), the in-place array and the
+  // second stage-1 output, 4 bytes each
+  static constexpr size_t SMEM = sizeof(double) * ((size_t)Q * NN + 2 * Q + BS / 32) + 4 * (6 * (size_t)Q * NN + Q);
+  static constexpr int MIN_BLOCKS = BS >= 256 ? 3 : 6;
+};
+
+template <int DIM, int K, int P>
+__global__ void __launch_bounds__(AGrp<DIM, K, P>::BS, AGrpI<DIM, K, P>::MIN_BLOCKS)
+active_group_int_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__ grp_nodes,
+                        const double* __restrict__ grp_coeff, const uint8_t* __restrict__ grp_level,
+                        const double* __restrict__ x, double* __restrict__ y, double* partials, unsigned* counter,
+                        double* energy_out, bool accumulate) {
+  using G = AGrp<DIM, K, P>;
+  constexpr int NG = G::NG, NN = G::NN, Q = G::Q, BS = G::BS;
+  static_assert(ikron_bound<DIM, K, P>() * 32768LL < 2147483648LL, "integer Kronecker sum exceeds int32");
+  extern __shared__ double smem_g[];
+  double (*X)[NN] = reinterpret_cast<double (*)[NN]>(smem_g);
+  double* scl = smem_g + Q * NN;       // per group: q 2^-15 a s / (DM^(d-1) DK)
+  double* red = scl + 2 * Q;
+  int (*A1)[NN] = reinterpret_cast<int (*)[NN]>(red + BS / 32);
+  int (*B1)[NN] = A1 + Q;
+  int (*A2)[NN] = B1 + Q;
+  int (*B2)[NN] = A2 + Q;
+  float (*A3)[NN] = reinterpret_cast<float (*)[NN]>(B2 + Q);
+  float (*B3)[NN] = A3 + Q;
+  int* emax = reinterpret_cast<int*>(B3 + Q);
+  constexpr double DEN = DIM == 3 ? (double)IntElem<K>::DM * IntElem<K>::DM * IntElem<K>::DK
+                                  : (double)IntElem<K>::DM * IntElem<K>::DK;
+  const int tid = threadIdx.x;
+  const int64_t nbatch = (n_grp + Q - 1) / Q;
+  double e = 0.0;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    if (tid < Q) emax[tid] = 1;
+    __syncthreads();
+    for (int idx = tid; idx < Q * NN; idx += BS) {
+      const int q = idx / NN, n = idx % NN;
+      const int64_t grp = batch * Q + q;
+      const double v = grp < n_grp ? gather_node(grp_nodes[grp * NN + n], x, a.xh) : 0.0;
+      X[q][n] = v;
+      atomicMax(&emax[q], (int)((__double_as_longlong(v) >> 52) & 0x7FF));
+    }
+    __syncthreads();
+    if (tid < Q) {
+      const int64_t grp = batch * Q + tid;
+      const bool ok = grp < n_grp;
+      const int lvl = ok ? grp_level[grp] : 0;
+      const double cs = ok ? grp_coeff[grp] * a.scale[lvl][0] / DEN : 0.0;
+      // q 2^-15 = 2^(emax - 1023 - 14 - 15); a NaN or Inf input makes the group's output NaN
+      const int eo = emax[tid] - 1023 - 29;
+      scl[tid] = emax[tid] == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
+                                     : cs * ldexp(1.0, eo);
+    }
+    for (int idx = tid; idx < Q * NN; idx += BS) {
+      const int q = idx / NN, n = idx % NN;
+      int p1, p2;
+      float r;
+      split_exact(X[q][n], emax[q] == 0x7FF ? 1010 : emax[q] - 1037, p1, p2, r);
+      A1[q][n] = p1;
+      A2[q][n] = p2;
+      A3[q][n] = r;
+    }
+    __syncthreads();
+    const int q = tid / G::LINES, line = tid % G::LINES;
+    const bool act = tid < Q * G::LINES;
+    // x direction, in place: A <- M~ v, B <- K~ v
+    auto xstage = [&](auto* Av, auto* Bv) {
+      using T = typename std::remove_reference<decltype(Av[0])>::type;
+      T v[NG];
+      sfor<0, NG>([&](auto c) { v[c] = Av[c + NG * line]; });
+      sfor<0, NG>([&](auto r) {
+        T am = 0, bk = 0;
+        sfor<0, NG>([&](auto c) {
+          constexpr int m = igrp<K, P, false>(r, c), kk = igrp<K, P, true>(r, c);
+          if constexpr (m != 0) am += (T)m * v[c];
+          if constexpr (kk != 0) bk += (T)kk * v[c];
+        });
+        Av[r + NG * line] = am;
+        Bv[r + NG * line] = bk;
+      });
+    };
+    if (act) {
+      xstage(A1[q], B1[q]);
+      xstage(A2[q], B2[q]);
+      xstage(A3[q], B3[q]);
+    }
+    __syncthreads();
+    if constexpr (DIM == 3) {
+      // y direction, in place: C = M~ A, D = M~ B + K~ A
+      auto ystage = [&](auto* Av, auto* Bv) {
+        using T = typename std::remove_reference<decltype(Av[0])>::type;
+        const int ix = line % NG, iz = line / NG;
+        T va[NG], vb[NG];
+        sfor<0, NG>([&](auto c) {
+          va[c] = Av[ix + NG * (c + NG * iz)];
+          vb[c] = Bv[ix + NG * (c + NG * iz)];
+        });
+        sfor<0, NG>([&](auto r) {
+          T cc = 0, dd = 0;
+          sfor<0, NG>([&](auto c) {
+            constexpr int m = igrp<K, P, false>(r, c), kk = igrp<K, P, true>(r, c);
+            if constexpr (m != 0) {
+              cc += (T)m * va[c];
+              dd += (T)m * vb[c];
+            }
+            if constexpr (kk != 0) dd += (T)kk * va[c];
+          });
+          Av[ix + NG * (r + NG * iz)] = cc;
+          Bv[ix + NG * (r + NG * iz)] = dd;
+        });
+      };
+      if (act) {
+        ystage(A1[q], B1[q]);
+        ystage(A2[q], B2[q]);
+        ystage(A3[q], B3[q]);
+      }
+      __syncthreads();
+    }
+    // last direction: out = M~ D + K~ C (3D) or M~ B + K~ A (2D), recombined in FP64
+    if (act) {
+      const int64_t grp = batch * Q + q;
+      if (grp < n_grp) {
+        const int ix = line % NG, iy = DIM == 3 ? line / NG : 0;
+        auto at = [&](int c) { return DIM == 3 ? ix + NG * (iy + NG * c) : ix + NG * c; };
+        int c1[NG], d1[NG], c2[NG], d2[NG];
+        float c3[NG], d3[NG];
+        sfor<0, NG>([&](auto c) {
+          c1[c] = A1[q][at(c)];
+          d1[c] = B1[q][at(c)];
+          c2[c] = A2[q][at(c)];
+          d2[c] = B2[q][at(c)];
+          c3[c] = A3[q][at(c)];
+          d3[c] = B3[q][at(c)];
+        });
+        const double sc = scl[q];
+        sfor<0, NG>([&](auto r) {
+          int o1 = 0, o2 = 0;
+          float o3 = 0.f;
+          sfor<0, NG>([&](auto c) {
+            constexpr int m = igrp<K, P, false>(r, c), kk = igrp<K, P, true>(r, c);
+            if constexpr (m != 0) {
+              o1 += m * d1[c];
+              o2 += m * d2[c];
+              o3 += (float)m * d3[c];
+            }
+            if constexpr (kk != 0) {
+              o1 += kk * c1[c];
+              o2 += kk * c2[c];
+              o3 += (float)kk * c3[c];
+            }
+          });
+          const double t = i64_to_double(((long long)o1 << 15) + (long long)o2) + f32_to_double(o3);
+          const double out = t * sc;
+          const int n = DIM == 3 ? ix + NG * (iy + NG * r) : ix + NG * r;
+          e += X[q][n] * out;
+          const int32_t id = grp_nodes[grp * NN + n];
+          const bool interior = ix > 0 && ix < NG - 1 && r > 0 && r < NG - 1 &&
+                                (DIM == 2 || (iy > 0 && iy < NG - 1));
+          if (interior && id >= 0)
+            y[id] = out;
+          else
+            scatter_node(id, out, y, a.yh);
+        });
+      }
+    }
+    __syncthreads();  // the next batch overwrites the shared arrays
+  }
+  if (energy_out) {
+    double s = block_sum<BS>(e, red);
+    finish_reduction<BS>(s, partials, counter, energy_out, accumulate);
+  }
+}
+
 template <int DIM, int K, int P>
 static void group_launch(const ActiveArgs& a, int64_t n, const int32_t* nodes, const double* coeff,
                          const uint8_t* level, const double* x, double* y, double* partials, unsigned* counter,
                          double* energy, bool accumulate, cudaStream_t s) {
   using G = AGrp<DIM, K, P>;
   static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
+  using GI = AGrpI<DIM, K, P>;
   static const bool init = [] {
-    cudaFuncSetAttribute(active_group_kernel<DIM, K, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)G::SMEM);
+    cudaFuncSetAttribute(active_group_int_kernel<DIM, K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)GI::SMEM);
     cudaFuncSetAttribute(active_group_kernel<DIM, K, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)G::SMEM);
     return true;
@@ -447,10 +736,12 @@ static void group_launch(const ActiveArgs& a, int64_t n, const int32_t* nodes, c
   (void)init;
   int64_t blocks = (n + G::Q - 1) / G::Q;
   if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
-  // cubic cells on every level (the ratios of the sides are those of the coarse cells)
+  // cubic cells on every level (the ratios of the sides are those of the coarse
+  // cells): one integer Kronecker sum; otherwise the FP64 kernel with
+  // per-direction factors
   const bool iso = a.scale[0][0] == a.scale[0][1] && (DIM == 2 || a.scale[0][1] == a.scale[0][2]);
   if (iso)
-    active_group_kernel<DIM, K, P, true><<<(unsigned)blocks, G::BS, G::SMEM, s>>>(
+    active_group_int_kernel<DIM, K, P><<<(unsigned)blocks, G::BS, GI::SMEM, s>>>(
         a, n, nodes, coeff, level, x, y, partials, counter, energy, accumulate);
   else
     active_group_kernel<DIM, K, P, false><<<(unsigned)blocks, G::BS, G::SMEM, s>>>(
