@@ -581,12 +581,30 @@ active_group_int_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
     if (tid < Q) emax[tid] = 1;
     __syncthreads();
-    for (int idx = tid; idx < Q * NN; idx += BS) {
-      const int q = idx / NN, n = idx % NN;
-      const int64_t grp = batch * Q + q;
-      const double v = grp < n_grp ? gather_node(grp_nodes[grp * NN + n], x, a.xh) : 0.0;
-      X[q][n] = v;
-      atomicMax(&emax[q], (int)((__double_as_longlong(v) >> 52) & 0x7FF));
+    {
+      // all node indices first, then all values: PER loads in flight per thread
+      constexpr int PER = (Q * NN + BS - 1) / BS;
+      int32_t ids[PER];
+      double vals[PER];
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int idx = tid + k * BS;
+        const int64_t grp = batch * Q + idx / NN;
+        ids[k] = (idx < Q * NN && grp < n_grp) ? grp_nodes[grp * NN + idx % NN] : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < PER; ++k) vals[k] = gather_node(ids[k], x, a.xh);
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const int idx = tid + k * BS;
+        const int qq = idx < Q * NN ? idx / NN : Q;  // lanes past the end form their own set
+        if (idx < Q * NN) X[qq][idx % NN] = vals[k];
+        // largest exponent per group: one shared atomic per group present in the warp
+        const int ex = (int)((__double_as_longlong(vals[k]) >> 52) & 0x7FF);
+        const unsigned same = __match_any_sync(0xffffffffu, qq);
+        const int mx = __reduce_max_sync(same, ex);
+        if (qq < Q && (threadIdx.x & 31) == __ffs(same) - 1) atomicMax(&emax[qq], mx);
+      }
     }
     __syncthreads();
     if (tid < Q) {

@@ -229,6 +229,40 @@ def test_active_apply(torch, name):
     assert rel_err(host(y), O.disc.A @ x) < 1e-12
 
 
+@pytest.mark.parametrize("name", NAMES)
+def test_active_apply_wide_range(torch, name):
+    """Inputs spanning sixteen decades, with exact zeros and subnormals: the
+    leaf operator stays within FP64 rounding of |A| |x| in the max norm (the
+    cubic-cell kernels split each group's values against its largest one)."""
+    O, H = gpu_hier(torch, name)
+    rng = np.random.default_rng(19)
+    n = O.disc.n
+    x = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-8, 8, n)
+    x[rng.random(n) < 0.1] = 0.0
+    x[rng.random(n) < 0.02] = 5e-324
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    H.apply(dev(torch, x), y)
+    torch.cuda.synchronize()
+    A = O.disc.A
+    bound = (abs(A) @ np.abs(x)).max()
+    assert np.all(np.isfinite(host(y)))
+    assert np.abs(host(y) - A @ x).max() <= 1e-13 * bound
+
+
+def test_active_apply_propagates_nan(torch):
+    O, H = gpu_hier(torch, "3d_q2_patches")
+    x = np.ones(O.disc.n)
+    x[O.disc.n // 2] = np.nan
+    y = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    H.apply(dev(torch, x), y)
+    torch.cuda.synchronize()
+    yh = host(y)
+    assert np.isnan(yh).any()
+    # the NaN reaches every row that couples to it
+    rows = O.disc.A[:, O.disc.n // 2].nonzero()[0]
+    assert np.all(np.isnan(yh[rows]))
+
+
 @pytest.mark.parametrize("name", [n for n in NAMES if small_workloads()[n].coeff is None])
 def test_rhs_sine(torch, name):
     O, H = gpu_hier(torch, name)
