@@ -206,6 +206,9 @@ static ActiveArgs active_args(const Hier& h) {
   a.grp_nodes = h.dev->grp_nodes;
   a.grp_coeff = h.dev->grp_coeff;
   a.grp_level = h.dev->grp_level;
+  a.loose_nodes = h.dev->loose_nodes;
+  a.loose_coeff = h.dev->loose_coeff;
+  a.loose_level = h.dev->loose_level;
   a.n_patches = h.dev->n_pat;
   a.pat_nodes = h.dev->pat_nodes;
   a.pat_coeff = h.dev->pat_coeff;
@@ -269,7 +272,8 @@ void device_free(Hier& h) {
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
                   d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level,
-                  d->pat_nodes, d->pat_coeff, d->pat_level, d->xh, d->yh, d->hm_node, d->hm_ptr,
+                  d->pat_nodes, d->pat_coeff, d->pat_level, d->loose_nodes, d->loose_coeff, d->loose_level,
+                  d->xh, d->yh, d->hm_node, d->hm_ptr,
                   d->hm_hang, d->hm_w};
   for (void* p : ptrs) cudaFree(p);
   if (d->scal_host) cudaFreeHost(d->scal_host);
@@ -442,6 +446,9 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->grp_nodes, A.grp_nodes));
   GMG_TRY(upload(d, &d->grp_coeff, A.grp_coeff));
   GMG_TRY(upload(d, &d->grp_level, A.grp_level));
+  GMG_TRY(upload(d, &d->loose_nodes, A.loose_nodes));
+  GMG_TRY(upload(d, &d->loose_coeff, A.loose_coeff));
+  GMG_TRY(upload(d, &d->loose_level, A.loose_level));
   GMG_TRY(upload(d, &d->pat_nodes, A.pat_nodes));
   GMG_TRY(upload(d, &d->pat_coeff, A.pat_coeff));
   GMG_TRY(upload(d, &d->pat_level, A.pat_level));

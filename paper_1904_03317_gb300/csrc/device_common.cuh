@@ -143,6 +143,9 @@ struct DeviceState {
   int32_t* grp_nodes = nullptr;
   double* grp_coeff = nullptr;
   uint8_t* grp_level = nullptr;
+  int32_t* loose_nodes = nullptr;
+  double* loose_coeff = nullptr;
+  uint8_t* loose_level = nullptr;
   int64_t n_pat = 0;
   int32_t* pat_nodes = nullptr;
   double* pat_coeff = nullptr;
@@ -210,6 +213,9 @@ struct ActiveArgs {
   const int32_t* grp_nodes;
   const double* grp_coeff;
   const uint8_t* grp_level;
+  const int32_t* loose_nodes;  // the cell_list cells as contiguous tables
+  const double* loose_coeff;
+  const uint8_t* loose_level;
   int64_t n_patches;         // leaf patches (4^d cells)
   const int32_t* pat_nodes;
   const double* pat_coeff;

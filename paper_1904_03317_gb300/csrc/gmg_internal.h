@@ -187,6 +187,10 @@ struct ActiveHost {
   std::vector<double> pat_coeff;
   std::vector<uint8_t> pat_level;
   std::vector<int32_t> loose_cells;  // leaf cells in neither a patch nor a full group
+  // the same cells as contiguous (k+1)^d node tables, coefficients and levels
+  std::vector<int32_t> loose_nodes;
+  std::vector<double> loose_coeff;
+  std::vector<uint8_t> loose_level;
 };
 
 struct DeviceState;  // defined in the CUDA translation units

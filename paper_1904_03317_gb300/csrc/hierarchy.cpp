@@ -791,6 +791,17 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     }
     A.n_groups = (int64_t)A.grp_coeff.size();
     A.n_patches = (int64_t)A.pat_coeff.size();
+    const size_t nl = A.loose_cells.size();
+    A.loose_nodes.resize(nl * NLOC);
+    A.loose_coeff.resize(nl);
+    A.loose_level.resize(nl);
+    for (size_t c = 0; c < nl; ++c) {
+      const int64_t cell = A.loose_cells[c];
+      std::copy(A.cell_nodes.begin() + cell * NLOC, A.cell_nodes.begin() + (cell + 1) * NLOC,
+                A.loose_nodes.begin() + c * NLOC);
+      A.loose_coeff[c] = A.cell_coeff[cell];
+      A.loose_level[c] = A.cell_level[cell];
+    }
   }
   // home slots
   A.home_slot.resize(nu);

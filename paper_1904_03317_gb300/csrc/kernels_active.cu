@@ -788,7 +788,13 @@ static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double*
     wrote = true;
   }
   const int64_t ncell = a.cell_list ? a.n_list : a.n_cells;
-  if (ncell > 0) {
+  const bool iso = a.scale[0][0] == a.scale[0][1] && (DIM == 2 || a.scale[0][1] == a.scale[0][2]);
+  if (ncell > 0 && iso && a.cell_list) {
+    // single cells of cubic shape: the split-integer kernel with one cell per group
+    group_launch<DIM, K, 1>(a, a.n_list, a.loose_nodes, a.loose_coeff, a.loose_level, x, y, partials, counter,
+                            energy, wrote, s);
+    wrote = true;
+  } else if (ncell > 0) {
     using G = ActGeo<DIM, K>;
     int64_t blocks = (ncell + G::CPB - 1) / G::CPB;
     if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
