@@ -167,6 +167,10 @@ def main():
     ap.add_argument("--adaptive-ref", type=int, default=ADAPTIVE_REF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker"],
+                    help="sphere: 3D Q2 Poisson refined at a sphere (the headline); checker: 3D Q2 with the "
+                         "{1, 100} subcube checkerboard coefficient refined at the subcube planes")
+    ap.add_argument("--finest-level", type=int, default=9, help="checker workload: finest level")
     ap.add_argument("--solve-mode", default="graph", choices=["graph", "stream"],
                     help="graph: each solve is one CUDA-graph launch; stream: one launch per kernel")
     args = ap.parse_args()
@@ -209,20 +213,26 @@ def main():
     from paper_1904_03317_gb300 import gmg as G
     from paper_1904_03317_gb300 import inputs
 
-    w = inputs.poisson3d_sphere(args.global_ref, args.adaptive_ref)
+    if args.workload == "sphere":
+        w = inputs.poisson3d_sphere(args.global_ref, args.adaptive_ref)
+    else:
+        w = inputs.checkerboard3d(args.global_ref, args.finest_level)
     t0 = time.perf_counter()
     mesh = G.build_mesh(w)
     t_mesh = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     ctx = G.Context(local, stream.cuda_stream)
     t0 = time.perf_counter()
-    H = G.Hierarchy(ctx, mesh, w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32,
+    H = G.Hierarchy(ctx, mesh, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32,
                     solve_graph=args.solve_mode == "graph")
     t_setup = time.perf_counter() - t0
     info = H.info
     n = H.n
     b = torch.empty(n, dtype=torch.float64, device="cuda")
-    H.assemble_rhs(b)
+    if w.rhs == "sine":
+        H.assemble_rhs(b)
+    else:  # seeded U[-1, 1) per unknown in canonical order
+        b.copy_(torch.from_numpy(inputs.random_rhs(w.seed, n)))
     x = torch.zeros_like(b)
     for _ in range(args.warmup):
         H.solve(b, x, tol=TOL)
@@ -274,7 +284,7 @@ def main():
     # ---- the FP64 V-cycle path on the same problem
     fp64 = None
     if not args.no_fp64:
-        H64 = G.Hierarchy(ctx, mesh, w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP64)
+        H64 = G.Hierarchy(ctx, mesh, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP64)
         x64 = torch.zeros_like(b)
         H64.solve(b, x64, tol=TOL)
         s64, st64 = time_solves(torch, H64, b, x64, max(1, min(args.steps, 3)), stream)
@@ -320,7 +330,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG",
             "data": "synthetic",
-            "config": {"workload": f"poisson3d_q2_sphere_g{args.global_ref}_a{args.adaptive_ref}",
+            "config": {"workload": w.name,
                        "unknowns": n, "leaves": int(info.n_leaves), "levels": int(info.n_levels),
                        "tol": TOL, "cheb_degree": w.cheb_degree, "cg_iterations": iters,
                        "parallelism": f"replicas x{world}", "solve_mode": args.solve_mode,
