@@ -162,6 +162,28 @@ gmg_status gmg_mesh_leaves(const gmg_mesh* mesh, int32_t* level, int32_t* coords
  * current number of leaves. */
 gmg_status gmg_mesh_refine(gmg_mesh* mesh, const uint8_t* flags, uint64_t n_flags);
 
+/* Partitioning efficiency model of Sec. 3.4 (Eq. for W and E): every cell of
+ * every level of the hierarchy is one unit of work.  The leaves, in
+ * gmg_mesh_leaves order (the space-filling curve), are split into n_parts
+ * contiguous pieces, part p taking leaves [p N / n_parts, (p+1) N / n_parts)
+ * in integer division; a refined cell belongs to the part that owns its
+ * first child, recursively (the first-child rule, Sec. 3.3).  With N_l the
+ * cells of level l and N_{l,p} those of part p:
+ *   w_opt = sum_l N_l / n_parts,  w_sync = sum_l ceil(N_l / n_parts),
+ *   w = sum_l max_p N_{l,p},      efficiency = w_opt / w.
+ * Level 0 stands for the coarse solve at one unit per coarse cell, as in the
+ * paper's worked example.  On one GPU, n_parts read as the number of
+ * resident cell batches makes w_sync / w_opt the predicted occupancy of a
+ * level-synchronous V-cycle.  Host only; n_parts in [1, 2^31).  Errors:
+ * GMG_EINVAL on a null argument or n_parts out of range. */
+typedef struct gmg_partition_model {
+  int n_levels;
+  double n_cells[GMG_MAX_LEVELS];  /* N_l */
+  double w_level[GMG_MAX_LEVELS];  /* max_p N_{l,p} */
+  double w_opt, w_sync, w, efficiency;
+} gmg_partition_model;
+gmg_status gmg_mesh_partition_model(const gmg_mesh* mesh, int64_t n_parts, gmg_partition_model* out);
+
 /* -------------------------------------------------------------- hierarchy */
 
 void gmg_params_default(gmg_params* p);

@@ -6,6 +6,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 
 #include "gmg_internal.h"
 
@@ -138,6 +139,52 @@ gmg_status gmg_mesh_leaves(const gmg_mesh* mesh, int32_t* level, int32_t* coords
     for (int d = 0; d < 3; ++d) coords[3 * i + d] = (int32_t)f.leaf_coords[3 * i + d];
   }
   return GMG_OK;
+}
+
+gmg_status gmg_mesh_partition_model(const gmg_mesh* mesh, int64_t n_parts, gmg_partition_model* out) {
+  CHECK_ARG(mesh && out, "null argument");
+  CHECK_ARG(n_parts >= 1 && n_parts < ((int64_t)1 << 31), "n_parts out of range");
+  GMG_GUARD_BEGIN
+  const Forest& f = mesh->f;
+  const int L = f.num_levels();
+  CHECK_ARG(L <= GMG_MAX_LEVELS, "too many levels");
+  const int64_t nleaf = (int64_t)f.leaf_level.size();
+  // owner of every cell, finest level first (first-child rule)
+  std::vector<std::unordered_map<uint64_t, int64_t>> own(L);
+  for (int64_t i = 0; i < nleaf; ++i) {
+    const int64_t* c = &f.leaf_coords[3 * i];
+    own[f.leaf_level[i]][pack3(c[0], c[1], c[2])] = (int64_t)((__int128)i * n_parts / nleaf);
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->n_levels = L;
+  std::unordered_map<int64_t, int64_t> counts;
+  for (int l = L - 1; l >= 0; --l) {
+    f.cells[l].for_each([&](uint64_t k, int32_t refined) {
+      if (!refined) return;
+      int64_t c[3];
+      unpack3(k, c);
+      const int64_t first[3] = {2 * c[0], f.dim > 1 ? 2 * c[1] : 0, f.dim > 2 ? 2 * c[2] : 0};
+      own[l][k] = own[l + 1].at(pack3(first[0], first[1], first[2]));
+    });
+    counts.clear();
+    int64_t nl = 0, wl = 0;
+    for (const auto& kv : own[l]) {
+      wl = std::max(wl, ++counts[kv.second]);
+      ++nl;
+    }
+    out->n_cells[l] = (double)nl;
+    out->w_level[l] = (double)wl;
+  }
+  double tot = 0.0;
+  for (int l = 0; l < L; ++l) {
+    tot += out->n_cells[l];
+    out->w_sync += std::ceil(out->n_cells[l] / (double)n_parts);
+    out->w += out->w_level[l];
+  }
+  out->w_opt = tot / (double)n_parts;
+  out->efficiency = out->w > 0 ? out->w_opt / out->w : 0.0;
+  return GMG_OK;
+  GMG_GUARD_END
 }
 
 gmg_status gmg_mesh_refine(gmg_mesh* mesh, const uint8_t* flags, uint64_t n_flags) {

@@ -905,15 +905,20 @@ struct Brick2S {
   static constexpr int T2 = B::HB * ZS;
   static constexpr int XO = B::OB * B::OB * B::OB;
   static constexpr size_t bytes() { return (size_t)(T1 + T2) * sizeof(float2) + XO * sizeof(float) + 64 * 4 + 8 * 8 + 16; }
+  // threads per brick (64 was measured slower: fewer warps to hide latency)
+  static constexpr int TB = 128;
+  static constexpr int R = TB / B::L3 > 0 ? TB / B::L3 : 1;
+  static constexpr int OPT = (B::OB + R - 1) / R;
 };
 
 template <int K, int MODE>
-__global__ void __launch_bounds__(BrickG<K>::TB)
+__global__ void __launch_bounds__(Brick2S<K>::TB)
 level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float* xprev,
                            const float* __restrict__ gvec, float* out, float c1, float c2) {
   using B = BrickG<K>;
   using S = Brick2S<K>;
-  constexpr int NO = B::NO, OB = B::OB, HB = B::HB, TB = B::TB, L3 = B::L3, R = B::R, OPT = B::OPT;
+  constexpr int NO = B::NO, OB = B::OB, HB = B::HB, TB = S::TB, L3 = B::L3, R = S::R, OPT = S::OPT;
+  static_assert(TB >= 64, "the brick table is loaded by 64 threads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* T1 = reinterpret_cast<float2*>(smem_raw);
   float2* T2 = T1 + S::T1;
@@ -1004,16 +1009,21 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
   if (!has_out) return;
   float2 pq[HB];
   static_for<0, HB>([&](auto z) { pq[z] = T2[z * S::ZS + ol]; });
-  float c2d = 0.f;
+  // the diagonal depends on the node only through index parities: one
+  // reciprocal per parity of k
+  float c2d[2] = {0.f, 0.f};
   if constexpr (MODE == 1) {
     const float md0 = (float)bbrick<K, false>(0, K), kd0 = (float)bbrick<K, true>(0, K);
     const float md1 = (float)bbrick<K, false>(1, K + 1), kd1 = (float)bbrick<K, true>(1, K + 1);
     const float mdx = (oi & 1) ? md1 : md0, kdx = (oi & 1) ? kd1 : kd0;
     const float mdy = (oj & 1) ? md1 : md0, kdy = (oj & 1) ? kd1 : kd0;
-    const float mdz = (part & 1) ? md1 : md0, kdz = (part & 1) ? kd1 : kd0;
-    c2d = c2 / (coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz));
+#pragma unroll
+    for (int pz = 0; pz < 2; ++pz) {
+      if (R % 2 == 0 && pz != (part & 1)) continue;
+      const float mdz = pz ? md1 : md0, kdz = pz ? kd1 : kd0;
+      c2d[pz] = c2 / (coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz));
+    }
   }
-  static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share the parity of k");
 #pragma unroll
   for (int o = 0; o < OPT; ++o) {
     const int kk = part + R * o;
@@ -1037,7 +1047,7 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
       out[slots[o]] = y;
     } else {
       const float xv = Xown[oi + OB * (oj + OB * kk)];
-      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2d * (pre_g[o] - y);
+      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2d[kk & 1] * (pre_g[o] - y);
     }
   }
 }
@@ -1451,8 +1461,8 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
                                (int)sm);
           init = true;
         }
-        level_cheb_brick_f2_kernel<K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1,
-                                                                                            c2);
+        level_cheb_brick_f2_kernel<K, MODE><<<(unsigned)a.n_bricks, Brick2S<K>::TB, sm, s>>>(a, x, xprev, g, out,
+                                                                                             c1, c2);
         GMG_COUNT_LAUNCH();
       } else {
         const size_t sm = BrickSmem<T, K>::bytes();

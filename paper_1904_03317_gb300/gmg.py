@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5:
 EXPORTED = [
     "gmg_create", "gmg_destroy", "gmg_last_error", "gmg_build_info",
     "gmg_mesh_create", "gmg_mesh_destroy", "gmg_mesh_num_leaves", "gmg_mesh_num_levels",
-    "gmg_mesh_leaves", "gmg_mesh_refine",
+    "gmg_mesh_leaves", "gmg_mesh_refine", "gmg_mesh_partition_model",
     "gmg_params_default", "gmg_hier_build", "gmg_hier_destroy", "gmg_hier_info", "gmg_hier_export",
     "gmg_assemble_rhs", "gmg_apply", "gmg_vcycle", "gmg_solve",
     "gmg_level_apply", "gmg_level_residual_restrict", "gmg_level_prolongate", "gmg_level_smooth",
@@ -58,6 +58,11 @@ class ParamsC(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("eig_lo", C.c_double), ("eig_hi", C.c_double),
                 ("eig_iters", C.c_int), ("vcycle_prec", C.c_int),
                 ("fixed_lambda", C.POINTER(C.c_double)), ("solve_graph", C.c_int)]
+
+
+class PartitionModelC(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("n_cells", C.c_double * MAX_LEVELS), ("w_level", C.c_double * MAX_LEVELS),
+                ("w_opt", C.c_double), ("w_sync", C.c_double), ("w", C.c_double), ("efficiency", C.c_double)]
 
 
 class InfoC(C.Structure):
@@ -108,6 +113,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "gmg_mesh_num_levels": [vp, C.POINTER(i32)],
         "gmg_mesh_leaves": [vp, vp, vp],
         "gmg_mesh_refine": [vp, vp, u64],
+        "gmg_mesh_partition_model": [vp, C.c_int64, C.POINTER(PartitionModelC)],
         "gmg_params_default": [C.POINTER(ParamsC)],
         "gmg_hier_build": [vp, vp, i32, vp, C.POINTER(ParamsC), C.POINTER(vp)],
         "gmg_hier_destroy": [vp],
@@ -209,6 +215,15 @@ class Mesh:
         coords = np.zeros((n, 3), dtype=np.int32)
         _check(load_library().gmg_mesh_leaves(self.handle, _ptr(level), _ptr(coords)), "gmg_mesh_leaves")
         return level, coords
+
+    def partition_model(self, n_parts: int) -> dict:
+        """Partitioning efficiency model (W_opt, W_sync, W, E) for n_parts parts."""
+        m = PartitionModelC()
+        _check(load_library().gmg_mesh_partition_model(self.handle, int(n_parts), C.byref(m)),
+               "gmg_mesh_partition_model")
+        L = m.n_levels
+        return {"n_cells": [int(v) for v in m.n_cells[:L]], "w_level": [int(v) for v in m.w_level[:L]],
+                "w_opt": m.w_opt, "w_sync": m.w_sync, "w": m.w, "efficiency": m.efficiency}
 
     def refine(self, flags) -> None:
         f = np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
