@@ -22,7 +22,21 @@ notes of the repository):
   level(x) = the coarsest level of the leaves containing x, where it is an
   S-node; g^I = 0 on every level (the residual r^L is deferred to the lower
   levels, Sec. 2.3).
-* Coarse solve: dense Cholesky of A_0 (a "direct solver", Sec. 2.2).
+* Coarse solve: dense Cholesky of A_0 (a "direct solver", Sec. 2.2) by
+  default.  Variants:
+  - Chebyshev (Sec. 4.1): Chebyshev-Jacobi on A_0 over [lmin, 1.2 lmax]
+    where lmin, lmax are the extreme Ritz values of D^{-1} A_0 from a
+    Jacobi-preconditioned CG run on A_0 y = b0 (the start pattern above) to
+    the relative unpreconditioned residual 1e-3; degree
+    m = ceil(ln(2 / eps) / ln((sqrt(k) + 1) / (sqrt(k) - 1))), k = 1.2 lmax /
+    lmin, eps = 1e-3, from the a-priori bound 2 ((sqrt(k) - 1) / (sqrt(k) +
+    1))^m <= eps on the reduction (the paper names the bound, not the
+    formula; the 1.2 safety factor on lmax is this reading's).
+  - CG (Sec. 4.3, "MF"): unpreconditioned CG on A_0 from zero to the
+    relative residual coarse_tol (the paper gives no tolerance; 1e-3 is this
+    reading's default, matching the Chebyshev variant's target reduction).
+* Smoother variant (Sec. 4.3, "MF"): m undamped Jacobi steps
+  x <- x + D^{-1} (g - A x) instead of Chebyshev.
 """
 from __future__ import annotations
 
@@ -95,6 +109,75 @@ def estimate_lambda_max(A, dinv, b0, iters: int = 10) -> float:
     return float(np.linalg.eigvalsh(T)[-1])
 
 
+def jacobi(A, dinv, x0, b, steps, x0_is_zero=False):
+    """``steps`` undamped Jacobi updates x <- x + D^{-1} (b - A x) (Sec. 4.3)."""
+    x = np.zeros_like(b) if x0_is_zero else np.array(x0, dtype=np.float64, copy=True)
+    for _ in range(steps):
+        x = x + dinv * (b - A @ x)
+    return x
+
+
+def lanczos_extremes(A, dinv, b0, rtol: float):
+    """Smallest and largest Ritz values of D^{-1} A from Jacobi-PCG on A y = b0,
+    stopped when ||r|| <= rtol ||b0|| (unpreconditioned) or after n steps."""
+    n = A.shape[0]
+    r = np.array(b0, dtype=np.float64, copy=True)
+    nb = float(np.linalg.norm(r))
+    z = dinv * r
+    p = z.copy()
+    rz = float(r @ z)
+    alphas, betas = [], []
+    for j in range(n):
+        Ap = A @ p
+        alpha = rz / float(p @ Ap)
+        alphas.append(alpha)
+        r = r - alpha * Ap
+        if float(np.linalg.norm(r)) <= rtol * nb or j == n - 1:
+            break
+        z = dinv * r
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        betas.append(beta)
+        p = z + beta * p
+        rz = rz_new
+    m = len(alphas)
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1])
+
+
+def chebyshev_degree(kappa: float, eps: float) -> int:
+    """Smallest m with 2 ((sqrt(k) - 1) / (sqrt(k) + 1))^m <= eps."""
+    q = (np.sqrt(kappa) + 1.0) / (np.sqrt(kappa) - 1.0)
+    return int(np.ceil(np.log(2.0 / eps) / np.log(q)))
+
+
+def cg_plain(A, b, rtol: float):
+    """Unpreconditioned CG from zero to ||r|| <= rtol ||b|| (at most n steps)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    nb = float(np.linalg.norm(b))
+    if nb == 0.0:
+        return x
+    p = r.copy()
+    rr = float(r @ r)
+    for _ in range(len(b)):
+        Ap = A @ p
+        alpha = rr / float(p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = float(r @ r)
+        if np.sqrt(rr_new) <= rtol * nb:
+            break
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x
+
+
 def eigen_start_vector(n: int) -> np.ndarray:
     """(-5.5, -4.5, ..., 5.5, -5.5, ...) of length n (Sec. 4.1)."""
     return -5.5 + (np.arange(n) % 12).astype(np.float64)
@@ -125,6 +208,41 @@ class Hierarchy:
     eig_lo: float = 0.08
     eig_hi: float = 1.2
     coarse_chol: object = None
+    smoother: str = "chebyshev"      # or "jacobi"
+    coarse: str = "cholesky"         # or "chebyshev", "cg"
+    coarse_tol: float = 1e-3
+    coarse_range: tuple = None       # (lmin, 1.2 lmax) of D^{-1} A_0 for the Chebyshev coarse solver
+    coarse_degree: int = 0
+    coarse_dinv: np.ndarray = None
+
+
+def setup_coarse(H: "Hierarchy", coarse: str, coarse_tol: float = 1e-3) -> None:
+    """Choose the coarse solver (Sec. 2.2 direct, Sec. 4.1 Chebyshev, Sec. 4.3 CG)."""
+    H.coarse, H.coarse_tol = coarse, coarse_tol
+    A0 = H.levels[0].A
+    H.coarse_dinv = 1.0 / A0.diagonal()
+    if coarse == "chebyshev":
+        lmin, lmax = lanczos_extremes(A0, H.coarse_dinv, eigen_start_vector(A0.shape[0]), coarse_tol)
+        H.coarse_range = (lmin, 1.2 * lmax)
+        H.coarse_degree = chebyshev_degree(1.2 * lmax / lmin, coarse_tol)
+
+
+def coarse_solve(H: "Hierarchy", g0: np.ndarray) -> np.ndarray:
+    A0 = H.levels[0].A
+    if H.coarse == "chebyshev":
+        a, b = H.coarse_range
+        return chebyshev(A0, H.coarse_dinv, np.zeros_like(g0), g0, 1.0, H.coarse_degree, x0_is_zero=True,
+                         lo=a, hi=b)
+    if H.coarse == "cg":
+        return cg_plain(A0, g0, H.coarse_tol)
+    return sla.cho_solve(H.coarse_chol, g0)
+
+
+def smooth(H: "Hierarchy", lev: "Level", x0, g, x0_is_zero: bool):
+    if H.smoother == "jacobi":
+        return jacobi(lev.A_S, lev.dinv, x0, g, H.cheb_degree, x0_is_zero)
+    return chebyshev(lev.A_S, lev.dinv, x0, g, lev.lam, H.cheb_degree, x0_is_zero=x0_is_zero,
+                     lo=H.eig_lo, hi=H.eig_hi)
 
 
 def build_hierarchy(disc: Discretization, cheb_degree: int, eig_iters: int = 10,
@@ -176,21 +294,19 @@ def vcycle(H: Hierarchy, r: np.ndarray) -> np.ndarray:
     for l in range(L, 0, -1):
         x = lv[l]
         # pre-smoothing on V^S from zero; u^I stays 0
-        u[l][x.S] = chebyshev(x.A_S, x.dinv, np.zeros(len(x.S)), g[l][x.S], x.lam, m,
-                              x0_is_zero=True, lo=H.eig_lo, hi=H.eig_hi)
+        u[l][x.S] = smooth(H, x, np.zeros(len(x.S)), g[l][x.S], True)
         # residual on S u I: t^S = g^S - A^S u^S, t^I = g^I - A^IS u^S
         t = np.zeros(len(x.keys))
         t[x.S] = g[l][x.S] - x.A_S @ u[l][x.S]
         t[x.I] = g[l][x.I] - x.A_IS @ u[l][x.S]
         g[l - 1] += x.P.T @ t  # R = P^T
-    u[0] = sla.cho_solve(H.coarse_chol, g[0])
+    u[0] = coarse_solve(H, g[0])
     for l in range(1, L + 1):
         x = lv[l]
         u[l] += x.P @ u[l - 1]
         # post-smoothing on V^S with the edge term A^SI u^I moved to the right
         gs = g[l][x.S] - x.A_SI @ u[l][x.I]
-        u[l][x.S] = chebyshev(x.A_S, x.dinv, u[l][x.S], gs, x.lam, m,
-                              lo=H.eig_lo, hi=H.eig_hi)
+        u[l][x.S] = smooth(H, x, u[l][x.S], gs, False)
     z = np.zeros_like(r)
     for l in range(L + 1):
         sel = np.nonzero(H.disc.home_level == l)[0]
