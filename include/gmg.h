@@ -70,6 +70,13 @@ typedef struct gmg_coarse_mesh {
 typedef enum gmg_precision { GMG_PREC_FP64 = 0, GMG_PREC_FP32 = 1 } gmg_precision;
 
 /* Solver parameters (defaults from Sec. 4.1 of the paper). */
+/* smoothers and coarse solvers (gmg_params.smoother, .coarse_solver) */
+#define GMG_SMOOTHER_CHEBYSHEV 0
+#define GMG_SMOOTHER_JACOBI 1
+#define GMG_COARSE_CHOLESKY 0
+#define GMG_COARSE_CHEBYSHEV 1
+#define GMG_COARSE_CG 2
+
 typedef struct gmg_params {
   int cheb_degree;            /* m: Chebyshev updates per smoothing (Sec. 4.1 uses 5); >= 1 */
   double eig_lo;              /* damping range [eig_lo, eig_hi] x lambda_max: 0.08 */
@@ -79,6 +86,18 @@ typedef struct gmg_params {
   const double* fixed_lambda; /* optional host array, one value per level (index 0
                                  unused): use these lambda_max instead of estimating.
                                  NULL = estimate. Copied during gmg_hier_build. */
+  int smoother;               /* GMG_SMOOTHER_CHEBYSHEV (default; Sec. 4.1) or GMG_SMOOTHER_JACOBI:
+                                 cheb_degree undamped Jacobi steps x += D^-1 (g - A x), the
+                                 "MF" setting of Sec. 4.3 with cheb_degree = 1 */
+  int coarse_solver;          /* GMG_COARSE_CHOLESKY (default; "direct solver", Sec. 2.2),
+                                 GMG_COARSE_CHEBYSHEV (Sec. 4.1: Chebyshev-Jacobi over
+                                 [lmin, 1.2 lmax] of D^-1 A_0 from a Jacobi-PCG run to the
+                                 relative residual coarse_tol, degree from the a-priori bound
+                                 2 ((sqrt k - 1)/(sqrt k + 1))^m <= coarse_tol; at most 2048
+                                 coarse unknowns) or GMG_COARSE_CG (Sec. 4.3: unpreconditioned
+                                 CG from zero to the relative residual coarse_tol, on one
+                                 thread block; at most 4096 coarse unknowns) */
+  double coarse_tol;          /* default 1e-3 */
   int solve_graph;            /* 1 (default): gmg_solve runs the whole CG loop as one CUDA
                                  graph whose loop is controlled on the device (a conditional
                                  WHILE node): one launch and one synchronisation per solve.
@@ -115,6 +134,9 @@ typedef struct gmg_info {
    * (the grandchildren of one cell, all leaves), full sibling groups of 2^d
    * leaf cells, and single cells */
   uint64_t leaf_patches, leaf_groups, leaf_single_cells;
+  /* Chebyshev coarse solver: degree and eigenvalue range [lmin, 1.2 lmax] */
+  int coarse_degree;
+  double coarse_range[2];
 } gmg_info;
 
 typedef struct gmg_stats {

@@ -219,6 +219,9 @@ void gmg_params_default(gmg_params* p) {
   p->eig_iters = 10;
   p->vcycle_prec = GMG_PREC_FP32;
   p->fixed_lambda = nullptr;
+  p->smoother = GMG_SMOOTHER_CHEBYSHEV;
+  p->coarse_solver = GMG_COARSE_CHOLESKY;
+  p->coarse_tol = 1e-3;
   p->solve_graph = 1;
 }
 
@@ -234,6 +237,11 @@ gmg_status gmg_hier_build(gmg_ctx* ctx, const gmg_mesh* mesh, int degree, const 
   CHECK_ARG(prm.eig_iters >= 1 && prm.eig_iters <= 1000, "eig_iters out of range");
   CHECK_ARG(prm.eig_lo > 0 && prm.eig_hi > prm.eig_lo, "need 0 < eig_lo < eig_hi");
   CHECK_ARG(prm.vcycle_prec == GMG_PREC_FP32 || prm.vcycle_prec == GMG_PREC_FP64, "bad vcycle_prec");
+  CHECK_ARG(prm.smoother == GMG_SMOOTHER_CHEBYSHEV || prm.smoother == GMG_SMOOTHER_JACOBI, "bad smoother");
+  CHECK_ARG(prm.coarse_solver == GMG_COARSE_CHOLESKY || prm.coarse_solver == GMG_COARSE_CHEBYSHEV ||
+                prm.coarse_solver == GMG_COARSE_CG,
+            "bad coarse_solver");
+  CHECK_ARG(prm.coarse_tol > 0.0 && prm.coarse_tol < 1.0, "coarse_tol must be in (0, 1)");
   const Forest& f = mesh->f;
   CHECK_ARG(f.num_levels() <= GMG_MAX_LEVELS, "too many levels");
   GMG_GUARD_BEGIN
@@ -270,9 +278,10 @@ gmg_status gmg_hier_build(gmg_ctx* ctx, const gmg_mesh* mesh, int degree, const 
     delete hh;
     throw;
   }
-  if (h.n_coarse > 25600) {
+  if (h.coarse_too_large) {
     delete hh;
-    set_error("coarse level too large for the dense coarse solve (> 25600 unknowns)");
+    set_error("coarse level too large for the chosen coarse solver (Cholesky: 25600, Chebyshev: 2048, "
+              "CG: 4096 unknowns)");
     return GMG_EUNSUPPORTED;
   }
   if (ctx->c.device >= 0) {
@@ -335,6 +344,9 @@ gmg_status gmg_hier_info(const gmg_hier* hh, gmg_info* info) {
   info->leaf_patches = (uint64_t)h.active.n_patches;
   info->leaf_groups = (uint64_t)h.active.n_groups;
   info->leaf_single_cells = h.active.loose_cells.size();
+  info->coarse_degree = h.coarse_degree;
+  info->coarse_range[0] = h.coarse_range[0];
+  info->coarse_range[1] = h.coarse_range[1];
   return GMG_OK;
 }
 

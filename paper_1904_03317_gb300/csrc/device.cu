@@ -269,7 +269,7 @@ void device_free(Hier& h) {
     cudaFree(L.list_jump);
     cudaFree(L.list_rest);
   }
-  void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->cell_nodes, d->cell_coeff, d->cell_level,
+  void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->coarse_ptr, d->coarse_col, d->coarse_val, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
                   d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level,
                   d->pat_nodes, d->pat_coeff, d->pat_level, d->loose_nodes, d->loose_coeff, d->loose_level,
@@ -412,6 +412,9 @@ gmg_status device_setup(Hier& h) {
   for (int dd = 0; dd < 3; ++dd) d->coarse_lat[dd] = h.coarse_lattice[dd];
   d->n_coarse = h.n_coarse;
   GMG_TRY(upload(d, &d->coarse_inv, h.coarse_inverse));
+  GMG_TRY(upload(d, &d->coarse_ptr, h.coarse_ptr));
+  GMG_TRY(upload(d, &d->coarse_col, h.coarse_col));
+  GMG_TRY(upload(d, &d->coarse_val, h.coarse_val));
   // level vectors
   const size_t esz = d->prec == GMG_PREC_FP32 ? sizeof(float) : sizeof(double);
   const int64_t ns = h.total_slots;
@@ -543,6 +546,18 @@ gmg_status device_setup(Hier& h) {
   return GMG_OK;
 }
 
+// ------------------------------------------------------------ coarse solve
+// u_0 = A_0^{-1} g_0 by the dense inverse (or the dense Chebyshev operator),
+// or by the unpreconditioned CG kernel; level-0 lattice slots in and out.
+template <typename T>
+static cudaError_t coarse(const Hier& h, const T* g0, T* u0, cudaStream_t s) {
+  const DeviceState* d = h.dev;
+  if (h.params.coarse_solver == GMG_COARSE_CG)
+    return launch_coarse_cg<T>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_ptr, d->coarse_col, d->coarse_val,
+                               h.params.coarse_tol, g0, u0, s);
+  return launch_coarse_solve<T>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv, g0, u0, s);
+}
+
 // ------------------------------------------------------------- smoothing
 // m Chebyshev updates on level l: x_{j+1} = x_j + rho_j rho_{j-1} (x_j - x_{j-1})
 // + (2 rho_j / delta) D^{-1} (g - A x_j), x_1 = x_0 + D^{-1}(g - A x_0) / theta
@@ -561,18 +576,21 @@ static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cu
   // x (S and I), x_prev, g and the new x on S nodes; D^-1 is read only by
   // groups at coefficient jumps (the others recompute it)
   const double cheb_bytes = sizeof(T) * (4.0 * D.n_S + D.n_S_jump + D.n_I);
+  // undamped Jacobi (Sec. 4.3): every step x <- x + D^{-1} (g - A x)
+  const bool jacobi = h.params.smoother == GMG_SMOOTHER_JACOBI;
+  const double first = jacobi ? 1.0 : 1.0 / D.theta;
   if (from_zero) {
     Track t(h.dev, GMG_K_SMOOTH_FIRST, 3.0 * sizeof(T) * D.n_slots, 2.0 * D.n_slots);
-    e = launch_scale_vec<T>(D.n_slots, dinv, g, (T)(1.0 / D.theta), cur, s);
+    e = launch_scale_vec<T>(D.n_slots, dinv, g, (T)first, cur, s);
   } else {
     Track t(h.dev, GMG_K_CHEB, cheb_bytes, D.cheb_flops);
-    e = launch_level_cheb<T>(h.dim, h.k, a, cur, nullptr, g, dinv, other, (T)0, (T)(1.0 / D.theta), false, s);
+    e = launch_level_cheb<T>(h.dim, h.k, a, cur, nullptr, g, dinv, other, (T)0, (T)first, false, s);
     std::swap(cur, other);
   }
   if (e != cudaSuccess) return e;
   for (int j = 1; j < m; ++j) {
     double rho_new = 1.0 / (2.0 * D.sigma - rho);
-    T c1 = (T)(rho_new * rho), c2 = (T)(2.0 * rho_new / D.delta);
+    T c1 = jacobi ? (T)0 : (T)(rho_new * rho), c2 = jacobi ? (T)1 : (T)(2.0 * rho_new / D.delta);
     Track t(h.dev, GMG_K_CHEB, cheb_bytes, D.cheb_flops);
     e = launch_level_cheb<T>(h.dim, h.k, a, cur, other, g, dinv, other, c1, c2, false, s);
     if (e != cudaSuccess) return e;
@@ -617,7 +635,7 @@ static gmg_status vcycle_impl(Hier& h, const double* r, double* z, double* rz_ou
   {
     const double nc = (double)d->n_coarse;
     Track t(d, GMG_K_COARSE, 8.0 * nc * nc + 2.0 * sizeof(T) * nc, 2.0 * nc * nc);
-    GMG_CUDA_TRY(launch_coarse_solve<T>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv, g, uB, s));
+    GMG_CUDA_TRY(coarse<T>(h, g, uB, s));
   }
   for (int l = 1; l <= L; ++l) {
     const LevelDev& D = d->lv[l];
@@ -1023,11 +1041,8 @@ gmg_status device_level_inv_diag(Hier& h, int l, void* out) {
 
 gmg_status device_coarse_solve(Hier& h, const void* g0, void* u0) {
   DeviceState* d = h.dev;
-  cudaError_t e = d->prec == GMG_PREC_FP32
-                      ? launch_coarse_solve<float>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv,
-                                                   (const float*)g0, (float*)u0, d->stream)
-                      : launch_coarse_solve<double>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv,
-                                                    (const double*)g0, (double*)u0, d->stream);
+  cudaError_t e = d->prec == GMG_PREC_FP32 ? coarse<float>(h, (const float*)g0, (float*)u0, d->stream)
+                                           : coarse<double>(h, (const double*)g0, (double*)u0, d->stream);
   GMG_CUDA_TRY(e);
   return GMG_OK;
 }

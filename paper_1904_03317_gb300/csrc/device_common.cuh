@@ -130,6 +130,9 @@ struct DeviceState {
   void* dinv = nullptr;
   // coarse level
   double* coarse_inv = nullptr;  // n_coarse^2
+  int32_t* coarse_ptr = nullptr;  // CG coarse solver: A_0 in CSR
+  int32_t* coarse_col = nullptr;
+  double* coarse_val = nullptr;
   int64_t n_coarse = 0;
   int64_t coarse_lat[3] = {1, 1, 1};
   // active (leaf) mesh
@@ -255,6 +258,9 @@ cudaError_t launch_copy_from_mg(int64_t n, const T* u, const uint32_t* home, con
 template <typename T>
 cudaError_t launch_coarse_solve(int dim, int64_t n_coarse, const int64_t lat[3],
                                 const double* inv, const T* g0, T* u0, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_cg(int dim, int64_t nc, const int64_t lat[3], const int32_t* ptr, const int32_t* col,
+                             const double* val, double tol, const T* g0, T* u0, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, cudaStream_t s);
 cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials,

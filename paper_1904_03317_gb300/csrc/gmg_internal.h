@@ -211,7 +211,13 @@ struct Hier {
   // coarse level: lattice (k n0 + 1)^d; interior nodes are the unknowns of A_0
   int64_t coarse_lattice[3] = {1, 1, 1};
   int64_t n_coarse = 0;
-  std::vector<double> coarse_inverse;  // n_coarse^2, row-major
+  std::vector<double> coarse_inverse;  // n_coarse^2, row-major: A_0^-1, or the Chebyshev coarse operator
+  // unpreconditioned CG coarse solver: A_0 in CSR
+  std::vector<int32_t> coarse_ptr, coarse_col;
+  std::vector<double> coarse_val;
+  int coarse_degree = 0;
+  double coarse_range[2] = {0, 0};
+  bool coarse_too_large = false;  // the chosen coarse solver does not take this many unknowns
   std::vector<double> lambda;          // per level
   double setup_host_s = 0, setup_device_s = 0;
   DeviceState* dev = nullptr;
@@ -229,6 +235,10 @@ void build_host_hierarchy(Hier& h, const Forest& f);
 void reference_1d(int k, std::vector<double>& M, std::vector<double>& K, std::vector<double>& E);
 // dense SPD inverse via Cholesky (returns false if not SPD)
 bool spd_inverse(std::vector<double>& A, int64_t n);
+// Chebyshev-Jacobi coarse operator of Sec. 4.1 (dense, row-major): the linear
+// map g -> u of the iteration from zero; sets degree and range
+void chebyshev_coarse_operator(const std::vector<double>& A, int64_t n, double tol, std::vector<double>& C,
+                               int& degree, double range[2]);
 double tridiag_max_eig(const std::vector<double>& diag, const std::vector<double>& off);
 
 // device side (device.cu)

@@ -128,9 +128,16 @@ bool spd_inverse(std::vector<double>& A, int64_t n) {
   return true;
 }
 
+// smallest (largest = false) or largest eigenvalue of the symmetric
+// tridiagonal (diag a, off-diagonal b) by Sturm-sequence bisection on a
+// Gershgorin interval
+static double tridiag_extreme_eig(const std::vector<double>& a, const std::vector<double>& b, bool largest);
+
 double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
-  // largest eigenvalue of the symmetric tridiagonal (diag a, off-diagonal b)
-  // by Sturm-sequence bisection on a Gershgorin interval
+  return tridiag_extreme_eig(a, b, true);
+}
+
+static double tridiag_extreme_eig(const std::vector<double>& a, const std::vector<double>& b, bool largest) {
   size_t m = a.size();
   if (m == 0) return 0.0;
   double lo = a[0], hi = a[0];
@@ -150,12 +157,94 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
     }
     return cnt;
   };
+  const int want = largest ? (int)m : 1;  // eigenvalues below the answer's upper bracket
   for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
     double mid = 0.5 * (lo + hi);
-    if (count_below(mid) >= (int)m) hi = mid;
+    if (count_below(mid) >= want) hi = mid;
     else lo = mid;
   }
   return 0.5 * (lo + hi);
+}
+
+void chebyshev_coarse_operator(const std::vector<double>& A, int64_t n, double tol, std::vector<double>& C,
+                               int& degree, double range[2]) {
+  std::vector<double> dinv(n);
+  for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / A[i * n + i];
+  auto matvec = [&](const std::vector<double>& x, std::vector<double>& y) {
+    for (int64_t i = 0; i < n; ++i) {
+      double t = 0.0;
+      for (int64_t j = 0; j < n; ++j) t += A[i * n + j] * x[j];
+      y[i] = t;
+    }
+  };
+  // Jacobi-PCG on A y = b0 (the start pattern of the eigenvalue estimate) to
+  // the relative unpreconditioned residual tol; Lanczos tridiagonal
+  std::vector<double> r(n), z(n), p(n), Ap(n);
+  double nb = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    r[i] = -5.5 + (double)(i % 12);
+    nb += r[i] * r[i];
+  }
+  nb = std::sqrt(nb);
+  for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i], p[i] = z[i];
+  double rz = 0.0;
+  for (int64_t i = 0; i < n; ++i) rz += r[i] * z[i];
+  std::vector<double> alphas, betas;
+  for (int64_t j = 0; j < n; ++j) {
+    matvec(p, Ap);
+    double pAp = 0.0;
+    for (int64_t i = 0; i < n; ++i) pAp += p[i] * Ap[i];
+    const double alpha = rz / pAp;
+    alphas.push_back(alpha);
+    double rr = 0.0;
+    for (int64_t i = 0; i < n; ++i) r[i] -= alpha * Ap[i], rr += r[i] * r[i];
+    if (std::sqrt(rr) <= tol * nb || j == n - 1) break;
+    double rz_new = 0.0;
+    for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i], rz_new += r[i] * z[i];
+    const double beta = rz_new / rz;
+    betas.push_back(beta);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    rz = rz_new;
+  }
+  const size_t m = alphas.size();
+  std::vector<double> ta(m), tb(m > 0 ? m - 1 : 0);
+  for (size_t j = 0; j < m; ++j) {
+    ta[j] = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
+    if (j + 1 < m) tb[j] = std::sqrt(betas[j]) / alphas[j];
+  }
+  const double lmin = tridiag_extreme_eig(ta, tb, false), lmax = tridiag_extreme_eig(ta, tb, true);
+  const double a = lmin, b = 1.2 * lmax;
+  range[0] = a;
+  range[1] = b;
+  const double kappa = b / a, q = (std::sqrt(kappa) + 1.0) / (std::sqrt(kappa) - 1.0);
+  degree = (int)std::ceil(std::log(2.0 / tol) / std::log(q));
+  if (degree < 1) degree = 1;
+  // the iteration from zero (Saad, Alg. 12.1, as the smoother) applied to
+  // every unit vector at once: X = sum of updates, R = I - A X
+  const double theta = 0.5 * (a + b), delta = 0.5 * (b - a), sigma = theta / delta;
+  std::vector<double> X((size_t)n * n, 0.0), R((size_t)n * n, 0.0), D((size_t)n * n), AD((size_t)n * n);
+  for (int64_t i = 0; i < n; ++i) R[i * n + i] = 1.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) D[i * n + j] = dinv[i] * R[i * n + j] / theta;
+  double rho = 1.0 / sigma;
+  for (int step = 0; step < degree; ++step) {
+    for (size_t e = 0; e < X.size(); ++e) X[e] += D[e];
+    if (step == degree - 1) break;
+#pragma omp parallel for if (n > 128)
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        double t = 0.0;
+        for (int64_t k2 = 0; k2 < n; ++k2) t += A[i * n + k2] * D[k2 * n + j];
+        AD[i * n + j] = t;
+      }
+    for (size_t e = 0; e < R.size(); ++e) R[e] -= AD[e];
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j)
+        D[i * n + j] = rho_new * rho * D[i * n + j] + (2.0 * rho_new / delta) * (dinv[i] * R[i * n + j]);
+    rho = rho_new;
+  }
+  C.swap(X);
 }
 
 // ---------------------------------------------------------------- helpers
@@ -879,8 +968,34 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
             for (int b1 = 0; b1 < NLOC; ++b1)
               if (id[a1] >= 0 && id[b1] >= 0) A0[id[a1] * ni + id[b1]] += a * Ae[(size_t)a1 * NLOC + b1];
         }
-    if (ni > 0 && !spd_inverse(A0, ni)) throw std::runtime_error("coarse matrix is not SPD");
-    h.coarse_inverse.swap(A0);
+    h.coarse_degree = 0;
+    h.coarse_range[0] = h.coarse_range[1] = 0.0;
+    h.coarse_ptr.clear();
+    h.coarse_col.clear();
+    h.coarse_val.clear();
+    h.coarse_inverse.clear();
+    const int64_t limit = h.params.coarse_solver == GMG_COARSE_CG ? 4096
+                          : h.params.coarse_solver == GMG_COARSE_CHEBYSHEV ? 2048 : 25600;
+    h.coarse_too_large = ni > limit;
+    if (h.coarse_too_large) {
+      // nothing to build; gmg_hier_build reports GMG_EUNSUPPORTED
+    } else if (h.params.coarse_solver == GMG_COARSE_CG) {
+      h.coarse_ptr.assign(1, 0);
+      for (int64_t i = 0; i < ni; ++i) {
+        for (int64_t j = 0; j < ni; ++j)
+          if (A0[i * ni + j] != 0.0) {
+            h.coarse_col.push_back((int32_t)j);
+            h.coarse_val.push_back(A0[i * ni + j]);
+          }
+        h.coarse_ptr.push_back((int32_t)h.coarse_col.size());
+      }
+    } else if (h.params.coarse_solver == GMG_COARSE_CHEBYSHEV) {
+      if (ni > 0) chebyshev_coarse_operator(A0, ni, h.params.coarse_tol, h.coarse_inverse, h.coarse_degree,
+                                            h.coarse_range);
+    } else {
+      if (ni > 0 && !spd_inverse(A0, ni)) throw std::runtime_error("coarse matrix is not SPD");
+      h.coarse_inverse.swap(A0);
+    }
   }
   h.setup_host_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }

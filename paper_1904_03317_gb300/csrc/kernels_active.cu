@@ -984,6 +984,97 @@ cudaError_t launch_coarse_solve(int dim, int64_t nc, const int64_t lat[3], const
   return cudaGetLastError();
 }
 
+// Unpreconditioned CG coarse solver (Sec. 4.3): one block iterates from zero
+// until ||r|| <= tol ||g|| or nc steps, with A_0 in CSR and the vectors in
+// shared memory; dot products reduce in a fixed order.
+__device__ __forceinline__ double block_dot_all(const double* a, const double* b, int64_t n, double* red) {
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) s += red[i];
+    red[32] = s;
+  }
+  __syncthreads();
+  const double s = red[32];
+  __syncthreads();
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) coarse_cg_kernel(int dim, int64_t nc, int64_t lx, int64_t ly,
+                                                         const int32_t* __restrict__ ptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const double* __restrict__ val, double tol,
+                                                         const T* __restrict__ g0, T* __restrict__ u0) {
+  extern __shared__ double cg_sm[];
+  double* x = cg_sm;
+  double* r = x + nc;
+  double* p = r + nc;
+  double* Ap = p + nc;
+  __shared__ double red[33];
+  const int64_t ix = lx - 2, iy = dim > 1 ? ly - 2 : 1;
+  auto slot_of = [&](int64_t i) {
+    int64_t a = i % ix, b = (i / ix) % iy, c = i / (ix * iy);
+    return (a + 1) + lx * ((b + 1) + ly * (dim > 2 ? c + 1 : 0));
+  };
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
+    x[i] = 0.0;
+    r[i] = (double)g0[slot_of(i)];
+    p[i] = r[i];
+  }
+  __syncthreads();
+  double rr = block_dot_all(r, r, nc, red);
+  const double stop = tol * tol * rr;
+  for (int64_t it = 0; it < nc && rr > stop; ++it) {
+    for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
+      double t = 0.0;
+      for (int32_t m = ptr[i]; m < ptr[i + 1]; ++m) t += val[m] * p[col[m]];
+      Ap[i] = t;
+    }
+    __syncthreads();
+    const double pAp = block_dot_all(p, Ap, nc, red);
+    if (!(pAp > 0.0)) break;
+    const double alpha = rr / pAp;
+    for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * Ap[i];
+    }
+    __syncthreads();
+    const double rr_new = block_dot_all(r, r, nc, red);
+    const double beta = rr_new / rr;
+    rr = rr_new;
+    if (!(rr > stop)) break;
+    for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) p[i] = r[i] + beta * p[i];
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) u0[slot_of(i)] = (T)x[i];
+}
+
+template <typename T>
+cudaError_t launch_coarse_cg(int dim, int64_t nc, const int64_t lat[3], const int32_t* ptr, const int32_t* col,
+                             const double* val, double tol, const T* g0, T* u0, cudaStream_t s) {
+  if (nc == 0) return cudaSuccess;
+  const size_t sm = 4 * (size_t)nc * sizeof(double);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(coarse_cg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    init = true;
+  }
+  coarse_cg_kernel<T><<<1, 1024, sm, s>>>(dim, nc, lat[0], lat[1], ptr, col, val, tol, g0, u0);
+  GMG_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse_cg<float>(int, int64_t, const int64_t*, const int32_t*, const int32_t*,
+                                             const double*, double, const float*, float*, cudaStream_t);
+template cudaError_t launch_coarse_cg<double>(int, int64_t, const int64_t*, const int32_t*, const int32_t*,
+                                              const double*, double, const double*, double*, cudaStream_t);
+
 // --------------------------------------------------------- vector kernels
 template <typename T>
 __global__ void scale_vec_kernel(int64_t n, const T* __restrict__ dinv, const T* __restrict__ g, T c,

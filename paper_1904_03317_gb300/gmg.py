@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libgmg.so")
 MAX_LEVELS = 24
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ENAN, ETIMEOUT, EUNSUPPORTED = range(9)
 PREC_FP64, PREC_FP32 = 0, 1
+SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI = 0, 1
+COARSE_CHOLESKY, COARSE_CHEBYSHEV, COARSE_CG = 0, 1, 2
 EXPORT_UNKNOWN_KEYS, EXPORT_HOME_LEVEL, EXPORT_HANGING, EXPORT_LEVEL_KEYS, EXPORT_LEVEL_CLASS, \
     EXPORT_HOME_SLOT = range(6)
 
@@ -57,7 +59,8 @@ class CoarseMeshC(C.Structure):
 class ParamsC(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("eig_lo", C.c_double), ("eig_hi", C.c_double),
                 ("eig_iters", C.c_int), ("vcycle_prec", C.c_int),
-                ("fixed_lambda", C.POINTER(C.c_double)), ("solve_graph", C.c_int)]
+                ("fixed_lambda", C.POINTER(C.c_double)), ("smoother", C.c_int), ("coarse_solver", C.c_int),
+                ("coarse_tol", C.c_double), ("solve_graph", C.c_int)]
 
 
 class PartitionModelC(C.Structure):
@@ -76,7 +79,8 @@ class InfoC(C.Structure):
                 ("bricks", C.c_uint64 * MAX_LEVELS), ("groups_jump", C.c_uint64 * MAX_LEVELS),
                 ("lambda_max", C.c_double * MAX_LEVELS), ("device_bytes", C.c_uint64),
                 ("setup_host_s", C.c_double), ("setup_device_s", C.c_double),
-                ("leaf_patches", C.c_uint64), ("leaf_groups", C.c_uint64), ("leaf_single_cells", C.c_uint64)]
+                ("leaf_patches", C.c_uint64), ("leaf_groups", C.c_uint64), ("leaf_single_cells", C.c_uint64),
+                ("coarse_degree", C.c_int), ("coarse_range", C.c_double * 2)]
 
 
 class KernelStatsC(C.Structure):
@@ -251,12 +255,14 @@ class Hierarchy:
 
     def __init__(self, ctx: Context, mesh: Mesh, degree: int, coarse_coeff=None, cheb_degree: int = 5,
                  vcycle_prec: int = PREC_FP32, eig_lo: float = 0.08, eig_hi: float = 1.2, eig_iters: int = 10,
-                 fixed_lambda: Optional[Sequence[float]] = None, solve_graph: bool = True):
+                 fixed_lambda: Optional[Sequence[float]] = None, solve_graph: bool = True,
+                 smoother: int = 0, coarse_solver: int = 0, coarse_tol: float = 1e-3):
         lib = load_library()
         p = ParamsC()
         lib.gmg_params_default(C.byref(p))
         p.cheb_degree, p.eig_lo, p.eig_hi, p.eig_iters, p.vcycle_prec = cheb_degree, eig_lo, eig_hi, eig_iters, vcycle_prec
         p.solve_graph = int(solve_graph)
+        p.smoother, p.coarse_solver, p.coarse_tol = smoother, coarse_solver, coarse_tol
         self._lam = None
         if fixed_lambda is not None:
             self._lam = np.ascontiguousarray(np.asarray(fixed_lambda, dtype=np.float64))

@@ -135,3 +135,28 @@ def test_closure_after_deep_refinement_matches_oracle():
     lv, co = m.leaves()
     assert set((l, tuple(c)) for l, c in f.leaves()) == set(
         (int(l), tuple(int(x) for x in c)) for l, c in zip(lv, co))
+
+
+@pytest.mark.parametrize("name", ["3d_q2_sphere", "2d_q2_circle", "3d_q2_checker"])
+def test_chebyshev_coarse_setup_matches_oracle(name):
+    """Degree and eigenvalue range of the Chebyshev coarse solver (Sec. 4.1)
+    from the host builder equal the oracle's."""
+    from oracle import gmg as ogmg
+    from tests.helpers import oracle_hierarchy
+    w = small_workloads()[name]
+    H = G.Hierarchy(G.Context(-1), G.build_mesh(w), w.degree, w.coeff, coarse_solver=G.COARSE_CHEBYSHEV)
+    O = oracle_hierarchy(name)
+    try:
+        ogmg.setup_coarse(O, "chebyshev")
+        assert H.info.coarse_degree == O.coarse_degree
+        np.testing.assert_allclose(list(H.info.coarse_range), O.coarse_range, rtol=1e-9)
+    finally:
+        ogmg.setup_coarse(O, "cholesky")
+
+
+def test_invalid_solver_variants_rejected():
+    w = small_workloads()["2d_q1_circle"]
+    m = G.build_mesh(w)
+    for kw in (dict(smoother=7), dict(coarse_solver=3), dict(coarse_tol=0.0), dict(coarse_tol=1.5)):
+        with pytest.raises(Exception):
+            G.Hierarchy(G.Context(-1), m, w.degree, **kw)

@@ -365,3 +365,49 @@ def test_solve_error_paths(torch, solve_graph):
     z = torch.zeros_like(b)
     st = H.solve(z, x, tol=1e-8)
     assert st.iterations == 0 and torch.count_nonzero(x).item() == 0
+
+
+VARIANTS = {
+    "cheb_coarse": dict(smoother="chebyshev", coarse="chebyshev", degree=None),
+    "cg_coarse": dict(smoother="chebyshev", coarse="cg", degree=None),
+    "jacobi1_cg": dict(smoother="jacobi", coarse="cg", degree=1),
+    "jacobi2_cheb": dict(smoother="jacobi", coarse="chebyshev", degree=2),
+}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("name", ["2d_q1_circle", "3d_q2_sphere", "3d_q2_checker"])
+def test_solver_variants_match_oracle(torch, name, variant):
+    """Chebyshev coarse solver (Sec. 4.1), unpreconditioned CG coarse solver and
+    undamped Jacobi smoothing (Sec. 4.3) against the oracle's same variant,
+    FP64 V-cycle: iteration counts within one; with the linear coarse solvers
+    the iterates agree to 1e-10 at the oracle's count."""
+    v = VARIANTS[variant]
+    O = oracle_hierarchy(name)
+    w = small_workloads()[name]
+    deg = v["degree"] or O.cheb_degree
+    lam = [lev.lam for lev in O.levels]
+    ctx = G.Context(0)
+    H = G.Hierarchy(ctx, G.build_mesh(w), w.degree, w.coeff, cheb_degree=deg, vcycle_prec=G.PREC_FP64,
+                    fixed_lambda=lam,
+                    smoother=G.SMOOTHER_JACOBI if v["smoother"] == "jacobi" else G.SMOOTHER_CHEBYSHEV,
+                    coarse_solver={"cholesky": G.COARSE_CHOLESKY, "chebyshev": G.COARSE_CHEBYSHEV,
+                                   "cg": G.COARSE_CG}[v["coarse"]])
+    saved = (O.smoother, O.coarse, O.cheb_degree)
+    try:
+        O.smoother, O.cheb_degree = v["smoother"], deg
+        ogmg.setup_coarse(O, v["coarse"])
+        b = _rhs(O, w)
+        ref = ogmg.solve(O, b, 1e-8)
+        x = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+        st = H.solve(dev(torch, b), x, tol=1e-8, max_iter=200)
+        assert st.converged and abs(st.iterations - ref.iterations) <= 1
+        true_res = np.linalg.norm(b - O.disc.A @ host(x)) / np.linalg.norm(b)
+        assert true_res <= 2e-8
+        if v["coarse"] != "cg":  # a linear preconditioner: same iterates to rounding
+            st = H.solve(dev(torch, b), x, fixed_iterations=ref.iterations)
+            assert rel_err(host(x), ref.x) < 1e-10
+    finally:
+        O.smoother, O.cheb_degree = saved[0], saved[2]
+        ogmg.setup_coarse(O, saved[1])
+        H.close()
