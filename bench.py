@@ -157,6 +157,99 @@ def time_solves(torch, H, b, x, steps, stream):
     return e0.elapsed_time(e1) / 1e3, st
 
 
+def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_ranks, rank, world):
+    """Independent problems solved together (gmg_solve_batch): each step solves
+    every problem of the list once; the stream count is tuned in the warm-up."""
+    from concurrent.futures import ThreadPoolExecutor
+    ws = inputs.batched_problems(args.batch_count)
+    stream = torch.cuda.current_stream()
+    ctx = G.Context(local, stream.cuda_stream)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=8) as ex:  # host setup in parallel (the ABI releases the GIL)
+        meshes = list(ex.map(G.build_mesh, ws))
+    t_mesh = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hs = [G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32)
+          for m, w in zip(meshes, ws)]
+    t_setup = time.perf_counter() - t0
+    ns = [h.n for h in hs]
+    bs = [torch.tensor(inputs.random_rhs(w.seed, n), dtype=torch.float64, device="cuda") for w, n in zip(ws, ns)]
+    xs = [torch.zeros_like(b) for b in bs]
+    # warm-up, and pick the stream count (a one-parameter autotune)
+    best = None
+    for nst in (8, 16, 32, 64):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        stats, status = G.solve_batch(hs, bs, xs, tol=TOL, n_streams=nst)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - a
+        assert all(rc == G.OK for rc in status), status
+        if best is None or dt < best[1]:
+            best = (nst, dt)
+    nst = best[0]
+    for _ in range(max(0, args.warmup - 1)):
+        G.solve_batch(hs, bs, xs, tol=TOL, n_streams=nst)
+    sampler = ClockSampler(local)
+    sampler.start()
+    for h in hs:
+        h.profile_reset(timing=False)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        stats, status = G.solve_batch(hs, bs, xs, tol=TOL, n_streams=nst)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    secs = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    launches = int(sum(sum(v["launches"] for v in h.profile_read().values()) for h in hs))
+    total = sum_over_ranks(float(sum(ns)) * args.steps)
+    value = total / secs
+    its = [s.iterations for s in stats]
+    # the same problems one at a time (graph mode, FP32 V-cycle), and a sample
+    # with the plain FP64 V-cycle
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    for h, b, x in zip(hs, bs, xs):
+        h.solve(b, x, tol=TOL)
+    torch.cuda.synchronize()
+    serial32 = float(sum(ns)) / (time.perf_counter() - a)
+    k = min(args.serial_sample, len(ws))
+    h64 = [G.Hierarchy(ctx, meshes[i], ws[i].degree, ws[i].coeff, cheb_degree=ws[i].cheb_degree,
+                       vcycle_prec=G.PREC_FP64) for i in range(k)]
+    x64 = [torch.zeros_like(bs[i]) for i in range(k)]
+    for i in range(k):
+        h64[i].solve(bs[i], x64[i], tol=TOL)  # builds the graphs
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    for i in range(k):
+        h64[i].solve(bs[i], x64[i], tol=TOL)
+    torch.cuda.synchronize()
+    serial64 = float(sum(ns[:k])) / (time.perf_counter() - a)
+    diff = max(float(torch.linalg.vector_norm(xs[i] - x64[i]) / torch.linalg.vector_norm(x64[i])) for i in range(k))
+    if rank == 0:
+        dims = [w.coarse.dim for w in ws]
+        line = {
+            "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG", "data": "synthetic",
+            "config": {"workload": f"batched_{len(ws)}_poisson_2d3d_q1q2_random_rounds",
+                       "problems": len(ws), "unknowns_total": int(sum(ns)), "unknowns_min": int(min(ns)),
+                       "unknowns_median": int(np.median(ns)), "unknowns_max": int(max(ns)),
+                       "problems_3d": int(sum(1 for d in dims if d == 3)),
+                       "cg_iterations_min_max": [int(min(its)), int(max(its))], "tol": TOL,
+                       "n_streams": nst, "parallelism": f"replicas x{world}",
+                       "setup_s": {"mesh": round(t_mesh, 2), "hierarchies": round(t_setup, 2)}},
+            "gpu_launches": launches,
+            "serial_fp32_graph": {"value": serial32, "unit": "DoFs/s"},
+            "serial_fp64": {"value": serial64, "unit": "DoFs/s", "sample": f"first {k} problems",
+                            "max_rel_diff_vs_batched": diff},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,9 +260,13 @@ def main():
     ap.add_argument("--adaptive-ref", type=int, default=ADAPTIVE_REF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker"],
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker", "batch"],
                     help="sphere: 3D Q2 Poisson refined at a sphere (the headline); checker: 3D Q2 with the "
-                         "{1, 100} subcube checkerboard coefficient refined at the subcube planes")
+                         "{1, 100} subcube checkerboard coefficient refined at the subcube planes; batch: "
+                         "512 independent 2D/3D Q1/Q2 problems solved together")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serial-sample", type=int, default=64,
+                    help="batch workload: problems timed one by one with plain FP64 V-cycles")
     ap.add_argument("--finest-level", type=int, default=9, help="checker workload: finest level")
     ap.add_argument("--solve-mode", default="graph", choices=["graph", "stream"],
                     help="graph: each solve is one CUDA-graph launch; stream: one launch per kernel")
@@ -212,6 +309,11 @@ def main():
     __graft_entry__.build()
     from paper_1904_03317_gb300 import gmg as G
     from paper_1904_03317_gb300 import inputs
+    if args.workload == "batch":
+        run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_ranks, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     if args.workload == "sphere":
         w = inputs.poisson3d_sphere(args.global_ref, args.adaptive_ref)

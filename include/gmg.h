@@ -272,6 +272,21 @@ gmg_status gmg_vcycle(gmg_hier* h, const double* d_r, double* d_z);
 gmg_status gmg_solve(gmg_hier* h, const double* d_b, double* d_x, double tol, int max_iter,
                      int fixed_iterations, gmg_stats* stats);
 
+/* Independent solves at once (batched): problem i solves hs[i] x = b with
+ * d_b[i], d_x[i] as in gmg_solve (graph mode, x0 = 0, tol, max_iter).  The
+ * problems' solve graphs are launched round-robin on n_streams streams of a
+ * pool owned by the library, so small problems fill the GPU together; the
+ * call returns after all have finished.  Each problem first waits for the
+ * work already queued on its hierarchy's context stream.  stats (optional)
+ * and status receive one entry per problem (status as gmg_solve's return);
+ * the return value is GMG_OK, or the first error met while launching.  All
+ * hierarchies must live on one device, be built with solve_graph = 1, appear
+ * once, and have per-launch timing off.  Serialised against other batched
+ * calls (the stream pool is shared).  The paper solves one problem at a time;
+ * this is the GPU's way to batch many small ones. */
+gmg_status gmg_solve_batch(gmg_hier* const* hs, const double* const* d_b, double* const* d_x, int n, double tol,
+                           int max_iter, int n_streams, gmg_stats* stats, gmg_status* status);
+
 /* ----------------------------------------------- level operations (tests)
  * These expose the individual V-cycle steps on device level vectors in the
  * hierarchy's V-cycle precision (float for FP32, double for FP64), laid out

@@ -7,6 +7,7 @@
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "gmg_internal.h"
 
@@ -438,6 +439,31 @@ gmg_status gmg_solve(gmg_hier* hh, const double* d_b, double* d_x, double tol, i
   gmg_status st = bind_device(hh->h);
   if (st != GMG_OK) return st;
   return device_solve(hh->h, d_b, d_x, tol, max_iter, fixed_iterations, stats);
+  GMG_GUARD_END
+}
+
+gmg_status gmg_solve_batch(gmg_hier* const* hs, const double* const* d_b, double* const* d_x, int n, double tol,
+                           int max_iter, int n_streams, gmg_stats* stats, gmg_status* status) {
+  CHECK_ARG(hs && d_b && d_x && status, "null argument");
+  CHECK_ARG(n >= 1 && n <= (1 << 20), "n out of range [1, 2^20]");
+  CHECK_ARG(n_streams >= 1 && n_streams <= 128, "n_streams out of range [1, 128]");
+  CHECK_ARG(tol > 0 && std::isfinite(tol), "tol must be finite and > 0");
+  CHECK_ARG(max_iter >= 1 && max_iter <= 100000, "max_iter out of range [1, 100000]");
+  GMG_GUARD_BEGIN
+  std::vector<Hier*> h(n);
+  for (int i = 0; i < n; ++i) {
+    CHECK_ARG(hs[i] && d_b[i] && d_x[i], "null hierarchy or vector");
+    CHECK_ARG((const void*)d_b[i] != (const void*)d_x[i], "b and x must not overlap");
+    h[i] = &hs[i]->h;
+    CHECK_ARG(h[i]->ctx && h[i]->ctx->c.device >= 0 && h[i]->dev, "needs hierarchies built on a device");
+    CHECK_ARG(h[i]->ctx->c.device == h[0]->ctx->c.device, "all hierarchies must live on one device");
+    CHECK_ARG(h[i]->params.solve_graph, "batched solves need solve_graph = 1");
+    for (int j = 0; j < i; ++j) CHECK_ARG(h[j] != h[i], "a hierarchy appears twice in the batch");
+    status[i] = GMG_OK;
+  }
+  gmg_status st = bind_device(*h[0]);
+  if (st != GMG_OK) return st;
+  return device_solve_batch(h.data(), d_b, d_x, n, tol, max_iter, n_streams, stats, status);
   GMG_GUARD_END
 }
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <numeric>
 
 #include "device_common.cuh"
@@ -929,11 +930,12 @@ static void add_tally(Profile& p, const Tally& t, uint64_t times) {
   }
 }
 
-static gmg_status solve_graph(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
-                              gmg_stats* st) {
+// Enqueue one graph-mode solve on stream s (no synchronisation); the status
+// and scalars land in the pinned control mirror.
+static gmg_status enqueue_graph_solve(Hier& h, const double* b, double* x, double tol, int max_iter,
+                                      int fixed_iterations, cudaStream_t s) {
   DeviceState* d = h.dev;
   if (!d->cg_exec) GMG_TRY(build_solve_graph(h));
-  cudaStream_t s = d->stream;
   const int64_t n = d->n_unknowns;
   GraphCtl* c = d->ctl_host;
   *c = GraphCtl();
@@ -946,7 +948,13 @@ static gmg_status solve_graph(Hier& h, const double* b, double* x, double tol, i
   GMG_CUDA_TRY(cudaGraphLaunch(d->cg_exec, s));
   GMG_CUDA_TRY(cudaMemcpyAsync(x, d->x_iter, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GMG_CUDA_TRY(cudaMemcpyAsync(c, d->ctl, sizeof(GraphCtl), cudaMemcpyDeviceToHost, s));
-  GMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return GMG_OK;
+}
+
+// After the stream has been synchronised: statistics and status of the solve.
+static gmg_status finish_graph_solve(Hier& h, double tol, gmg_stats* st) {
+  DeviceState* d = h.dev;
+  const GraphCtl* c = d->ctl_host;
   add_tally(d->prof, d->cg_pre, 1);
   add_tally(d->prof, d->cg_body, (uint64_t)std::max(c->it, 0));
   gmg_stats stats;
@@ -971,6 +979,61 @@ static gmg_status solve_graph(Hier& h, const double* b, double* x, double tol, i
       set_error("internal: graph-mode CG ended without a status");
       return GMG_ECUDA;
   }
+}
+
+static gmg_status solve_graph(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
+                              gmg_stats* st) {
+  cudaStream_t s = h.dev->stream;
+  GMG_TRY(enqueue_graph_solve(h, b, x, tol, max_iter, fixed_iterations, s));
+  GMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return finish_graph_solve(h, tol, st);
+}
+
+// Independent solves at once: the problems' solve graphs go round-robin onto
+// a pool of streams, so small problems share the GPU; one wait at the end.
+// Each problem starts after the work already queued on its own stream.
+gmg_status device_solve_batch(Hier* const* hs, const double* const* b, double* const* x, int n, double tol,
+                              int max_iter, int n_streams, gmg_stats* st, gmg_status* status) {
+  static std::mutex pool_mutex;
+  static std::vector<cudaStream_t> pool;
+  static std::vector<cudaEvent_t> ready;
+  std::lock_guard<std::mutex> lock(pool_mutex);
+  while ((int)pool.size() < n_streams) {
+    cudaStream_t s = nullptr;
+    GMG_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    pool.push_back(s);
+  }
+  while ((int)ready.size() < n) {
+    cudaEvent_t e = nullptr;
+    GMG_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ready.push_back(e);
+  }
+  for (int i = 0; i < n; ++i)
+    if (hs[i]->dev->prof.timing) {
+      set_error("batched solves run without per-launch timing (gmg_profile_reset with timing off)");
+      return GMG_EINVAL;
+    }
+  // graphs are captured (and their buffers allocated) before any launch
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]->dev->cg_exec) GMG_TRY(build_solve_graph(*hs[i]));
+  gmg_status first_error = GMG_OK;
+  std::vector<char> launched(n, 0);
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t s = pool[i % n_streams];
+    GMG_CUDA_TRY(cudaEventRecord(ready[i], hs[i]->dev->stream));
+    GMG_CUDA_TRY(cudaStreamWaitEvent(s, ready[i], 0));
+    gmg_status e = enqueue_graph_solve(*hs[i], b[i], x[i], tol, max_iter, 0, s);
+    if (e != GMG_OK) {
+      status[i] = e;
+      if (first_error == GMG_OK) first_error = e;
+      continue;
+    }
+    launched[i] = 1;
+  }
+  for (int k = 0; k < n_streams && k < n; ++k) GMG_CUDA_TRY(cudaStreamSynchronize(pool[k]));
+  for (int i = 0; i < n; ++i)
+    if (launched[i]) status[i] = finish_graph_solve(*hs[i], tol, st ? st + i : nullptr);
+  return first_error;
 }
 
 // Graph mode unless it is switched off or per-kernel timing is on (the

@@ -973,11 +973,12 @@ cudaError_t launch_coarse_solve(int dim, int64_t nc, const int64_t lat[3], const
   if (nc == 0) return cudaSuccess;
   size_t sm = (size_t)nc * sizeof(double);
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
-  static bool init = false;
-  if (!init) {
+  // set once, thread-safe (function-local static)
+  static const bool init = [&] {
     cudaFuncSetAttribute(coarse_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    init = true;
-  }
+    return true;
+  }();
+  (void)init;
   unsigned grid = (unsigned)((nc + 7) / 8);  // 8 rows (warps) per block
   coarse_solve_kernel<T><<<grid, 256, sm, s>>>(dim, nc, lat[0], lat[1], lat[2], inv, g0, u0);
   GMG_COUNT_LAUNCH();
@@ -1061,11 +1062,12 @@ cudaError_t launch_coarse_cg(int dim, int64_t nc, const int64_t lat[3], const in
   if (nc == 0) return cudaSuccess;
   const size_t sm = 4 * (size_t)nc * sizeof(double);
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
-  static bool init = false;
-  if (!init) {
+  // set once, thread-safe (function-local static)
+  static const bool init = [&] {
     cudaFuncSetAttribute(coarse_cg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    init = true;
-  }
+    return true;
+  }();
+  (void)init;
   coarse_cg_kernel<T><<<1, 1024, sm, s>>>(dim, nc, lat[0], lat[1], ptr, col, val, tol, g0, u0);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();

@@ -1455,23 +1455,25 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
     if (a.n_bricks > 0) {
       if constexpr (std::is_same<T, float>::value) {
         const size_t sm = Brick2S<K>::bytes();
-        static bool init = false;
-        if (!init) {
+        // set once, thread-safe (function-local static)
+        static const bool init = [&] {
           cudaFuncSetAttribute(level_cheb_brick_f2_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm);
-          init = true;
-        }
+          return true;
+        }();
+        (void)init;
         level_cheb_brick_f2_kernel<K, MODE><<<(unsigned)a.n_bricks, Brick2S<K>::TB, sm, s>>>(a, x, xprev, g, out,
                                                                                              c1, c2);
         GMG_COUNT_LAUNCH();
       } else {
         const size_t sm = BrickSmem<T, K>::bytes();
-        static bool init = false;
-        if (!init) {
+        // set once, thread-safe (function-local static)
+        static const bool init = [&] {
           cudaFuncSetAttribute(level_cheb_brick_kernel<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm);
-          init = true;
-        }
+          return true;
+        }();
+        (void)init;
         level_cheb_brick_kernel<T, K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1,
                                                                                            c2);
         GMG_COUNT_LAUNCH();
@@ -1481,11 +1483,12 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
   if (a.n_uniform > 0) {
     using F = Fast<DIM, K>;
     const size_t sm = FastSmem<T, DIM, K>::bytes();
-    static bool init = false;
-    if (!init) {
+    // set once, thread-safe (function-local static)
+    static const bool init = [&] {
       cudaFuncSetAttribute(level_cheb_fast_kernel<T, DIM, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      init = true;
-    }
+      return true;
+    }();
+    (void)init;
     dim3 grid((unsigned)((a.n_uniform + F::TPB - 1) / F::TPB));
     level_cheb_fast_kernel<T, DIM, K, MODE><<<grid, 256, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
     GMG_COUNT_LAUNCH();
@@ -1493,11 +1496,12 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
   if (a.n_jump > 0) {
     using G = Geo<DIM, K>;
     const size_t sm = ChebSmem<T, DIM, K>::bytes() + 16;
-    static bool init = false;
-    if (!init) {
+    // set once, thread-safe (function-local static)
+    static const bool init = [&] {
       cudaFuncSetAttribute(level_cheb_kernel<T, DIM, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      init = true;
-    }
+      return true;
+    }();
+    (void)init;
     dim3 grid((unsigned)((a.n_jump + G::GPB - 1) / G::GPB));
     level_cheb_kernel<T, DIM, K, MODE><<<grid, G::GPB * G::TEAM, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
     GMG_COUNT_LAUNCH();
@@ -1530,11 +1534,12 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
   using F = Fast<DIM, K>;
   if (a.n_groups == 0) return cudaSuccess;
   const size_t sm = RestrictSmem<T, DIM, K>::bytes();
-  static bool init = false;
-  if (!init) {
+  // set once, thread-safe (function-local static)
+  static const bool init = [&] {
     cudaFuncSetAttribute(level_residual_restrict_kernel<T, DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    init = true;
-  }
+    return true;
+  }();
+  (void)init;
   dim3 grid((unsigned)((a.n_groups + F::TPB - 1) / F::TPB));
   level_residual_restrict_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, u, g, gc);
   GMG_COUNT_LAUNCH();
@@ -1673,12 +1678,13 @@ static cudaError_t pro_dispatch(const LevelArgs& a, const T* uc, T* u, T* u2, cu
   if constexpr (DIM == 3) {
     if (bricks) {
       const size_t sm = ProBrick<T, K>::bytes();
-      static bool init = false;
-      if (!init) {
+      // set once, thread-safe (function-local static)
+      static const bool init = [&] {
         cudaFuncSetAttribute(level_prolongate_brick_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm);
-        init = true;
-      }
+        return true;
+      }();
+      (void)init;
       level_prolongate_brick_kernel<T, K><<<(unsigned)a.n_bricks, ProBrick<T, K>::TB, sm, s>>>(a, uc, u, u2);
       GMG_COUNT_LAUNCH();
     }
@@ -1687,11 +1693,12 @@ static cudaError_t pro_dispatch(const LevelArgs& a, const T* uc, T* u, T* u2, cu
   const int64_t n = bricks ? a.n_rest : a.n_groups;
   if (n == 0) return cudaGetLastError();
   const size_t sm = ProlongSmem<T, DIM, K>::bytes();
-  static bool init = false;
-  if (!init) {
+  // set once, thread-safe (function-local static)
+  static const bool init = [&] {
     cudaFuncSetAttribute(level_prolongate_kernel<T, DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    init = true;
-  }
+    return true;
+  }();
+  (void)init;
   dim3 grid((unsigned)((n + F::TPB - 1) / F::TPB));
   level_prolongate_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, uc, u, u2, list, n);
   GMG_COUNT_LAUNCH();

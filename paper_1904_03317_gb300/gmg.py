@@ -36,7 +36,7 @@ EXPORTED = [
     "gmg_mesh_create", "gmg_mesh_destroy", "gmg_mesh_num_leaves", "gmg_mesh_num_levels",
     "gmg_mesh_leaves", "gmg_mesh_refine", "gmg_mesh_partition_model",
     "gmg_params_default", "gmg_hier_build", "gmg_hier_destroy", "gmg_hier_info", "gmg_hier_export",
-    "gmg_assemble_rhs", "gmg_apply", "gmg_vcycle", "gmg_solve",
+    "gmg_assemble_rhs", "gmg_apply", "gmg_vcycle", "gmg_solve", "gmg_solve_batch",
     "gmg_level_apply", "gmg_level_residual_restrict", "gmg_level_prolongate", "gmg_level_smooth",
     "gmg_level_inv_diag", "gmg_coarse_solve", "gmg_profile_reset", "gmg_profile_read",
     "gmg_level_smooth_noalloc",
@@ -127,6 +127,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "gmg_apply": [vp, vp, vp],
         "gmg_vcycle": [vp, vp, vp],
         "gmg_solve": [vp, vp, vp, C.c_double, i32, i32, C.POINTER(StatsC)],
+        "gmg_solve_batch": [vp, vp, vp, i32, C.c_double, i32, i32, vp, vp],
         "gmg_level_apply": [vp, i32, vp, vp],
         "gmg_level_residual_restrict": [vp, i32, vp, vp, vp],
         "gmg_level_prolongate": [vp, i32, vp, vp, vp],
@@ -363,6 +364,21 @@ class Hierarchy:
             self.close()
         except Exception:
             pass
+
+
+def solve_batch(hiers, bs, xs, tol: float = 1e-8, max_iter: int = 1000, n_streams: int = 16):
+    """Batched solves (gmg_solve_batch): hiers[i] x_i = b_i for device tensors
+    b_i, x_i.  Returns (stats list, status list)."""
+    n = len(hiers)
+    H = (C.c_void_p * n)(*[h.handle for h in hiers])
+    B = (C.c_void_p * n)(*[_ptr(b) for b in bs])
+    X = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    st = (StatsC * n)()
+    status = (C.c_int * n)()
+    rc = load_library().gmg_solve_batch(H, B, X, n, tol, max_iter, n_streams, st, status)
+    if rc not in (OK, ENOTCONV, ENAN, EBREAKDOWN):
+        _check(rc, "gmg_solve_batch")
+    return list(st), list(status)
 
 
 def build_mesh(workload: Workload) -> Mesh:

@@ -174,6 +174,19 @@ def round_random_interface(seed: int, round_index: int, prob: float,
     return fn
 
 
+def round_random(seed: int, round_index: int, prob: float) -> RoundFn:
+    """Flag each current leaf with probability ``prob``; the draw is keyed by
+    (seed, round, cell), independent of the order of the leaves."""
+
+    def fn(cm, level, coords, finest):
+        level = np.asarray(level, dtype=np.int64)
+        coords = np.asarray(coords, dtype=np.int64)
+        key = cell_hash_key(level, coords) ^ (np.uint64(round_index + 1) << np.uint64(56))
+        return uniform01(seed, key) < prob
+
+    return fn
+
+
 def checkerboard_coefficients(cm: CoarseMesh, low: float = 1.0, high: float = 100.0) -> np.ndarray:
     """Coefficient per coarse cell: ``high`` where the coarse-cell index sum is odd.
 
@@ -236,3 +249,39 @@ def checkerboard3d(global_refinements: int = 5, finest_level: int = 9, seed: int
         rounds.append(round_random_interface(seed, r, prob))
     return Workload(f"checkerboard3d_q2_g{global_refinements}_L{finest_level}", cm, 2, rounds,
                     checkerboard_coefficients(cm), "random", 4, seed=seed)
+
+
+# Leaf growth of r random rounds (p = 0.2, closure after each) on a uniform
+# mesh, measured with this generator: the closure multiplies the count far
+# beyond the (1 + p (2^d - 1))^r of the flags alone.
+RANDOM_ROUND_GROWTH = {2: {3: 6.5, 4: 13.1, 5: 26.8, 6: 55.1}, 3: {3: 34.1, 4: 124.2, 5: 470.8, 6: 1732.9}}
+
+
+def batched_problems(count: int = 512, seed: int = 20190404, n_min: float = 1e4, n_max: float = 5e5,
+                     prob: float = 0.2):
+    """Independent Poisson problems of mixed dimension, degree and size: per
+    problem d in {2, 3}, k in {1, 2}, a target size N log-uniform in
+    [n_min, n_max], 3..6 rounds that flag every leaf with probability prob,
+    and the global level g whose expected size k^d (4 2^g)^d G(d, rounds) is
+    closest to N in ratio, G the measured growth of the random rounds with
+    closure (RANDOM_ROUND_GROWTH; sizes are counted, not assumed).  Coarse
+    mesh 4^d on the unit brick, seeded random right-hand side, Chebyshev
+    degree 2 (2D) / 4 (3D).  All draws are keyed by (seed, problem index), so
+    the list does not depend on how it is consumed."""
+    out = []
+    for i in range(count):
+        key = np.arange(6, dtype=np.uint64) + np.uint64(8 * i)
+        u = uniform01(seed, key)
+        dim = 2 if u[0] < 0.5 else 3
+        k = 1 if u[1] < 0.5 else 2
+        target = float(np.exp(np.log(n_min) + u[2] * (np.log(n_max) - np.log(n_min))))
+        rounds = 3 + int(u[3] * 4)
+        growth = RANDOM_ROUND_GROWTH[dim][rounds]
+        sizes = [(k ** dim) * (4 * 2 ** gg) ** dim * growth for gg in range(12)]
+        g = int(np.argmin([abs(np.log(sz / target)) for sz in sizes]))
+        cm = CoarseMesh(dim, (4, 4, 4) if dim == 3 else (4, 4, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+        rs = [round_uniform()] * g + [round_random(seed + i, r, prob) for r in range(rounds)]
+        out.append(Workload(f"batch{i}_d{dim}_q{k}_g{g}_r{rounds}", cm, k, rs, None, "random",
+                            2 if dim == 2 else 4, seed=seed + i))
+    return out
+
