@@ -157,6 +157,68 @@ def time_solves(torch, H, b, x, steps, stream):
     return e0.elapsed_time(e1) / 1e3, st
 
 
+def run_serve(args, torch, G, inputs, local, rank, world):
+    """Request loop: Poisson arrivals of 3D Q2 sphere-surface problems of
+    log-uniform size, served with continuous batching (serve.Server); latency
+    is arrival to result, throughput counts the measured requests only."""
+    from paper_1904_03317_gb300 import serve
+    total = args.warm_requests + args.requests
+    arrivals, ws = inputs.serving_requests(total, rate=args.rate)
+    sampler = ClockSampler(local)
+    sampler.start()
+    srv = serve.Server(torch, device=local)
+    res = srv.run(arrivals, ws)
+    clocks = sampler.stop()
+    meas = res[args.warm_requests:]
+    assert all(r.status == G.OK for r in meas), [r.status for r in meas]
+    lat = [r.latency for r in meas]
+    span = max(r.ready for r in meas) - min(r.arrival for r in meas)
+    dofs = float(sum(r.n for r in meas))
+    setup = [r.setup_done - r.admitted for r in meas]
+    solve = [r.ready - r.setup_done for r in meas]
+    queue = [r.admitted - r.arrival for r in meas]
+    # the same requests one at a time with the plain FP64 V-cycle (a sample)
+    k = min(16, len(meas))
+    ctx = G.Context(local, torch.cuda.current_stream().cuda_stream)
+    t_setup64 = t_solve64 = 0.0
+    n64 = 0
+    for r in meas[:k]:
+        w = ws[r.rid]
+        a = time.perf_counter()
+        h = G.Hierarchy(ctx, G.build_mesh(w), w.degree, w.coeff, cheb_degree=w.cheb_degree,
+                        vcycle_prec=G.PREC_FP64)
+        b = torch.tensor(inputs.random_rhs(w.seed, h.n), dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        m = time.perf_counter()
+        h.solve(b, x, tol=TOL)
+        torch.cuda.synchronize()
+        e = time.perf_counter()
+        t_setup64 += m - a
+        t_solve64 += e - m
+        n64 += h.n
+        h.close()
+    if rank == 0:
+        ns = [r.n for r in meas]
+        line = {
+            "metric": METRIC, "value": dofs / span, "unit": "DoFs/s", "n_gpus": world, "steps": len(meas),
+            "warmup": args.warm_requests, "ms_per_step": 1e3 * span / len(meas), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG", "data": "synthetic",
+            "config": {"workload": "serving_3d_q2_sphere_surface_requests", "requests": len(meas),
+                       "warm_requests": args.warm_requests, "rate_per_s": args.rate,
+                       "unknowns_min": int(min(ns)), "unknowns_median": int(np.median(ns)),
+                       "unknowns_max": int(max(ns)), "tol": TOL, "setup_workers": srv.workers,
+                       "memory_budget_gb": round(srv.budget / 1e9, 1)},
+            "latency_s": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99),
+                          "queue_p50": serve.percentile(queue, 50), "setup_p50": serve.percentile(setup, 50),
+                          "solve_p50": serve.percentile(solve, 50), "solve_p99": serve.percentile(solve, 99)},
+            "serial_fp64": {"sample": k, "solve_dofs_per_s": n64 / t_solve64,
+                            "setup_and_solve_dofs_per_s": n64 / (t_setup64 + t_solve64)},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_ranks, rank, world):
     """Independent problems solved together (gmg_solve_batch): each step solves
     every problem of the list once; the stream count is tuned in the warm-up."""
@@ -260,11 +322,14 @@ def main():
     ap.add_argument("--adaptive-ref", type=int, default=ADAPTIVE_REF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker", "batch"],
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker", "batch", "serve"],
                     help="sphere: 3D Q2 Poisson refined at a sphere (the headline); checker: 3D Q2 with the "
                          "{1, 100} subcube checkerboard coefficient refined at the subcube planes; batch: "
                          "512 independent 2D/3D Q1/Q2 problems solved together")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=200, help="serve workload: measured requests")
+    ap.add_argument("--warm-requests", type=int, default=20, help="serve workload: requests before them")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve workload: arrivals per second")
     ap.add_argument("--serial-sample", type=int, default=64,
                     help="batch workload: problems timed one by one with plain FP64 V-cycles")
     ap.add_argument("--finest-level", type=int, default=9, help="checker workload: finest level")
@@ -309,6 +374,11 @@ def main():
     __graft_entry__.build()
     from paper_1904_03317_gb300 import gmg as G
     from paper_1904_03317_gb300 import inputs
+    if args.workload == "serve":
+        run_serve(args, torch, G, inputs, local, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.workload == "batch":
         run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_ranks, rank, world)
         if dist:

@@ -272,6 +272,19 @@ gmg_status gmg_vcycle(gmg_hier* h, const double* d_r, double* d_z);
 gmg_status gmg_solve(gmg_hier* h, const double* d_b, double* d_x, double tol, int max_iter,
                      int fixed_iterations, gmg_stats* stats);
 
+/* Asynchronous solve for request loops: enqueue the graph-mode solve of
+ * gmg_solve (x0 = 0, tol, max_iter) on the context stream and return at
+ * once; d_b must stay valid and d_x untouched until gmg_solve_poll reports
+ * the solve ready.  One pending solve per hierarchy.  Needs solve_graph = 1
+ * and per-launch timing off.  Hierarchies on different contexts (streams)
+ * overlap on the device.  No counterpart in the paper. */
+gmg_status gmg_solve_async(gmg_hier* h, const double* d_b, double* d_x, double tol, int max_iter);
+/* Completion of the pending asynchronous solve: *ready = 0 while it runs
+ * (wait = 0 never blocks; wait = 1 blocks until it ends); once ready,
+ * stats (optional) and *status are those gmg_solve would have returned.
+ * GMG_EINVAL if no solve is pending. */
+gmg_status gmg_solve_poll(gmg_hier* h, int wait, int* ready, gmg_stats* stats, gmg_status* status);
+
 /* Independent solves at once (batched): problem i solves hs[i] x = b with
  * d_b[i], d_x[i] as in gmg_solve (graph mode, x0 = 0, tol, max_iter).  The
  * problems' solve graphs are launched round-robin on n_streams streams of a

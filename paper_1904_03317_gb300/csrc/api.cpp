@@ -442,6 +442,32 @@ gmg_status gmg_solve(gmg_hier* hh, const double* d_b, double* d_x, double tol, i
   GMG_GUARD_END
 }
 
+gmg_status gmg_solve_async(gmg_hier* hh, const double* d_b, double* d_x, double tol, int max_iter) {
+  CHECK_ARG(hh && d_b && d_x, "null argument");
+  CHECK_ARG((const void*)d_b != (const void*)d_x, "b and x must not overlap");
+  CHECK_ARG(tol > 0 && std::isfinite(tol), "tol must be finite and > 0");
+  CHECK_ARG(max_iter >= 1 && max_iter <= 100000, "max_iter out of range [1, 100000]");
+  Hier& h = hh->h;
+  CHECK_ARG(h.ctx && h.ctx->c.device >= 0 && h.dev, "needs a hierarchy built on a device");
+  CHECK_ARG(h.params.solve_graph, "asynchronous solves need solve_graph = 1");
+  GMG_GUARD_BEGIN
+  gmg_status st = bind_device(h);
+  if (st != GMG_OK) return st;
+  return device_solve_async(h, d_b, d_x, tol, max_iter);
+  GMG_GUARD_END
+}
+
+gmg_status gmg_solve_poll(gmg_hier* hh, int wait, int* ready, gmg_stats* stats, gmg_status* status) {
+  CHECK_ARG(hh && ready && status, "null argument");
+  Hier& h = hh->h;
+  CHECK_ARG(h.ctx && h.ctx->c.device >= 0 && h.dev, "needs a hierarchy built on a device");
+  GMG_GUARD_BEGIN
+  gmg_status st = bind_device(h);
+  if (st != GMG_OK) return st;
+  return device_solve_poll(h, wait, ready, stats, status);
+  GMG_GUARD_END
+}
+
 gmg_status gmg_solve_batch(gmg_hier* const* hs, const double* const* d_b, double* const* d_x, int n, double tol,
                            int max_iter, int n_streams, gmg_stats* stats, gmg_status* status) {
   CHECK_ARG(hs && d_b && d_x && status, "null argument");

@@ -284,6 +284,7 @@ void device_free(Hier& h) {
   cudaFree(d->ctl);
   if (d->ctl_host) cudaFreeHost(d->ctl_host);
   if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
+  if (d->done) cudaEventDestroy(d->done);
   for (auto& q : d->prof.pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -987,6 +988,39 @@ static gmg_status solve_graph(Hier& h, const double* b, double* x, double tol, i
   GMG_TRY(enqueue_graph_solve(h, b, x, tol, max_iter, fixed_iterations, s));
   GMG_CUDA_TRY(cudaStreamSynchronize(s));
   return finish_graph_solve(h, tol, st);
+}
+
+// Asynchronous graph-mode solve on the context stream: enqueue, then poll.
+gmg_status device_solve_async(Hier& h, const double* b, double* x, double tol, int max_iter) {
+  DeviceState* d = h.dev;
+  if (d->prof.timing) {
+    set_error("asynchronous solves run without per-launch timing");
+    return GMG_EINVAL;
+  }
+  if (!d->done) GMG_CUDA_TRY(cudaEventCreateWithFlags(&d->done, cudaEventDisableTiming));
+  GMG_TRY(enqueue_graph_solve(h, b, x, tol, max_iter, 0, d->stream));
+  GMG_CUDA_TRY(cudaEventRecord(d->done, d->stream));
+  d->async_tol = tol;
+  d->async_pending = true;
+  return GMG_OK;
+}
+
+gmg_status device_solve_poll(Hier& h, int wait, int* ready, gmg_stats* st, gmg_status* status) {
+  DeviceState* d = h.dev;
+  if (!d->async_pending) {
+    set_error("no asynchronous solve pending");
+    return GMG_EINVAL;
+  }
+  cudaError_t e = wait ? cudaEventSynchronize(d->done) : cudaEventQuery(d->done);
+  if (e == cudaErrorNotReady) {
+    *ready = 0;
+    return GMG_OK;
+  }
+  GMG_CUDA_TRY(e);
+  *ready = 1;
+  d->async_pending = false;
+  *status = finish_graph_solve(h, d->async_tol, st);
+  return GMG_OK;
 }
 
 // Independent solves at once: the problems' solve graphs go round-robin onto

@@ -187,6 +187,9 @@ struct DeviceState {
   double* x_iter = nullptr;        // iterate of the graph-mode CG
   GraphCtl* ctl = nullptr;
   GraphCtl* ctl_host = nullptr;    // pinned mirror
+  cudaEvent_t done = nullptr;      // end of the pending asynchronous solve
+  bool async_pending = false;
+  double async_tol = 0.0;
 };
 
 constexpr int kMaxReduceBlocks = 4096;

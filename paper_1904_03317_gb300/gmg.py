@@ -36,7 +36,7 @@ EXPORTED = [
     "gmg_mesh_create", "gmg_mesh_destroy", "gmg_mesh_num_leaves", "gmg_mesh_num_levels",
     "gmg_mesh_leaves", "gmg_mesh_refine", "gmg_mesh_partition_model",
     "gmg_params_default", "gmg_hier_build", "gmg_hier_destroy", "gmg_hier_info", "gmg_hier_export",
-    "gmg_assemble_rhs", "gmg_apply", "gmg_vcycle", "gmg_solve", "gmg_solve_batch",
+    "gmg_assemble_rhs", "gmg_apply", "gmg_vcycle", "gmg_solve", "gmg_solve_batch", "gmg_solve_async", "gmg_solve_poll",
     "gmg_level_apply", "gmg_level_residual_restrict", "gmg_level_prolongate", "gmg_level_smooth",
     "gmg_level_inv_diag", "gmg_coarse_solve", "gmg_profile_reset", "gmg_profile_read",
     "gmg_level_smooth_noalloc",
@@ -128,6 +128,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "gmg_vcycle": [vp, vp, vp],
         "gmg_solve": [vp, vp, vp, C.c_double, i32, i32, C.POINTER(StatsC)],
         "gmg_solve_batch": [vp, vp, vp, i32, C.c_double, i32, i32, vp, vp],
+        "gmg_solve_async": [vp, vp, vp, C.c_double, i32],
+        "gmg_solve_poll": [vp, i32, C.POINTER(i32), C.POINTER(StatsC), C.POINTER(i32)],
         "gmg_level_apply": [vp, i32, vp, vp],
         "gmg_level_residual_restrict": [vp, i32, vp, vp, vp],
         "gmg_level_prolongate": [vp, i32, vp, vp, vp],
@@ -344,6 +346,17 @@ class Hierarchy:
 
     def coarse_solve(self, g0, u0):
         _check(load_library().gmg_coarse_solve(self.handle, _ptr(g0), _ptr(u0)), "gmg_coarse_solve")
+
+    def solve_async(self, b, x, tol: float = 1e-8, max_iter: int = 1000) -> None:
+        """Enqueue a graph-mode solve on the context stream (gmg_solve_async)."""
+        _check(load_library().gmg_solve_async(self.handle, _ptr(b), _ptr(x), tol, max_iter), "gmg_solve_async")
+
+    def solve_poll(self, wait: bool = False):
+        """(ready, stats, status) of the pending asynchronous solve."""
+        ready, st, status = C.c_int(0), StatsC(), C.c_int(0)
+        _check(load_library().gmg_solve_poll(self.handle, int(wait), C.byref(ready), C.byref(st), C.byref(status)),
+               "gmg_solve_poll")
+        return bool(ready.value), st, status.value
 
     def profile_reset(self, timing: bool = False):
         _check(load_library().gmg_profile_reset(self.handle, int(timing)), "gmg_profile_reset")

@@ -285,3 +285,37 @@ def batched_problems(count: int = 512, seed: int = 20190404, n_min: float = 1e4,
                             2 if dim == 2 else 4, seed=seed + i))
     return out
 
+
+def serving_requests(count: int, seed: int = 20190405, n_min: float = 1e4, n_max: float = 2e7,
+                     rate: float = 200.0):
+    """Solve requests for a request loop: Poisson arrivals at ``rate`` per
+    second (exponential gaps) and, per request, a 3D Q2 problem on the unit
+    cube (4^3 coarse cells) refined twice at the surface of a sphere with
+    centre U[0.3, 0.7]^3 and radius U[0.15, 0.35], a random right-hand side,
+    and a target size N log-uniform in [n_min, n_max] met by the choice of the
+    global level g (the one whose estimated size is closest to N; sizes are
+    counted, not assumed).  Returns (arrival times in s, workloads)."""
+    out, times = [], []
+    t = 0.0
+    for i in range(count):
+        key = np.arange(8, dtype=np.uint64) + np.uint64(8 * i)
+        u = uniform01(seed, key)
+        t += -np.log(max(1.0 - u[0], 1e-300)) / rate
+        times.append(t)
+        target = float(np.exp(np.log(n_min) + u[1] * (np.log(n_max) - np.log(n_min))))
+        c = tuple(0.3 + 0.4 * float(v) for v in u[2:5])
+        r = 0.15 + 0.2 * float(u[5])
+
+        def est(g):
+            # uniform cells, plus 7 new leaves per refined surface cell in
+            # each of the two rounds (about 1.5 cells per h^2 of sphere area)
+            cells = 64 * 8 ** g
+            surf = lambda lvl: 1.5 * 4 * np.pi * r * r * (4 * 2 ** lvl) ** 2
+            return 8 * (cells + 7 * surf(g) + 7 * surf(g + 1))
+
+        g = int(np.argmin([abs(np.log(est(gg) / target)) for gg in range(8)]))
+        cm = CoarseMesh(3, (4, 4, 4), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+        rs = [round_uniform()] * g + [round_sphere_surface(c, r)] * 2
+        out.append(Workload(f"request{i}_g{g}", cm, 2, rs, None, "random", 4, seed=seed + 1000 + i))
+    return np.asarray(times), out
+
