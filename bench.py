@@ -42,6 +42,11 @@ def peaks():
 # FP64 arithmetic peak of the part: 1.25 TFLOP/s nominal (dense FP64, incl. FMA = 2 flops)
 FP64_PEAK_TFLOPS = 1.25
 
+# DRAM bytes (read + write) per launch of a kernel kind on the headline
+# workload, from one ncu capture (profiles/level_smoother_dram_traffic_*.md);
+# None where no capture matches the current kernels
+TRAFFIC_PER_LAUNCH = {"cheb": 53.55e6}
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
@@ -436,22 +441,55 @@ def main():
     clocks = sampler.stop()
     stream_ms = 1e3 * max_over_ranks(secs_stream) / args.steps
 
-    # ---- end to end through host buffers: pinned b in, x out, every step
+    # ---- end to end through host buffers: every step copies its b from
+    # pinned host memory and its x back; serially, and pipelined (step i+1's
+    # input and step i's result move on a copy stream while a solve runs)
     hb = b.cpu().pin_memory()
-    hx = torch.empty_like(hb).pin_memory()
-    db = torch.empty_like(b)
+    hx = [torch.empty_like(hb).pin_memory() for _ in range(2)]
+    db = [torch.empty_like(b) for _ in range(2)]
+    dx = [torch.zeros_like(b) for _ in range(2)]
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        db.copy_(hb, non_blocking=True)
-        H.solve(db, x, tol=TOL)
-        hx.copy_(x, non_blocking=True)
+        db[0].copy_(hb, non_blocking=True)
+        H.solve(db[0], dx[0], tol=TOL)
+        hx[0].copy_(dx[0], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_serial = total_dofs / max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    copy_s = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_done = torch.cuda.Event()
+    barrier()
+    e0.record(stream)
+    copy_s.wait_stream(stream)
+    with torch.cuda.stream(copy_s):
+        db[0].copy_(hb, non_blocking=True)
+        ev_in[0].record(copy_s)
+    for i in range(args.steps):
+        j = i % 2
+        if i + 1 < args.steps:
+            with torch.cuda.stream(copy_s):
+                db[1 - j].copy_(hb, non_blocking=True)
+                ev_in[1 - j].record(copy_s)
+        stream.wait_event(ev_in[j])
+        if i >= 2:
+            stream.wait_event(ev_out[j])  # x of step i-2 has left the device
+        H.solve(db[j], dx[j], tol=TOL)
+        ev_done.record(stream)
+        copy_s.wait_event(ev_done)
+        with torch.cuda.stream(copy_s):
+            hx[j].copy_(dx[j], non_blocking=True)
+            ev_out[j].record(copy_s)
+    stream.wait_stream(copy_s)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_secs = max_over_ranks(e0.elapsed_time(e1) / 1e3)
     e2e_value = total_dofs / e2e_secs
-    x32 = x.clone()
+    assert torch.equal(hx[(args.steps - 1) % 2], dx[(args.steps - 1) % 2].cpu())
+    x32 = dx[(args.steps - 1) % 2].clone()
 
     # ---- the FP64 V-cycle path on the same problem
     fp64 = None
@@ -479,8 +517,11 @@ def main():
                 "peak_src": "nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2070 MHz x 2)"}
     else:
         achieved = kd["bytes"] / (kd["ms"] / 1e3) / 1e9
+        traffic = TRAFFIC_PER_LAUNCH.get(dom) if args.workload == "sphere" and \
+            (args.global_ref, args.adaptive_ref) == (GLOBAL_REF, ADAPTIVE_REF) else None
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"]}
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": kd["bytes"] / max(kd["launches"], 1), "peak_src": pk["src"]}
     t_all = sum(v["ms"] for v in kern.values())
     kernels = {}
     for k, v in kern.items():
@@ -511,7 +552,9 @@ def main():
                                    "hierarchy_device": round(info.setup_device_s, 3),
                                    "total": round(t_setup, 3)}},
             "gpu_launches": launches,
-            "e2e": {"value": e2e_value, "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "e2e": {"value": e2e_value, "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                    "copies": "pipelined: step i+1's b in and step i's x out on a copy stream during solves",
+                    "serial_value": e2e_serial},
             "roofline": roof,
             "kernels": kernels,
             "kernel_timing": {"mode": "stream (one launch per kernel, CUDA events per launch)",

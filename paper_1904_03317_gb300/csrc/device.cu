@@ -582,8 +582,10 @@ static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cu
   const bool jacobi = h.params.smoother == GMG_SMOOTHER_JACOBI;
   const double first = jacobi ? 1.0 : 1.0 / D.theta;
   if (from_zero) {
-    Track t(h.dev, GMG_K_SMOOTH_FIRST, 3.0 * sizeof(T) * D.n_slots, 2.0 * D.n_slots);
-    e = launch_scale_vec<T>(D.n_slots, dinv, g, (T)first, cur, s);
+    // x_1 = c D^{-1} g on the groups' own slots; ghost slots (I nodes) stay 0
+    const int64_t owned = D.n_groups * ipow_h(2 * h.k, h.dim);
+    Track t(h.dev, GMG_K_SMOOTH_FIRST, 3.0 * sizeof(T) * owned, 2.0 * owned);
+    e = launch_scale_vec<T>(owned, dinv, g, (T)first, cur, s);
   } else {
     Track t(h.dev, GMG_K_CHEB, cheb_bytes, D.cheb_flops);
     e = launch_level_cheb<T>(h.dim, h.k, a, cur, nullptr, g, dinv, other, (T)0, (T)first, false, s);
