@@ -101,6 +101,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def over_ranks(dist, torch, value: float, op: str, device: str = "cuda") -> float:
+    """Whole-job reduction of a per-rank number for replica runs: "max" for
+    the timed seconds (the slowest rank sets the job time), "sum" for the
+    unknowns solved; the value itself on a single process."""
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def cpu_baseline(steps=1, min_seconds=8.0):
     """The oracle (FP64, scipy sparse, single thread) on a bounded sample of the
     same generator; returns (DoFs/s, sample description, seconds)."""
@@ -362,18 +373,10 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return over_ranks(dist, torch, v, "max")
 
     def sum_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return over_ranks(dist, torch, v, "sum")
 
     import __graft_entry__
     __graft_entry__.build()
