@@ -137,6 +137,10 @@ typedef struct gmg_info {
   /* Chebyshev coarse solver: degree and eigenvalue range [lmin, 1.2 lmax] */
   int coarse_degree;
   double coarse_range[2];
+  /* host setup phases (s): level blocks and classes, leaf nodes, node classes
+   * and numbering, hanging constraints, leaf cell tables, leaf patches and
+   * groups, home slots, coarse matrix */
+  double setup_phase_s[8];
 } gmg_info;
 
 typedef struct gmg_stats {

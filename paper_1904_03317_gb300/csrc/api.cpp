@@ -348,6 +348,7 @@ gmg_status gmg_hier_info(const gmg_hier* hh, gmg_info* info) {
   info->coarse_degree = h.coarse_degree;
   info->coarse_range[0] = h.coarse_range[0];
   info->coarse_range[1] = h.coarse_range[1];
+  for (int i = 0; i < 8; ++i) info->setup_phase_s[i] = h.setup_phase_s[i];
   return GMG_OK;
 }
 

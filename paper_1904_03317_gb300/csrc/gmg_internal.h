@@ -217,7 +217,8 @@ struct Hier {
   std::vector<double> coarse_val;
   int coarse_degree = 0;
   double coarse_range[2] = {0, 0};
-  bool coarse_too_large = false;  // the chosen coarse solver does not take this many unknowns
+  bool coarse_too_large = false;
+  double setup_phase_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // the chosen coarse solver does not take this many unknowns
   std::vector<double> lambda;          // per level
   double setup_host_s = 0, setup_device_s = 0;
   DeviceState* dev = nullptr;

@@ -298,9 +298,42 @@ static inline int64_t lower_index(const std::vector<uint64_t>& keys, uint64_t k)
   return it - keys.begin();
 }
 
+// Lookup in the sorted node-key array through row offsets: keys are
+// (z << 42) | (y << 21) | x, so all keys of one lattice row (z, y) are
+// contiguous; a search touches only that row.
+struct RowIndex {
+  const std::vector<uint64_t>* keys = nullptr;
+  int64_t ny = 1;
+  std::vector<int64_t> start;  // (nz * ny + 1) row offsets
+  void build(const std::vector<uint64_t>& k, int64_t nz, int64_t ny_) {
+    keys = &k;
+    ny = ny_;
+    start.assign((size_t)(nz * ny + 1), 0);
+    for (uint64_t v : k) start[(size_t)(row(v) + 1)]++;
+    for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+  }
+  int64_t row(uint64_t v) const { return (int64_t)(v >> 42) * ny + (int64_t)((v >> 21) & ((1u << 21) - 1)); }
+  int64_t find(uint64_t v) const {
+    const int64_t r = row(v);
+    if (r < 0 || r + 1 >= (int64_t)start.size()) return -1;
+    auto b = keys->begin() + start[(size_t)r], e = keys->begin() + start[(size_t)r + 1];
+    auto it = std::lower_bound(b, e, v);
+    if (it == e || *it != v) return -1;
+    return it - keys->begin();
+  }
+};
+
 // ------------------------------------------------------------------ build
 void build_host_hierarchy(Hier& h, const Forest& f) {
   auto t0 = std::chrono::steady_clock::now();
+  // wall time of the build phases (gmg_info.setup_phase_s)
+  auto last = t0;
+  auto phase_mark = [&](int ph) {
+    const auto now = std::chrono::steady_clock::now();
+    if (ph > 0) h.setup_phase_s[ph - 1] = std::chrono::duration<double>(now - last).count();
+    last = now;
+  };
+  phase_mark(0);
   const int dim = f.dim, k = h.k;
   h.dim = dim;
   for (int d = 0; d < 3; ++d) {
@@ -368,6 +401,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   auto pad64 = [](int64_t v) { return (v + 63) / 64 * 64; };  // level starts 256-byte aligned
   h.level_offset[1] = pad64((int64_t)h.levels[0].slot_class.size());
 
+  phase_mark(0);
   // ------------------------------------------------ levels l >= 1: blocks
   std::vector<HashMap64> block_map(L + 1);  // parent position (level l-1) -> block index
   for (int l = 1; l <= L; ++l) {
@@ -605,6 +639,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   h.total_slots = h.level_offset[L + 1];
   if (h.total_slots >= (int64_t)1 << 32) throw std::runtime_error("level vectors exceed 2^32 slots");
 
+  phase_mark(1);
   // --------------------------------------------------------- leaf mesh
   ActiveHost& A = h.active;
   const int64_t nleaf = (int64_t)f.leaf_level.size();
@@ -629,8 +664,10 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   const int64_t nn = (int64_t)nodes.size();
   A.n_leaf_nodes = nn;
   std::vector<int32_t> node_of((size_t)nleaf * NLOC);
+  RowIndex node_index;
+  node_index.build(nodes, dim > 2 ? node_ext[2] + 1 : 1, dim > 1 ? node_ext[1] + 1 : 1);
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < (int64_t)keys.size(); ++i) node_of[i] = (int32_t)lower_index(nodes, keys[i]);
+  for (int64_t i = 0; i < (int64_t)keys.size(); ++i) node_of[i] = (int32_t)node_index.find(keys[i]);
   std::vector<uint64_t>().swap(keys);
   // coarsest leaf level having each node
   std::vector<int8_t> lmin(nn, 127);
@@ -644,6 +681,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
         for (int j = 0; j < NLOC; ++j) lmin[node_of[(size_t)cl[t] * NLOC + j]] = (int8_t)l;
     }
   }
+  phase_mark(2);
   // classify: 0 unknown, 1 Dirichlet, 2 hanging
   std::vector<int8_t> ncls(nn, 0);
   std::vector<int32_t> hang_of(nn, -1);
@@ -736,6 +774,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       A.unknown_keys[unk_of[i]] = (int64_t)nodes[i];
       A.home_level[unk_of[i]] = lmin[i];
     }
+  phase_mark(3);
   // hanging rows
   A.hang_key.resize(hrows.size());
   A.hang_ptr.assign(hrows.size() + 1, 0);
@@ -746,7 +785,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     hang_of[hrows[r].node] = (int32_t)r;
     A.hang_key[r] = (int64_t)nodes[hrows[r].node];
     for (int m = 0; m < hrows[r].n; ++m) {
-      int64_t mi = lower_index(nodes, (uint64_t)hrows[r].mkey[m]);
+      int64_t mi = node_index.find((uint64_t)hrows[r].mkey[m]);
       if (mi < 0) throw std::runtime_error("master node of a hanging node is not a leaf node");
       if (ncls[mi] == 2) throw std::runtime_error("constraint chain");
       if (ncls[mi] == 1) continue;  // Dirichlet master carries 0
@@ -779,6 +818,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
         A.hm_ptr.push_back(cnt[u + 1]);
       }
   }
+  phase_mark(4);
   // per leaf cell tables
   A.cell_nodes.resize((size_t)nleaf * NLOC);
   A.cell_coeff.resize(nleaf);
@@ -799,6 +839,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       A.cell_nodes[(size_t)i * NLOC + j] = v;
     }
   }
+  phase_mark(5);
   // leaf patches and full leaf sibling groups: in canonical (Morton) order
   // the 2^d children of a parent (and the 4^d grandchildren of a grandparent)
   // are consecutive, the first one with the low coordinate bits 0
@@ -892,6 +933,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       A.loose_level[c] = A.cell_level[cell];
     }
   }
+  phase_mark(6);
   // home slots
   A.home_slot.resize(nu);
   A.home_global.resize(nu);
@@ -926,6 +968,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   }
   if (bad_home) throw std::runtime_error("an unknown is not an S node of its home level");
 
+  phase_mark(7);
   // ------------------------------------------------- coarse matrix A_0
   {
     const int n1 = k + 1;
@@ -997,6 +1040,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       h.coarse_inverse.swap(A0);
     }
   }
+  phase_mark(8);
   h.setup_host_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 

@@ -80,7 +80,7 @@ class InfoC(C.Structure):
                 ("lambda_max", C.c_double * MAX_LEVELS), ("device_bytes", C.c_uint64),
                 ("setup_host_s", C.c_double), ("setup_device_s", C.c_double),
                 ("leaf_patches", C.c_uint64), ("leaf_groups", C.c_uint64), ("leaf_single_cells", C.c_uint64),
-                ("coarse_degree", C.c_int), ("coarse_range", C.c_double * 2)]
+                ("coarse_degree", C.c_int), ("coarse_range", C.c_double * 2), ("setup_phase_s", C.c_double * 8)]
 
 
 class KernelStatsC(C.Structure):
