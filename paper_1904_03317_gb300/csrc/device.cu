@@ -185,6 +185,7 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.n_bricks = L.n_bricks;
   a.list_rest = L.list_rest;
   a.n_rest = L.n_rest;
+  a.no_ghosts = L.n_slots == L.n_groups * (int64_t)ipow_h(2 * h.k, h.dim);
   a.list_jump = L.list_jump;
   a.n_uniform = L.n_uniform;
   a.n_jump = L.n_jump;

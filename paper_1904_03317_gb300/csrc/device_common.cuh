@@ -72,6 +72,7 @@ struct LevelArgs {
   int64_t n_bricks;
   const int32_t* list_rest;
   int64_t n_rest;
+  bool no_ghosts;             // the level has no refinement-edge (ghost) blocks
   int64_t n_uniform, n_jump;
   const int32_t* nbr_coarse;  // level l-1 neighbour table (l >= 2)
   int64_t coarse_lat[3];      // coarse lattice extents (l == 1)

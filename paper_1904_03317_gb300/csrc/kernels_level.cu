@@ -911,6 +911,18 @@ struct Brick2S {
   static constexpr int OPT = (B::OB + R - 1) / R;
 };
 
+template <int K>
+__host__ __device__ constexpr double ebrick(int f, int c) {
+  const int cell = f / (2 * K) > 1 ? 1 : f / (2 * K);
+  const int r = f - 2 * K * cell, j = c - K * cell;
+  return (j >= 0 && j <= K) ? embed1<K>(r, j) : 0.0;
+}
+
+// MODE 2 (residual + restriction, levels >= 2 without refinement-edge nodes):
+// r = g - A x on the brick's own nodes, then g_{l-1} += R r with R = P^T on
+// the parent group's (2K+1)^3 coarse nodes; `out` is g_{l-1}.  Coarse nodes
+// inside the parent group receive only this brick's fine nodes; those on its
+// faces are shared with neighbouring bricks (atomics).
 template <int K, int MODE>
 __global__ void __launch_bounds__(Brick2S<K>::TB)
 level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float* xprev,
@@ -945,8 +957,8 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
     if (has_out && kk < OB) {
       const int32_t gid = own_group(oi / NO, oj / NO, kk / NO);
       slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
+      if constexpr (MODE >= 1) pre_g[o] = gvec[slots[o]];
       if constexpr (MODE == 1) {
-        pre_g[o] = gvec[slots[o]];
         if (xprev) pre_xp[o] = xprev[slots[o]];
       }
     }
@@ -1006,6 +1018,85 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
   }
   __syncthreads();
   // stage 3: z direction and the update
+  if constexpr (MODE == 2) {
+    // residual on the own nodes into shared memory (T1 is free now)
+    float* Rs = reinterpret_cast<float*>(T1);
+    if (has_out) {
+      float2 pq[HB];
+      static_for<0, HB>([&](auto z) { pq[z] = T2[z * S::ZS + ol]; });
+#pragma unroll
+      for (int o = 0; o < OPT; ++o) {
+        const int kk = part + R * o;
+        if (kk >= OB) break;
+        float2 acc = make_float2(0.f, 0.f);
+        static_for<0, OB>([&](auto r) {
+          if (kk == r) {
+            static_for<0, HB>([&](auto c) {
+              constexpr double bm = bbrick<K, false>(r, c);
+              constexpr double bk = bbrick<K, true>(r, c);
+              if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bk, (float)bm), pq[c], acc);
+            });
+          }
+        });
+        Rs[oi + OB * (oj + OB * kk)] = pre_g[o] - coef * (acc.x + acc.y);
+      }
+    }
+    __syncthreads();
+    constexpr int NC = 2 * K + 1;  // coarse nodes per direction of the parent group
+    float* Q1 = Rs + OB * OB * OB;  // [fz][fy][cx]
+    float* Q2 = Q1 + OB * OB * NC;  // [fz][cy][cx]
+    int32_t* cnb = reinterpret_cast<int32_t*>(Q2 + OB * NC * NC);
+    if (tid < 27) cnb[tid] = a.nbr_coarse[(int64_t)a.parent[own_group(0, 0, 0)] * 27 + tid];
+    for (int line = tid; line < OB * OB; line += TB) {  // x: (fy, fz)
+      float v[OB];
+      static_for<0, OB>([&](auto f) { v[f] = Rs[f + OB * line]; });
+      static_for<0, NC>([&](auto c) {
+        float t = 0.f;
+        static_for<0, OB>([&](auto f) {
+          constexpr double e = ebrick<K>(f, c);
+          if constexpr (e != 0.0) t += (float)e * v[f];
+        });
+        Q1[line * NC + c] = t;
+      });
+    }
+    __syncthreads();
+    for (int line = tid; line < OB * NC; line += TB) {  // y: (fz, cx)
+      const int fz = line / NC, cx = line % NC;
+      float v[OB];
+      static_for<0, OB>([&](auto f) { v[f] = Q1[(fz * OB + f) * NC + cx]; });
+      static_for<0, NC>([&](auto c) {
+        float t = 0.f;
+        static_for<0, OB>([&](auto f) {
+          constexpr double e = ebrick<K>(f, c);
+          if constexpr (e != 0.0) t += (float)e * v[f];
+        });
+        Q2[(fz * NC + c) * NC + cx] = t;
+      });
+    }
+    __syncthreads();
+    for (int line = tid; line < NC * NC; line += TB) {  // z: (cx, cy), then add into g_{l-1}
+      const int cx = line % NC, cy = line / NC;
+      float v[OB];
+      static_for<0, OB>([&](auto f) { v[f] = Q2[(f * NC + cy) * NC + cx]; });
+      static_for<0, NC>([&](auto cz) {
+        float t = 0.f;
+        static_for<0, OB>([&](auto f) {
+          constexpr double e = ebrick<K>(f, cz);
+          if constexpr (e != 0.0) t += (float)e * v[f];
+        });
+        const int ox = cx == 2 * K, oy = cy == 2 * K, oz = (int)cz == 2 * K;
+        const int32_t blk = cnb[(ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1))];
+        if (blk >= 0) {
+          float* dst = out + (int64_t)blk * NO * NO * NO + (cx - 2 * K * ox) +
+                       NO * ((cy - 2 * K * oy) + NO * ((int)cz - 2 * K * oz));
+          const bool inner = cx > 0 && cx < 2 * K && cy > 0 && cy < 2 * K && (int)cz > 0 && (int)cz < 2 * K;
+          if (inner) *dst += t;
+          else atomicAdd(dst, t);
+        }
+      });
+    }
+    return;
+  }
   if (!has_out) return;
   float2 pq[HB];
   static_for<0, HB>([&](auto z) { pq[z] = T2[z * S::ZS + ol]; });
@@ -1116,15 +1207,16 @@ struct RestrictSmem {
 template <typename T, int DIM, int K>
 __global__ void __launch_bounds__(256)
 level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __restrict__ gvec,
-                               T* __restrict__ gc) {
+                               T* __restrict__ gc, const int32_t* __restrict__ list, int64_t n_list) {
   using F = Fast<DIM, K>;
   using S = RestrictSmem<T, DIM, K>;
   constexpr int NG = S::NG, N1 = S::N1, NO = F::NO, TW = F::TW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int team = threadIdx.x / TW;
   const int lane = threadIdx.x % TW;
-  const int64_t g = (int64_t)blockIdx.x * F::TPB + team;
-  const bool active = g < a.n_groups;
+  const int64_t gi = (int64_t)blockIdx.x * F::TPB + team;
+  const bool active = gi < n_list;
+  const int64_t g = active ? (list ? (int64_t)list[gi] : gi) : 0;
   uint64_t* states = reinterpret_cast<uint64_t*>(smem_raw);
   T* coefs = reinterpret_cast<T*>(states + F::TPB);
   int32_t* nb = reinterpret_cast<int32_t*>(coefs + F::TPB) + team * F::NNB;
@@ -1533,6 +1625,29 @@ template <typename T, int DIM, int K>
 static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* gc, cudaStream_t s) {
   using F = Fast<DIM, K>;
   if (a.n_groups == 0) return cudaSuccess;
+  // FP32, above level 1, every group of the level in a brick and no
+  // refinement-edge nodes: one brick pass for residual and restriction.  (The
+  // brick pass assigns each fine node's whole residual to the brick owning
+  // it, the per-group kernel splits g between the groups touching a node and
+  // takes each group's own cells' A u: the two do not mix on one level.)
+  const bool bricks = DIM == 3 && std::is_same<T, float>::value && a.level >= 2 && a.n_bricks > 0 &&
+                      a.n_rest == 0 && a.no_ghosts;
+  if constexpr (DIM == 3 && std::is_same<T, float>::value) {
+    if (bricks) {
+      const size_t smb = Brick2S<K>::bytes();
+      static const bool initb = [&] {
+        cudaFuncSetAttribute(level_cheb_brick_f2_kernel<K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+        return true;
+      }();
+      (void)initb;
+      level_cheb_brick_f2_kernel<K, 2><<<(unsigned)a.n_bricks, Brick2S<K>::TB, smb, s>>>(a, u, nullptr, g, gc, 0.f,
+                                                                                           0.f);
+      GMG_COUNT_LAUNCH();
+    }
+  }
+  const int32_t* list = bricks ? a.list_rest : nullptr;
+  const int64_t n = bricks ? a.n_rest : a.n_groups;
+  if (n == 0) return cudaGetLastError();
   const size_t sm = RestrictSmem<T, DIM, K>::bytes();
   // set once, thread-safe (function-local static)
   static const bool init = [&] {
@@ -1540,8 +1655,8 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
     return true;
   }();
   (void)init;
-  dim3 grid((unsigned)((a.n_groups + F::TPB - 1) / F::TPB));
-  level_residual_restrict_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, u, g, gc);
+  dim3 grid((unsigned)((n + F::TPB - 1) / F::TPB));
+  level_residual_restrict_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, u, g, gc, list, n);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -1563,12 +1678,6 @@ cudaError_t launch_level_residual_restrict(int dim, int k, const LevelArgs& a, c
 // three 1-D passes shared by the eight groups.  Each fine node is written by
 // the brick group whose lattice holds it with the smallest offset, with that
 // group's add / set masks, exactly as the per-group kernel would.
-template <int K>
-__host__ __device__ constexpr double ebrick(int f, int c) {
-  const int cell = f / (2 * K) > 1 ? 1 : f / (2 * K);
-  const int r = f - 2 * K * cell, j = c - K * cell;
-  return (j >= 0 && j <= K) ? embed1<K>(r, j) : 0.0;
-}
 
 template <typename T, int K>
 struct ProBrick {
