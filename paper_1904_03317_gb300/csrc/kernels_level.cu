@@ -684,6 +684,156 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   }
 }
 
+// ------------------------------- smoothing kernel, groups at coefficient jumps
+// The extended operator of level_cheb_kernel (rows 0..2K-1 for the group's
+// own cells, row 2K for the lower neighbour's cell, combined per neighbour
+// coefficient) with the memory pattern of level_cheb_fast_kernel: one warp
+// per group, halo rows by vector loads, warp-level synchronisation only.
+template <typename T, int K>
+struct JumpSmem {
+  using F = Fast<3, K>;
+  static constexpr int NE = 2 * K + 1;
+  static constexpr int T1 = F::L1 * NE;
+  static constexpr int T2 = F::NH * NE * NE;
+  static constexpr int Y = NE * NE * NE;
+  static constexpr int PER = 2 * T1 + 3 * T2 + Y + F::NOWN + 8;
+  static constexpr size_t HEADER = ((size_t)F::TPB * (8 + 4 * F::NNB) + 15) / 16 * 16;
+  static constexpr size_t bytes() { return HEADER + (size_t)F::TPB * PER * sizeof(T); }
+};
+
+template <typename T, int K, int MODE>
+__global__ void __launch_bounds__(256)
+level_cheb_jump_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, const T* __restrict__ gvec,
+                       const T* __restrict__ dinv, T* out, T c1, T c2) {
+  using F = Fast<3, K>;
+  using S = JumpSmem<T, K>;
+  constexpr int NH = F::NH, NO = F::NO, TW = F::TW, NE = S::NE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / TW;
+  const int lane = threadIdx.x % TW;
+  const int64_t t = (int64_t)blockIdx.x * F::TPB + team;
+  const bool active = t < a.n_jump;
+  const int64_t g = active ? a.list_jump[t] : 0;
+  uint64_t* masks = reinterpret_cast<uint64_t*>(smem_raw);
+  int32_t* nb = reinterpret_cast<int32_t*>(masks + F::TPB) + team * F::NNB;
+  T* T1M = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
+  T* T1K = T1M + S::T1;
+  T* T2MM = T1K + S::T1;
+  T* T2MK = T2MM + S::T2;
+  T* T2KM = T2MK + S::T2;
+  T* Y = T2KM + S::T2;
+  T* Xown = Y + S::Y;
+  T* coefs = Xown + F::NOWN;
+  if (active) {
+    for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
+    if (lane < 8) coefs[lane] = lower_coefs<T>(a)[g * 8 + lane];
+    if (lane == 0) masks[team] = a.smask[g];
+  }
+  __syncwarp();
+  const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
+  if (active) {
+    // stage 1: halo rows along x -> extended mass and stiffness rows
+    for (int line = lane; line < F::L1; line += TW) {
+      int oy = 0, ly = 0, oz = 0, lz = 0;
+      halo_seg<K>(line % NH, oy, ly);
+      halo_seg<K>(line / NH, oz, lz);
+      const int row = NO * (ly + NO * lz);
+      T v[NH];
+      const int32_t b0 = nb[nbi<3>(-1, oy, oz)], b1 = nb[nbi<3>(0, oy, oz)], b2 = nb[nbi<3>(1, oy, oz)];
+      if (b0 >= 0) load_run<T, K>(x + (int64_t)b0 * F::NOWN + row + K, v);
+      else for (int i = 0; i < K; ++i) v[i] = T(0);
+      if (b1 >= 0) load_run<T, 2 * K>(x + (int64_t)b1 * F::NOWN + row, v + K);
+      else for (int i = 0; i < 2 * K; ++i) v[K + i] = T(0);
+      v[3 * K] = b2 >= 0 ? x[(int64_t)b2 * F::NOWN + row] : T(0);
+      if (oy == 0 && oz == 0) store_run<T, NO>(Xown + row, v + K);
+      static_for<0, NE>([&](auto e) {
+        T m = 0, kk = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bm != 0.0) m += (T)bm * v[c];
+          if constexpr (bk != 0.0) kk += (T)bk * v[c];
+        });
+        T1M[line * NE + e] = m;
+        T1K[line * NE + e] = kk;
+      });
+    }
+  }
+  __syncwarp();
+  if (active) {
+    // stage 2: y direction, lines (z, ex); T1 layout [z][y][ex]
+    for (int line = lane; line < NH * NE; line += TW) {
+      const int z = line / NE, ex = line % NE;
+      T vm[NH], vk[NH];
+      static_for<0, NH>([&](auto y) {
+        vm[y] = T1M[(z * NH + y) * NE + ex];
+        vk[y] = T1K[(z * NH + y) * NE + ex];
+      });
+      static_for<0, NE>([&](auto e) {
+        T mm = 0, mk = 0, km = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bm != 0.0) {
+            mm += (T)bm * vm[c];
+            km += (T)bm * vk[c];
+          }
+          if constexpr (bk != 0.0) mk += (T)bk * vm[c];
+        });
+        const int o = (z * NE + e) * NE + ex;
+        T2MM[o] = mm;
+        T2MK[o] = mk;
+        T2KM[o] = km;
+      });
+    }
+  }
+  __syncwarp();
+  if (active) {
+    // stage 3: z direction, lines (ey, ex)
+    for (int line = lane; line < NE * NE; line += TW) {
+      T p[NH], q[NH];
+      static_for<0, NH>([&](auto z) {
+        p[z] = sz * T2MM[z * NE * NE + line];
+        q[z] = sy * T2MK[z * NE * NE + line] + sx * T2KM[z * NE * NE + line];
+      });
+      static_for<0, NE>([&](auto e) {
+        T acc = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr double bm = bext<K, false>(e, c);
+          constexpr double bk = bext<K, true>(e, c);
+          if constexpr (bk != 0.0) acc += (T)bk * p[c];
+          if constexpr (bm != 0.0) acc += (T)bm * q[c];
+        });
+        Y[e * NE * NE + line] = acc;
+      });
+    }
+  }
+  __syncwarp();
+  if (!active) return;
+  const uint64_t smask = masks[team];
+  // combine the extended rows: row 2K stands for the lower neighbour's cell
+  for (int n = lane; n < F::NOWN; n += TW) {
+    if (!((smask >> n) & 1ull)) continue;
+    const int i0 = n % NO, i1 = (n / NO) % NO, i2 = n / (NO * NO);
+    T y = 0;
+    const int nbx = i0 == 0 ? 2 : 1, nby = i1 == 0 ? 2 : 1, nbz = i2 == 0 ? 2 : 1;
+    for (int bz = 0; bz < nbz; ++bz)
+      for (int by = 0; by < nby; ++by)
+        for (int bx = 0; bx < nbx; ++bx) {
+          const int ex = bx ? 2 * K : i0, ey = by ? 2 * K : i1, ez = bz ? 2 * K : i2;
+          y += coefs[bx | (by << 1) | (bz << 2)] * Y[(ez * NE + ey) * NE + ex];
+        }
+    const int64_t slot = g * F::NOWN + n;
+    if constexpr (MODE == 0) {
+      out[slot] = y;
+    } else {
+      const T xv = Xown[n];
+      const T xp = xprev ? xprev[slot] : T(0);
+      out[slot] = xv + c1 * (xv - xp) + c2 * dinv[slot] * (gvec[slot] - y);
+    }
+  }
+}
+
 // --------------------------------------------- smoothing kernel, 2x2x2 bricks
 // Eight uniform sibling groups at positions p + {0,1}^3 (one coefficient)
 // form a brick of (4K)^3 stored nodes whose halo is (5K+1)^3: the halo rows
@@ -1584,6 +1734,21 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
     dim3 grid((unsigned)((a.n_uniform + F::TPB - 1) / F::TPB));
     level_cheb_fast_kernel<T, DIM, K, MODE><<<grid, 256, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
     GMG_COUNT_LAUNCH();
+  }
+  if constexpr (DIM == 3) {
+    if (a.n_jump > 0) {
+      using F = Fast<3, K>;
+      const size_t sm = JumpSmem<T, K>::bytes();
+      static const bool initj = [&] {
+        cudaFuncSetAttribute(level_cheb_jump_kernel<T, K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        return true;
+      }();
+      (void)initj;
+      dim3 grid((unsigned)((a.n_jump + F::TPB - 1) / F::TPB));
+      level_cheb_jump_kernel<T, K, MODE><<<grid, 256, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+      GMG_COUNT_LAUNCH();
+    }
+    return cudaGetLastError();
   }
   if (a.n_jump > 0) {
     using G = Geo<DIM, K>;
