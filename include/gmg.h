@@ -125,7 +125,7 @@ typedef struct gmg_info {
   uint64_t n_S[GMG_MAX_LEVELS];         /* S nodes of each level (Sec. 2.3) */
   uint64_t n_I[GMG_MAX_LEVELS];         /* I (refinement-edge) nodes of each level */
   uint64_t n_home[GMG_MAX_LEVELS];      /* unknowns whose home level is l */
-  uint64_t bricks[GMG_MAX_LEVELS];      /* 2x2x2 bricks of uniform groups (3D smoother tiles) */
+  uint64_t bricks[GMG_MAX_LEVELS];      /* full 2x2x2 bricks of uniform groups (3D tiles) */
   uint64_t groups_jump[GMG_MAX_LEVELS]; /* groups next to a coefficient jump (general kernel) */
   double lambda_max[GMG_MAX_LEVELS];    /* estimated (or fixed) lambda_max of D^-1 A_l^S */
   uint64_t device_bytes;                /* device memory held by the hierarchy */
@@ -141,6 +141,9 @@ typedef struct gmg_info {
    * and numbering, hanging constraints, leaf cell tables, leaf patches and
    * groups, home slots, coarse matrix */
   double setup_phase_s[8];
+  /* partial bricks of each level (3D smoother tiles with 4 to 7 member
+   * groups; the other positions are read as halo only) */
+  uint64_t bricks_partial[GMG_MAX_LEVELS];
 } gmg_info;
 
 typedef struct gmg_stats {

@@ -334,7 +334,8 @@ gmg_status gmg_hier_info(const gmg_hier* hh, gmg_info* info) {
     info->slots[l] = h.level_offset[l + 1] - h.level_offset[l];
     info->n_S[l] = L.n_S;
     info->n_I[l] = L.n_I;
-    info->bricks[l] = L.bricks.size() / 64;
+    info->bricks[l] = L.n_bricks_full;
+    info->bricks_partial[l] = L.bricks.size() / 64 - L.n_bricks_full;
     info->groups_jump[l] = L.list_jump.size();
     info->lambda_max[l] = l < (int)h.lambda.size() ? h.lambda[l] : 0.0;
   }

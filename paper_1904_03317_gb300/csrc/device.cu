@@ -183,6 +183,8 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.pmask = L.pmask;
   a.bricks = L.bricks;
   a.n_bricks = L.n_bricks;
+  a.n_bricks_all = L.n_bricks_all;
+  a.brick_members = L.brick_members;
   a.list_rest = L.list_rest;
   a.n_rest = L.n_rest;
   a.no_ghosts = L.n_slots == L.n_groups * (int64_t)ipow_h(2 * h.k, h.dim);
@@ -268,6 +270,7 @@ void device_free(Hier& h) {
     cudaFree(L.list_uniform);
     cudaFree(L.pmask);
     cudaFree(L.bricks);
+    cudaFree(L.brick_members);
     cudaFree(L.list_jump);
     cudaFree(L.list_rest);
   }
@@ -401,7 +404,9 @@ gmg_status device_setup(Hier& h) {
     GMG_TRY(upload(d, &D.list_uniform, H.list_uniform));
     GMG_TRY(upload(d, &D.pmask, H.pmask));
     GMG_TRY(upload(d, &D.bricks, H.bricks));
-    D.n_bricks = (int64_t)H.bricks.size() / 64;
+    D.n_bricks = H.n_bricks_full;
+    D.n_bricks_all = (int64_t)H.bricks.size() / 64;
+    GMG_TRY(upload(d, &D.brick_members, H.brick_members));
     GMG_TRY(upload(d, &D.list_rest, H.list_rest));
     D.n_rest = (int64_t)H.list_rest.size();
     GMG_TRY(upload(d, &D.list_jump, H.list_jump));

@@ -42,9 +42,11 @@ struct LevelDev {
   int32_t* list_uniform = nullptr;
   int32_t* list_jump = nullptr;
   uint64_t* pmask = nullptr;    // n_groups x 4
-  int32_t* bricks = nullptr;    // n_bricks x 64
-  int64_t n_bricks = 0;
-  int32_t* list_rest = nullptr; // groups outside bricks
+  int32_t* bricks = nullptr;    // n_bricks_all x 64: full bricks, then partial ones
+  int64_t n_bricks = 0;         // full bricks
+  int64_t n_bricks_all = 0;
+  uint8_t* brick_members = nullptr;  // per partial brick: member positions
+  int32_t* list_rest = nullptr; // groups outside full bricks
   int64_t n_rest = 0;
   int64_t n_uniform = 0, n_jump = 0;
   double scale[3] = {0, 0, 0};  // K-term factor per direction: prod_{j!=i} h_j / h_i
@@ -69,7 +71,9 @@ struct LevelArgs {
   const int32_t* list_jump;
   const uint64_t* pmask;
   const int32_t* bricks;
-  int64_t n_bricks;
+  int64_t n_bricks;           // full bricks (smoothing, residual, prolongation)
+  int64_t n_bricks_all;       // with the partial bricks (smoothing only)
+  const uint8_t* brick_members;
   const int32_t* list_rest;
   int64_t n_rest;
   bool no_ghosts;             // the level has no refinement-edge (ghost) blocks

@@ -134,11 +134,17 @@ struct LevelHost {
   // (one merged tensor product suffices), and the rest
   std::vector<int32_t> list_uniform, list_jump;
   // 2x2x2 bricks of uniform groups sharing one coefficient (3D): per brick the
-  // 4^3 block indices of positions -1..2 around it (own groups at 0..1);
-  // list_uniform then holds only the uniform groups outside bricks
+  // 4^3 block indices of positions -1..2 around it (own groups at 0..1).  The
+  // first n_bricks_full are full (eight member groups); the rest are partial
+  // bricks, smoothed only, whose members are marked in brick_members (bit
+  // bx + 2 by + 4 bz).  list_uniform then holds only the uniform groups
+  // outside bricks.
   std::vector<int32_t> bricks;
-  // groups outside bricks (all groups when there are none), increasing
+  int64_t n_bricks_full = 0;
+  std::vector<uint8_t> brick_members;  // per partial brick
+  // groups outside full bricks (all groups when there are none), increasing
   std::vector<int32_t> list_rest;
+
   // prolongation write masks over the group's (2k+1)^d nodes (2 x 64 bits):
   // add = stored S nodes (u += P uc), set = I nodes this group writes
   std::vector<uint64_t> pmask;      // n_groups x 4: add[0], add[1], set[0], set[1]

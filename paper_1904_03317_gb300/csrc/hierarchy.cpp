@@ -25,6 +25,7 @@
 #include <cmath>
 #include <numeric>
 #include <stdexcept>
+#include <unordered_set>
 
 #include "gmg_internal.h"
 
@@ -622,12 +623,52 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
         lv.bricks.insert(lv.bricks.end(), tab.begin(), tab.end());
         for (int b = 0; b < 8; ++b) taken[own[b]] = 1;
       }
+      lv.n_bricks_full = (int64_t)lv.bricks.size() / 64;
+      // groups outside full bricks go to the per-group residual and
+      // prolongation kernels
+      for (int32_t g : lv.list_uniform)
+        if (!taken[g]) lv.list_rest.push_back(g);
+      // partial bricks (smoothing only): a brick position holding at least
+      // kMinMembers uniform groups of one coefficient outside full bricks.
+      // The other positions keep whatever block is there (another group or a
+      // ghost block) and are read as halo only; a position without a block
+      // reads zeros: the stencil of an S node of a member covers only cells
+      // of this level, whose nodes all lie in blocks.
+      constexpr int kMinMembers = 4;
+      std::unordered_set<uint64_t> seen;
+      for (int32_t g0 : lv.list_uniform) {
+        if (taken[g0]) continue;
+        const int64_t* c = gs[g0].c;
+        const int64_t p[3] = {c[0] & ~int64_t(1), c[1] & ~int64_t(1), c[2] & ~int64_t(1)};
+        if (!seen.insert(pack3(p[0], p[1], p[2])).second) continue;
+        int32_t own[8];
+        unsigned members = 0;
+        for (int b = 0; b < 8; ++b) {
+          own[b] = slot_at(p[0] + (b & 1), p[1] + ((b >> 1) & 1), p[2] + ((b >> 2) & 1));
+          const int32_t s = own[b];
+          if (s >= 0 && s < lv.n_groups && is_uniform[s] && !taken[s] && lv.coeff[s] == lv.coeff[g0])
+            members |= 1u << b;
+        }
+        if (__builtin_popcount(members) < kMinMembers) continue;
+        std::vector<int32_t> tab(64);
+        for (int z = 0; z < 4; ++z)
+          for (int y = 0; y < 4; ++y)
+            for (int x = 0; x < 4; ++x) {
+              const int32_t s = slot_at(p[0] + x - 1, p[1] + y - 1, p[2] + z - 1);
+              tab[x + 4 * (y + 4 * z)] = s < 0 ? -1 : s;
+            }
+        lv.bricks.insert(lv.bricks.end(), tab.begin(), tab.end());
+        lv.brick_members.push_back((uint8_t)members);
+        for (int b = 0; b < 8; ++b)
+          if ((members >> b) & 1) taken[own[b]] = 1;
+      }
       std::vector<int32_t> rest;
       for (int32_t g : lv.list_uniform)
         if (!taken[g]) rest.push_back(g);
       lv.list_uniform.swap(rest);
+    } else {
+      lv.list_rest = lv.list_uniform;
     }
-    lv.list_rest = lv.list_uniform;
     lv.list_rest.insert(lv.list_rest.end(), lv.list_jump.begin(), lv.list_jump.end());
     std::sort(lv.list_rest.begin(), lv.list_rest.end());
     for (int64_t s = 0; s < nslots; ++s) {

@@ -114,6 +114,19 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
+// The last stage of the sum factorisations gives a thread the output rows
+// r = part + R o (o = 0, 1, ...), r < N.  `part` is uniform over a warp, so
+// one branch per part selects fully unrolled bodies in which r and o are
+// compile-time constants: f(o, r).
+template <int N, int R, class F>
+__device__ __forceinline__ void own_rows(int part, F&& f) {
+  static_for<0, R>([&](auto p) {
+    if (part == p) {
+      static_for<0, (N - p + R - 1) / R>([&](auto o) { f(o, std::integral_constant<int, p + R * o>{}); });
+    }
+  });
+}
+
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 template <int DIM, int K>
@@ -880,6 +893,12 @@ __device__ __forceinline__ void brick_seg(int h, int& gidx, int& l) {
   l = p - 2 * K * gidx;
 }
 
+// Member positions (bit bx + 2 by + 4 bz) of brick br: all eight for a full
+// brick, those of the table for a partial one (smoothing launches only).
+__device__ __forceinline__ unsigned brick_members(const LevelArgs& a, int64_t br) {
+  return br < a.n_bricks ? 0xFFu : (unsigned)a.brick_members[br - a.n_bricks];
+}
+
 template <typename T, int K, int MODE>
 __global__ void __launch_bounds__(BrickG<K>::TB)
 level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, const T* __restrict__ gvec, T* out,
@@ -902,8 +921,10 @@ level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, co
   __syncthreads();
   // own groups sit at table positions (1..2)^3
   auto own_group = [&](int bx, int by, int bz) { return tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))]; };
-  if (tid < 8) smask[tid] = a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)];
-  const T coef = group_coef<T>(a, own_group(0, 0, 0));
+  const unsigned members = brick_members(a, br);
+  if (tid < 8) smask[tid] = ((members >> tid) & 1u) ? a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)] : 0ull;
+  const int m0 = __ffs(members) - 1;  // a member: the coefficient is common to all
+  const T coef = group_coef<T>(a, own_group(m0 & 1, (m0 >> 1) & 1, m0 >> 2));
   // this thread's outputs: line ol = (i, j), k = part + R * o
   const int ol = tid % L3, part = tid / L3;
   const bool has_out = tid < L3 * R;
@@ -915,7 +936,7 @@ level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, co
     const int kk = part + R * o;
     slots[o] = -1;
     pre_xp[o] = pre_g[o] = T(0);
-    if (has_out && kk < OB) {
+    if (has_out && kk < OB && ((members >> ((oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO)))) & 1u)) {
       const int32_t gid = own_group(oi / NO, oj / NO, kk / NO);
       slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
       if constexpr (MODE == 1) {
@@ -1092,8 +1113,10 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
   if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
   __syncthreads();
   auto own_group = [&](int bx, int by, int bz) { return tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))]; };
-  if (tid < 8) smask[tid] = a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)];
-  const float coef = a.coeff32[own_group(0, 0, 0)];
+  const unsigned members = MODE == 2 ? 0xFFu : brick_members(a, br);
+  if (tid < 8) smask[tid] = ((members >> tid) & 1u) ? a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)] : 0ull;
+  const int m0 = __ffs(members) - 1;  // a member: the coefficient is common to all
+  const float coef = a.coeff32[own_group(m0 & 1, (m0 >> 1) & 1, m0 >> 2)];
   const int ol = tid % L3, part = tid / L3;
   const bool has_out = tid < L3 * R;
   const int oi = ol % OB, oj = ol / OB;
@@ -1104,7 +1127,7 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
     const int kk = part + R * o;
     slots[o] = -1;
     pre_xp[o] = pre_g[o] = 0.f;
-    if (has_out && kk < OB) {
+    if (has_out && kk < OB && ((members >> ((oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO)))) & 1u)) {
       const int32_t gid = own_group(oi / NO, oj / NO, kk / NO);
       slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
       if constexpr (MODE >= 1) pre_g[o] = gvec[slots[o]];
@@ -1174,22 +1197,15 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
     if (has_out) {
       float2 pq[HB];
       static_for<0, HB>([&](auto z) { pq[z] = T2[z * S::ZS + ol]; });
-#pragma unroll
-      for (int o = 0; o < OPT; ++o) {
-        const int kk = part + R * o;
-        if (kk >= OB) break;
+      own_rows<OB, R>(part, [&](auto o, auto r) {
         float2 acc = make_float2(0.f, 0.f);
-        static_for<0, OB>([&](auto r) {
-          if (kk == r) {
-            static_for<0, HB>([&](auto c) {
-              constexpr double bm = bbrick<K, false>(r, c);
-              constexpr double bk = bbrick<K, true>(r, c);
-              if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bk, (float)bm), pq[c], acc);
-            });
-          }
+        static_for<0, HB>([&](auto c) {
+          constexpr double bm = bbrick<K, false>(r, c);
+          constexpr double bk = bbrick<K, true>(r, c);
+          if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bk, (float)bm), pq[c], acc);
         });
-        Rs[oi + OB * (oj + OB * kk)] = pre_g[o] - coef * (acc.x + acc.y);
-      }
+        Rs[oi + OB * (oj + OB * (int)r)] = pre_g[o] - coef * (acc.x + acc.y);
+      });
     }
     __syncthreads();
     constexpr int NC = 2 * K + 1;  // coarse nodes per direction of the parent group
@@ -1265,32 +1281,26 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
       c2d[pz] = c2 / (coef * (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz));
     }
   }
-#pragma unroll
-  for (int o = 0; o < OPT; ++o) {
-    const int kk = part + R * o;
-    if (kk >= OB) break;
+  const int gsel_xy = (oi / NO) + 2 * (oj / NO), node_xy = (oi % NO) + NO * (oj % NO);
+  own_rows<OB, R>(part, [&](auto o, auto r) {
     float2 acc = make_float2(0.f, 0.f);
-    static_for<0, OB>([&](auto r) {
-      if (kk == r) {
-        static_for<0, HB>([&](auto c) {
-          constexpr double bm = bbrick<K, false>(r, c);
-          constexpr double bk = bbrick<K, true>(r, c);
-          if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bk, (float)bm), pq[c], acc);
-        });
-      }
+    static_for<0, HB>([&](auto c) {
+      constexpr double bm = bbrick<K, false>(r, c);
+      constexpr double bk = bbrick<K, true>(r, c);
+      if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bk, (float)bm), pq[c], acc);
     });
     float y = acc.x + acc.y;
-    const int gsel = (oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO));
-    const int node = (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
-    if (!((smask[gsel] >> node) & 1ull)) continue;
+    constexpr int gz = r / NO, nz = r % NO;
+    const int node = node_xy + NO * NO * nz;
+    if (!((smask[gsel_xy + 4 * gz] >> node) & 1ull)) return;
     y *= coef;
     if constexpr (MODE == 0) {
       out[slots[o]] = y;
     } else {
-      const float xv = Xown[oi + OB * (oj + OB * kk)];
-      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2d[kk & 1] * (pre_g[o] - y);
+      const float xv = Xown[oi + OB * (oj + OB * (int)r)];
+      out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2d[r & 1] * (pre_g[o] - y);
     }
-  }
+  });
 }
 
 // Slot (in the level l-1 vector) of node jd of the parent cell of group g
@@ -1694,7 +1704,7 @@ template <typename T, int DIM, int K, int MODE>
 static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, const T* g, const T* dinv,
                                T* out, T c1, T c2, cudaStream_t s) {
   if constexpr (DIM == 3) {
-    if (a.n_bricks > 0) {
+    if (a.n_bricks_all > 0) {  // full and partial bricks
       if constexpr (std::is_same<T, float>::value) {
         const size_t sm = Brick2S<K>::bytes();
         // set once, thread-safe (function-local static)
@@ -1704,8 +1714,8 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
           return true;
         }();
         (void)init;
-        level_cheb_brick_f2_kernel<K, MODE><<<(unsigned)a.n_bricks, Brick2S<K>::TB, sm, s>>>(a, x, xprev, g, out,
-                                                                                             c1, c2);
+        level_cheb_brick_f2_kernel<K, MODE><<<(unsigned)a.n_bricks_all, Brick2S<K>::TB, sm, s>>>(a, x, xprev, g,
+                                                                                                 out, c1, c2);
         GMG_COUNT_LAUNCH();
       } else {
         const size_t sm = BrickSmem<T, K>::bytes();
@@ -1716,8 +1726,8 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
           return true;
         }();
         (void)init;
-        level_cheb_brick_kernel<T, K, MODE><<<(unsigned)a.n_bricks, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out, c1,
-                                                                                           c2);
+        level_cheb_brick_kernel<T, K, MODE><<<(unsigned)a.n_bricks_all, BrickG<K>::TB, sm, s>>>(a, x, xprev, g, out,
+                                                                                               c1, c2);
         GMG_COUNT_LAUNCH();
       }
     }

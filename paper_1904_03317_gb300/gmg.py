@@ -80,7 +80,8 @@ class InfoC(C.Structure):
                 ("lambda_max", C.c_double * MAX_LEVELS), ("device_bytes", C.c_uint64),
                 ("setup_host_s", C.c_double), ("setup_device_s", C.c_double),
                 ("leaf_patches", C.c_uint64), ("leaf_groups", C.c_uint64), ("leaf_single_cells", C.c_uint64),
-                ("coarse_degree", C.c_int), ("coarse_range", C.c_double * 2), ("setup_phase_s", C.c_double * 8)]
+                ("coarse_degree", C.c_int), ("coarse_range", C.c_double * 2), ("setup_phase_s", C.c_double * 8),
+                ("bricks_partial", C.c_uint64 * MAX_LEVELS)]
 
 
 class KernelStatsC(C.Structure):

@@ -62,6 +62,23 @@ def test_leaf_cells_partitioned_into_patches_groups_and_single_cells():
     assert seen["3d_q2_patches"][0] % 3 != 0
 
 
+def test_smoother_tiles_of_the_parity_workloads():
+    """The 3D parity workloads exercise both brick forms of the smoother:
+    full bricks (eight uniform groups of one coefficient) and partial bricks
+    (four to seven), and every group is in at most one brick."""
+    for name, w in small_workloads().items():
+        m = G.build_mesh(w)
+        i = G.Hierarchy(G.Context(-1), m, w.degree, w.coeff).info
+        full = sum(i.bricks[l] for l in range(i.n_levels))
+        partial = sum(i.bricks_partial[l] for l in range(i.n_levels))
+        for l in range(1, i.n_levels):
+            assert 8 * i.bricks[l] + 4 * i.bricks_partial[l] <= i.groups[l]
+        if w.coarse.dim == 3:
+            assert full > 0 and partial > 0, name
+        else:
+            assert full == 0 and partial == 0, name
+
+
 @pytest.mark.parametrize("name", list(small_workloads()))
 def test_host_hierarchy_matches_oracle(name):
     w = small_workloads()[name]

@@ -188,6 +188,37 @@ def test_chebyshev_smoother(torch, name):
 
 
 @pytest.mark.parametrize("name", NAMES)
+def test_chebyshev_smoother_fp32(torch, name):
+    """The FP32 smoothers (full and partial bricks, single groups, groups at
+    coefficient jumps) against the FP64 oracle: m Chebyshev steps in FP32
+    from zero and from a nonzero start, to single-precision rounding."""
+    O, H = gpu_hier(torch, name, G.PREC_FP32)
+    rng = np.random.default_rng(18)
+    m = O.cheb_degree
+    for l in range(1, len(O.levels)):
+        lev = O.levels[l]
+        idx, cls = level_maps(H, O, l)
+        g = np.zeros(len(lev.keys)); g[lev.S] = rng.uniform(-1, 1, len(lev.S))
+        want = np.zeros(len(lev.keys))
+        want[lev.S] = ogmg.chebyshev(lev.A_S, lev.dinv, np.zeros(len(lev.S)), g[lev.S], lev.lam, m, x0_is_zero=True)
+        ud = torch.zeros(len(idx), dtype=torch.float32, device="cuda")
+        tmp = torch.zeros_like(ud)
+        gd = dev(torch, to_slots(g, idx, len(idx)), G.PREC_FP32)
+        H.level_smooth(l, gd, ud, tmp, True)
+        torch.cuda.synchronize()
+        assert rel_err(from_slots(host(ud), idx, len(lev.keys)), want) < 5e-5
+        u0 = rng.uniform(-1, 1, len(lev.keys))
+        want = u0.copy()
+        want[lev.S] = ogmg.chebyshev(lev.A_S, lev.dinv, u0[lev.S], g[lev.S] - lev.A_SI @ u0[lev.I], lev.lam, m)
+        ud = dev(torch, to_slots(u0, idx, len(idx)), G.PREC_FP32)
+        H.level_smooth(l, gd, ud, tmp, False)
+        torch.cuda.synchronize()
+        got = from_slots(host(ud), idx, len(lev.keys))
+        assert rel_err(got[lev.S], want[lev.S]) < 5e-5
+        assert np.array_equal(got[lev.I], u0[lev.I].astype(np.float32).astype(np.float64))  # I values kept
+
+
+@pytest.mark.parametrize("name", NAMES)
 def test_eigenvalue_estimates(torch, name):
     O, H = gpu_hier(torch, name, fixed=False)
     for l in range(1, len(O.levels)):
