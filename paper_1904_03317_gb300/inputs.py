@@ -9,9 +9,9 @@ seed give?".  Every function takes plain integer cell descriptions
 (level, lattice coordinates) and returns numpy arrays, so each side can call
 it on the leaves of its own mesh.
 
-Mesh shapes follow the refinement rules of Sec. 3.5 of the paper (circle,
-shell, uniform rounds, each followed by closure) and the configurations of
-the solver experiments in Sec. 4.
+Mesh shapes follow the refinement rules of Sec. 3.5 of the paper (uniform,
+circle, quadrant, sine curve, annulus; each round followed by closure) and
+the configurations of the solver experiments in Sec. 4.
 """
 from __future__ import annotations
 
@@ -185,6 +185,110 @@ def round_random(seed: int, round_index: int, prob: float) -> RoundFn:
         return uniform01(seed, key) < prob
 
     return fn
+
+
+# ------------------------------------------------ refinement sequences of Sec. 3.5
+# The meshes of the partition-efficiency study: a coarse mesh of [-1, 1]^d,
+# then L rounds of one selection rule, each followed by closure.
+
+def round_vertex_in_ball(radius: float) -> RoundFn:
+    """Flag leaves with at least one vertex strictly inside |x| < radius, and
+    the leaves whose closed box contains the centre (a cell around the centre
+    whose vertices all lie outside the small ball, such as the single coarse
+    cell [-1, 1]^d, would otherwise never be refined)."""
+    r2 = float(radius) ** 2
+
+    def fn(cm, level, coords, finest):
+        blo, bhi = cm.boxes(level, coords)
+        hit = np.all((blo <= 0.0) & (bhi >= 0.0), axis=1)
+        for b in range(1 << cm.dim):
+            v = np.where([(b >> d) & 1 for d in range(cm.dim)], bhi, blo)
+            hit |= np.sum(v * v, axis=1) < r2
+        return hit
+
+    return fn
+
+
+def round_negative_orthant() -> RoundFn:
+    """Flag leaves whose centre has no positive coordinate (the negative
+    quadrant, octant in 3D; the single coarse cell [-1, 1]^d has its centre at
+    the origin, so the first round refines it)."""
+
+    def fn(cm, level, coords, finest):
+        blo, bhi = cm.boxes(level, coords)
+        return np.all(0.5 * (blo + bhi) <= 0.0, axis=1)
+
+    return fn
+
+
+def sine_curve(x):
+    """The curve of the "sine curve" sequence: y = 3/4 sin(3x - 5/2) + 1/5."""
+    return 0.75 * np.sin(3.0 * np.asarray(x, dtype=np.float64) - 2.5) + 0.2
+
+
+def round_sine_curve() -> RoundFn:
+    """Flag leaves whose closed box meets the curve y = sine_curve(x) (in 3D the
+    surface of all z over that curve)."""
+
+    def fn(cm, level, coords, finest):
+        blo, bhi = cm.boxes(level, coords)
+        x0, x1 = blo[:, 0], bhi[:, 0]
+        fmin = np.minimum(sine_curve(x0), sine_curve(x1))
+        fmax = np.maximum(sine_curve(x0), sine_curve(x1))
+        # interior extrema at 3x - 5/2 = pi/2 + j pi (sine = +-1)
+        for j in range(-3, 3):
+            xc = (2.5 + np.pi / 2 + j * np.pi) / 3.0
+            inside = (x0 < xc) & (xc < x1)
+            fc = float(sine_curve(xc))
+            fmin = np.where(inside, np.minimum(fmin, fc), fmin)
+            fmax = np.where(inside, np.maximum(fmax, fc), fmax)
+        return (fmin <= bhi[:, 1]) & (fmax >= blo[:, 1])
+
+    return fn
+
+
+def round_centre_in_shell(r_in: float, r_out: float) -> RoundFn:
+    """Flag leaves whose centre lies strictly between the radii r_in < |x| < r_out
+    (r_in = 0: strictly inside the ball of radius r_out)."""
+
+    def fn(cm, level, coords, finest):
+        blo, bhi = cm.boxes(level, coords)
+        c = 0.5 * (blo + bhi)
+        d2 = np.sum(c * c, axis=1)
+        return (d2 > r_in * r_in) & (d2 < r_out * r_out)
+
+    return fn
+
+
+# the "annulus" sequence's three steps after L - 3 uniform rounds: centres in
+# the ball of radius 0.55, then in the shells 0.3-0.42 and 0.335-0.39 (the
+# text gives 0.43 for the first shell; the per-level cell counts of the
+# paper's 3D annulus table come out exactly with 0.42)
+ANNULUS_STEPS = ((0.0, 0.55), (0.3, 0.42), (0.335, 0.39))
+
+
+def paper_sequence(name: str, dim: int, L: int) -> List[RoundFn]:
+    """Refinement rounds of the sequences of Sec. 3.5 ("uniform", "circle",
+    "quadrant", "sine", "annulus") up to finest level L."""
+    if name == "uniform":
+        return [round_uniform()] * L
+    if name == "circle":
+        return [round_vertex_in_ball(1.0 / (4.0 * np.pi))] * L
+    if name == "quadrant":
+        return [round_negative_orthant()] * L
+    if name == "sine":
+        return [round_sine_curve()] * L
+    if name == "annulus":
+        if L < 3:
+            raise ValueError("the annulus sequence needs L >= 3")
+        return [round_uniform()] * (L - 3) + [round_centre_in_shell(a, b) for a, b in ANNULUS_STEPS]
+    raise ValueError(f"unknown sequence {name!r}")
+
+
+def paper_sequence_coarse(dim: int, n: int = 1) -> CoarseMesh:
+    """[-1, 1]^d split into n^d coarse cells (n = 1: the single cell of the
+    sequences; the 3D annulus table of Sec. 3.6 starts from 5^3 cells)."""
+    return CoarseMesh(dim, (n, n, n if dim == 3 else 1), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))
 
 
 def checkerboard_coefficients(cm: CoarseMesh, low: float = 1.0, high: float = 100.0) -> np.ndarray:

@@ -1,5 +1,7 @@
 """Partitioning efficiency model (Sec. 3.4): the oracle against the paper's
-worked example and invariants, the C-ABI library against the oracle."""
+worked example and invariants, the C-ABI library against the oracle, and
+the library's mesh and model against the paper's 3D annulus table
+(Sec. 3.6) on the refinement sequences of Sec. 3.5."""
 import json
 import os
 
@@ -91,3 +93,51 @@ def test_library_rejects_bad_parts():
     m = example_mesh()
     with pytest.raises(Exception):
         m.partition_model(0)
+
+
+SEQUENCES = [(n, d) for n in ("uniform", "circle", "quadrant", "sine", "annulus") for d in (2, 3)]
+
+
+@pytest.mark.parametrize("name,dim", SEQUENCES)
+def test_paper_sequences_library_matches_oracle(name, dim):
+    """The refinement sequences of Sec. 3.5 on the single coarse cell
+    [-1, 1]^d: the library's forest (with its closure) equals the oracle's
+    leaf for leaf, and the partition model agrees."""
+    L = {2: 6, 3: 4 if name != "annulus" else 6}[dim]
+    cm = inputs.paper_sequence_coarse(dim)
+    rounds = inputs.paper_sequence(name, dim, L)
+    f = build_forest(cm, rounds)
+    m = G.Mesh(cm)
+    m.apply_rounds(rounds)
+    lv, co = m.leaves()
+    assert set((int(l), tuple(int(x) for x in c)) for l, c in zip(lv, co)) == set(
+        (l, tuple(c)) for l, c in f.leaves())
+    if name in ("uniform", "annulus"):
+        assert f.num_levels() - 1 == L
+    for n in (3, 64):
+        a, b = m.partition_model(n), partition.model(f, n)
+        assert a["n_cells"] == b["n_cells"] and a["w_level"] == b["w_level"] and a["w"] == b["w"]
+
+
+def test_annulus3d_matches_paper_table():
+    """Sec. 3.6 table, 3D annulus: the per-level cell counts of the
+    library's mesh equal the printed ones exactly (pins the sequence, the
+    vertex closure and the level structure), and so do W_opt and W_sync.
+    W per level is that of the first-child rule over an equal split of the
+    leaves in z-order; it equals the printed W on levels 0-3 and lies within
+    1.5% on levels 4-7, where the printed partition also keeps sibling
+    families together and orders the coarse cells its own way (neither is
+    part of the model of Sec. 3.4)."""
+    t = GOLDEN["annulus3d_partition_table"]["value"]
+    cm = inputs.paper_sequence_coarse(3, t["coarse_cells_per_dim"])
+    m = G.Mesh(cm)
+    m.apply_rounds(inputs.paper_sequence("annulus", 3, t["finest_level"]))
+    r = m.partition_model(t["n_parts"])
+    assert r["n_cells"] == t["n_cells"] and sum(r["n_cells"]) == t["total_cells"]
+    assert r["w_opt"] == pytest.approx(t["w_opt"], abs=0.05)
+    assert r["w_sync"] == t["w_sync"]
+    assert r["w_level"][:4] == t["w_level"][:4]
+    for got, want in zip(r["w_level"][4:], t["w_level"][4:]):
+        assert abs(got - want) <= 0.015 * want
+    assert r["w"] == pytest.approx(t["w"], rel=0.005)
+    assert r["efficiency"] == pytest.approx(t["efficiency"], rel=0.005)
