@@ -83,6 +83,9 @@ struct HashMap64 {
   }
 };
 
+// Radix sort of 64-bit keys (OpenMP), ascending.
+void parallel_sort_u64(std::vector<uint64_t>& v);
+
 // Cell lattice coordinates packed into 64 bits (21 bits each).
 inline uint64_t pack3(int64_t x, int64_t y, int64_t z) {
   return (uint64_t)x | ((uint64_t)y << 21) | ((uint64_t)z << 42);

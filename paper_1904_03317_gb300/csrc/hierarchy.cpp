@@ -255,7 +255,7 @@ static inline int ipow(int b, int e) {
   return r;
 }
 
-static void parallel_sort_u64(std::vector<uint64_t>& v) {
+void parallel_sort_u64(std::vector<uint64_t>& v) {
   // LSD radix sort, 16-bit digits, skipping digits above the largest key
   if (v.empty()) return;
   uint64_t mx = 0;
