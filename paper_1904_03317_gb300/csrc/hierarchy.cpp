@@ -549,6 +549,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     // node is written by its own group, or -- when its block is a ghost -- by
     // every group that touches it (the same value)
     lv.pmask.assign((size_t)lv.n_groups * 4, 0);
+#pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < lv.n_groups; ++g) {
       for (int n = 0; n < NGRP; ++n) {
         int loc[3] = {n % NG, dim > 1 ? (n / NG) % NG : 0, dim > 2 ? n / (NG * NG) : 0};
