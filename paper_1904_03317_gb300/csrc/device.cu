@@ -390,6 +390,7 @@ gmg_status device_setup(Hier& h) {
     D.n_S = (double)H.n_S;
     D.n_I = (double)H.n_I;
     D.n_S_jump = (double)H.n_S_jump;
+    D.zero_each_cycle = l == 0 || H.n_I > 0 || H.n_ghosts > 0;
     if (l == 0) continue;
     D.cheb_flops = (double)H.n_groups * cheb_group_flops(dim, k);
     D.n_groups = H.n_groups;
@@ -432,6 +433,9 @@ gmg_status device_setup(Hier& h) {
     GMG_TRY(dev_alloc(d, &p, ns * esz)); d->uB = p;
     GMG_TRY(dev_alloc(d, &p, ns * esz)); d->g = p;
     GMG_TRY(dev_alloc(d, &p, ns * esz)); d->dinv = p;
+    // Dirichlet slots of the smoother vectors are never written: zero once
+    GMG_CUDA_TRY(cudaMemsetAsync(d->uA, 0, ns * esz, d->stream));
+    GMG_CUDA_TRY(cudaMemsetAsync(d->uB, 0, ns * esz, d->stream));
   }
   // active mesh
   const ActiveHost& A = h.active;
@@ -570,7 +574,8 @@ static cudaError_t coarse(const Hier& h, const T* g0, T* u0, cudaStream_t s) {
 // m Chebyshev updates on level l: x_{j+1} = x_j + rho_j rho_{j-1} (x_j - x_{j-1})
 // + (2 rho_j / delta) D^{-1} (g - A x_j), x_1 = x_0 + D^{-1}(g - A x_0) / theta
 // (Saad, Alg. 12.1, written as a three-term recurrence).  `cur` holds x_0;
-// from_zero: x_0 = 0 and `other` must be zero on every slot.  Returns the
+// from_zero: x_0 = 0 and `other` must be zero on I slots (its S slots are
+// written before they are read; x_prev = 0 is not read).  Returns the
 // buffer that holds the result.
 template <typename T>
 static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cur, T* other, bool from_zero,
@@ -602,7 +607,9 @@ static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cu
     double rho_new = 1.0 / (2.0 * D.sigma - rho);
     T c1 = jacobi ? (T)0 : (T)(rho_new * rho), c2 = jacobi ? (T)1 : (T)(2.0 * rho_new / D.delta);
     Track t(h.dev, GMG_K_CHEB, cheb_bytes, D.cheb_flops);
-    e = launch_level_cheb<T>(h.dim, h.k, a, cur, other, g, dinv, other, c1, c2, false, s);
+    // from zero, x_prev = x_0 = 0 on S: passed as null instead of read
+    const T* xprev = from_zero && j == 1 ? nullptr : other;
+    e = launch_level_cheb<T>(h.dim, h.k, a, cur, xprev, g, dinv, other, c1, c2, false, s);
     if (e != cudaSuccess) return e;
     std::swap(cur, other);
     rho = rho_new;
@@ -622,9 +629,24 @@ static gmg_status vcycle_impl(Hier& h, const double* r, double* z, double* rz_ou
   T* uB = (T*)d->uB;
   T* g = (T*)d->g;
   const T* dinv = (const T*)d->dinv;
-  GMG_CUDA_TRY(cudaMemsetAsync(uA, 0, bytes, s));
-  GMG_CUDA_TRY(cudaMemsetAsync(uB, 0, bytes, s));
   GMG_CUDA_TRY(cudaMemsetAsync(g, 0, bytes, s));
+  // u_A, u_B: the down-sweep needs zeros on I and ghost slots (the up-sweep's
+  // prolongation sets them).  S slots need none: the first smoothing update
+  // writes every stored slot of u_A and the second takes no x_prev, and
+  // Dirichlet slots stay zero from setup.  So only levels with I nodes or
+  // ghost blocks (and level 0) are cleared, in runs of consecutive levels.
+  for (int l = 0; l <= L;) {
+    if (!d->lv[l].zero_each_cycle) {
+      ++l;
+      continue;
+    }
+    int e = l;
+    while (e + 1 <= L && d->lv[e + 1].zero_each_cycle) ++e;
+    const int64_t a = d->lv[l].offset, b = d->lv[e].offset + d->lv[e].n_slots;
+    GMG_CUDA_TRY(cudaMemsetAsync(uA + a, 0, (size_t)(b - a) * sizeof(T), s));
+    GMG_CUDA_TRY(cudaMemsetAsync(uB + a, 0, (size_t)(b - a) * sizeof(T), s));
+    l = e + 1;
+  }
   {
     Track t(d, GMG_K_COPY_TO, (12.0 + sizeof(T)) * d->n_unknowns, 0.0);
     GMG_CUDA_TRY(launch_copy_to_mg<T>(d->n_unknowns, r, d->home, g, s));

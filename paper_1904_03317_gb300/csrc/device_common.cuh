@@ -31,6 +31,9 @@ struct LevelDev {
   int64_t n_groups = 0;
   int64_t n_slots = 0;
   int64_t offset = 0;           // in the concatenated level vectors
+  // the V-cycle zeroes the level's smoother vectors before each down-sweep:
+  // level 0 and levels with refinement-edge (I) nodes or ghost blocks
+  bool zero_each_cycle = true;
   int32_t* nbr = nullptr;       // n_groups x 3^d
   uint64_t* state = nullptr;    // n_groups
   double* coeff = nullptr;      // n_groups
