@@ -606,9 +606,9 @@ static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cu
   for (int j = 1; j < m; ++j) {
     double rho_new = 1.0 / (2.0 * D.sigma - rho);
     T c1 = jacobi ? (T)0 : (T)(rho_new * rho), c2 = jacobi ? (T)1 : (T)(2.0 * rho_new / D.delta);
-    Track t(h.dev, GMG_K_CHEB, cheb_bytes, D.cheb_flops);
     // from zero, x_prev = x_0 = 0 on S: passed as null instead of read
     const T* xprev = from_zero && j == 1 ? nullptr : other;
+    Track t(h.dev, GMG_K_CHEB, xprev ? cheb_bytes : cheb_bytes - sizeof(T) * D.n_S, D.cheb_flops);
     e = launch_level_cheb<T>(h.dim, h.k, a, cur, xprev, g, dinv, other, c1, c2, false, s);
     if (e != cudaSuccess) return e;
     std::swap(cur, other);
