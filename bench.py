@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch of a kernel kind on the headline
 # workload, from one ncu capture (profiles/level_smoother_dram_traffic_*.md);
 # None where no capture matches the current kernels
-TRAFFIC_PER_LAUNCH = {"cheb": 50.00e6}
+TRAFFIC_PER_LAUNCH = {"cheb": 48.34e6}
 
 
 class ClockSampler:
