@@ -800,9 +800,18 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
         }
   }
   if (chain_or_bad) throw std::runtime_error("hanging node with too many masters");
-  std::vector<HRow> hrows;
-  for (auto& v : hrows_t) hrows.insert(hrows.end(), v.begin(), v.end());
-  std::sort(hrows.begin(), hrows.end(), [](const HRow& a, const HRow& b) { return a.node < b.node; });
+  // rows in node order: a row's place is the number of hanging nodes before it
+  std::vector<int32_t> hrank(nn + 1, 0);
+  for (int64_t i = 0; i < nn; ++i) hrank[i + 1] = hrank[i] + (ncls[i] == 2 ? 1 : 0);
+  std::vector<HRow> hrows((size_t)hrank[nn]);
+  {
+    std::vector<size_t> base(hrows_t.size() + 1, 0);
+    for (size_t t = 0; t < hrows_t.size(); ++t) base[t + 1] = base[t] + hrows_t[t].size();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < (int64_t)hrows_t.size(); ++t)
+      for (const HRow& r : hrows_t[t]) hrows[(size_t)hrank[r.node]] = r;
+    std::vector<std::vector<HRow>>().swap(hrows_t);
+  }
   // unknown numbering
   std::vector<int64_t> unk_of(nn, -1);
   int64_t nu = 0;
@@ -823,19 +832,50 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   A.hang_col.clear();
   A.hang_w.clear();
   A.hang_master_key.clear();
-  for (size_t r = 0; r < hrows.size(); ++r) {
-    hang_of[hrows[r].node] = (int32_t)r;
-    A.hang_key[r] = (int64_t)nodes[hrows[r].node];
-    for (int m = 0; m < hrows[r].n; ++m) {
-      int64_t mi = node_index.find((uint64_t)hrows[r].mkey[m]);
-      if (mi < 0) throw std::runtime_error("master node of a hanging node is not a leaf node");
-      if (ncls[mi] == 2) throw std::runtime_error("constraint chain");
-      if (ncls[mi] == 1) continue;  // Dirichlet master carries 0
-      A.hang_col.push_back((int32_t)unk_of[mi]);
-      A.hang_w.push_back(hrows[r].w[m]);
-      A.hang_master_key.push_back(hrows[r].mkey[m]);
+  {
+    // masters of every row resolved in parallel (Dirichlet masters dropped),
+    // then laid out by a prefix sum over the rows
+    const int64_t nh = (int64_t)hrows.size();
+    std::vector<int32_t> mnode((size_t)nh * 9, -1);
+    std::vector<int32_t> nkeep(nh + 1, 0);
+    bool not_leaf = false, chain = false;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nh; ++r) {
+      hang_of[hrows[r].node] = (int32_t)r;
+      A.hang_key[r] = (int64_t)nodes[hrows[r].node];
+      int keep = 0;
+      for (int m = 0; m < hrows[r].n; ++m) {
+        const int64_t mi = node_index.find((uint64_t)hrows[r].mkey[m]);
+        if (mi < 0) {
+          not_leaf = true;
+          continue;
+        }
+        if (ncls[mi] == 2) chain = true;
+        if (ncls[mi] != 0) continue;  // Dirichlet master carries 0
+        mnode[(size_t)r * 9 + m] = (int32_t)mi;
+        ++keep;
+      }
+      nkeep[r + 1] = keep;
     }
-    A.hang_ptr[r + 1] = (int32_t)A.hang_col.size();
+    if (not_leaf) throw std::runtime_error("master node of a hanging node is not a leaf node");
+    if (chain) throw std::runtime_error("constraint chain");
+    for (int64_t r = 0; r < nh; ++r) A.hang_ptr[r + 1] = A.hang_ptr[r] + nkeep[r + 1];
+    const size_t nnz = (size_t)A.hang_ptr[nh];
+    A.hang_col.resize(nnz);
+    A.hang_w.resize(nnz);
+    A.hang_master_key.resize(nnz);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nh; ++r) {
+      int32_t at = A.hang_ptr[r];
+      for (int m = 0; m < hrows[r].n; ++m) {
+        const int32_t mi = mnode[(size_t)r * 9 + m];
+        if (mi < 0) continue;
+        A.hang_col[at] = (int32_t)unk_of[mi];
+        A.hang_w[at] = hrows[r].w[m];
+        A.hang_master_key[at] = hrows[r].mkey[m];
+        ++at;
+      }
+    }
   }
   {
     // transposed constraints, masters in increasing unknown order
