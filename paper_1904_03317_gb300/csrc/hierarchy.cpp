@@ -700,10 +700,24 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < nleaf; ++i)
     for (int j = 0; j < NLOC; ++j) keys[(size_t)i * NLOC + j] = cell_key(i, j);
-  std::vector<uint64_t> nodes(keys);
+  // distinct node keys in key order, sorted as dense lattice indices
+  // (z ny + y) nx + x, which keep the order and need fewer radix passes
+  const uint64_t lnx = (uint64_t)node_ext[0] + 1, lny = (uint64_t)node_ext[1] + 1;
+  std::vector<uint64_t> nodes(keys.size());
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < (int64_t)keys.size(); ++i) {
+    int64_t q[3];
+    unpack3(keys[i], q);
+    nodes[i] = ((uint64_t)q[2] * lny + (uint64_t)q[1]) * lnx + (uint64_t)q[0];
+  }
   parallel_sort_u64(nodes);
   nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
   const int64_t nn = (int64_t)nodes.size();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < nn; ++i) {
+    const uint64_t t = nodes[i] / lnx;
+    nodes[i] = pack3((int64_t)(nodes[i] % lnx), (int64_t)(t % lny), (int64_t)(t / lny));
+  }
   A.n_leaf_nodes = nn;
   std::vector<int32_t> node_of((size_t)nleaf * NLOC);
   RowIndex node_index;
