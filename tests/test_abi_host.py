@@ -177,3 +177,21 @@ def test_invalid_solver_variants_rejected():
     for kw in (dict(smoother=7), dict(coarse_solver=3), dict(coarse_tol=0.0), dict(coarse_tol=1.5)):
         with pytest.raises(Exception):
             G.Hierarchy(G.Context(-1), m, w.degree, **kw)
+
+
+@pytest.mark.parametrize("depth", [6, 20])
+def test_leaf_order_is_depth_first_z_order(depth):
+    """The library lists leaves in the canonical order (coarse cells in
+    lexicographic order, then depth-first with children in z-order), both
+    when tree, Morton index and level fit one 64-bit sort key and at the
+    deepest allowed level (3D, level 20), where they do not."""
+    from oracle import partition
+    cm = inputs.CoarseMesh(3, (2, 1, 1), (0.0, 0.0, 0.0), (2.0, 1.0, 1.0))
+    rounds = [inputs.round_sphere_surface((0.3001, 0.4001, 0.5001), 1e-7)] * depth
+    f = build_forest(cm, rounds)
+    m = G.Mesh(cm)
+    m.apply_rounds(rounds)
+    lv, co = m.leaves()
+    assert int(lv.max()) == depth
+    got = [(int(l), tuple(int(x) for x in c)) for l, c in zip(lv, co)]
+    assert got == [(l, tuple(c)) for l, c in partition._dfs_leaves(f)]
