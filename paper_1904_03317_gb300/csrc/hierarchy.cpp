@@ -500,7 +500,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     // pass 0 writes every node's class and key; pass 1 re-derives them from
     // every group that touches the node and checks that all groups agree
     for (int pass = 0; pass < 2; ++pass) {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) reduction(|| : bad)
     for (int64_t g = 0; g < lv.n_groups; ++g) {
       const int64_t* p = gs[g].c;
       uint64_t st = lv.state[g];
@@ -749,7 +749,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   };
   std::vector<std::vector<HRow>> hrows_t(omp_get_max_threads());
   bool chain_or_bad = false;
-#pragma omp parallel for schedule(dynamic, 4096)
+#pragma omp parallel for schedule(dynamic, 4096) reduction(|| : chain_or_bad)
   for (int64_t i = 0; i < nn; ++i) {
     if (key_is_boundary(nodes[i])) {
       ncls[i] = 1;
@@ -853,7 +853,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     std::vector<int32_t> mnode((size_t)nh * 9, -1);
     std::vector<int32_t> nkeep(nh + 1, 0);
     bool not_leaf = false, chain = false;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) reduction(|| : not_leaf, chain)
     for (int64_t r = 0; r < nh; ++r) {
       hang_of[hrows[r].node] = (int32_t)r;
       A.hang_key[r] = (int64_t)nodes[hrows[r].node];
