@@ -951,8 +951,10 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     A.pat_coeff.clear();
     A.pat_level.clear();
     A.loose_cells.clear();
-    int64_t i = 0;
-    while (i < nleaf) {
+    // whether a patch or a full group starts at leaf i (independent per i)
+    std::vector<uint8_t> starts((size_t)nleaf, 0);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nleaf; ++i) {
       const int lvl = f.leaf_level[i];
       bool patch = lvl > 1 && i + npc <= nleaf;
       for (int d = 0; d < dim && patch; ++d)
@@ -964,44 +966,61 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
           if (f.leaf_coords[3 * (i + b) + d] != f.leaf_coords[3 * i + d] + 2 * ((hi >> d) & 1) + ((lo >> d) & 1))
             patch = false;
       }
-      if (patch) {
-        const size_t base = A.pat_nodes.size();
-        A.pat_nodes.resize(base + NPN);
-        for (int b = 0; b < npc; ++b) {
-          const int hi = b >> dim, lo = b & (nch - 1);
-          int pc[3] = {0, 0, 0};
-          for (int d = 0; d < dim; ++d) pc[d] = 2 * ((hi >> d) & 1) + ((lo >> d) & 1);
-          for (int j = 0; j < NLOC; ++j) {
-            const int lx = j % (k + 1), ly = dim > 1 ? (j / (k + 1)) % (k + 1) : 0,
-                      lz = dim > 2 ? j / ((k + 1) * (k + 1)) : 0;
-            const int gx = pc[0] * k + lx, gy = pc[1] * k + ly, gz = pc[2] * k + lz;
-            A.pat_nodes[base + gx + NP * (gy + NP * gz)] = A.cell_nodes[(size_t)(i + b) * NLOC + j];
-          }
-        }
-        A.pat_coeff.push_back(A.cell_coeff[i]);
-        A.pat_level.push_back((uint8_t)lvl);
-        i += npc;
-        continue;
-      }
       bool full = lvl > 0 && i + nch <= nleaf;
-      if (full) {
-        for (int d = 0; d < dim; ++d)
-          if (f.leaf_coords[3 * i + d] & 1) full = false;
+      for (int d = 0; d < dim && full; ++d)
+        if (f.leaf_coords[3 * i + d] & 1) full = false;
+      for (int b = 1; b < nch && full; ++b) {
+        if (f.leaf_level[i + b] != lvl) full = false;
+        for (int d = 0; d < dim && full; ++d)
+          if (f.leaf_coords[3 * (i + b) + d] != f.leaf_coords[3 * i + d] + ((b >> d) & 1)) full = false;
       }
-      if (full) {
-        for (int b = 1; b < nch && full; ++b) {
-          if (f.leaf_level[i + b] != lvl) full = false;
-          for (int d = 0; d < dim && full; ++d)
-            if (f.leaf_coords[3 * (i + b) + d] != f.leaf_coords[3 * i + d] + ((b >> d) & 1)) full = false;
-        }
-      }
-      if (!full) {
+      starts[i] = (uint8_t)((patch ? 2 : 0) | (full ? 1 : 0));
+    }
+    // greedy walk in canonical order: a patch where one starts, else a full
+    // group, else a single cell
+    std::vector<int64_t> pat_at, grp_at;
+    for (int64_t i = 0; i < nleaf;) {
+      if (starts[i] & 2) {
+        pat_at.push_back(i);
+        i += npc;
+      } else if (starts[i] & 1) {
+        grp_at.push_back(i);
+        i += nch;
+      } else {
         A.loose_cells.push_back((int32_t)i);
         ++i;
-        continue;
       }
-      const size_t base = A.grp_nodes.size();
-      A.grp_nodes.resize(base + NGN);
+    }
+    std::vector<uint8_t>().swap(starts);
+    const int64_t np = (int64_t)pat_at.size(), ngr = (int64_t)grp_at.size();
+    A.pat_nodes.resize((size_t)np * NPN);
+    A.pat_coeff.resize(np);
+    A.pat_level.resize(np);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < np; ++p) {
+      const int64_t i = pat_at[p];
+      const size_t base = (size_t)p * NPN;
+      for (int b = 0; b < npc; ++b) {
+        const int hi = b >> dim, lo = b & (nch - 1);
+        int pc[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) pc[d] = 2 * ((hi >> d) & 1) + ((lo >> d) & 1);
+        for (int j = 0; j < NLOC; ++j) {
+          const int lx = j % (k + 1), ly = dim > 1 ? (j / (k + 1)) % (k + 1) : 0,
+                    lz = dim > 2 ? j / ((k + 1) * (k + 1)) : 0;
+          const int gx = pc[0] * k + lx, gy = pc[1] * k + ly, gz = pc[2] * k + lz;
+          A.pat_nodes[base + gx + NP * (gy + NP * gz)] = A.cell_nodes[(size_t)(i + b) * NLOC + j];
+        }
+      }
+      A.pat_coeff[p] = A.cell_coeff[i];
+      A.pat_level[p] = (uint8_t)f.leaf_level[i];
+    }
+    A.grp_nodes.resize((size_t)ngr * NGN);
+    A.grp_coeff.resize(ngr);
+    A.grp_level.resize(ngr);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < ngr; ++q) {
+      const int64_t i = grp_at[q];
+      const size_t base = (size_t)q * NGN;
       for (int b = 0; b < nch; ++b) {
         const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
         for (int j = 0; j < NLOC; ++j) {
@@ -1011,9 +1030,8 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
           A.grp_nodes[base + gx + NG * (gy + NG * gz)] = A.cell_nodes[(size_t)(i + b) * NLOC + j];
         }
       }
-      A.grp_coeff.push_back(A.cell_coeff[i]);
-      A.grp_level.push_back((uint8_t)lvl);
-      i += nch;
+      A.grp_coeff[q] = A.cell_coeff[i];
+      A.grp_level[q] = (uint8_t)f.leaf_level[i];
     }
     A.n_groups = (int64_t)A.grp_coeff.size();
     A.n_patches = (int64_t)A.pat_coeff.size();
