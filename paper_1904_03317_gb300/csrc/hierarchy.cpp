@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <memory>
 #include <cmath>
 #include <numeric>
 #include <stdexcept>
@@ -255,25 +256,27 @@ static inline int ipow(int b, int e) {
   return r;
 }
 
-void parallel_sort_u64(std::vector<uint64_t>& v) {
-  // LSD radix sort, 16-bit digits, skipping digits above the largest key
-  if (v.empty()) return;
+// LSD radix sort of n keys in place, 16-bit digits, skipping digits above
+// the largest key; `scratch` holds n keys (contents ignored)
+static void radix_sort_u64(uint64_t* v, uint64_t* scratch, size_t n) {
+  if (n == 0) return;
   uint64_t mx = 0;
 #pragma omp parallel for reduction(max : mx)
-  for (size_t i = 0; i < v.size(); ++i) mx = std::max(mx, v[i]);
+  for (size_t i = 0; i < n; ++i) mx = std::max(mx, v[i]);
   int bits = 0;
   while (bits < 64 && (mx >> bits)) bits += 16;
-  std::vector<uint64_t> tmp(v.size());
-  int nt = omp_get_max_threads();
+  const int nt = omp_get_max_threads();
+  std::vector<size_t> hist((size_t)nt * 65536);
+  uint64_t* src = v;
+  uint64_t* dst = scratch;
   for (int shift = 0; shift < bits; shift += 16) {
-    std::vector<size_t> hist((size_t)nt * 65536, 0);
-    size_t n = v.size();
+    std::fill(hist.begin(), hist.end(), 0);
 #pragma omp parallel num_threads(nt)
     {
       int t = omp_get_thread_num();
       size_t b = n * t / nt, e = n * (t + 1) / nt;
       size_t* h = &hist[(size_t)t * 65536];
-      for (size_t i = b; i < e; ++i) ++h[(v[i] >> shift) & 0xFFFF];
+      for (size_t i = b; i < e; ++i) ++h[(src[i] >> shift) & 0xFFFF];
     }
     size_t sum = 0;
     for (int d = 0; d < 65536; ++d)
@@ -287,10 +290,22 @@ void parallel_sort_u64(std::vector<uint64_t>& v) {
       int t = omp_get_thread_num();
       size_t b = n * t / nt, e = n * (t + 1) / nt;
       size_t* h = &hist[(size_t)t * 65536];
-      for (size_t i = b; i < e; ++i) tmp[h[(v[i] >> shift) & 0xFFFF]++] = v[i];
+      for (size_t i = b; i < e; ++i) dst[h[(src[i] >> shift) & 0xFFFF]++] = src[i];
     }
-    v.swap(tmp);
+    std::swap(src, dst);
   }
+  if (src != v) {
+#pragma omp parallel for schedule(static)
+    for (size_t i = 0; i < n; ++i) v[i] = src[i];
+  }
+}
+
+// a buffer of n keys that is not zero-filled (every element is written before it is read)
+static std::unique_ptr<uint64_t[]> raw_keys(size_t n) { return std::unique_ptr<uint64_t[]>(new uint64_t[n]); }
+
+void parallel_sort_u64(std::vector<uint64_t>& v) {
+  std::unique_ptr<uint64_t[]> tmp = raw_keys(v.size());
+  radix_sort_u64(v.data(), tmp.get(), v.size());
 }
 
 static inline int64_t lower_index(const std::vector<uint64_t>& keys, uint64_t k) {
@@ -309,9 +324,15 @@ struct RowIndex {
   void build(const std::vector<uint64_t>& k, int64_t nz, int64_t ny_) {
     keys = &k;
     ny = ny_;
-    start.assign((size_t)(nz * ny + 1), 0);
-    for (uint64_t v : k) start[(size_t)(row(v) + 1)]++;
-    for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+    const int64_t nr = nz * ny;
+    start.assign((size_t)(nr + 1), 0);
+    // the keys are sorted: row r starts at the first key >= (z << 42) | (y << 21)
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nr; ++r) {
+      const uint64_t first = ((uint64_t)(r / ny) << 42) | ((uint64_t)(r % ny) << 21);
+      start[(size_t)r] = std::lower_bound(k.begin(), k.end(), first) - k.begin();
+    }
+    start[(size_t)nr] = (int64_t)k.size();
   }
   int64_t row(uint64_t v) const { return (int64_t)(v >> 42) * ny + (int64_t)((v >> 21) & ((1u << 21) - 1)); }
   int64_t find(uint64_t v) const {
@@ -688,43 +709,48 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   A.n_cells = nleaf;
   for (int l = 0; l <= L; ++l) h.levels[l].n_leaves = 0;
   for (int64_t i = 0; i < nleaf; ++i) h.levels[f.leaf_level[i]].n_leaves++;
-  std::vector<uint64_t> keys((size_t)nleaf * NLOC);
-  auto cell_key = [&](int64_t i, int j) -> uint64_t {
-    int lvl = f.leaf_level[i];
-    int loc[3] = {j % (k + 1), dim > 1 ? (j / (k + 1)) % (k + 1) : 0,
-                  dim > 2 ? j / ((k + 1) * (k + 1)) : 0};
-    int64_t q[3];
-    for (int d = 0; d < 3; ++d) q[d] = d < dim ? f.leaf_coords[3 * i + d] * k + loc[d] : 0;
-    return (uint64_t)node_key(lvl, q);
-  };
-#pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < nleaf; ++i)
-    for (int j = 0; j < NLOC; ++j) keys[(size_t)i * NLOC + j] = cell_key(i, j);
-  // distinct node keys in key order, sorted as dense lattice indices
-  // (z ny + y) nx + x, which keep the order and need fewer radix passes
+  // every leaf cell's nodes as dense lattice indices (z ny + y) nx + x on the
+  // finest node lattice: the order of the node keys, with fewer radix passes
   const uint64_t lnx = (uint64_t)node_ext[0] + 1, lny = (uint64_t)node_ext[1] + 1;
-  std::vector<uint64_t> nodes(keys.size());
+  const size_t nk = (size_t)nleaf * NLOC;
+  std::unique_ptr<uint64_t[]> ckeys = raw_keys(nk);
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < (int64_t)keys.size(); ++i) {
-    int64_t q[3];
-    unpack3(keys[i], q);
-    nodes[i] = ((uint64_t)q[2] * lny + (uint64_t)q[1]) * lnx + (uint64_t)q[0];
+  for (int64_t i = 0; i < nleaf; ++i) {
+    const int s = L - f.leaf_level[i];
+    for (int j = 0; j < NLOC; ++j) {
+      const int loc[3] = {j % (k + 1), dim > 1 ? (j / (k + 1)) % (k + 1) : 0, dim > 2 ? j / ((k + 1) * (k + 1)) : 0};
+      uint64_t q[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) q[d] = (uint64_t)(f.leaf_coords[3 * i + d] * k + loc[d]) << s;
+      ckeys[(size_t)i * NLOC + j] = (q[2] * lny + q[1]) * lnx + q[0];
+    }
   }
-  parallel_sort_u64(nodes);
-  nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+  // distinct nodes in key order, then back to node keys
+  std::vector<uint64_t> nodes;
+  {
+    std::unique_ptr<uint64_t[]> srt = raw_keys(nk), tmp = raw_keys(nk);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)nk; ++i) srt[i] = ckeys[i];
+    radix_sort_u64(srt.get(), tmp.get(), nk);
+    tmp.reset();
+    const size_t nu0 = (size_t)(std::unique(srt.get(), srt.get() + nk) - srt.get());
+    nodes.resize(nu0);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)nu0; ++i) {
+      const uint64_t t = srt[i] / lnx;
+      nodes[i] = pack3((int64_t)(srt[i] % lnx), (int64_t)(t % lny), (int64_t)(t / lny));
+    }
+  }
   const int64_t nn = (int64_t)nodes.size();
-#pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < nn; ++i) {
-    const uint64_t t = nodes[i] / lnx;
-    nodes[i] = pack3((int64_t)(nodes[i] % lnx), (int64_t)(t % lny), (int64_t)(t / lny));
-  }
   A.n_leaf_nodes = nn;
-  std::vector<int32_t> node_of((size_t)nleaf * NLOC);
+  std::vector<int32_t> node_of(nk);
   RowIndex node_index;
   node_index.build(nodes, dim > 2 ? node_ext[2] + 1 : 1, dim > 1 ? node_ext[1] + 1 : 1);
 #pragma omp parallel for schedule(static)
-  for (int64_t i = 0; i < (int64_t)keys.size(); ++i) node_of[i] = (int32_t)node_index.find(keys[i]);
-  std::vector<uint64_t>().swap(keys);
+  for (int64_t i = 0; i < (int64_t)nk; ++i) {
+    const uint64_t t = ckeys[i] / lnx;
+    node_of[i] = (int32_t)node_index.find(pack3((int64_t)(ckeys[i] % lnx), (int64_t)(t % lny), (int64_t)(t / lny)));
+  }
+  ckeys.reset();
   // coarsest leaf level having each node
   std::vector<int8_t> lmin(nn, 127);
   {
