@@ -467,7 +467,11 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
     lv.state.assign(lv.n_groups, 0);
     lv.coeff.resize(lv.n_groups);
     lv.parent.resize(lv.n_groups);
-    int64_t next_ghost = lv.n_groups;
+    // neighbour states and the blocks of refined neighbours (lookups only, in
+    // parallel); ghost blocks are then numbered in (group, offset) order
+    constexpr int32_t kGhostPending = -3;
+    bool bad_parent = false;
+#pragma omp parallel for schedule(static) reduction(|| : bad_parent)
     for (int64_t g = 0; g < lv.n_groups; ++g) {
       const int64_t* p = gs[g].c;
       uint64_t st = 0;
@@ -484,12 +488,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
           slot = *bm.find(pack3(q[0], q[1], q[2]));
         } else {
           s = kStateGhost;
-          auto ins = bm.insert(pack3(q[0], q[1], q[2]), (int32_t)next_ghost);
-          if (ins.second) {
-            ++next_ghost;
-            for (int d = 0; d < 3; ++d) lv.block_pos.push_back(q[d]);
-          }
-          slot = *ins.first;
+          slot = kGhostPending;
         }
         lv.nbr[(size_t)g * NNB + nb] = slot;
         st |= (uint64_t)s << (2 * nb);
@@ -504,9 +503,24 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       } else {
         const int32_t* pp = block_map[l - 1].find(pack3(p[0] >> 1, dim > 1 ? p[1] >> 1 : 0,
                                                         dim > 2 ? p[2] >> 1 : 0));
-        if (!pp || *pp >= h.levels[l - 1].n_groups)
-          throw std::runtime_error("parent of a refined cell is not a sibling group");
-        lv.parent[g] = *pp;
+        if (!pp || *pp >= h.levels[l - 1].n_groups) bad_parent = true;
+        else lv.parent[g] = *pp;
+      }
+    }
+    if (bad_parent) throw std::runtime_error("parent of a refined cell is not a sibling group");
+    int64_t next_ghost = lv.n_groups;
+    for (int64_t g = 0; g < lv.n_groups; ++g) {
+      const int64_t* p = gs[g].c;
+      for (int nb = 0; nb < NNB; ++nb) {
+        if (lv.nbr[(size_t)g * NNB + nb] != kGhostPending) continue;
+        int o[3] = {nb % 3 - 1, dim > 1 ? (nb / 3) % 3 - 1 : 0, dim > 2 ? nb / 9 - 1 : 0};
+        int64_t q[3] = {p[0] + o[0], p[1] + o[1], p[2] + o[2]};
+        auto ins = bm.insert(pack3(q[0], q[1], q[2]), (int32_t)next_ghost);
+        if (ins.second) {
+          ++next_ghost;
+          for (int d = 0; d < 3; ++d) lv.block_pos.push_back(q[d]);
+        }
+        lv.nbr[(size_t)g * NNB + nb] = *ins.first;
       }
     }
     lv.n_ghosts = next_ghost - lv.n_groups;
