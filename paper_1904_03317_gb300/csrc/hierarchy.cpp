@@ -866,19 +866,40 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       for (const HRow& r : hrows_t[t]) hrows[(size_t)hrank[r.node]] = r;
     std::vector<std::vector<HRow>>().swap(hrows_t);
   }
-  // unknown numbering
+  // unknown numbering: unknowns in node (key) order, by a prefix sum over
+  // contiguous pieces of the node range
   std::vector<int64_t> unk_of(nn, -1);
   int64_t nu = 0;
-  for (int64_t i = 0; i < nn; ++i)
-    if (ncls[i] == 0) unk_of[i] = nu++;
-  A.n_unknowns = nu;
-  A.unknown_keys.resize(nu);
-  A.home_level.resize(nu);
-  for (int64_t i = 0; i < nn; ++i)
-    if (ncls[i] == 0) {
-      A.unknown_keys[unk_of[i]] = (int64_t)nodes[i];
-      A.home_level[unk_of[i]] = lmin[i];
+  {
+    const int nt = omp_get_max_threads();
+    std::vector<int64_t> cnt(nt + 1, 0);
+#pragma omp parallel num_threads(nt)
+    {
+      const int t = omp_get_thread_num();
+      const int64_t b = nn * t / nt, e = nn * (t + 1) / nt;
+      int64_t c = 0;
+      for (int64_t i = b; i < e; ++i) c += ncls[i] == 0;
+      cnt[t + 1] = c;
     }
+    for (int t = 0; t < nt; ++t) cnt[t + 1] += cnt[t];
+    nu = cnt[nt];
+    A.n_unknowns = nu;
+    A.unknown_keys.resize(nu);
+    A.home_level.resize(nu);
+#pragma omp parallel num_threads(nt)
+    {
+      const int t = omp_get_thread_num();
+      const int64_t b = nn * t / nt, e = nn * (t + 1) / nt;
+      int64_t u = cnt[t];
+      for (int64_t i = b; i < e; ++i)
+        if (ncls[i] == 0) {
+          unk_of[i] = u;
+          A.unknown_keys[u] = (int64_t)nodes[i];
+          A.home_level[u] = lmin[i];
+          ++u;
+        }
+    }
+  }
   phase_mark(3);
   // hanging rows
   A.hang_key.resize(hrows.size());
