@@ -201,6 +201,17 @@ gmg_status gmg_mesh_refine(gmg_mesh* mesh, const uint8_t* flags, uint64_t n_flag
       return GMG_EINVAL;
     }
   }
+  {
+    // room for the children first: one rehash per level instead of a doubling cascade
+    std::vector<uint64_t> per_level(f.cells.size() + 1, 0);
+    for (uint64_t i = 0; i < n_flags; ++i)
+      if (flags[i]) per_level[(size_t)f.leaf_level[i] + 1] += (uint64_t)1 << f.dim;
+    for (size_t l = 1; l < per_level.size(); ++l) {
+      if (!per_level[l]) continue;
+      if (l == f.cells.size()) f.cells.emplace_back();
+      f.cells[l].reserve(f.cells[l].count + per_level[l]);
+    }
+  }
   for (uint64_t i = 0; i < n_flags; ++i) {
     if (!flags[i]) continue;
     int64_t c[3] = {f.leaf_coords[3 * i], f.leaf_coords[3 * i + 1], f.leaf_coords[3 * i + 2]};
