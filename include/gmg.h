@@ -230,6 +230,28 @@ gmg_status gmg_hier_build(gmg_ctx* ctx, const gmg_mesh* mesh, int degree,
 void gmg_hier_destroy(gmg_hier* h);
 gmg_status gmg_hier_info(const gmg_hier* h, gmg_info* info);
 
+/* Flags of one refinement round (Sec. 3.5: a round refines the flagged
+ * leaves, then the closure restores 2:1 balance).  Called with the current
+ * leaves in gmg_mesh_leaves order (level[i], coords[3i..3i+2], n_leaves
+ * entries, valid for the call only); writes flags[i] != 0 for each leaf to
+ * refine (the library zero-fills flags first).  Returns 0 to go on; any
+ * other value stops the build, which then fails with GMG_EINVAL. */
+typedef int (*gmg_refine_fn)(void* user, int round, uint64_t n_leaves, const int32_t* level,
+                             const int32_t* coords, uint8_t* flags);
+
+/* The hierarchy in one call, as the paper states the problem (Sec. 2.3 and
+ * Sec. 3.5): the forest of the coarse brick `cm`, n_rounds >= 0 refinement
+ * rounds whose flags `refine` computes on the leaves of the mesh as it
+ * stands (closure after each), then gmg_hier_build with degree,
+ * coarse_coeff and p as there.  The mesh is internal and released before
+ * returning (use the gmg_mesh_* calls to keep it).  Errors: those of
+ * gmg_mesh_create, gmg_mesh_refine and gmg_hier_build; GMG_EINVAL for a null
+ * argument, n_rounds < 0, refine NULL with n_rounds > 0, or a callback that
+ * stops the build.  *out is NULL on failure. */
+gmg_status gmg_build_hierarchy(gmg_ctx* ctx, const gmg_coarse_mesh* cm, int n_rounds, gmg_refine_fn refine,
+                               void* user, int degree, const double* coarse_coeff, const gmg_params* p,
+                               gmg_hier** out);
+
 /* What gmg_hier_export writes (host buffers; *count in/out = entries). */
 typedef enum gmg_export_what {
   GMG_EXPORT_UNKNOWN_KEYS = 0,  /* int64 node key per unknown (canonical order) */

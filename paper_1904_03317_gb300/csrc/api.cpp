@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -322,6 +323,39 @@ void gmg_hier_destroy(gmg_hier* h) {
     device_free(h->h);
   }
   delete h;
+}
+
+gmg_status gmg_build_hierarchy(gmg_ctx* ctx, const gmg_coarse_mesh* cm, int n_rounds, gmg_refine_fn refine,
+                               void* user, int degree, const double* coarse_coeff, const gmg_params* p,
+                               gmg_hier** out) {
+  CHECK_ARG(ctx && cm && out, "null argument");
+  *out = nullptr;
+  CHECK_ARG(n_rounds >= 0, "n_rounds must be >= 0");
+  CHECK_ARG(refine || n_rounds == 0, "refine callback is null");
+  gmg_mesh* m = nullptr;
+  gmg_status st = gmg_mesh_create(cm, &m);
+  if (st != GMG_OK) return st;
+  std::unique_ptr<gmg_mesh, void (*)(gmg_mesh*)> hold(m, gmg_mesh_destroy);  // released on every path
+  GMG_GUARD_BEGIN
+  std::vector<int32_t> level, coords;
+  std::vector<uint8_t> flags;
+  for (int r = 0; r < n_rounds && st == GMG_OK; ++r) {
+    const uint64_t n = m->f.leaf_level.size();
+    level.resize(n);
+    coords.resize(3 * n);
+    st = gmg_mesh_leaves(m, level.data(), coords.data());
+    if (st != GMG_OK) break;
+    flags.assign(n, 0);
+    if (refine(user, r, n, level.data(), coords.data(), flags.data()) != 0) {
+      set_error("refinement callback stopped the build in round " + std::to_string(r));
+      st = GMG_EINVAL;
+      break;
+    }
+    st = gmg_mesh_refine(m, flags.data(), n);
+  }
+  if (st == GMG_OK) st = gmg_hier_build(ctx, m, degree, coarse_coeff, p, out);
+  return st;
+  GMG_GUARD_END
 }
 
 gmg_status gmg_hier_info(const gmg_hier* hh, gmg_info* info) {

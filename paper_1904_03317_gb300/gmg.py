@@ -35,7 +35,8 @@ EXPORTED = [
     "gmg_create", "gmg_destroy", "gmg_last_error", "gmg_build_info",
     "gmg_mesh_create", "gmg_mesh_destroy", "gmg_mesh_num_leaves", "gmg_mesh_num_levels",
     "gmg_mesh_leaves", "gmg_mesh_refine", "gmg_mesh_partition_model",
-    "gmg_params_default", "gmg_hier_build", "gmg_hier_destroy", "gmg_hier_info", "gmg_hier_export",
+    "gmg_params_default", "gmg_hier_build", "gmg_build_hierarchy", "gmg_hier_destroy", "gmg_hier_info",
+    "gmg_hier_export",
     "gmg_assemble_rhs", "gmg_apply", "gmg_vcycle", "gmg_solve", "gmg_solve_batch", "gmg_solve_async", "gmg_solve_poll",
     "gmg_level_apply", "gmg_level_residual_restrict", "gmg_level_prolongate", "gmg_level_smooth",
     "gmg_level_inv_diag", "gmg_coarse_solve", "gmg_profile_reset", "gmg_profile_read",
@@ -54,6 +55,11 @@ class GmgError(RuntimeError):
 
 class CoarseMeshC(C.Structure):
     _fields_ = [("dim", C.c_int), ("n0", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+# gmg_refine_fn: (user, round, n_leaves, level*, coords*, flags*) -> int
+REFINE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                        C.POINTER(C.c_uint8))
 
 
 class ParamsC(C.Structure):
@@ -121,6 +127,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "gmg_mesh_partition_model": [vp, C.c_int64, C.POINTER(PartitionModelC)],
         "gmg_params_default": [C.POINTER(ParamsC)],
         "gmg_hier_build": [vp, vp, i32, vp, C.POINTER(ParamsC), C.POINTER(vp)],
+        "gmg_build_hierarchy": [vp, C.POINTER(CoarseMeshC), i32, REFINE_FN, vp, i32, vp, C.POINTER(ParamsC),
+                                C.POINTER(vp)],
         "gmg_hier_destroy": [vp],
         "gmg_hier_info": [vp, C.POINTER(InfoC)],
         "gmg_hier_export": [vp, i32, i32, vp, C.POINTER(u64)],
@@ -254,34 +262,43 @@ class Mesh:
             pass
 
 
+def _make_params(cheb_degree: int = 5, vcycle_prec: int = PREC_FP32, eig_lo: float = 0.08, eig_hi: float = 1.2,
+                 eig_iters: int = 10, fixed_lambda: Optional[Sequence[float]] = None, solve_graph: bool = True,
+                 smoother: int = 0, coarse_solver: int = 0, coarse_tol: float = 1e-3):
+    """gmg_params from keyword arguments; returns (params, array to keep alive)."""
+    p = ParamsC()
+    load_library().gmg_params_default(C.byref(p))
+    p.cheb_degree, p.eig_lo, p.eig_hi, p.eig_iters, p.vcycle_prec = cheb_degree, eig_lo, eig_hi, eig_iters, vcycle_prec
+    p.solve_graph = int(solve_graph)
+    p.smoother, p.coarse_solver, p.coarse_tol = smoother, coarse_solver, coarse_tol
+    lam = None
+    if fixed_lambda is not None:
+        lam = np.ascontiguousarray(np.asarray(fixed_lambda, dtype=np.float64))
+        p.fixed_lambda = lam.ctypes.data_as(C.POINTER(C.c_double))
+    return p, lam
+
+
 class Hierarchy:
     """Multigrid hierarchy of a mesh (gmg_hier_*), with the solve-path calls."""
 
-    def __init__(self, ctx: Context, mesh: Mesh, degree: int, coarse_coeff=None, cheb_degree: int = 5,
-                 vcycle_prec: int = PREC_FP32, eig_lo: float = 0.08, eig_hi: float = 1.2, eig_iters: int = 10,
-                 fixed_lambda: Optional[Sequence[float]] = None, solve_graph: bool = True,
-                 smoother: int = 0, coarse_solver: int = 0, coarse_tol: float = 1e-3):
-        lib = load_library()
-        p = ParamsC()
-        lib.gmg_params_default(C.byref(p))
-        p.cheb_degree, p.eig_lo, p.eig_hi, p.eig_iters, p.vcycle_prec = cheb_degree, eig_lo, eig_hi, eig_iters, vcycle_prec
-        p.solve_graph = int(solve_graph)
-        p.smoother, p.coarse_solver, p.coarse_tol = smoother, coarse_solver, coarse_tol
-        self._lam = None
-        if fixed_lambda is not None:
-            self._lam = np.ascontiguousarray(np.asarray(fixed_lambda, dtype=np.float64))
-            p.fixed_lambda = self._lam.ctypes.data_as(C.POINTER(C.c_double))
-        coeff = None
-        if coarse_coeff is not None:
-            coeff = np.ascontiguousarray(np.asarray(coarse_coeff, dtype=np.float64))
+    def __init__(self, ctx: Context, mesh: Mesh, degree: int, coarse_coeff=None, **params):
+        """params: cheb_degree (5), vcycle_prec (PREC_FP32), eig_lo (0.08), eig_hi (1.2),
+        eig_iters (10), fixed_lambda (None), solve_graph (True), smoother (0),
+        coarse_solver (0), coarse_tol (1e-3) -- the fields of gmg_params."""
+        p, keep = _make_params(**params)
+        coeff = None if coarse_coeff is None else np.ascontiguousarray(np.asarray(coarse_coeff, dtype=np.float64))
         h = C.c_void_p()
-        _check(lib.gmg_hier_build(ctx.handle, mesh.handle, degree, _ptr(coeff), C.byref(p), C.byref(h)),
+        _check(load_library().gmg_hier_build(ctx.handle, mesh.handle, degree, _ptr(coeff), C.byref(p), C.byref(h)),
                "gmg_hier_build")
-        self.handle = h
+        self._attach(ctx, h, p.vcycle_prec, keep)
+
+    def _attach(self, ctx: Context, handle: C.c_void_p, prec: int, keep) -> None:
+        self.handle = handle
         self.ctx = ctx
+        self._lam = keep
         self.info = self.get_info()
         self.n = int(self.info.n_unknowns)
-        self.prec = vcycle_prec
+        self.prec = prec
 
     def get_info(self) -> InfoC:
         info = InfoC()
@@ -399,3 +416,42 @@ def build_mesh(workload: Workload) -> Mesh:
     m = Mesh(workload.coarse)
     m.apply_rounds(workload.rounds)
     return m
+
+
+def build_hierarchy(ctx: Context, coarse: CoarseMesh, rounds, degree: int, coarse_coeff=None,
+                    **params) -> "Hierarchy":
+    """gmg_build_hierarchy: forest, refinement rounds (each a function of the
+    current leaves, as in Mesh.apply_rounds) and hierarchy in one call."""
+    lib = load_library()
+    cm = CoarseMeshC()
+    cm.dim = coarse.dim
+    for d in range(3):
+        cm.n0[d] = int(coarse.n0[d]) if d < coarse.dim else 1
+        cm.lo[d] = float(coarse.lo[d])
+        cm.hi[d] = float(coarse.hi[d])
+    rounds = list(rounds)
+    failure = []
+
+    def refine(user, r, n, level_p, coords_p, flags_p):
+        try:
+            level = np.ctypeslib.as_array(level_p, shape=(n,)).astype(np.int64)
+            coords = np.ctypeslib.as_array(coords_p, shape=(n, 3)).astype(np.int64)
+            flags = np.asarray(rounds[r](coarse, level, coords, int(level.max()) if n else 0), dtype=bool)
+            np.ctypeslib.as_array(flags_p, shape=(n,))[:] = flags.astype(np.uint8)
+            return 0
+        except Exception as e:  # an exception must not cross the C frames
+            failure.append(e)
+            return 1
+
+    cb = REFINE_FN(refine)
+    p, keep = _make_params(**params)
+    coeff = None if coarse_coeff is None else np.ascontiguousarray(np.asarray(coarse_coeff, dtype=np.float64))
+    h = C.c_void_p()
+    status = lib.gmg_build_hierarchy(ctx.handle, C.byref(cm), len(rounds), cb, None, degree, _ptr(coeff),
+                                     C.byref(p), C.byref(h))
+    if failure:
+        raise failure[0]
+    _check(status, "gmg_build_hierarchy")
+    H = Hierarchy.__new__(Hierarchy)
+    H._attach(ctx, h, p.vcycle_prec, keep)
+    return H

@@ -195,3 +195,48 @@ def test_leaf_order_is_depth_first_z_order(depth):
     assert int(lv.max()) == depth
     got = [(int(l), tuple(int(x) for x in c)) for l, c in zip(lv, co)]
     assert got == [(l, tuple(c)) for l, c in partition._dfs_leaves(f)]
+
+
+@pytest.mark.parametrize("name", ["2d_q2_circle", "3d_q2_checker", "3d_q1_sphere"])
+def test_build_hierarchy_in_one_call_equals_stepwise(name):
+    """gmg_build_hierarchy (forest, rounds through the flag callback, then the
+    hierarchy) gives the hierarchy of gmg_mesh_create + gmg_mesh_refine per
+    round + gmg_hier_build."""
+    w = small_workloads()[name]
+    ctx = G.Context(-1)
+    a = G.Hierarchy(ctx, G.build_mesh(w), w.degree, w.coeff, cheb_degree=w.cheb_degree)
+    b = G.build_hierarchy(ctx, w.coarse, w.rounds, w.degree, w.coeff, cheb_degree=w.cheb_degree)
+    assert a.n == b.n and a.info.n_levels == b.info.n_levels
+    for what in (G.EXPORT_UNKNOWN_KEYS, G.EXPORT_HOME_LEVEL, G.EXPORT_HOME_SLOT):
+        np.testing.assert_array_equal(a.export(what), b.export(what))
+    np.testing.assert_array_equal(a.export(G.EXPORT_HANGING), b.export(G.EXPORT_HANGING))
+    for l in range(a.info.n_levels):
+        np.testing.assert_array_equal(a.export(G.EXPORT_LEVEL_KEYS, l), b.export(G.EXPORT_LEVEL_KEYS, l))
+        np.testing.assert_array_equal(a.export(G.EXPORT_LEVEL_CLASS, l), b.export(G.EXPORT_LEVEL_CLASS, l))
+
+
+def test_build_hierarchy_errors():
+    w = small_workloads()["2d_q1_circle"]
+    ctx = G.Context(-1)
+    # no rounds: the coarse mesh alone
+    h = G.build_hierarchy(ctx, w.coarse, [], w.degree)
+    assert h.info.n_levels == 1 and h.n == (4 - 1) * (4 - 1)
+
+    def stop(cm, level, coords, finest):
+        raise KeyError("flag function failed")
+
+    with pytest.raises(KeyError):
+        G.build_hierarchy(ctx, w.coarse, [inputs.round_uniform(), stop], w.degree)
+    import ctypes as C
+    lib = G.load_library()
+    cm = G.CoarseMeshC()
+    cm.dim, cm.n0[0], cm.n0[1], cm.n0[2] = 2, 2, 2, 1
+    for d in range(3):
+        cm.lo[d], cm.hi[d] = 0.0, 1.0
+    out = C.c_void_p()
+    halt = G.REFINE_FN(lambda user, r, n, lv, co, fl: 1)
+    assert lib.gmg_build_hierarchy(ctx.handle, C.byref(cm), 1, halt, None, 1, None, None, C.byref(out)) == G.EINVAL
+    assert not out.value
+    assert lib.gmg_build_hierarchy(ctx.handle, C.byref(cm), 1, G.REFINE_FN(), None, 1, None, None,
+                                   C.byref(out)) == G.EINVAL
+    assert lib.gmg_build_hierarchy(ctx.handle, C.byref(cm), -1, halt, None, 1, None, None, C.byref(out)) == G.EINVAL
