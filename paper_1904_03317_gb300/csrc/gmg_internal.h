@@ -111,6 +111,9 @@ struct Forest {
   bool inside(int level, const int64_t* c) const;
   bool exists(int level, const int64_t* c) const;
   bool refined(int level, const int64_t* c) const;
+  // one lookup: -1 if the cell does not exist (or lies outside), 0 for a
+  // leaf, 1 for a refined cell
+  int state(int level, const int64_t* c) const;
   void refine_cell(int level, const int64_t* c);
   void ensure_exists(int level, const int64_t* c);
   void close();

@@ -480,10 +480,11 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
         int64_t q[3] = {p[0] + o[0], p[1] + o[1], p[2] + o[2]};
         int s;
         int32_t slot;
+        const int fs = f.state(Lp, q);
         if (!f.inside(Lp, q)) {
           s = kStateOutside;
           slot = -1;
-        } else if (f.refined(Lp, q)) {
+        } else if (fs == 1) {
           s = kStateRefined;
           slot = *bm.find(pack3(q[0], q[1], q[2]));
         } else {
@@ -825,7 +826,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       for (int b = 0; b < nc[1]; ++b)
         for (int c2 = 0; c2 < nc[2]; ++c2) {
           int64_t cc[3] = {cand[0][a], cand[1][b], cand[2][c2]};
-          if (!f.inside(lc, cc) || !f.exists(lc, cc) || f.refined(lc, cc)) continue;
+          if (f.state(lc, cc) != 0) continue;  // not a leaf of level lc
           if (ncls[i] == 2) continue;
           // a coarser leaf contains the node, which is not one of its nodes
           HRow row;

@@ -52,6 +52,12 @@ bool Forest::refined(int level, const int64_t* c) const {
   return v && *v;
 }
 
+int Forest::state(int level, const int64_t* c) const {
+  if (level >= (int)cells.size() || !inside(level, c)) return -1;
+  const int32_t* v = cells[level].find(pack3(c[0], c[1], c[2]));
+  return v ? (*v ? 1 : 0) : -1;
+}
+
 void Forest::refine_cell(int level, const int64_t* c) {
   int32_t* v = cells[level].find(pack3(c[0], c[1], c[2]));
   if (!v || *v) return;
