@@ -113,16 +113,22 @@ def round_sphere_surface(center, radius, finest_only: bool = True) -> RoundFn:
     center = np.asarray(center, dtype=np.float64)
     r2 = float(radius) ** 2
 
-    def fn(cm, level, coords, finest):
+    def meets(cm, level, coords):
         blo, bhi = cm.boxes(level, coords)
         c = center[None, : cm.dim]
         near = np.clip(c, blo, bhi) - c
         far = np.maximum(np.abs(blo - c), np.abs(bhi - c))
         dmin = np.sum(near * near, axis=1)
         dmax = np.sum(far * far, axis=1)
-        hit = (dmin <= r2) & (dmax >= r2)
-        if finest_only:
-            hit &= np.asarray(level) == finest
+        return (dmin <= r2) & (dmax >= r2)
+
+    def fn(cm, level, coords, finest):
+        if not finest_only:
+            return meets(cm, level, coords)
+        level = np.asarray(level)
+        sel = np.nonzero(level == finest)[0]  # only these can be flagged
+        hit = np.zeros(len(level), dtype=bool)
+        hit[sel] = meets(cm, level[sel], np.asarray(coords)[sel])
         return hit
 
     return fn
