@@ -352,7 +352,9 @@ gmg_status gmg_level_prolongate(gmg_hier* h, int level, const void* d_uc, void* 
  * S slots of level l, right-hand side d_g, starting from d_u (from_zero=0)
  * or from 0 (from_zero=1, d_u is then overwritten); I slots of d_u are kept.
  * d_tmp: second level vector used by the recurrence (contents destroyed).
- * The result ends in d_u. */
+ * The result ends in d_u.  d_g, d_u and d_tmp must be three distinct
+ * buffers (GMG_EINVAL otherwise: the updates write d_u and d_tmp while later
+ * updates still read d_g). */
 gmg_status gmg_level_smooth(gmg_hier* h, int level, const void* d_g, void* d_u, void* d_tmp,
                             int from_zero);
 /* Same smoothing as gmg_level_smooth, but the recurrence's second level
@@ -363,13 +365,17 @@ gmg_status gmg_level_smooth(gmg_hier* h, int level, const void* d_g, void* d_u, 
  * latency-critical loops that cannot pay the device-wide synchronisation of
  * cudaMalloc/cudaFree.  The paper has no counterpart to this entry point.
  * Limit: the level vector (its slot count times 4 bytes for an FP32 V-cycle,
- * 8 for FP64) must fit in the 8 MiB array, else GMG_EINVAL.  The array is
- * held by every GPU that loads the library until the process exits, and is
- * shared by all calls: calls whose work overlaps on the GPU (other streams,
- * other hierarchies on the same device) race on it.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  The contents of d_u are as
- * after gmg_level_smooth; the array's contents afterwards are unspecified. */
+ * 8 for FP64) must fit in the 8 MiB array, else GMG_EINVAL; d_g and d_u must
+ * not alias (GMG_EINVAL).  The array is held by every GPU that loads the
+ * library until the process exits, and is shared by all calls: calls whose
+ * work overlaps on the GPU (other streams, other hierarchies on the same
+ * device) race on it.  gmg_hier_build on a device context looks up the
+ * array's device address (cudaGetSymbolAddress, with the device current),
+ * which loads the part of the library that holds it, so the array's 8 MiB are
+ * allocated during that build (once per device and process) and never during
+ * this call; the address is kept with the hierarchy and is valid as long as
+ * the hierarchy's own device memory is.  The contents of d_u are as after
+ * gmg_level_smooth; the array's contents afterwards are unspecified. */
 gmg_status gmg_level_smooth_noalloc(gmg_hier* h, int level, const void* d_g, void* d_u, int from_zero);
 /* Inverse diagonal of A_l^S on S slots, 0 elsewhere (level >= 1). */
 gmg_status gmg_level_inv_diag(gmg_hier* h, int level, void* d_out);

@@ -305,6 +305,7 @@ gmg_status gmg_hier_build(gmg_ctx* ctx, const gmg_mesh* mesh, int degree, const 
       return GMG_ECUDA;
     }
     gmg_status st = device_setup(h);
+    if (st == GMG_OK) st = noalloc_prepare(h);
     if (st != GMG_OK) {
       device_free(h);
       delete hh;
@@ -576,7 +577,7 @@ gmg_status gmg_level_prolongate(gmg_hier* hh, int level, const void* d_uc, void*
 gmg_status gmg_level_smooth(gmg_hier* hh, int level, const void* d_g, void* d_u, void* d_tmp, int from_zero) {
   gmg_status st = check_level(hh, level, 1);
   if (st != GMG_OK) return st;
-  CHECK_ARG(d_g && d_u && d_tmp && d_u != d_tmp, "bad vectors");
+  CHECK_ARG(d_g && d_u && d_tmp && d_u != d_tmp && d_g != d_u && d_g != d_tmp, "bad vectors");
   return device_level_smooth(hh->h, level, d_g, d_u, d_tmp, from_zero);
 }
 

@@ -234,6 +234,9 @@ struct Hier {
   std::vector<double> lambda;          // per level
   double setup_host_s = 0, setup_device_s = 0;
   DeviceState* dev = nullptr;
+  // device address of the library's static smoothing scratch array, looked up
+  // in this hierarchy's context when it is built (noalloc.cu)
+  void* noalloc_scratch = nullptr;
 };
 
 struct Ctx {
@@ -274,6 +277,9 @@ gmg_status device_level_smooth(Hier& h, int level, const void* g, void* u, void*
                                int from_zero);
 gmg_status device_level_inv_diag(Hier& h, int level, void* out);
 gmg_status device_coarse_solve(Hier& h, const void* g0, void* u0);
+// looks up the static scratch array of gmg_level_smooth_noalloc in the current
+// context (loading the module that holds it) and keeps its address in h
+gmg_status noalloc_prepare(Hier& h);
 uint64_t device_bytes(const Hier& h);
 void profile_reset(Hier& h, bool timing);
 void profile_read(Hier& h, gmg_kernel_stats* out);

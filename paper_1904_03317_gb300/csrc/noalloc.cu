@@ -5,7 +5,6 @@
 // afford the device-wide synchronisation cudaMalloc and cudaFree imply.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "gmg_internal.h"
@@ -17,28 +16,22 @@ namespace gmg {
 // Shared by every call on a device and kept until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GMG_NOALLOC_SCRATCH_BYTES];
 
-static std::mutex g_noalloc_mutex;
-static void* g_noalloc_ptr[128] = {};
-
-// Device address of the array on `device` (which must be current).  In host
-// code the array's name is only a host-side stand-in, so the address comes
-// from cudaGetSymbolAddress, once per device.
-static gmg_status noalloc_scratch(int device, void** out) {
-  if (device < 0 || device >= 128) {
-    set_error("gmg_level_smooth_noalloc: device index out of range");
-    return GMG_EINVAL;
+// In host code the array's name is only a host-side stand-in, so its device
+// address comes from cudaGetSymbolAddress, with the hierarchy's device
+// current.  The lookup loads the module that holds the array (its 8 MiB are
+// allocated then, if this process has not loaded it on this device yet), so
+// it runs while the hierarchy is built, where allocating is expected; the
+// no-allocation entry point only uses the address kept here.  The address
+// belongs to the context current during the build, the same context that owns
+// the hierarchy's other device memory.
+gmg_status noalloc_prepare(Hier& h) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("static smoothing scratch: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    return GMG_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("gmg_level_smooth_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-      return GMG_ECUDA;
-    }
-    g_noalloc_ptr[device] = p;
-  }
-  *out = g_noalloc_ptr[device];
+  h.noalloc_scratch = p;
   return GMG_OK;
 }
 
@@ -52,8 +45,12 @@ extern "C" gmg_status gmg_level_smooth_noalloc(gmg_hier* hh, int level, const vo
     set_error("gmg_level_smooth_noalloc: null argument");
     return GMG_EINVAL;
   }
+  if (d_g == d_u) {
+    set_error("gmg_level_smooth_noalloc: g and u must not alias");
+    return GMG_EINVAL;
+  }
   Hier& h = hh->h;
-  if (!h.ctx || h.ctx->c.device < 0 || !h.dev) {
+  if (!h.ctx || h.ctx->c.device < 0 || !h.dev || !h.noalloc_scratch) {
     set_error("gmg_level_smooth_noalloc: needs a hierarchy built on a device context");
     return GMG_EINVAL;
   }
@@ -74,10 +71,7 @@ extern "C" gmg_status gmg_level_smooth_noalloc(gmg_hier* hh, int level, const vo
     set_error(std::string("gmg_level_smooth_noalloc: cudaSetDevice: ") + cudaGetErrorString(e));
     return GMG_ECUDA;
   }
-  void* tmp = nullptr;
-  gmg_status st = noalloc_scratch(h.ctx->c.device, &tmp);
-  if (st != GMG_OK) return st;
   // the smoothing driver clears (from zero) or fills (from a start value) the
   // part of the array it uses before reading it
-  return device_level_smooth(h, level, d_g, d_u, tmp, from_zero);
+  return device_level_smooth(h, level, d_g, d_u, h.noalloc_scratch, from_zero);
 }

@@ -32,7 +32,6 @@ def test_noalloc_smoother_matches_caller_buffer_version(torch, prec):
     H = G.Hierarchy(ctx, mesh, w.degree, cheb_degree=w.cheb_degree, vcycle_prec=prec)
     dt = torch.float64 if prec == G.PREC_FP64 else torch.float32
     esz = 8 if prec == G.PREC_FP64 else 4
-    tol = 1e-11 if prec == G.PREC_FP64 else 2e-5
     rng = np.random.default_rng(5)
     checked = 0
     for level in range(1, H.info.n_levels):
@@ -45,15 +44,40 @@ def test_noalloc_smoother_matches_caller_buffer_version(torch, prec):
         u_ref = torch.zeros(n, dtype=dt, device="cuda")
         u_new = torch.zeros(n, dtype=dt, device="cuda")
         tmp = torch.zeros(n, dtype=dt, device="cuda")
+        kept_ref = [torch.empty_like(u_ref) for _ in range(2)]
+        kept_new = [torch.empty_like(u_ref) for _ in range(2)]
+        torch.cuda.synchronize()
+        # every tensor of this level exists now, and nothing below allocates
+        # until the window closes: the no-allocation calls, the first one
+        # included, must leave the device's free memory unchanged (the
+        # library looked the array up when H was built)
+        free_before = torch.cuda.mem_get_info()[0]
         # two calls in a row: from zero, then from the first result
-        for from_zero in (True, False):
+        for i, from_zero in enumerate((True, False)):
             H.level_smooth(level, g, u_ref, tmp, from_zero)
             H.level_smooth_noalloc(level, g, u_new, from_zero)
-            torch.cuda.synchronize()
-            a, b = u_new.double().cpu().numpy(), u_ref.double().cpu().numpy()
-            assert np.abs(a - b).max() <= tol * max(np.abs(b).max(), 1e-300)
+            kept_ref[i].copy_(u_ref)
+            kept_new[i].copy_(u_new)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free_before
+        # both paths launch the same kernels on the same values, so they
+        # agree bit for bit
+        for i in range(2):
+            assert torch.equal(kept_new[i], kept_ref[i])
+            assert float(kept_ref[i].abs().max()) > 0.0
         checked += 1
     assert checked >= 2
+
+
+def test_noalloc_smoother_rejects_aliased_vectors(torch):
+    w = inputs.poisson3d_sphere(2, 0)
+    ctx = G.Context(0)
+    H = G.Hierarchy(ctx, G.build_mesh(w), w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32)
+    n = len(H.export(G.EXPORT_LEVEL_KEYS, 1))
+    u = torch.zeros(n, dtype=torch.float32, device="cuda")
+    with pytest.raises(G.GmgError) as e:
+        H.level_smooth_noalloc(1, u, u, True)
+    assert e.value.status == G.EINVAL
 
 
 def test_noalloc_smoother_rejects_levels_beyond_the_scratch(torch):
