@@ -185,6 +185,8 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.n_bricks = L.n_bricks;
   a.n_bricks_all = L.n_bricks_all;
   a.brick_members = L.brick_members;
+  a.brick_info = L.brick_info;
+  a.iso = L.iso;
   a.list_rest = L.list_rest;
   a.n_rest = L.n_rest;
   a.no_ghosts = L.n_slots == L.n_groups * (int64_t)ipow_h(2 * h.k, h.dim);
@@ -271,6 +273,7 @@ void device_free(Hier& h) {
     cudaFree(L.pmask);
     cudaFree(L.bricks);
     cudaFree(L.brick_members);
+    cudaFree(L.brick_info);
     cudaFree(L.list_jump);
     cudaFree(L.list_rest);
   }
@@ -408,6 +411,29 @@ gmg_status device_setup(Hier& h) {
     D.n_bricks = H.n_bricks_full;
     D.n_bricks_all = (int64_t)H.bricks.size() / 64;
     GMG_TRY(upload(d, &D.brick_members, H.brick_members));
+    {
+      // per-brick flags and coefficient, read once per brick by the brick
+      // smoother instead of per node
+      const uint64_t full = NOWN >= 64 ? ~0ull : ((1ull << NOWN) - 1);
+      std::vector<uint2> info((size_t)D.n_bricks_all);
+      for (int64_t br = 0; br < D.n_bricks_all; ++br) {
+        const unsigned members = br < D.n_bricks ? 0xFFu : (unsigned)H.brick_members[br - D.n_bricks];
+        bool all_s = true;
+        int32_t m0 = -1;
+        for (int b = 0; b < 8; ++b) {
+          if (!((members >> b) & 1u)) continue;
+          const int32_t gid = H.bricks[(size_t)br * 64 + ((b & 1) + 1) + 4 * ((((b >> 1) & 1) + 1) + 4 * ((b >> 2) + 1))];
+          if (m0 < 0) m0 = gid;
+          if ((H.smask[gid] & full) != full) all_s = false;
+        }
+        const float c = m0 >= 0 ? (float)H.coeff[m0] : 0.f;
+        unsigned cb;
+        std::memcpy(&cb, &c, 4);
+        info[br] = make_uint2(members | (all_s ? kBrickAllS : 0u), cb);
+      }
+      GMG_TRY(upload(d, &D.brick_info, info));
+    }
+    D.iso = dim == 3 && D.scale[0] == D.scale[1] && D.scale[1] == D.scale[2];
     GMG_TRY(upload(d, &D.list_rest, H.list_rest));
     D.n_rest = (int64_t)H.list_rest.size();
     GMG_TRY(upload(d, &D.list_jump, H.list_jump));

@@ -49,6 +49,10 @@ struct LevelDev {
   int64_t n_bricks = 0;         // full bricks
   int64_t n_bricks_all = 0;
   uint8_t* brick_members = nullptr;  // per partial brick: member positions
+  // per brick (full and partial): x = member bits 0..7 | kBrickAllS, y = the
+  // bits of the bricks' FP32 coefficient
+  uint2* brick_info = nullptr;
+  bool iso = false;             // cubic cells: one scale factor for all directions
   int32_t* list_rest = nullptr; // groups outside full bricks
   int64_t n_rest = 0;
   int64_t n_uniform = 0, n_jump = 0;
@@ -77,6 +81,8 @@ struct LevelArgs {
   int64_t n_bricks;           // full bricks (smoothing, residual, prolongation)
   int64_t n_bricks_all;       // with the partial bricks (smoothing only)
   const uint8_t* brick_members;
+  const uint2* brick_info;    // per brick: member bits | kBrickAllS, coefficient bits
+  bool iso;                   // s_x = s_y = s_z (cubic cells)
   const int32_t* list_rest;
   int64_t n_rest;
   bool no_ghosts;             // the level has no refinement-edge (ghost) blocks
@@ -201,6 +207,8 @@ struct DeviceState {
 };
 
 constexpr int kMaxReduceBlocks = 4096;
+// brick_info flag: every stored node of every member group is an S node
+constexpr unsigned kBrickAllS = 1u << 8;
 
 // ------------------------------------------------------------ launchers
 // Level kernels (kernels_level.cu).  T = float or double; all pointers are

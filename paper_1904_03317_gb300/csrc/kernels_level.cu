@@ -29,7 +29,10 @@
 // groups sharing the node), then R = P^T restricted to the parent cell's
 // (K+1)^d nodes and accumulated atomically.  Summed over groups this is
 // R (g - A u) exactly, without forming t.
+#include <algorithm>
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "device_common.cuh"
 
@@ -1303,6 +1306,207 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
   });
 }
 
+// ------------------------------------- Q2 brick smoother, persistent blocks
+// The FP32 Q2 brick smoother (apply and Chebyshev step) with the same three
+// packed contractions as level_cheb_brick_f2_kernel, arranged so that the
+// work per stored node is mostly the contractions themselves:
+//   * each block loops over bricks (grid = resident blocks), so every
+//     thread's halo-line geometry, output columns and diagonal factors are
+//     computed once per launch, not once per brick;
+//   * slots are 32-bit (level vectors stay below 2^32 slots);
+//   * the members, an "every member node is an S node" flag and the
+//     coefficient come from one 8-byte record per brick, so interior bricks
+//     skip the S-mask tests;
+//   * with cubic cells (s_x = s_y = s_z = s) the scale factor joins the
+//     coefficient and the contractions carry no scale multiplications;
+//   * in the last stage a thread takes four consecutive z rows of its
+//     column (two vertex and two interior rows, so both halves of the block
+//     do the same work), all in one group of the brick: one base slot and
+//     compile-time offsets.
+// The Chebyshev step is out = x + c1 (x - x_prev) + (c2 / d) (g / (a s) - y)
+// with A x = a s y and D = a s d, d the node's diagonal of the unscaled
+// Kronecker sum (it depends on index parities only).
+// Shared arrays (float2 units for T1, T2): stage-1 result of halo line
+// (hy, hz), output row r at T1[hz PZ1 + 9 hy + 2 r]; stage-2 result at
+// T2[z ZS + 8 j + i]; the brick's own x values at Xown[64 z + 8 y + (x ^ 4
+// ((y >> 2) & 1))].  8-byte accesses are served per half-warp; with these
+// strides the 16 lanes of a half-warp meet 16 distinct bank pairs in the
+// stage-1 stores and the stage-2 loads (no bank conflicts), and the swizzle
+// spreads the own-value rows of eight consecutive lines over distinct banks.
+struct BrickQ2 {
+  static constexpr int K = 2, NO = 4, OB = 8, HB = 11, NOWN = 64, TB = 128;
+  static constexpr int HY1 = 9;    // stage-1 halo-line stride (float2)
+  static constexpr int R1 = 2;     // stage-1 output-row stride (float2)
+  static constexpr int PZ1 = 115;  // stage-1 z-plane stride (float2)
+  static constexpr int ZS = 72;    // stage-2 z-plane stride (float2), 8 mod 16
+  // array sizes in bytes, each rounded up to 16 so that every array starts
+  // 16-byte aligned (the own values and the table are read and written as
+  // 16-byte vectors)
+  static constexpr size_t T1B = ((size_t)HB * PZ1 * 8 + 15) / 16 * 16;
+  static constexpr size_t T2B = ((size_t)HB * ZS * 8 + 15) / 16 * 16;
+  static constexpr size_t XOB = (size_t)OB * OB * OB * 4;
+  static constexpr size_t bytes() { return T1B + T2B + XOB + 64 * 4; }
+};
+
+template <int MODE, bool ISO>
+__global__ void __launch_bounds__(BrickQ2::TB, 9)
+level_cheb_brick_q2_kernel(LevelArgs a, const float* __restrict__ x, const float* __restrict__ xprev,
+                           const float* __restrict__ gvec, float* __restrict__ out, float c1, float c2) {
+  using B = BrickQ2;
+  constexpr int K = B::K, NO = B::NO, OB = B::OB, HB = B::HB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* T1 = reinterpret_cast<float2*>(smem_raw);
+  float2* T2 = reinterpret_cast<float2*>(smem_raw + B::T1B);
+  float* Xown = reinterpret_cast<float*>(smem_raw + B::T1B + B::T2B);
+  int32_t* tab = reinterpret_cast<int32_t*>(smem_raw + B::T1B + B::T2B + B::XOB);
+  static_assert(B::T1B % 16 == 0 && B::T2B % 16 == 0 && B::XOB % 16 == 0, "16-byte aligned arrays");
+  const int tid = threadIdx.x;
+
+  // ---- per-thread constants of the launch
+  // stage 1: halo line (hy, hz), one per thread below HB * HB
+  const bool st1 = tid < HB * HB;
+  const int hy = tid % HB, hz = tid / HB;
+  int gy, ly, gz, lz;
+  brick_seg<K>(hy, gy, ly);
+  brick_seg<K>(hz, gz, lz);
+  const uint32_t row = NO * (ly + NO * lz);
+  const int tb = 4 * ((gy + 1) + 4 * (gz + 1));
+  const bool own_line = gy >= 0 && gy <= 1 && gz >= 0 && gz <= 1;
+  const int by1 = gy * NO + ly;
+  float* xo_dst = Xown + OB * (by1 + OB * (gz * NO + lz));
+  const int xo_swz = 4 * ((by1 >> 2) & 1);  // own x halves swap places on rows 4..7
+  float2* t1_dst = T1 + hz * B::PZ1 + B::HY1 * hy;
+  // stage 2: line (z, i)
+  const bool st2 = tid < HB * OB;
+  const int z2 = tid / OB, i2 = tid % OB;
+  // stage 3: column (oi, oj), rows 4 part .. 4 part + 3 of the brick, i.e.
+  // z planes 0..3 of the groups at brick position (oi / 4, oj / 4, part)
+  const int ol = tid % (OB * OB), part = tid / (OB * OB);
+  const int oi = ol % OB, oj = ol / OB;
+  const int gsel = (oi / NO) + 2 * (oj / NO) + 4 * part;
+  const int own_tab = (oi / NO + 1) + 4 * ((oj / NO + 1) + 4 * (part + 1));
+  const uint32_t node_xy = (oi % NO) + NO * (oj % NO);
+  const float sx = a.scale32[0], sy = a.scale32[1], sz = a.scale32[2];
+  const float s_iso = ISO ? sx : 1.f;
+  // c2 / d for the two z parities of the rows (x and y parities are fixed)
+  float c2od[2] = {0.f, 0.f};
+  if constexpr (MODE == 1) {
+    const float md0 = (float)bbrick<K, false>(0, K), kd0 = (float)bbrick<K, true>(0, K);
+    const float md1 = (float)bbrick<K, false>(1, K + 1), kd1 = (float)bbrick<K, true>(1, K + 1);
+    const float mdx = (oi & 1) ? md1 : md0, kdx = (oi & 1) ? kd1 : kd0;
+    const float mdy = (oj & 1) ? md1 : md0, kdy = (oj & 1) ? kd1 : kd0;
+#pragma unroll
+    for (int pz = 0; pz < 2; ++pz) {
+      const float mdz = pz ? md1 : md0, kdz = pz ? kd1 : kd0;
+      const float d = ISO ? (kdx * mdy * mdz + mdx * kdy * mdz + mdx * mdy * kdz)
+                          : (sx * kdx * mdy * mdz + sy * mdx * kdy * mdz + sz * mdx * mdy * kdz);
+      c2od[pz] = c2 / d;
+    }
+  }
+
+  for (int64_t br = blockIdx.x; br < a.n_bricks_all; br += gridDim.x) {
+    if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
+    const uint2 info = a.brick_info[br];
+    __syncthreads();
+    const float ce = __uint_as_float(info.y) * s_iso;  // a s (ISO) or a
+    const bool member = (info.x >> gsel) & 1u;
+    // this thread's four outputs: slots base + 16 nz, nz = 0..3
+    const uint32_t base = (uint32_t)tab[own_tab] * B::NOWN + node_xy;
+    float pg[4] = {0.f, 0.f, 0.f, 0.f}, pxp[4] = {0.f, 0.f, 0.f, 0.f};
+    if constexpr (MODE == 1) {
+      if (member) {
+#pragma unroll
+        for (int nz = 0; nz < 4; ++nz) pg[nz] = gvec[base + 16 * nz];
+        if (xprev) {
+#pragma unroll
+          for (int nz = 0; nz < 4; ++nz) pxp[nz] = xprev[base + 16 * nz];
+        }
+      }
+    }
+    // stage 1: halo rows along x -> (mass, stiffness) pairs
+    if (st1) {
+      const int4 b = *reinterpret_cast<const int4*>(tab + tb);
+      float v[HB];
+      if (b.x >= 0) load_run<float, K>(x + ((uint32_t)b.x * B::NOWN + row + K), v);
+      else v[0] = v[1] = 0.f;
+      if (b.y >= 0) load_run<float, 2 * K>(x + ((uint32_t)b.y * B::NOWN + row), v + K);
+      else v[2] = v[3] = v[4] = v[5] = 0.f;
+      if (b.z >= 0) load_run<float, 2 * K>(x + ((uint32_t)b.z * B::NOWN + row), v + 3 * K);
+      else v[6] = v[7] = v[8] = v[9] = 0.f;
+      v[5 * K] = b.w >= 0 ? x[(uint32_t)b.w * B::NOWN + row] : 0.f;
+      if (own_line) {
+        *reinterpret_cast<float4*>(xo_dst + xo_swz) = make_float4(v[2], v[3], v[4], v[5]);
+        *reinterpret_cast<float4*>(xo_dst + (4 ^ xo_swz)) = make_float4(v[6], v[7], v[8], v[9]);
+      }
+      float2 vv[HB];
+      static_for<0, HB>([&](auto c) { vv[c] = make_float2(v[c], v[c]); });
+      static_for<0, OB>([&](auto r) {
+        float2 acc = make_float2(0.f, 0.f);
+        static_for<0, HB>([&](auto c) {
+          constexpr double bm = bbrick<K, false>(r, c);
+          constexpr double bk = bbrick<K, true>(r, c);
+          if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bm, (float)bk), vv[c], acc);
+        });
+        t1_dst[B::R1 * r] = acc;
+      });
+    }
+    __syncthreads();
+    // stage 2: y direction; stores (P, Q) = (sz MM, sy MK + sx KM), or
+    // (MM, MK + KM) for cubic cells
+    if (st2) {
+      float2 w[HB];
+      static_for<0, HB>([&](auto yy) { w[yy] = T1[z2 * B::PZ1 + B::HY1 * yy + B::R1 * i2]; });
+      static_for<0, OB>([&](auto j) {
+        float2 acc = make_float2(0.f, 0.f);  // (MM, KM)
+        float mk = 0.f;
+        static_for<0, HB>([&](auto c) {
+          constexpr double bm = bbrick<K, false>(j, c);
+          constexpr double bk = bbrick<K, true>(j, c);
+          if constexpr (bm != 0.0) acc = __ffma2_rn(make_float2((float)bm, (float)bm), w[c], acc);
+          if constexpr (bk != 0.0) mk = fmaf((float)bk, w[c].x, mk);
+        });
+        T2[z2 * B::ZS + j * OB + i2] = ISO ? make_float2(acc.x, mk + acc.y)
+                                           : make_float2(sz * acc.x, sy * mk + sx * acc.y);
+      });
+    }
+    __syncthreads();
+    // stage 3: z direction for rows 4 part .. 4 part + 3, then the update
+    if (member) {
+      uint32_t wmask = 0xFu;  // outputs that are S nodes
+      if (!(info.x & kBrickAllS)) {
+        const uint64_t m = a.smask[base / B::NOWN] >> node_xy;
+        wmask = (uint32_t)(m & 1u) | (uint32_t)((m >> 15) & 2u) | (uint32_t)((m >> 30) & 4u) |
+                (uint32_t)((m >> 45) & 8u);
+      }
+      const float inv_ce = MODE == 1 ? __frcp_rn(ce) : 0.f;
+      auto rows = [&](auto P) {
+        constexpr int R0 = decltype(P)::value * 4;
+        float2 pq[HB];
+        static_for<0, HB>([&](auto c) { pq[c] = T2[c * B::ZS + ol]; });
+        static_for<0, 4>([&](auto nz) {
+          constexpr int r = R0 + nz;
+          float2 acc = make_float2(0.f, 0.f);
+          static_for<0, HB>([&](auto c) {
+            constexpr double bm = bbrick<K, false>(r, c);
+            constexpr double bk = bbrick<K, true>(r, c);
+            if constexpr (bm != 0.0 || bk != 0.0) acc = __ffma2_rn(make_float2((float)bk, (float)bm), pq[c], acc);
+          });
+          const float y = acc.x + acc.y;
+          if (!((wmask >> nz) & 1u)) return;
+          if constexpr (MODE == 0) {
+            out[base + 16 * nz] = ce * y;
+          } else {
+            const float xv = Xown[(oi ^ (4 * ((oj >> 2) & 1))) + OB * (oj + OB * r)];
+            out[base + 16 * nz] = fmaf(c2od[nz & 1], fmaf(pg[nz], inv_ce, -y), fmaf(c1, xv - pxp[nz], xv));
+          }
+        });
+      };
+      if (part == 0) rows(std::integral_constant<int, 0>{});
+      else rows(std::integral_constant<int, 1>{});
+    }
+  }
+}
+
 // Slot (in the level l-1 vector) of node jd of the parent cell of group g
 // at level l: level 1 parents are coarse cells on the (K n0 + 1)^d lattice;
 // otherwise the parent is child cb of its own group, whose node block and
@@ -1700,12 +1904,47 @@ __global__ void __launch_bounds__(256) level_diag_kernel(LevelArgs a, double* __
 }
 
 // ----------------------------------------------------------- launchers
+// Grid of a persistent kernel: the blocks that are resident at once on the
+// current device (looked up once per kernel and device), at most `work`.
+template <typename KERN>
+static unsigned persistent_grid(KERN kern, int threads, size_t smem, int64_t work) {
+  struct Entry {
+    const void* fn;
+    int device;
+    unsigned blocks;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  unsigned blocks = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+      if (e.fn == (const void*)kern && e.device == dev) blocks = e.blocks;
+    if (!blocks) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per_sm = 0, sms = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      blocks = (unsigned)std::max(1, per_sm * sms);
+      cache.push_back({(const void*)kern, dev, blocks});
+    }
+  }
+  return (unsigned)std::min<int64_t>(work, blocks);
+}
+
 template <typename T, int DIM, int K, int MODE>
 static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, const T* g, const T* dinv,
                                T* out, T c1, T c2, cudaStream_t s) {
   if constexpr (DIM == 3) {
     if (a.n_bricks_all > 0) {  // full and partial bricks
-      if constexpr (std::is_same<T, float>::value) {
+      if constexpr (std::is_same<T, float>::value && K == 2) {
+        auto kern = a.iso ? level_cheb_brick_q2_kernel<MODE, true> : level_cheb_brick_q2_kernel<MODE, false>;
+        const unsigned grid = persistent_grid(kern, BrickQ2::TB, BrickQ2::bytes(), a.n_bricks_all);
+        kern<<<grid, BrickQ2::TB, BrickQ2::bytes(), s>>>(a, x, xprev, g, out, c1, c2);
+        GMG_COUNT_LAUNCH();
+      } else if constexpr (std::is_same<T, float>::value) {
         const size_t sm = Brick2S<K>::bytes();
         // set once, thread-safe (function-local static)
         static const bool init = [&] {
