@@ -394,11 +394,14 @@ enum gmg_kernel_kind {
   GMG_K_RESTRICT = 2,      /* residual on S u I + restriction R = P^T */
   GMG_K_PROLONG = 3,       /* prolongation P */
   GMG_K_COARSE = 4,        /* coarse solve */
-  GMG_K_COPY_TO = 5,       /* active residual -> level right-hand sides */
-  GMG_K_COPY_FROM = 6,     /* level solutions -> active z, fused r.z */
+  GMG_K_COPY_TO = 5,       /* active residual -> level right-hand sides (gmg_vcycle); in
+                              gmg_solve: r = b with b.b and the first level right-hand sides */
+  GMG_K_COPY_FROM = 6,     /* level solutions -> active z with r.z (gmg_vcycle); in gmg_solve:
+                              r.z with z read from the level solutions (z is not stored) */
   GMG_K_ACTIVE = 7,        /* leaf-mesh operator with hanging nodes, fused p.Ap */
-  GMG_K_CG_XR = 8,         /* x += alpha p, r -= alpha Ap, fused r.r */
-  GMG_K_CG_P = 9,          /* p = z + beta p */
+  GMG_K_CG_XR = 8,         /* x += alpha p, r -= alpha Ap, fused r.r and the next V-cycle's
+                              level right-hand sides */
+  GMG_K_CG_P = 9,          /* p = z + beta p with z read from the level solutions, Ap = 0 */
   GMG_K_OTHER = 10,        /* dot products, setup kernels */
   GMG_NUM_KERNEL_KINDS = 11
 };

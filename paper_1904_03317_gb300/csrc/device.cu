@@ -278,7 +278,7 @@ void device_free(Hier& h) {
     cudaFree(L.list_rest);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->coarse_ptr, d->coarse_col, d->coarse_val, d->cell_nodes, d->cell_coeff, d->cell_level,
-                  d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap, d->z,
+                  d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap,
                   d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level,
                   d->pat_nodes, d->pat_coeff, d->pat_level, d->loose_nodes, d->loose_coeff, d->loose_level,
                   d->xh, d->yh, d->hm_node, d->hm_ptr,
@@ -527,7 +527,6 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(dev_alloc(d, &d->r, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->p, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->Ap, A.n_unknowns));
-  GMG_TRY(dev_alloc(d, &d->z, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->partials, kMaxReduceBlocks));
   GMG_TRY(dev_alloc(d, &d->counter, 1));
   GMG_CUDA_TRY(cudaMemset(d->counter, 0, sizeof(unsigned)));
@@ -644,18 +643,19 @@ static cudaError_t smooth(const Hier& h, int l, const T* g, const T* dinv, T* cu
   return cudaSuccess;
 }
 
-// z = B r (one V-cycle); rz_out (device) receives r.z.
+// The V-cycle on the level vectors, Algorithm 2 in the local-smoothing form
+// of Sec. 2.3: the level right-hand sides g are in place (the active
+// residual at each unknown's home slot, zero elsewhere); the result ends in
+// u_B, each unknown's value at its home slot.
 template <typename T>
-static gmg_status vcycle_impl(Hier& h, const double* r, double* z, double* rz_out) {
+static gmg_status vcycle_levels(Hier& h) {
   DeviceState* d = h.dev;
   cudaStream_t s = d->stream;
   const int L = h.L;
-  const size_t bytes = (size_t)h.total_slots * sizeof(T);
   T* uA = (T*)d->uA;
   T* uB = (T*)d->uB;
   T* g = (T*)d->g;
   const T* dinv = (const T*)d->dinv;
-  GMG_CUDA_TRY(cudaMemsetAsync(g, 0, bytes, s));
   // u_A, u_B: the down-sweep needs zeros on I and ghost slots (the up-sweep's
   // prolongation sets them).  S slots need none: the first smoothing update
   // writes every stored slot of u_A and the second takes no x_prev, and
@@ -672,10 +672,6 @@ static gmg_status vcycle_impl(Hier& h, const double* r, double* z, double* rz_ou
     GMG_CUDA_TRY(cudaMemsetAsync(uA + a, 0, (size_t)(b - a) * sizeof(T), s));
     GMG_CUDA_TRY(cudaMemsetAsync(uB + a, 0, (size_t)(b - a) * sizeof(T), s));
     l = e + 1;
-  }
-  {
-    Track t(d, GMG_K_COPY_TO, (12.0 + sizeof(T)) * d->n_unknowns, 0.0);
-    GMG_CUDA_TRY(launch_copy_to_mg<T>(d->n_unknowns, r, d->home, g, s));
   }
   const double kd = ipow_d(h.k, h.dim);
   // down-sweep: pre-smoothing on V^S from zero, residual on S u I, restriction
@@ -711,14 +707,83 @@ static gmg_status vcycle_impl(Hier& h, const double* r, double* z, double* rz_ou
       return GMG_EINVAL;
     }
   }
+  return GMG_OK;
+}
+
+// z = B r (one V-cycle, gmg_vcycle); rz_out (device) receives r.z.
+template <typename T>
+static gmg_status vcycle_impl(Hier& h, const double* r, double* z, double* rz_out) {
+  DeviceState* d = h.dev;
+  cudaStream_t s = d->stream;
+  GMG_CUDA_TRY(cudaMemsetAsync(d->g, 0, (size_t)h.total_slots * sizeof(T), s));
+  {
+    Track t(d, GMG_K_COPY_TO, (12.0 + sizeof(T)) * d->n_unknowns, 0.0);
+    GMG_CUDA_TRY(launch_copy_to_mg<T>(d->n_unknowns, r, d->home, (T*)d->g, s));
+  }
+  GMG_TRY(vcycle_levels<T>(h));
   Track t(d, GMG_K_COPY_FROM, (20.0 + sizeof(T)) * d->n_unknowns, 2.0 * d->n_unknowns);
-  GMG_CUDA_TRY(launch_copy_from_mg<T>(d->n_unknowns, uB, d->home, r, z, d->partials, d->counter, rz_out, s));
+  GMG_CUDA_TRY(launch_copy_from_mg<T>(d->n_unknowns, (const T*)d->uB, d->home, r, z, d->partials, d->counter,
+                                      rz_out, s));
   return GMG_OK;
 }
 
 static gmg_status vcycle_any(Hier& h, const double* r, double* z, double* rz_out) {
   if (h.dev->prec == GMG_PREC_FP32) return vcycle_impl<float>(h, r, z, rz_out);
   return vcycle_impl<double>(h, r, z, rz_out);
+}
+
+// ---------------------------------------------- CG passes around the V-cycle
+// One preconditioned CG iteration in the order both solve modes use
+// (Sec. 4.1: CG preconditioned by one V-cycle), with z = B r read from the
+// level solutions and never stored:
+//   V-cycle on g (filled by the previous pass), rz = r.z,
+//   p = z + (rz / rz_old) p with Ap = 0, Ap = A p with pAp = p.Ap,
+//   x += (rz / pAp) p, r -= (rz / pAp) Ap with rr = r.r and g = r at the home slots.
+// With p = 0 and rz_old = 1 before the first iteration this is the textbook
+// PCG recurrence.
+
+// r = b (b may be r), bb = b.b, g = b at the home slots and 0 elsewhere
+template <typename T>
+static gmg_status cg_start_t(Hier& h, const double* b, double* bb) {
+  DeviceState* d = h.dev;
+  const int64_t n = d->n_unknowns;
+  GMG_CUDA_TRY(cudaMemsetAsync(d->g, 0, (size_t)h.total_slots * sizeof(T), d->stream));
+  Track t(d, GMG_K_COPY_TO, (20.0 + sizeof(T)) * n, 2.0 * n);
+  GMG_CUDA_TRY(launch_cg_start<T>(n, b, d->home, d->r, (T*)d->g, d->partials, d->counter, bb, d->stream));
+  return GMG_OK;
+}
+
+template <typename T>
+static gmg_status cg_iteration_t(Hier& h, double* x, double* rz, const double* rz_old, double* pAp, double* rr) {
+  DeviceState* d = h.dev;
+  cudaStream_t s = d->stream;
+  const int64_t n = d->n_unknowns;
+  const T* u = (const T*)d->uB;
+  GMG_TRY(vcycle_levels<T>(h));
+  {
+    Track t(d, GMG_K_COPY_FROM, (12.0 + sizeof(T)) * n, 2.0 * n);
+    GMG_CUDA_TRY(launch_cg_rz<T>(n, u, d->home, d->r, d->partials, d->counter, rz, s));
+  }
+  {
+    Track t(d, GMG_K_CG_P, (28.0 + sizeof(T)) * n, 2.0 * n);
+    GMG_CUDA_TRY(launch_cg_p<T>(n, u, d->home, d->p, d->Ap, rz, rz_old, s));
+  }
+  {
+    Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
+    GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), d->p, d->Ap, d->partials, d->counter, pAp, s));
+  }
+  GMG_CUDA_TRY(cudaMemsetAsync(d->g, 0, (size_t)h.total_slots * sizeof(T), s));
+  Track t(d, GMG_K_CG_XR, (52.0 + sizeof(T)) * n, 6.0 * n);
+  GMG_CUDA_TRY(launch_cg_xr<T>(n, x, d->r, d->p, d->Ap, d->home, (T*)d->g, rz, pAp, d->partials, d->counter, rr, s));
+  return GMG_OK;
+}
+
+static gmg_status cg_start(Hier& h, const double* b, double* bb) {
+  return h.dev->prec == GMG_PREC_FP32 ? cg_start_t<float>(h, b, bb) : cg_start_t<double>(h, b, bb);
+}
+static gmg_status cg_iteration(Hier& h, double* x, double* rz, const double* rz_old, double* pAp, double* rr) {
+  return h.dev->prec == GMG_PREC_FP32 ? cg_iteration_t<float>(h, x, rz, rz_old, pAp, rr)
+                                      : cg_iteration_t<double>(h, x, rz, rz_old, pAp, rr);
 }
 
 gmg_status device_vcycle(Hier& h, const double* r, double* z) {
@@ -747,8 +812,8 @@ gmg_status device_rhs(Hier& h, int kind, double* b) {
 
 // Preconditioned CG (x0 = 0), stream mode: the host reads the scalars of
 // every iteration and decides whether to go on.  Scalars live on the device:
-// slot 0 = b.b, slots 1+3i .. 3+3i = (r_i.z_i, p_i.A p_i, r_{i+1}.r_{i+1}) of
-// iteration i.
+// slot 0 = b.b, slot 1 = 1 (r.z before the first iteration), slots 2+3i ..
+// 4+3i = (r_i.z_i, p_i.A p_i, r_{i+1}.r_{i+1}) of iteration i.
 static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, int max_iter, int fixed_iterations,
                                gmg_stats* st) {
   DeviceState* d = h.dev;
@@ -759,11 +824,10 @@ static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, 
   double* S = d->scal;
   double* H = d->scal_host;
   GMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-  GMG_CUDA_TRY(cudaMemcpyAsync(d->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  {
-    Track t(d, GMG_K_OTHER, 8.0 * n, 2.0 * n);
-    GMG_CUDA_TRY(launch_dot(n, b, b, d->partials, d->counter, S, s));
-  }
+  GMG_CUDA_TRY(cudaMemsetAsync(d->p, 0, sizeof(double) * n, s));
+  H[1] = 1.0;
+  GMG_CUDA_TRY(cudaMemcpyAsync(S + 1, H + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+  GMG_TRY(cg_start(h, b, S));
   GMG_CUDA_TRY(cudaMemcpyAsync(H, S, sizeof(double), cudaMemcpyDeviceToHost, s));
   GMG_CUDA_TRY(cudaStreamSynchronize(s));
   const double bb = H[0];
@@ -781,23 +845,14 @@ static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, 
     }
     return GMG_OK;
   }
-  GMG_TRY(vcycle_any(h, d->r, d->z, S + 1));
-  GMG_CUDA_TRY(cudaMemcpyAsync(d->p, d->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   gmg_status result = GMG_ENOTCONV;
   for (int it = 0; it < limit; ++it) {
-    double* base = S + 1 + 3 * it;
-    GMG_CUDA_TRY(cudaMemsetAsync(d->Ap, 0, sizeof(double) * n, s));
-    {
-      Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
-      GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), d->p, d->Ap, d->partials, d->counter, base + 1, s));
-    }
-    {
-      Track t(d, GMG_K_CG_XR, 48.0 * n, 6.0 * n);
-      GMG_CUDA_TRY(launch_cg_update_xr(n, x, d->r, d->p, d->Ap, base, base + 1, d->partials, d->counter, base + 2, s));
-    }
-    GMG_CUDA_TRY(cudaMemcpyAsync(H + 1 + 3 * it, base, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double* base = S + 2 + 3 * it;
+    const double* rz_old = it == 0 ? S + 1 : base - 3;
+    GMG_TRY(cg_iteration(h, x, base, rz_old, base + 1, base + 2));
+    GMG_CUDA_TRY(cudaMemcpyAsync(H + 2 + 3 * it, base, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     GMG_CUDA_TRY(cudaStreamSynchronize(s));
-    const double rz = H[1 + 3 * it], pAp = H[2 + 3 * it], rr = H[3 + 3 * it];
+    const double rz = H[2 + 3 * it], pAp = H[3 + 3 * it], rr = H[4 + 3 * it];
     stats.iterations = it + 1;
     stats.rel_residual = std::sqrt(rr / bb);
     if (std::isnan(rz) || std::isnan(pAp) || std::isnan(rr) || std::isinf(rr)) {
@@ -821,10 +876,6 @@ static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, 
       result = GMG_OK;
       break;
     }
-    if (it + 1 == limit) break;
-    GMG_TRY(vcycle_any(h, d->r, d->z, base + 3));
-    Track t(d, GMG_K_CG_P, 24.0 * n, 2.0 * n);
-    GMG_CUDA_TRY(launch_cg_update_p(n, d->p, d->z, base + 3, base, s));
   }
   if (result == GMG_ENOTCONV) set_error("CG did not converge within max_iter");
   if (st) *st = stats;
@@ -832,13 +883,10 @@ static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, 
 }
 
 // ------------------------------------------------------ graph-mode CG
-// The same iteration as solve_stream, reordered so that the loop body starts
-// with the preconditioner: with p_{-1} = 0 and r_{-1}.z_{-1} = 1, pass i is
-//   z = B r, rz = r.z, p = z + (rz / rz_old) p, Ap = A p, pAp = p.Ap,
-//   x += (rz/pAp) p, r -= (rz/pAp) Ap, rr = r.r, check,
-// which performs exactly the stream-mode operations.  The loop is a
-// conditional WHILE node whose condition the check kernel sets, so a solve is
-// one graph launch and one host synchronisation.
+// The iteration of solve_stream (cg_iteration) as the body of a conditional
+// WHILE node whose condition a check kernel sets after each pass, with the
+// stream mode's stopping rules: a solve is one graph launch and one host
+// synchronisation, and performs exactly the stream-mode operations.
 
 // Ends a capture that failed and passes its status on.
 static gmg_status abandon_capture(cudaStream_t s, gmg_status st) {
@@ -854,10 +902,7 @@ static gmg_status capture_prelude(Hier& h, cudaGraph_t g, cudaGraphConditionalHa
   const int64_t n = d->n_unknowns;
   GMG_CUDA_TRY(cudaMemsetAsync(d->x_iter, 0, sizeof(double) * n, s));
   GMG_CUDA_TRY(cudaMemsetAsync(d->p, 0, sizeof(double) * n, s));
-  {
-    Track t(d, GMG_K_OTHER, 8.0 * n, 2.0 * n);
-    GMG_CUDA_TRY(launch_dot(n, d->r, d->r, d->partials, d->counter, &d->ctl->bb, s));
-  }
+  GMG_TRY(cg_start(h, d->r, &d->ctl->bb));  // b was copied into r before the launch
   GMG_CUDA_TRY(cudaGraphConditionalHandleCreate(loop, g, 0, cudaGraphCondAssignDefault));
   {
     Track t(d, GMG_K_OTHER, 0.0, 0.0);
@@ -882,23 +927,8 @@ static gmg_status capture_prelude(Hier& h, cudaGraph_t g, cudaGraphConditionalHa
 static gmg_status capture_body(Hier& h, cudaGraphConditionalHandle loop) {
   DeviceState* d = h.dev;
   cudaStream_t s = d->stream;
-  const int64_t n = d->n_unknowns;
   GraphCtl* c = d->ctl;
-  GMG_TRY(vcycle_any(h, d->r, d->z, &c->rz));
-  {
-    Track t(d, GMG_K_CG_P, 24.0 * n, 2.0 * n);
-    GMG_CUDA_TRY(launch_cg_update_p(n, d->p, d->z, &c->rz, &c->rz_old, s));
-  }
-  GMG_CUDA_TRY(cudaMemsetAsync(d->Ap, 0, sizeof(double) * n, s));
-  {
-    Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
-    GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), d->p, d->Ap, d->partials, d->counter, &c->pAp, s));
-  }
-  {
-    Track t(d, GMG_K_CG_XR, 48.0 * n, 6.0 * n);
-    GMG_CUDA_TRY(launch_cg_update_xr(n, d->x_iter, d->r, d->p, d->Ap, &c->rz, &c->pAp, d->partials, d->counter,
-                                     &c->rr, s));
-  }
+  GMG_TRY(cg_iteration(h, d->x_iter, &c->rz, &c->rz_old, &c->pAp, &c->rr));
   Track t(d, GMG_K_OTHER, 0.0, 0.0);
   GMG_CUDA_TRY(launch_cg_graph_check(c, loop, s));
   return GMG_OK;

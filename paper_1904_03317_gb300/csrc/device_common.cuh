@@ -184,7 +184,6 @@ struct DeviceState {
   double* r = nullptr;
   double* p = nullptr;
   double* Ap = nullptr;
-  double* z = nullptr;
   // reductions
   double* partials = nullptr;     // kMaxReduceBlocks
   unsigned* counter = nullptr;
@@ -284,12 +283,23 @@ template <typename T>
 cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, cudaStream_t s);
 cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials,
                        unsigned* counter, double* out, cudaStream_t s);
-cudaError_t launch_cg_update_xr(int64_t n, double* x, double* r, const double* p,
-                                const double* Ap, const double* rz, const double* pAp,
-                                double* partials, unsigned* counter, double* rr_out,
-                                cudaStream_t s);
-cudaError_t launch_cg_update_p(int64_t n, double* p, const double* z, const double* rz_new,
-                               const double* rz_old, cudaStream_t s);
+// The outer CG's streaming passes, fused with the active <-> level copies
+// (z_i = u[home_i] is never stored): r = b with b.b and the first level
+// right-hand sides; r.z; p = z + (rz_new / rz_old) p with Ap = 0; and x += a
+// p, r -= a Ap with r.r and the next level right-hand sides (a = rz / pAp).
+template <typename T>
+cudaError_t launch_cg_start(int64_t n, const double* b, const uint32_t* home, double* r, T* g, double* partials,
+                            unsigned* counter, double* bb_out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_rz(int64_t n, const T* u, const uint32_t* home, const double* r, double* partials,
+                         unsigned* counter, double* rz_out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_p(int64_t n, const T* u, const uint32_t* home, double* p, double* Ap, const double* rz_new,
+                        const double* rz_old, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_xr(int64_t n, double* x, double* r, const double* p, const double* Ap, const uint32_t* home,
+                         T* g, const double* rz, const double* pAp, double* partials, unsigned* counter,
+                         double* rr_out, cudaStream_t s);
 // Loop control of the graph-mode CG: `init` starts the loop when b.b > 0,
 // `check` counts an iteration, applies the stopping rules and sets the loop
 // condition.

@@ -1112,49 +1112,124 @@ cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* part
   return cudaGetLastError();
 }
 
-// x += alpha p, r -= alpha Ap, rr = r.r   with alpha = rz / pAp read on the device
-__global__ void __launch_bounds__(256) cg_update_xr_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
-                                                           const double* __restrict__ p,
-                                                           const double* __restrict__ Ap, const double* rz,
-                                                           const double* pAp, double* partials,
-                                                           unsigned* counter, double* rr_out) {
+// ------------------------------------------- CG passes fused with the copies
+// The outer CG of the solve keeps no z = B r vector: its entries are the
+// level solutions at the unknowns' home slots, z_i = u[home_i], read where
+// they are needed, and the level right-hand sides of the next V-cycle are
+// written by the pass that updates r.
+
+// r = b, b.b, and g[home_i] = b_i (the first V-cycle's right-hand sides; g
+// must be zero elsewhere)
+// (b may be r itself)
+template <typename T>
+__global__ void __launch_bounds__(256) cg_start_kernel(int64_t n, const double* b,
+                                                       const uint32_t* __restrict__ home, double* r,
+                                                       T* __restrict__ g, double* partials, unsigned* counter,
+                                                       double* bb_out) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[i];
+    r[i] = v;
+    g[home[i]] = (T)v;
+    acc += v * v;
+  }
+  double s = block_sum<256>(acc, sh);
+  finish_reduction<256>(s, partials, counter, bb_out);
+}
+
+// r.z with z_i = u[home_i]
+template <typename T>
+__global__ void __launch_bounds__(256) cg_rz_kernel(int64_t n, const T* __restrict__ u,
+                                                    const uint32_t* __restrict__ home, const double* __restrict__ r,
+                                                    double* partials, unsigned* counter, double* rz_out) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += r[i] * (double)u[home[i]];
+  double s = block_sum<256>(acc, sh);
+  finish_reduction<256>(s, partials, counter, rz_out);
+}
+
+// p = z + beta p with z_i = u[home_i], beta = rz_new / rz_old, and Ap = 0
+// (the leaf operator accumulates into it)
+template <typename T>
+__global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restrict__ u,
+                                                   const uint32_t* __restrict__ home, double* __restrict__ p,
+                                                   double* __restrict__ Ap, const double* rz_new,
+                                                   const double* rz_old) {
+  const double beta = *rz_new / *rz_old;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = (double)u[home[i]] + beta * p[i];
+    Ap[i] = 0.0;
+  }
+}
+
+// x += alpha p, r -= alpha Ap, r.r, and g[home_i] = r_i for the next V-cycle
+// (alpha = rz / pAp read on the device; g must be zero elsewhere)
+template <typename T>
+__global__ void __launch_bounds__(256) cg_xr_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                    const double* __restrict__ p, const double* __restrict__ Ap,
+                                                    const uint32_t* __restrict__ home, T* __restrict__ g,
+                                                    const double* rz, const double* pAp, double* partials,
+                                                    unsigned* counter, double* rr_out) {
   __shared__ double sh[8];
   const double alpha = *rz / *pAp;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
-    double ri = r[i] - alpha * Ap[i];
+    const double ri = r[i] - alpha * Ap[i];
     r[i] = ri;
+    g[home[i]] = (T)ri;
     acc += ri * ri;
   }
   double s = block_sum<256>(acc, sh);
   finish_reduction<256>(s, partials, counter, rr_out);
 }
 
-cudaError_t launch_cg_update_xr(int64_t n, double* x, double* r, const double* p, const double* Ap,
-                                const double* rz, const double* pAp, double* partials, unsigned* counter,
-                                double* rr_out, cudaStream_t s) {
-  cg_update_xr_kernel<<<reduce_grid(n, 256), 256, 0, s>>>(n, x, r, p, Ap, rz, pAp, partials, counter, rr_out);
+template <typename T>
+cudaError_t launch_cg_start(int64_t n, const double* b, const uint32_t* home, double* r, T* g, double* partials,
+                            unsigned* counter, double* bb_out, cudaStream_t s) {
+  cg_start_kernel<T><<<reduce_grid(n, 256), 256, 0, s>>>(n, b, home, r, g, partials, counter, bb_out);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
-
-// p = z + beta p, beta = rz_new / rz_old
-__global__ void cg_update_p_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ z,
-                                   const double* rz_new, const double* rz_old) {
-  const double beta = *rz_new / *rz_old;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+template <typename T>
+cudaError_t launch_cg_rz(int64_t n, const T* u, const uint32_t* home, const double* r, double* partials,
+                         unsigned* counter, double* rz_out, cudaStream_t s) {
+  cg_rz_kernel<T><<<reduce_grid(n, 256), 256, 0, s>>>(n, u, home, r, partials, counter, rz_out);
+  GMG_COUNT_LAUNCH();
+  return cudaGetLastError();
 }
-
-cudaError_t launch_cg_update_p(int64_t n, double* p, const double* z, const double* rz_new,
-                               const double* rz_old, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_cg_p(int64_t n, const T* u, const uint32_t* home, double* p, double* Ap, const double* rz_new,
+                        const double* rz_old, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   int64_t b = (n + 255) / 256;
-  cg_update_p_kernel<<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, p, z, rz_new, rz_old);
+  cg_p_kernel<T><<<(unsigned)(b > 152 * 64 ? 152 * 64 : b), 256, 0, s>>>(n, u, home, p, Ap, rz_new, rz_old);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_cg_xr(int64_t n, double* x, double* r, const double* p, const double* Ap, const uint32_t* home,
+                         T* g, const double* rz, const double* pAp, double* partials, unsigned* counter,
+                         double* rr_out, cudaStream_t s) {
+  cg_xr_kernel<T><<<reduce_grid(n, 256), 256, 0, s>>>(n, x, r, p, Ap, home, g, rz, pAp, partials, counter, rr_out);
+  GMG_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+#define GMG_CG_INST(T)                                                                                          \
+  template cudaError_t launch_cg_start<T>(int64_t, const double*, const uint32_t*, double*, T*, double*,        \
+                                          unsigned*, double*, cudaStream_t);                                     \
+  template cudaError_t launch_cg_rz<T>(int64_t, const T*, const uint32_t*, const double*, double*, unsigned*,   \
+                                       double*, cudaStream_t);                                                   \
+  template cudaError_t launch_cg_p<T>(int64_t, const T*, const uint32_t*, double*, double*, const double*,      \
+                                      const double*, cudaStream_t);                                              \
+  template cudaError_t launch_cg_xr<T>(int64_t, double*, double*, const double*, const double*, const uint32_t*, \
+                                       T*, const double*, const double*, double*, unsigned*, double*, cudaStream_t);
+GMG_CG_INST(float)
+GMG_CG_INST(double)
+#undef GMG_CG_INST
 
 // ---------------------------------------------------- graph-mode CG control
 // Single-thread kernels; the stopping rules are those of the stream-mode loop
