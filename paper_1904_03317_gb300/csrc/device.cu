@@ -278,7 +278,7 @@ void device_free(Hier& h) {
     cudaFree(L.list_rest);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->coarse_ptr, d->coarse_col, d->coarse_val, d->cell_nodes, d->cell_coeff, d->cell_level,
-                  d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->r, d->p, d->Ap,
+                  d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->perm, d->r, d->p, d->Ap,
                   d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level,
                   d->pat_nodes, d->pat_coeff, d->pat_level, d->loose_nodes, d->loose_coeff, d->loose_level,
                   d->xh, d->yh, d->hm_node, d->hm_ptr,
@@ -463,34 +463,61 @@ gmg_status device_setup(Hier& h) {
     GMG_CUDA_TRY(cudaMemsetAsync(d->uA, 0, ns * esz, d->stream));
     GMG_CUDA_TRY(cudaMemsetAsync(d->uB, 0, ns * esz, d->stream));
   }
-  // active mesh
+  // active mesh, unknowns renumbered by home slot (every unknown has one
+  // home slot, so this is a permutation); tables keep their encoding (-1
+  // Dirichlet, <= -2 hanging row) and only unknown indices change
   const ActiveHost& A = h.active;
   d->n_unknowns = A.n_unknowns;
   d->n_cells = A.n_cells;
-  GMG_TRY(upload(d, &d->cell_nodes, A.cell_nodes));
+  std::vector<int32_t> perm, inv;
+  {
+    const int64_t nu = A.n_unknowns;
+    std::vector<int32_t> at_slot((size_t)h.total_slots, -1);
+    for (int64_t u = 0; u < nu; ++u) at_slot[A.home_global[u]] = (int32_t)u;
+    perm.reserve((size_t)nu);
+    for (int64_t sl = 0; sl < h.total_slots; ++sl)
+      if (at_slot[sl] >= 0) perm.push_back(at_slot[sl]);
+    if ((int64_t)perm.size() != nu) {
+      set_error("internal: home slots are not one per unknown");
+      return GMG_EINVAL;
+    }
+    inv.assign((size_t)nu, 0);
+    for (int64_t j = 0; j < nu; ++j) inv[perm[j]] = (int32_t)j;
+  }
+  auto renumbered = [&](const std::vector<int32_t>& v) {
+    std::vector<int32_t> out(v.size());
+    const int64_t m = (int64_t)v.size();
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) out[i] = v[i] >= 0 ? inv[v[i]] : v[i];
+    return out;
+  };
+  std::vector<uint32_t> home_int((size_t)A.n_unknowns);
+  for (int64_t j = 0; j < A.n_unknowns; ++j) home_int[j] = A.home_global[perm[j]];
+  GMG_TRY(upload(d, &d->perm, perm));
+  GMG_TRY(upload(d, &d->cell_nodes, renumbered(A.cell_nodes)));
   GMG_TRY(upload(d, &d->cell_coeff, A.cell_coeff));
   GMG_TRY(upload(d, &d->cell_level, A.cell_level));
   GMG_TRY(upload(d, &d->cell_coords, A.cell_coords));
   GMG_TRY(upload(d, &d->hang_ptr, A.hang_ptr));
-  GMG_TRY(upload(d, &d->hang_col, A.hang_col));
+  GMG_TRY(upload(d, &d->hang_col, renumbered(A.hang_col)));
   GMG_TRY(upload(d, &d->hang_w, A.hang_w));
   d->n_hang = (int64_t)A.hang_key.size();
   d->n_masters = (int64_t)A.hm_node.size();
   GMG_TRY(dev_alloc(d, &d->xh, (size_t)d->n_hang));
   GMG_TRY(dev_alloc(d, &d->yh, (size_t)d->n_hang));
-  GMG_TRY(upload(d, &d->hm_node, A.hm_node));
+  GMG_TRY(upload(d, &d->hm_node, renumbered(A.hm_node)));
   GMG_TRY(upload(d, &d->hm_ptr, A.hm_ptr));
   GMG_TRY(upload(d, &d->hm_hang, A.hm_hang));
   GMG_TRY(upload(d, &d->hm_w, A.hm_w));
-  GMG_TRY(upload(d, &d->home, A.home_global));
+  GMG_TRY(upload(d, &d->home, home_int));
   GMG_TRY(upload(d, &d->loose, A.loose_cells));
-  GMG_TRY(upload(d, &d->grp_nodes, A.grp_nodes));
+  GMG_TRY(upload(d, &d->grp_nodes, renumbered(A.grp_nodes)));
   GMG_TRY(upload(d, &d->grp_coeff, A.grp_coeff));
   GMG_TRY(upload(d, &d->grp_level, A.grp_level));
-  GMG_TRY(upload(d, &d->loose_nodes, A.loose_nodes));
+  GMG_TRY(upload(d, &d->loose_nodes, renumbered(A.loose_nodes)));
   GMG_TRY(upload(d, &d->loose_coeff, A.loose_coeff));
   GMG_TRY(upload(d, &d->loose_level, A.loose_level));
-  GMG_TRY(upload(d, &d->pat_nodes, A.pat_nodes));
+  GMG_TRY(upload(d, &d->pat_nodes, renumbered(A.pat_nodes)));
   GMG_TRY(upload(d, &d->pat_coeff, A.pat_coeff));
   GMG_TRY(upload(d, &d->pat_level, A.pat_level));
   d->n_loose = (int64_t)A.loose_cells.size();
@@ -527,6 +554,7 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(dev_alloc(d, &d->r, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->p, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->Ap, A.n_unknowns));
+  GMG_TRY(dev_alloc(d, &d->x_iter, A.n_unknowns));
   GMG_TRY(dev_alloc(d, &d->partials, kMaxReduceBlocks));
   GMG_TRY(dev_alloc(d, &d->counter, 1));
   GMG_CUDA_TRY(cudaMemset(d->counter, 0, sizeof(unsigned)));
@@ -732,6 +760,19 @@ static gmg_status vcycle_any(Hier& h, const double* r, double* z, double* rz_out
   return vcycle_impl<double>(h, r, z, rz_out);
 }
 
+// A caller's canonical vector into the internal order (dst[j] = src[perm[j]])
+// and an internal one back out.
+static gmg_status to_internal(DeviceState* d, const double* src, double* dst, cudaStream_t s) {
+  Track t(d, GMG_K_OTHER, 20.0 * d->n_unknowns, 0.0);
+  GMG_CUDA_TRY(launch_perm(d->n_unknowns, d->perm, src, dst, false, s));
+  return GMG_OK;
+}
+static gmg_status to_canonical(DeviceState* d, const double* src, double* dst, cudaStream_t s) {
+  Track t(d, GMG_K_OTHER, 20.0 * d->n_unknowns, 0.0);
+  GMG_CUDA_TRY(launch_perm(d->n_unknowns, d->perm, src, dst, true, s));
+  return GMG_OK;
+}
+
 // ---------------------------------------------- CG passes around the V-cycle
 // One preconditioned CG iteration in the order both solve modes use
 // (Sec. 4.1: CG preconditioned by one V-cycle), with z = B r read from the
@@ -787,16 +828,23 @@ static gmg_status cg_iteration(Hier& h, double* x, double* rz, const double* rz_
 }
 
 gmg_status device_vcycle(Hier& h, const double* r, double* z) {
-  GMG_TRY(ensure_scalars(h.dev, 8));
-  return vcycle_any(h, r, z, h.dev->scal + 1);
+  DeviceState* d = h.dev;
+  GMG_TRY(ensure_scalars(d, 8));
+  GMG_TRY(to_internal(d, r, d->r, d->stream));
+  GMG_TRY(vcycle_any(h, d->r, d->p, d->scal + 1));
+  return to_canonical(d, d->p, z, d->stream);
 }
 
 gmg_status device_apply(Hier& h, const double* x, double* y) {
   DeviceState* d = h.dev;
-  GMG_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * d->n_unknowns, d->stream));
-  Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
-  GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), x, y, d->partials, d->counter, nullptr, d->stream));
-  return GMG_OK;
+  GMG_TRY(to_internal(d, x, d->p, d->stream));
+  GMG_CUDA_TRY(cudaMemsetAsync(d->Ap, 0, sizeof(double) * d->n_unknowns, d->stream));
+  {
+    Track t(d, GMG_K_ACTIVE, d->active_bytes, d->active_flops);
+    GMG_CUDA_TRY(launch_active_apply(h.dim, h.k, active_args(h), d->p, d->Ap, d->partials, d->counter, nullptr,
+                                     d->stream));
+  }
+  return to_canonical(d, d->Ap, y, d->stream);
 }
 
 gmg_status device_rhs(Hier& h, int kind, double* b) {
@@ -805,9 +853,9 @@ gmg_status device_rhs(Hier& h, int kind, double* b) {
     set_error("gmg_assemble_rhs: unknown kind");
     return GMG_EINVAL;
   }
-  GMG_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * d->n_unknowns, d->stream));
-  GMG_CUDA_TRY(launch_rhs_sine(h.dim, h.k, active_args(h), d->cell_coords, b, d->stream));
-  return GMG_OK;
+  GMG_CUDA_TRY(cudaMemsetAsync(d->r, 0, sizeof(double) * d->n_unknowns, d->stream));
+  GMG_CUDA_TRY(launch_rhs_sine(h.dim, h.k, active_args(h), d->cell_coords, d->r, d->stream));
+  return to_canonical(d, d->r, b, d->stream);
 }
 
 // Preconditioned CG (x0 = 0), stream mode: the host reads the scalars of
@@ -823,11 +871,14 @@ static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, 
   GMG_TRY(ensure_scalars(d, 3 * limit + 8));
   double* S = d->scal;
   double* H = d->scal_host;
+  double* xi = d->x_iter;  // the iterate in the internal order
   GMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  GMG_CUDA_TRY(cudaMemsetAsync(xi, 0, sizeof(double) * n, s));
   GMG_CUDA_TRY(cudaMemsetAsync(d->p, 0, sizeof(double) * n, s));
   H[1] = 1.0;
   GMG_CUDA_TRY(cudaMemcpyAsync(S + 1, H + 1, sizeof(double), cudaMemcpyHostToDevice, s));
-  GMG_TRY(cg_start(h, b, S));
+  GMG_TRY(to_internal(d, b, d->r, s));
+  GMG_TRY(cg_start(h, d->r, S));
   GMG_CUDA_TRY(cudaMemcpyAsync(H, S, sizeof(double), cudaMemcpyDeviceToHost, s));
   GMG_CUDA_TRY(cudaStreamSynchronize(s));
   const double bb = H[0];
@@ -849,7 +900,7 @@ static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, 
   for (int it = 0; it < limit; ++it) {
     double* base = S + 2 + 3 * it;
     const double* rz_old = it == 0 ? S + 1 : base - 3;
-    GMG_TRY(cg_iteration(h, x, base, rz_old, base + 1, base + 2));
+    GMG_TRY(cg_iteration(h, xi, base, rz_old, base + 1, base + 2));
     GMG_CUDA_TRY(cudaMemcpyAsync(H + 2 + 3 * it, base, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     GMG_CUDA_TRY(cudaStreamSynchronize(s));
     const double rz = H[2 + 3 * it], pAp = H[3 + 3 * it], rr = H[4 + 3 * it];
@@ -877,6 +928,8 @@ static gmg_status solve_stream(Hier& h, const double* b, double* x, double tol, 
       break;
     }
   }
+  GMG_TRY(to_canonical(d, xi, x, s));
+  GMG_CUDA_TRY(cudaStreamSynchronize(s));
   if (result == GMG_ENOTCONV) set_error("CG did not converge within max_iter");
   if (st) *st = stats;
   return result;
@@ -936,7 +989,6 @@ static gmg_status capture_body(Hier& h, cudaGraphConditionalHandle loop) {
 
 static gmg_status build_solve_graph(Hier& h) {
   DeviceState* d = h.dev;
-  if (!d->x_iter) GMG_TRY(dev_alloc(d, &d->x_iter, (size_t)d->n_unknowns));
   if (!d->ctl) GMG_TRY(dev_alloc(d, &d->ctl, 1));
   if (!d->ctl_host) GMG_CUDA_TRY(cudaMallocHost(&d->ctl_host, sizeof(GraphCtl)));
   // capture on a private stream: the context's stream may be the legacy
@@ -1030,10 +1082,10 @@ static gmg_status enqueue_graph_solve(Hier& h, const double* b, double* x, doubl
   c->limit = fixed_iterations > 0 ? fixed_iterations : max_iter;
   c->fixed = fixed_iterations > 0 ? fixed_iterations : 0;
   c->status = GS_RUNNING;
-  GMG_CUDA_TRY(cudaMemcpyAsync(d->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GMG_TRY(to_internal(d, b, d->r, s));
   GMG_CUDA_TRY(cudaMemcpyAsync(d->ctl, c, sizeof(GraphCtl), cudaMemcpyHostToDevice, s));
   GMG_CUDA_TRY(cudaGraphLaunch(d->cg_exec, s));
-  GMG_CUDA_TRY(cudaMemcpyAsync(x, d->x_iter, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GMG_TRY(to_canonical(d, d->x_iter, x, s));
   GMG_CUDA_TRY(cudaMemcpyAsync(c, d->ctl, sizeof(GraphCtl), cudaMemcpyDeviceToHost, s));
   return GMG_OK;
 }

@@ -178,6 +178,13 @@ struct DeviceState {
   int32_t* hm_hang = nullptr;
   double* hm_w = nullptr;
   uint32_t* home = nullptr;
+  // The device numbers the unknowns in the order of their home slots, so that
+  // the copies between active and level vectors and the leaf operator's
+  // gathers touch memory in order; perm[j] is the canonical index of internal
+  // unknown j.  Every table on the device (home, leaf node tables, hanging
+  // constraints) uses the internal numbering; the entry points convert the
+  // caller's canonical vectors on the way in and out.
+  int32_t* perm = nullptr;
   double level_scale[GMG_MAX_LEVELS][3];  // leaf-cell operator factors per level
   double cell_h[GMG_MAX_LEVELS][3];       // cell sizes per level
   // CG work vectors
@@ -283,6 +290,10 @@ template <typename T>
 cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, cudaStream_t s);
 cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials,
                        unsigned* counter, double* out, cudaStream_t s);
+// Canonical <-> internal unknown order: dst[j] = src[perm[j]] (gather) or
+// dst[perm[j]] = src[j] (scatter).
+cudaError_t launch_perm(int64_t n, const int32_t* perm, const double* src, double* dst, bool scatter,
+                        cudaStream_t s);
 // The outer CG's streaming passes, fused with the active <-> level copies
 // (z_i = u[home_i] is never stored): r = b with b.b and the first level
 // right-hand sides; r.z; p = z + (rz_new / rz_old) p with Ap = 0; and x += a

@@ -1112,15 +1112,45 @@ cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* part
   return cudaGetLastError();
 }
 
+// --------------------------------------------- internal unknown numbering
+// The device numbers the unknowns by their home slots (see device_setup); the
+// caller's vectors are in canonical order.  dst[j] = src[perm[j]] brings a
+// canonical vector in, dst[perm[j]] = src[j] takes an internal one out.
+__global__ void __launch_bounds__(256) perm_gather_kernel(int64_t n, const int32_t* __restrict__ perm,
+                                                          const double* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = src[perm[j]];
+}
+__global__ void __launch_bounds__(256) perm_scatter_kernel(int64_t n, const int32_t* __restrict__ perm,
+                                                           const double* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[j]] = src[j];
+}
+cudaError_t launch_perm(int64_t n, const int32_t* perm, const double* src, double* dst, bool scatter,
+                        cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t b = (n + 255) / 256;
+  const unsigned grid = (unsigned)(b > 152 * 64 ? 152 * 64 : b);
+  if (scatter) perm_scatter_kernel<<<grid, 256, 0, s>>>(n, perm, src, dst);
+  else perm_gather_kernel<<<grid, 256, 0, s>>>(n, perm, src, dst);
+  GMG_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 // ------------------------------------------- CG passes fused with the copies
 // The outer CG of the solve keeps no z = B r vector: its entries are the
 // level solutions at the unknowns' home slots, z_i = u[home_i], read where
 // they are needed, and the level right-hand sides of the next V-cycle are
 // written by the pass that updates r.
 
+// The passes below are grid-stride loops unrolled four times: each thread
+// first issues the independent loads of four entries (one grid stride apart,
+// so every group of loads is coalesced), then the dependent gathers and
+// stores, which keeps enough loads in flight to stream at HBM speed.
+constexpr int kUnroll = 4;
+
 // r = b, b.b, and g[home_i] = b_i (the first V-cycle's right-hand sides; g
-// must be zero elsewhere)
-// (b may be r itself)
+// must be zero elsewhere; b may be r itself)
 template <typename T>
 __global__ void __launch_bounds__(256) cg_start_kernel(int64_t n, const double* b,
                                                        const uint32_t* __restrict__ home, double* r,
@@ -1128,7 +1158,24 @@ __global__ void __launch_bounds__(256) cg_start_kernel(int64_t n, const double* 
                                                        double* bb_out) {
   __shared__ double sh[8];
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * st < n; i += kUnroll * st) {
+    double v[kUnroll];
+    uint32_t hm[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      v[k] = b[i + k * st];
+      hm[k] = home[i + k * st];
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      r[i + k * st] = v[k];
+      g[hm[k]] = (T)v[k];
+      acc += v[k] * v[k];
+    }
+  }
+  for (; i < n; i += st) {
     const double v = b[i];
     r[i] = v;
     g[home[i]] = (T)v;
@@ -1145,8 +1192,20 @@ __global__ void __launch_bounds__(256) cg_rz_kernel(int64_t n, const T* __restri
                                                     double* partials, unsigned* counter, double* rz_out) {
   __shared__ double sh[8];
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += r[i] * (double)u[home[i]];
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * st < n; i += kUnroll * st) {
+    double rv[kUnroll];
+    uint32_t hm[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      rv[k] = r[i + k * st];
+      hm[k] = home[i + k * st];
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) acc += rv[k] * (double)u[hm[k]];
+  }
+  for (; i < n; i += st) acc += r[i] * (double)u[home[i]];
   double s = block_sum<256>(acc, sh);
   finish_reduction<256>(s, partials, counter, rz_out);
 }
@@ -1159,7 +1218,23 @@ __global__ void __launch_bounds__(256) cg_p_kernel(int64_t n, const T* __restric
                                                    double* __restrict__ Ap, const double* rz_new,
                                                    const double* rz_old) {
   const double beta = *rz_new / *rz_old;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * st < n; i += kUnroll * st) {
+    double pv[kUnroll];
+    uint32_t hm[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      pv[k] = p[i + k * st];
+      hm[k] = home[i + k * st];
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      p[i + k * st] = (double)u[hm[k]] + beta * pv[k];
+      Ap[i + k * st] = 0.0;
+    }
+  }
+  for (; i < n; i += st) {
     p[i] = (double)u[home[i]] + beta * p[i];
     Ap[i] = 0.0;
   }
@@ -1176,7 +1251,31 @@ __global__ void __launch_bounds__(256) cg_xr_kernel(int64_t n, double* __restric
   __shared__ double sh[8];
   const double alpha = *rz / *pAp;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * st < n; i += kUnroll * st) {
+    double xv[kUnroll], rv[kUnroll], pv[kUnroll], av[kUnroll];
+    uint32_t hm[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int64_t j = i + k * st;
+      xv[k] = x[j];
+      rv[k] = r[j];
+      pv[k] = p[j];
+      av[k] = Ap[j];
+      hm[k] = home[j];
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const int64_t j = i + k * st;
+      x[j] = xv[k] + alpha * pv[k];
+      const double ri = rv[k] - alpha * av[k];
+      r[j] = ri;
+      g[hm[k]] = (T)ri;
+      acc += ri * ri;
+    }
+  }
+  for (; i < n; i += st) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * Ap[i];
     r[i] = ri;
