@@ -42,10 +42,6 @@ def peaks():
 # FP64 arithmetic peak of the part: 1.25 TFLOP/s nominal (dense FP64, incl. FMA = 2 flops)
 FP64_PEAK_TFLOPS = 1.25
 
-# DRAM bytes (read + write) per launch of a kernel kind on the headline
-# workload, from one ncu capture (profiles/level_smoother_dram_traffic_*.md);
-# None where no capture matches the current kernels
-TRAFFIC_PER_LAUNCH = {"cheb": 48.34e6}
 
 
 class ClockSampler:
@@ -112,51 +108,115 @@ def over_ranks(dist, torch, value: float, op: str, device: str = "cuda") -> floa
     return float(t.item())
 
 
-def cpu_baseline(steps=1, min_seconds=8.0):
-    """The oracle (FP64, scipy sparse, single thread) on a bounded sample of the
-    same generator; returns (DoFs/s, sample description, seconds)."""
+def _oracle_worker(conn, g, a):
+    """One oracle process: build the sample hierarchy once, then solve it on
+    every request and report the solve time."""
     from oracle import gmg as ogmg
     from paper_1904_03317_gb300 import inputs
-    w = inputs.poisson3d_sphere(SAMPLE_GLOBAL, SAMPLE_ADAPTIVE)
+    w = inputs.poisson3d_sphere(g, a)
     H = ogmg.setup(w)
     b = H.disc.rhs_sine()
-    n, solves, t = H.disc.n, 0, 0.0
-    while solves < steps or t < min_seconds:
+    conn.send(H.disc.n)
+    while conn.recv() == "solve":
         t0 = time.perf_counter()
         res = ogmg.solve(H, b, TOL)
-        t += time.perf_counter() - t0
-        solves += 1
-    desc = (f"oracle FP64 local-smoothing GMG-CG (scipy sparse) on the same sphere generator with "
-            f"{SAMPLE_GLOBAL} global + {SAMPLE_ADAPTIVE} adaptive refinements ({n} unknowns), "
-            f"{solves} solves to 1e-8 ({res.iterations} its)")
-    return n * solves / t, desc, t, n
+        conn.send((time.perf_counter() - t0, res.iterations))
+
+
+class OraclePool:
+    """The oracle (FP64, scipy sparse; one thread per process) on every host
+    core of this process's affinity mask: one spawned process per core, each
+    holding its own copy of the bounded sample of the headline generator.  A
+    step is one solve in every process at once; its wall time is the
+    slowest.  Spawned, not forked: the parent may already hold a CUDA
+    context."""
+
+    def __init__(self, g=SAMPLE_GLOBAL, a=SAMPLE_ADAPTIVE, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or len(os.sched_getaffinity(0))
+        self.g, self.a = g, a
+        ctx = mp.get_context("spawn")
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"  # each process computes on one core
+        try:
+            self.conns, self.procs = [], []
+            for _ in range(self.cores):
+                mine, theirs = ctx.Pipe()
+                pr = ctx.Process(target=_oracle_worker, args=(theirs, g, a), daemon=True)
+                pr.start()
+                self.conns.append(mine)
+                self.procs.append(pr)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.n = [c.recv() for c in self.conns][0]
+
+    def step(self):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("solve")
+        its = [c.recv()[1] for c in self.conns]
+        return time.perf_counter() - t0, its[0]
+
+    def close(self):
+        for c in self.conns:
+            c.send("stop")
+        for pr in self.procs:
+            pr.join(timeout=30)
+
+    def describe(self, steps, its):
+        return (f"oracle FP64 local-smoothing GMG-CG (scipy sparse), {self.cores} processes x one core, each solving "
+                f"the same sphere generator with {self.g} global + {self.a} adaptive refinements ({self.n} unknowns, "
+                f"{its} its to 1e-8; the headline workload has {GLOBAL_REF} + {ADAPTIVE_REF} rounds, 21.9M unknowns, "
+                f"which the assembled-matrix oracle cannot hold), {steps} rounds of {self.cores} concurrent solves")
+
+
+def cpu_baseline(min_seconds=10.0):
+    """The oracle on all host cores (OraclePool) for at least min_seconds of
+    solves; returns (DoFs/s, sample description, cores)."""
+    pool = OraclePool()
+    try:
+        pool.step()  # first solve of every process untimed
+        t = 0.0
+        steps = 0
+        while t < min_seconds:
+            dt, its = pool.step()
+            t += dt
+            steps += 1
+    finally:
+        pool.close()
+    return pool.n * pool.cores * steps / t, pool.describe(steps, its), pool.cores
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the oracle on the host cores (rank 0 only)."""
+    """Reference arm: the oracle on the host cores (rank 0 only); a step is
+    one solve of the bounded sample in every process of the pool."""
     if rank != 0:
         return
-    from oracle import gmg as ogmg
-    from paper_1904_03317_gb300 import inputs
-    w = inputs.poisson3d_sphere(SAMPLE_GLOBAL, SAMPLE_ADAPTIVE)
-    H = ogmg.setup(w)
-    b = H.disc.rhs_sine()
-    for _ in range(args.warmup):
-        ogmg.solve(H, b, TOL)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        res = ogmg.solve(H, b, TOL)
-    t = time.perf_counter() - t0
-    v = H.disc.n * args.steps / t
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        t = 0.0
+        for _ in range(args.steps):
+            dt, its = pool.step()
+            t += dt
+    finally:
+        pool.close()
+    v = pool.n * pool.cores * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoFs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"poisson3d_q2_sphere_g{SAMPLE_GLOBAL}_a{SAMPLE_ADAPTIVE} (bounded CPU sample "
-                                   f"of the g{GLOBAL_REF}_a{ADAPTIVE_REF} workload)", "unknowns": H.disc.n,
-                       "tol": TOL, "cheb_degree": w.cheb_degree},
-            "cpu_baseline": {"value": v, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} oracle solves of {H.disc.n} unknowns ({res.iterations} its)"},
+            "config": {"workload": f"poisson3d_q2_sphere_g{SAMPLE_GLOBAL}_a{SAMPLE_ADAPTIVE} x {pool.cores} "
+                                   f"(bounded CPU sample of the g{GLOBAL_REF}_a{ADAPTIVE_REF} workload, one per core)",
+                       "unknowns": pool.n, "tol": TOL, "cheb_degree": 4},
+            "cpu_baseline": {"value": v, "unit": "DoFs/s", "cores": pool.cores, "kind": "oracle",
+                             "sample": pool.describe(args.steps, its)},
             "e2e": {"value": v, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -173,19 +233,21 @@ def time_solves(torch, H, b, x, steps, stream):
     return e0.elapsed_time(e1) / 1e3, st
 
 
-def run_serve(args, torch, G, inputs, local, rank, world):
+def serve_measure(torch, G, inputs, local, requests, warm_requests, rate):
     """Request loop: Poisson arrivals of 3D Q2 sphere-surface problems of
     log-uniform size, served with continuous batching (serve.Server); latency
-    is arrival to result, throughput counts the measured requests only."""
+    is arrival to result, throughput counts the measured requests only.  The
+    same requests one at a time with the plain FP64 V-cycle (a sample) are
+    timed beside it.  Returns (record, clocks)."""
     from paper_1904_03317_gb300 import serve
-    total = args.warm_requests + args.requests
-    arrivals, ws = inputs.serving_requests(total, rate=args.rate)
+    total = warm_requests + requests
+    arrivals, ws = inputs.serving_requests(total, rate=rate)
     sampler = ClockSampler(local)
     sampler.start()
     srv = serve.Server(torch, device=local)
     res = srv.run(arrivals, ws)
     clocks = sampler.stop()
-    meas = res[args.warm_requests:]
+    meas = res[warm_requests:]
     assert all(r.status == G.OK for r in meas), [r.status for r in meas]
     lat = [r.latency for r in meas]
     span = max(r.ready for r in meas) - min(r.arrival for r in meas)
@@ -203,7 +265,8 @@ def run_serve(args, torch, G, inputs, local, rank, world):
         a = time.perf_counter()
         h = G.Hierarchy(ctx, G.build_mesh(w), w.degree, w.coeff, cheb_degree=w.cheb_degree,
                         vcycle_prec=G.PREC_FP64)
-        b = torch.tensor(inputs.random_rhs(w.seed, h.n), dtype=torch.float64, device="cuda")
+        b = torch.empty(h.n, dtype=torch.float64, device="cuda")
+        h.assemble_rhs(b, "random", w.seed)
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         m = time.perf_counter()
@@ -214,32 +277,47 @@ def run_serve(args, torch, G, inputs, local, rank, world):
         t_solve64 += e - m
         n64 += h.n
         h.close()
+    ns = [r.n for r in meas]
+    rec = {"value": dofs / span, "unit": "DoFs/s (served, setup included)", "requests": len(meas),
+           "warm_requests": warm_requests, "rate_per_s": rate, "span_s": span,
+           "unknowns_min": int(min(ns)), "unknowns_median": int(np.median(ns)), "unknowns_max": int(max(ns)),
+           "setup_workers": srv.workers, "memory_budget_gb": round(srv.budget / 1e9, 1),
+           "hierarchy_cache_hits": srv.cache_hits,
+           "latency_s": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99),
+                         "queue_p50": serve.percentile(queue, 50), "setup_p50": serve.percentile(setup, 50),
+                         "solve_p50": serve.percentile(solve, 50), "solve_p99": serve.percentile(solve, 99)},
+           "serial_fp64": {"sample": k, "solve_dofs_per_s": n64 / t_solve64,
+                           "setup_and_solve_dofs_per_s": n64 / (t_setup64 + t_solve64)}}
+    return rec, clocks
+
+
+def run_serve(args, torch, G, inputs, local, rank, world):
+    rec, clocks = serve_measure(torch, G, inputs, local, args.requests, args.warm_requests, args.rate)
     if rank == 0:
-        ns = [r.n for r in meas]
         line = {
-            "metric": METRIC, "value": dofs / span, "unit": "DoFs/s", "n_gpus": world, "steps": len(meas),
-            "warmup": args.warm_requests, "ms_per_step": 1e3 * span / len(meas), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG", "data": "synthetic",
-            "config": {"workload": "serving_3d_q2_sphere_surface_requests", "requests": len(meas),
-                       "warm_requests": args.warm_requests, "rate_per_s": args.rate,
-                       "unknowns_min": int(min(ns)), "unknowns_median": int(np.median(ns)),
-                       "unknowns_max": int(max(ns)), "tol": TOL, "setup_workers": srv.workers,
-                       "memory_budget_gb": round(srv.budget / 1e9, 1)},
-            "latency_s": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99),
-                          "queue_p50": serve.percentile(queue, 50), "setup_p50": serve.percentile(setup, 50),
-                          "solve_p50": serve.percentile(solve, 50), "solve_p99": serve.percentile(solve, 99)},
-            "serial_fp64": {"sample": k, "solve_dofs_per_s": n64 / t_solve64,
-                            "setup_and_solve_dofs_per_s": n64 / (t_setup64 + t_solve64)},
-            "clocks": clocks,
+            "metric": METRIC, "value": rec["value"], "unit": "DoFs/s", "n_gpus": world, "steps": rec["requests"],
+            "warmup": rec["warm_requests"], "ms_per_step": 1e3 * rec["span_s"] / rec["requests"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG",
+            "data": "synthetic",
+            "config": {"workload": "serving_3d_q2_sphere_surface_requests", "tol": TOL,
+                       **{k: rec[k] for k in ("requests", "warm_requests", "rate_per_s", "unknowns_min",
+                                              "unknowns_median", "unknowns_max", "setup_workers",
+                                              "memory_budget_gb")}},
+            "latency_s": rec["latency_s"], "serial_fp64": rec["serial_fp64"],
+            "hierarchy_cache_hits": rec["hierarchy_cache_hits"], "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
 
 
-def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_ranks, rank, world):
+def batch_measure(torch, G, inputs, local, count, steps, warmup, serial_sample, barrier, max_over_ranks,
+                  sum_over_ranks):
     """Independent problems solved together (gmg_solve_batch): each step solves
-    every problem of the list once; the stream count is tuned in the warm-up."""
+    every problem of the list once; the stream count is tuned in the warm-up.
+    The same problems one at a time (FP32 V-cycle, graph mode) and a sample
+    with the plain FP64 V-cycle are timed beside it.  Returns (record,
+    clocks)."""
     from concurrent.futures import ThreadPoolExecutor
-    ws = inputs.batched_problems(args.batch_count)
+    ws = inputs.batched_problems(count)
     stream = torch.cuda.current_stream()
     ctx = G.Context(local, stream.cuda_stream)
     t0 = time.perf_counter()
@@ -251,7 +329,9 @@ def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_r
           for m, w in zip(meshes, ws)]
     t_setup = time.perf_counter() - t0
     ns = [h.n for h in hs]
-    bs = [torch.tensor(inputs.random_rhs(w.seed, n), dtype=torch.float64, device="cuda") for w, n in zip(ws, ns)]
+    bs = [torch.empty(n, dtype=torch.float64, device="cuda") for n in ns]
+    for h, b, w in zip(hs, bs, ws):
+        h.assemble_rhs(b, "random", w.seed)
     xs = [torch.zeros_like(b) for b in bs]
     # warm-up, and pick the stream count (a one-parameter autotune)
     best = None
@@ -265,7 +345,7 @@ def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_r
         if best is None or dt < best[1]:
             best = (nst, dt)
     nst = best[0]
-    for _ in range(max(0, args.warmup - 1)):
+    for _ in range(max(0, warmup - 1)):
         G.solve_batch(hs, bs, xs, tol=TOL, n_streams=nst)
     sampler = ClockSampler(local)
     sampler.start()
@@ -274,7 +354,7 @@ def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_r
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         stats, status = G.solve_batch(hs, bs, xs, tol=TOL, n_streams=nst)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -282,7 +362,7 @@ def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_r
     clocks = sampler.stop()
     secs = max_over_ranks(e0.elapsed_time(e1) / 1e3)
     launches = int(sum(sum(v["launches"] for v in h.profile_read().values()) for h in hs))
-    total = sum_over_ranks(float(sum(ns)) * args.steps)
+    total = sum_over_ranks(float(sum(ns)) * steps)
     value = total / secs
     its = [s.iterations for s in stats]
     # the same problems one at a time (graph mode, FP32 V-cycle), and a sample
@@ -293,7 +373,7 @@ def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_r
         h.solve(b, x, tol=TOL)
     torch.cuda.synchronize()
     serial32 = float(sum(ns)) / (time.perf_counter() - a)
-    k = min(args.serial_sample, len(ws))
+    k = min(serial_sample, len(ws))
     h64 = [G.Hierarchy(ctx, meshes[i], ws[i].degree, ws[i].coeff, cheb_degree=ws[i].cheb_degree,
                        vcycle_prec=G.PREC_FP64) for i in range(k)]
     x64 = [torch.zeros_like(bs[i]) for i in range(k)]
@@ -306,24 +386,39 @@ def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_r
     torch.cuda.synchronize()
     serial64 = float(sum(ns[:k])) / (time.perf_counter() - a)
     diff = max(float(torch.linalg.vector_norm(xs[i] - x64[i]) / torch.linalg.vector_norm(x64[i])) for i in range(k))
+    for h in h64:
+        h.close()
+    dims = [w.coarse.dim for w in ws]
+    rec = {"value": value, "unit": "DoFs/s", "steps": steps, "ms_per_step": 1e3 * secs / steps,
+           "workload": f"batched_{len(ws)}_poisson_2d3d_q1q2_random_rounds",
+           "problems": len(ws), "unknowns_total": int(sum(ns)), "unknowns_min": int(min(ns)),
+           "unknowns_median": int(np.median(ns)), "unknowns_max": int(max(ns)),
+           "problems_3d": int(sum(1 for d in dims if d == 3)),
+           "cg_iterations_min_max": [int(min(its)), int(max(its))], "n_streams": nst,
+           "setup_s": {"mesh": round(t_mesh, 2), "hierarchies": round(t_setup, 2)},
+           "gpu_launches": launches,
+           "serial_fp32_graph": {"value": serial32, "unit": "DoFs/s"},
+           "serial_fp64": {"value": serial64, "unit": "DoFs/s", "sample": f"first {k} problems",
+                           "max_rel_diff_vs_batched": diff}}
+    for h in hs:
+        h.close()
+    return rec, clocks
+
+
+def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_ranks, rank, world):
+    rec, clocks = batch_measure(torch, G, inputs, local, args.batch_count, args.steps, args.warmup,
+                                args.serial_sample, barrier, max_over_ranks, sum_over_ranks)
     if rank == 0:
-        dims = [w.coarse.dim for w in ws]
         line = {
-            "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": rec["value"], "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG", "data": "synthetic",
-            "config": {"workload": f"batched_{len(ws)}_poisson_2d3d_q1q2_random_rounds",
-                       "problems": len(ws), "unknowns_total": int(sum(ns)), "unknowns_min": int(min(ns)),
-                       "unknowns_median": int(np.median(ns)), "unknowns_max": int(max(ns)),
-                       "problems_3d": int(sum(1 for d in dims if d == 3)),
-                       "cg_iterations_min_max": [int(min(its)), int(max(its))], "tol": TOL,
-                       "n_streams": nst, "parallelism": f"replicas x{world}",
-                       "setup_s": {"mesh": round(t_mesh, 2), "hierarchies": round(t_setup, 2)}},
-            "gpu_launches": launches,
-            "serial_fp32_graph": {"value": serial32, "unit": "DoFs/s"},
-            "serial_fp64": {"value": serial64, "unit": "DoFs/s", "sample": f"first {k} problems",
-                            "max_rel_diff_vs_batched": diff},
-            "clocks": clocks,
+            "config": {"tol": TOL, "parallelism": f"replicas x{world}",
+                       **{k: rec[k] for k in ("workload", "problems", "unknowns_total", "unknowns_min",
+                                              "unknowns_median", "unknowns_max", "problems_3d",
+                                              "cg_iterations_min_max", "n_streams", "setup_s")}},
+            "gpu_launches": rec["gpu_launches"], "serial_fp32_graph": rec["serial_fp32_graph"],
+            "serial_fp64": rec["serial_fp64"], "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
 
@@ -349,6 +444,14 @@ def main():
     ap.add_argument("--serial-sample", type=int, default=64,
                     help="batch workload: problems timed one by one with plain FP64 V-cycles")
     ap.add_argument("--finest-level", type=int, default=9, help="checker workload: finest level")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="sphere workload: skip the batched sub-record")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="sphere workload: skip the serving sub-record")
+    ap.add_argument("--sub-requests", type=int, default=60,
+                    help="sphere workload: measured requests of the serving sub-record")
+    ap.add_argument("--sub-warm-requests", type=int, default=10,
+                    help="sphere workload: requests before them")
     ap.add_argument("--solve-mode", default="graph", choices=["graph", "stream"],
                     help="graph: each solve is one CUDA-graph launch; stream: one launch per kernel")
     args = ap.parse_args()
@@ -409,10 +512,7 @@ def main():
     info = H.info
     n = H.n
     b = torch.empty(n, dtype=torch.float64, device="cuda")
-    if w.rhs == "sine":
-        H.assemble_rhs(b)
-    else:  # seeded U[-1, 1) per unknown in canonical order
-        b.copy_(torch.from_numpy(inputs.random_rhs(w.seed, n)))
+    H.assemble_rhs(b, w.rhs, w.seed)  # manufactured, or seeded U[-1, 1) per unknown
     x = torch.zeros_like(b)
     for _ in range(args.warmup):
         H.solve(b, x, tol=TOL)
@@ -509,6 +609,18 @@ def main():
                 "rel_diff_fp32_vs_fp64_solution": diff}
         H64.close()
 
+    # ---- the batched and served workloads, measured in the same run (one
+    # process; replicas run the headline only)
+    batch = serve_rec = None
+    if world == 1 and not args.no_batch:
+        H.close()
+        rec, bclocks = batch_measure(torch, G, inputs, local, args.batch_count, 2, 2, args.serial_sample,
+                                     barrier, max_over_ranks, sum_over_ranks)
+        batch = dict(rec, clocks=bclocks)
+    if world == 1 and not args.no_serve:
+        rec, sclocks = serve_measure(torch, G, inputs, local, args.sub_requests, args.sub_warm_requests, args.rate)
+        serve_rec = dict(rec, clocks=sclocks)
+
     # ---- roofline of the dominant kernel (largest share of the timed region)
     pk = peaks()
     dom = max(kern, key=lambda k: kern[k]["ms"])
@@ -520,10 +632,10 @@ def main():
                 "peak_src": "nominal FP64 (152 SMs x 2 FP64 FMA/clk x 2070 MHz x 2)"}
     else:
         achieved = kd["bytes"] / (kd["ms"] / 1e3) / 1e9
-        traffic = TRAFFIC_PER_LAUNCH.get(dom) if args.workload == "sphere" and \
-            (args.global_ref, args.adaptive_ref) == (GLOBAL_REF, ADAPTIVE_REF) else None
+        # DRAM traffic needs a profiler, which this timed run does not use:
+        # the measured per-launch traffic of the same kernels is in profiles/
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                "frac": achieved / pk["hbm_gbs"], "traffic": None,
                 "algorithmic_bytes_per_launch": kd["bytes"] / max(kd["launches"], 1), "peak_src": pk["src"]}
     t_all = sum(v["ms"] for v in kern.values())
     kernels = {}
@@ -537,8 +649,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, secs_cpu, ncpu = cpu_baseline()
-        cpu = {"value": v, "unit": "DoFs/s", "cores": 1, "kind": "oracle", "sample": desc}
+        v, desc, ncores = cpu_baseline()
+        cpu = {"value": v, "unit": "DoFs/s", "cores": ncores, "kind": "oracle", "sample": desc}
 
     if rank == 0:
         line = {
@@ -563,6 +675,8 @@ def main():
             "kernel_timing": {"mode": "stream (one launch per kernel, CUDA events per launch)",
                               "ms_per_step": stream_ms, "steps": args.steps},
             "fp64_vcycle": fp64,
+            "batch": batch,
+            "serve": serve_rec,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

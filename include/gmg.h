@@ -272,11 +272,20 @@ gmg_status gmg_hier_export(const gmg_hier* h, int what, int level, void* buf, ui
 
 /* ------------------------------------------------------------ solve path */
 
-/* Right-hand side b = C^T (int f phi_i) over the leaf cells with the
- * (k+1)^d-point Gauss-Legendre rule, for f = d pi^2 prod sin(pi x_i)
- * (manufactured u = prod sin(pi x_i) on [0,1]^d).  kind must be 0.
- * d_b: device pointer, n_unknowns FP64, overwritten. */
-gmg_status gmg_assemble_rhs(gmg_hier* h, int kind, double* d_b);
+/* Right-hand sides (gmg_assemble_rhs kind). */
+#define GMG_RHS_SINE 0   /* b = C^T (int f phi_i) over the leaf cells with the (k+1)^d-point
+                            Gauss-Legendre rule, f = d pi^2 prod sin(pi x_i): the manufactured
+                            solution u = prod sin(pi x_i) on [0,1]^d (seed unused) */
+#define GMG_RHS_RANDOM 1 /* b_i uniform in [-1, 1) per unknown i in canonical order: with the
+                            SplitMix64 output function s (Steele, Lea, Flood, OOPSLA 2014),
+                            b_i = 2 (s(seed xor (i * 0xD1B54A32D192ED03)) >> 11) 2^-53 - 1
+                            (64-bit wrapping arithmetic); the random right-hand sides of the
+                            variable-coefficient, batched and served workloads */
+
+/* Right-hand side of kind GMG_RHS_SINE or GMG_RHS_RANDOM (with `seed`).
+ * d_b: device pointer, n_unknowns FP64, overwritten.  GMG_EINVAL for another
+ * kind. */
+gmg_status gmg_assemble_rhs(gmg_hier* h, int kind, uint64_t seed, double* d_b);
 
 /* y = A x with the leaf-mesh operator A = C^T A_leaf C (hanging nodes
  * eliminated, Dirichlet rows removed).  d_x, d_y: device, n_unknowns FP64;

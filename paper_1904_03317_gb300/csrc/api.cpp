@@ -447,12 +447,13 @@ gmg_status gmg_hier_export(const gmg_hier* hh, int what, int level, void* buf, u
   return GMG_OK;
 }
 
-gmg_status gmg_assemble_rhs(gmg_hier* hh, int kind, double* d_b) {
+gmg_status gmg_assemble_rhs(gmg_hier* hh, int kind, uint64_t seed, double* d_b) {
   CHECK_ARG(hh && d_b, "null argument");
+  CHECK_ARG(kind == GMG_RHS_SINE || kind == GMG_RHS_RANDOM, "unknown right-hand side kind");
   GMG_GUARD_BEGIN
   gmg_status st = bind_device(hh->h);
   if (st != GMG_OK) return st;
-  return device_rhs(hh->h, kind, d_b);
+  return device_rhs(hh->h, kind, seed, d_b);
   GMG_GUARD_END
 }
 

@@ -847,9 +847,13 @@ gmg_status device_apply(Hier& h, const double* x, double* y) {
   return to_canonical(d, d->Ap, y, d->stream);
 }
 
-gmg_status device_rhs(Hier& h, int kind, double* b) {
+gmg_status device_rhs(Hier& h, int kind, uint64_t seed, double* b) {
   DeviceState* d = h.dev;
-  if (kind != 0) {
+  if (kind == GMG_RHS_RANDOM) {  // a function of the canonical index: written in place
+    GMG_CUDA_TRY(launch_rhs_random(d->n_unknowns, seed, b, d->stream));
+    return GMG_OK;
+  }
+  if (kind != GMG_RHS_SINE) {
     set_error("gmg_assemble_rhs: unknown kind");
     return GMG_EINVAL;
   }

@@ -273,6 +273,8 @@ cudaError_t launch_active_apply(int dim, int k, const ActiveArgs& a, const doubl
                                 cudaStream_t s);
 cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* cell_coords,
                             double* b, cudaStream_t s);
+// b_i = U[-1, 1) from SplitMix64 keyed by (seed, canonical index i)
+cudaError_t launch_rhs_random(int64_t n, uint64_t seed, double* b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_to_mg(int64_t n, const double* r, const uint32_t* home, T* g,
                               cudaStream_t s);

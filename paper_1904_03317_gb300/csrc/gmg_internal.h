@@ -264,7 +264,7 @@ gmg_status device_apply(Hier& h, const double* x, double* y);
 gmg_status device_vcycle(Hier& h, const double* r, double* z);
 gmg_status device_solve(Hier& h, const double* b, double* x, double tol, int max_iter,
                         int fixed_iterations, gmg_stats* st);
-gmg_status device_rhs(Hier& h, int kind, double* b);
+gmg_status device_rhs(Hier& h, int kind, uint64_t seed, double* b);
 gmg_status device_solve_async(Hier& h, const double* b, double* x, double tol, int max_iter);
 gmg_status device_solve_poll(Hier& h, int wait, int* ready, gmg_stats* st, gmg_status* status);
 gmg_status device_solve_batch(Hier* const* hs, const double* const* b, double* const* x, int n, double tol,

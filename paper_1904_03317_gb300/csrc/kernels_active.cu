@@ -900,6 +900,33 @@ cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* 
   return cudaGetLastError();
 }
 
+// Seeded uniform right-hand side: the SplitMix64 output function (Steele,
+// Lea, Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014)
+// applied to seed xor (i * 0xD1B54A32D192ED03) for canonical index i; its
+// top 53 bits give u in [0, 1), and b_i = 2 u - 1.
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void __launch_bounds__(256) rhs_random_kernel(int64_t n, uint64_t seed, double* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t bits = splitmix64_out(seed ^ ((uint64_t)i * 0xD1B54A32D192ED03ull)) >> 11;
+    const double u = (double)bits * (1.0 / 9007199254740992.0);
+    b[i] = __dsub_rn(__dmul_rn(2.0, u), 1.0);
+  }
+}
+
+cudaError_t launch_rhs_random(int64_t n, uint64_t seed, double* b, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t g = (n + 255) / 256;
+  rhs_random_kernel<<<(unsigned)(g > 152 * 64 ? 152 * 64 : g), 256, 0, s>>>(n, seed, b);
+  GMG_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ copy maps
 template <typename T>
 __global__ void copy_to_mg_kernel(int64_t n, const double* __restrict__ r, const uint32_t* __restrict__ home,

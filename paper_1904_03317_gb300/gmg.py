@@ -24,6 +24,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ENAN, ETIMEOUT, EUNSUPPORTED = 
 PREC_FP64, PREC_FP32 = 0, 1
 SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI = 0, 1
 COARSE_CHOLESKY, COARSE_CHEBYSHEV, COARSE_CG = 0, 1, 2
+RHS_SINE, RHS_RANDOM = 0, 1
 EXPORT_UNKNOWN_KEYS, EXPORT_HOME_LEVEL, EXPORT_HANGING, EXPORT_LEVEL_KEYS, EXPORT_LEVEL_CLASS, \
     EXPORT_HOME_SLOT = range(6)
 
@@ -132,7 +133,7 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
         "gmg_hier_destroy": [vp],
         "gmg_hier_info": [vp, C.POINTER(InfoC)],
         "gmg_hier_export": [vp, i32, i32, vp, C.POINTER(u64)],
-        "gmg_assemble_rhs": [vp, i32, vp],
+        "gmg_assemble_rhs": [vp, i32, u64, vp],
         "gmg_apply": [vp, vp, vp],
         "gmg_vcycle": [vp, vp, vp],
         "gmg_solve": [vp, vp, vp, C.c_double, i32, i32, C.POINTER(StatsC)],
@@ -319,8 +320,12 @@ class Hierarchy:
         return out
 
     # ---- solve path (device FP64 active vectors)
-    def assemble_rhs(self, b) -> None:
-        _check(load_library().gmg_assemble_rhs(self.handle, 0, _ptr(b)), "gmg_assemble_rhs")
+    def assemble_rhs(self, b, kind: str = "sine", seed: int = 0) -> None:
+        """gmg_assemble_rhs: kind "sine" (manufactured solution) or "random"
+        (U[-1, 1) per unknown from `seed`, as inputs.random_rhs)."""
+        k = {"sine": RHS_SINE, "random": RHS_RANDOM}[kind]
+        _check(load_library().gmg_assemble_rhs(self.handle, k, C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _ptr(b)),
+               "gmg_assemble_rhs")
 
     def apply(self, x, y) -> None:
         _check(load_library().gmg_apply(self.handle, _ptr(x), _ptr(y)), "gmg_apply")

@@ -1,11 +1,13 @@
 """Batched solves (gmg_solve_batch): each problem's result in the batch equals
-its result alone; a failing problem does not disturb the others."""
+its result alone and, for the problems the oracle can solve, the oracle's; a
+failing problem does not disturb the others."""
 import numpy as np
 import pytest
 
+from oracle import gmg as ogmg
 from paper_1904_03317_gb300 import gmg as G
 from paper_1904_03317_gb300 import inputs
-from tests.helpers import small_workloads
+from tests.helpers import oracle_hierarchy, small_workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +34,8 @@ def _setup(torch, prec):
     for w in _problems():
         m = G.build_mesh(w)
         H = G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=prec)
-        b = torch.tensor(inputs.random_rhs(w.seed + 11, H.n), dtype=torch.float64, device="cuda")
+        b = torch.empty(H.n, dtype=torch.float64, device="cuda")
+        H.assemble_rhs(b, "random", w.seed + 11)
         out.append((H, m, b))
     return ctx, out
 
@@ -53,6 +56,16 @@ def test_batch_equals_alone(torch, prec):
         assert abs(st.iterations - its) <= (0 if prec == G.PREC_FP64 else 1)
         if st.iterations == its:
             assert float(torch.linalg.vector_norm(xb - xa) / torch.linalg.vector_norm(xa)) <= tol
+    # the problems of the parity set against the FP64 oracle
+    if prec == G.PREC_FP64:
+        for name, (st, rc, xb) in zip(small_workloads(), zip(stats, status, xs)):
+            w = small_workloads()[name]
+            O = oracle_hierarchy(name)
+            ref = ogmg.solve(O, inputs.random_rhs(w.seed + 11, O.disc.n), 1e-8)
+            assert abs(ref.iterations - st.iterations) <= 1
+            if ref.iterations == st.iterations:
+                xh = xb.cpu().numpy()
+                assert np.abs(xh - ref.x).max() <= 1e-10 * np.abs(ref.x).max(), name
     # a second batch reuses the graphs and gives the same answers
     xs2 = [torch.zeros_like(b) for _, _, b in probs]
     stats2, status2 = G.solve_batch([H for H, _, _ in probs], [b for _, _, b in probs], xs2, tol=1e-8, n_streams=3)

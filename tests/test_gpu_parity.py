@@ -303,6 +303,31 @@ def test_rhs_sine(torch, name):
     assert rel_err(host(b), O.disc.rhs_sine()) < 1e-12
 
 
+@pytest.mark.parametrize("seed", [0, 20190403, 2**64 - 1])
+def test_rhs_random_equals_seeded_generator(torch, seed):
+    """gmg_assemble_rhs(GMG_RHS_RANDOM, seed) is the seeded U[-1, 1) input of
+    the variable-coefficient, batched and served workloads: the same counter
+    generator as inputs.random_rhs, so the two agree bit for bit, in the
+    canonical order, for every unknown (a ragged last block included)."""
+    from paper_1904_03317_gb300 import inputs
+    O, H = gpu_hier(torch, "3d_q2_checker")
+    n = O.disc.n
+    b = torch.full((n,), 7.0, dtype=torch.float64, device="cuda")
+    H.assemble_rhs(b, "random", seed)
+    torch.cuda.synchronize()
+    want = inputs.random_rhs(seed, n)
+    assert np.array_equal(host(b), want)
+    assert want.min() >= -1.0 and want.max() < 1.0 and n % 256 != 0
+
+
+def test_rhs_rejects_unknown_kind(torch):
+    O, H = gpu_hier(torch, "2d_q1_circle")
+    b = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(G.GmgError) as e:
+        G._check(G.load_library().gmg_assemble_rhs(H.handle, 7, 0, G._ptr(b)), "gmg_assemble_rhs")
+    assert e.value.status == G.EINVAL
+
+
 def _rhs(O, w):
     from paper_1904_03317_gb300 import inputs
     return O.disc.rhs_sine() if w.rhs == "sine" else inputs.random_rhs(w.seed, O.disc.n)

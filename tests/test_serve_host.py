@@ -21,19 +21,20 @@ class _FakeTorch:
 
 
 class _Info:
-    device_bytes = 1000
+    def __init__(self, device_bytes):
+        self.device_bytes = device_bytes
 
 
 class _FakeHier:
     """A solve that becomes ready `solve_s` seconds after it was enqueued."""
 
-    def __init__(self, n, solve_s, log, rid):
-        self.n, self.info, self.solve_s, self.log, self.rid = n, _Info(), solve_s, log, rid
+    def __init__(self, n, device_bytes, solve_s, log, key):
+        self.n, self.info, self.solve_s, self.log, self.key = n, _Info(device_bytes), solve_s, log, key
         self.t_ready = None
 
     def solve_async(self, b, x, tol):
         self.t_ready = time.perf_counter() + self.solve_s
-        self.log.append(("enqueue", self.rid, time.perf_counter()))
+        self.log.append(("enqueue", self.key, time.perf_counter()))
 
     def solve_poll(self, wait):
         ready = time.perf_counter() >= self.t_ready
@@ -42,27 +43,49 @@ class _FakeHier:
         return ready, st, G.OK
 
     def close(self):
-        self.log.append(("close", self.rid, time.perf_counter()))
+        self.log.append(("close", self.key, time.perf_counter()))
+
+
+def _rid(w):
+    return int(w.name.split("_")[0][len("request"):])
 
 
 class _FakeServer(serve.Server):
-    def __init__(self, setup_s=0.01, solve_s=0.02, **kw):
+    """The real scheduling with the setup phases replaced: request i has
+    1000 + i leaves and its hierarchy `bytes_per_leaf` device bytes per leaf;
+    requests with the same name have the same mesh."""
+
+    def __init__(self, setup_s=0.01, solve_s=0.02, bytes_per_leaf=100.0, **kw):
         super().__init__(_FakeTorch, mem_budget=kw.pop("mem_budget", 1e30), **kw)
-        self.setup_s, self.solve_s = setup_s, solve_s
+        self.setup_s, self.solve_s, self.bpl = setup_s, solve_s, bytes_per_leaf
         self.log = []
         self.live_setups = 0
         self.max_live_setups = 0
+        self.builds = 0
         self.lock = threading.Lock()
 
-    def _setup(self, req_id, w, stream, t0):
+    def _busy(self, dt):
         with self.lock:
             self.live_setups += 1
             self.max_live_setups = max(self.max_live_setups, self.live_setups)
-        time.sleep(self.setup_s)
+        time.sleep(dt)
         with self.lock:
             self.live_setups -= 1
-        h = _FakeHier(1000 + req_id, self.solve_s, self.log, req_id)
-        return None, None, h, None, None, time.perf_counter() - t0
+
+    def _mesh(self, w, t0):
+        self._busy(self.setup_s / 2)
+        return None, 1000 + _rid(w), w.name.encode(), time.perf_counter() - t0
+
+    def _hierarchy(self, w, m, stream, t0):
+        self._busy(self.setup_s / 2)
+        with self.lock:
+            self.builds += 1
+        leaves = 1000 + _rid(w)
+        return None, _FakeHier(leaves, self.bpl * leaves - 16.0 * leaves, self.solve_s, self.log, w.name), \
+            time.perf_counter() - t0
+
+    def _vectors(self, w, h, stream):
+        return None, None
 
 
 def _requests(n, rate):
@@ -76,10 +99,10 @@ def test_every_request_served_once_after_its_arrival():
     assert [r.rid for r in res] == list(range(12))
     for r, a in zip(res, arrivals):
         assert r.status == G.OK and r.converged and r.iterations == 7 and r.n == 1000 + r.rid
-        assert a - 1e-9 <= r.admitted <= r.setup_done <= r.ready
+        assert a - 1e-9 <= r.admitted <= r.meshed <= r.hier_start <= r.setup_done <= r.ready
     closes = [e[1] for e in srv.log if e[0] == "close"]
-    assert sorted(closes) == list(range(12))  # every hierarchy released exactly once
-    assert srv.max_live_setups <= 3
+    assert sorted(closes) == sorted(w.name for w in ws)  # every hierarchy released exactly once
+    assert srv.max_live_setups <= 3 and srv.builds == 12 and srv.cache_hits == 0
 
 
 def test_admission_in_arrival_order():
@@ -101,11 +124,45 @@ def test_stream_slots_bound_requests_in_the_system():
         assert in_system <= 2
 
 
-def test_memory_budget_serialises_admissions():
+def test_memory_budget_serialises_hierarchies():
+    """A budget below any two hierarchies: once the first hierarchy has been
+    measured, the next one is built only after the previous result (and its
+    cached hierarchy, evicted to make room) has freed the memory."""
     arrivals, ws = _requests(6, rate=1e6)
-    smallest = serve.BYTES_PER_UNKNOWN * 8 * min(serve.Server._leaves_estimate(w) for w in ws)
-    srv = _FakeServer(setup_workers=4, max_live=8, mem_budget=1.5 * smallest, setup_s=0.002, solve_s=0.01)
+    srv = _FakeServer(setup_workers=4, max_live=8, mem_budget=1.5 * 100.0 * 1000, setup_s=0.002, solve_s=0.01)
+    srv.bytes_per_leaf = 100.0  # the initial prediction equals the measured size here
     res = srv.run(arrivals, ws)
-    spans = sorted((r.admitted, r.ready) for r in res)
+    assert all(r.status == G.OK for r in res)
+    spans = sorted((r.hier_start, r.ready) for r in res)
     for (a0, e0), (a1, e1) in zip(spans, spans[1:]):
         assert a1 >= e0 - 1e-6
+
+
+def test_prediction_learns_from_measured_hierarchies():
+    """The first hierarchies are admitted with the initial bytes-per-leaf
+    guess; after a measurement the prediction is the measured ratio (with
+    margin), so a budget that fits two measured hierarchies runs two at once."""
+    arrivals, ws = _requests(8, rate=1e6)
+    srv = _FakeServer(setup_workers=4, max_live=8, bytes_per_leaf=300.0, mem_budget=2.2 * 300.0 * 1010,
+                      setup_s=0.004, solve_s=0.03)
+    res = srv.run(arrivals, ws)
+    assert all(r.status == G.OK for r in res)
+    assert abs(srv.bytes_per_leaf - 1.05 * 300.0) < 1e-9
+    spans = sorted((r.hier_start, r.ready) for r in res)
+    most = max(sum(1 for a, e in spans if a <= t + 1e-9 and e > t + 1e-9) for t, _ in spans)
+    assert most == 2
+
+
+def test_identical_meshes_reuse_the_cached_hierarchy():
+    """Requests whose meshes are identical (same key) after the first one has
+    finished take its idle hierarchy from the cache: no second build, and the
+    hierarchy is released once at the end."""
+    arrivals, ws = _requests(3, rate=1e6)
+    ws = [ws[0]] * 3
+    arrivals = np.array([0.0, 0.2, 0.4])
+    srv = _FakeServer(setup_workers=2, max_live=4, setup_s=0.004, solve_s=0.01)
+    res = srv.run(arrivals, ws)
+    assert all(r.status == G.OK for r in res)
+    assert srv.builds == 1 and srv.cache_hits == 2
+    assert [r.cache_hit for r in res] == [False, True, True]
+    assert sum(1 for e in srv.log if e[0] == "close") == 1
