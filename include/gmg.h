@@ -59,12 +59,18 @@ typedef struct gmg_hier gmg_hier;
 
 /* Coarse mesh: the brick [lo, hi] split into n0[0] x n0[1] (x n0[2]) equal
  * cells (Sec. 2.2: the coarse mesh T_0).  dim is 2 or 3; for dim 2 the third
- * entries are ignored. */
+ * entries are ignored.  present: NULL, or one byte per coarse cell in
+ * lexicographic order (x fastest), nonzero if the cell belongs to the
+ * domain; the domain is the union of the present cells (for instance the
+ * Fichera corner of Sec. 4.3, a brick with one octant removed), u = 0 on its
+ * whole boundary.  The array is copied when the mesh is created; at least one
+ * cell must be present. */
 typedef struct gmg_coarse_mesh {
   int dim;
   int n0[3];
   double lo[3];
   double hi[3];
+  const uint8_t* present;
 } gmg_coarse_mesh;
 
 typedef enum gmg_precision { GMG_PREC_FP64 = 0, GMG_PREC_FP32 = 1 } gmg_precision;
@@ -165,7 +171,7 @@ void gmg_destroy(gmg_ctx* ctx);
 /* Message of the last failing call on this thread ("" if none). */
 const char* gmg_last_error(void);
 /* *has_sm103a = 1 if the library was compiled with device code for sm_103a;
- * *version = ABI version (1). */
+ * *version = ABI version (2: gmg_coarse_mesh.present, the seed of gmg_assemble_rhs). */
 gmg_status gmg_build_info(int* has_sm103a, int* version);
 
 /* ------------------------------------------------------------------- mesh */
@@ -276,13 +282,15 @@ gmg_status gmg_hier_export(const gmg_hier* h, int what, int level, void* buf, ui
 #define GMG_RHS_SINE 0   /* b = C^T (int f phi_i) over the leaf cells with the (k+1)^d-point
                             Gauss-Legendre rule, f = d pi^2 prod sin(pi x_i): the manufactured
                             solution u = prod sin(pi x_i) on [0,1]^d (seed unused) */
+#define GMG_RHS_ONE 2    /* b = C^T (int f phi_i) with f = 1, the same quadrature as
+                            GMG_RHS_SINE (the Laplace example of Sec. 4.3; seed unused) */
 #define GMG_RHS_RANDOM 1 /* b_i uniform in [-1, 1) per unknown i in canonical order: with the
                             SplitMix64 output function s (Steele, Lea, Flood, OOPSLA 2014),
                             b_i = 2 (s(seed xor (i * 0xD1B54A32D192ED03)) >> 11) 2^-53 - 1
                             (64-bit wrapping arithmetic); the random right-hand sides of the
                             variable-coefficient, batched and served workloads */
 
-/* Right-hand side of kind GMG_RHS_SINE or GMG_RHS_RANDOM (with `seed`).
+/* Right-hand side of kind GMG_RHS_SINE, GMG_RHS_ONE or GMG_RHS_RANDOM (with `seed`).
  * d_b: device pointer, n_unknowns FP64, overwritten.  GMG_EINVAL for another
  * kind. */
 gmg_status gmg_assemble_rhs(gmg_hier* h, int kind, uint64_t seed, double* d_b);

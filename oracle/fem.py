@@ -208,11 +208,35 @@ class Discretization:
                          for d in range(3)], dtype=np.int64)
 
     def is_dirichlet(self, keys) -> np.ndarray:
+        """Nodes on the boundary of the domain (the union of the present
+        coarse cells): some coarse cell whose closure contains the node lies
+        outside the brick or is absent."""
         q = unpack_keys(keys)
-        ext = self.node_extent()
+        s0 = self.k << self.L  # node-lattice units per coarse cell
+        f = self.forest
+        sides = []
+        for d in range(3):
+            if d >= self.dim:
+                sides.append([np.zeros(q.shape[:-1], dtype=np.int64)])
+                continue
+            up = q[..., d] // s0
+            low = np.where(q[..., d] % s0 == 0, up - 1, up)
+            sides.append([low, up])
         on = np.zeros(q.shape[:-1], dtype=bool)
-        for d in range(self.dim):
-            on |= (q[..., d] == 0) | (q[..., d] == ext[d])
+        for cz in sides[2]:
+            for cy in sides[1]:
+                for cx in sides[0]:
+                    c = (cx, cy, cz)
+                    inb = np.ones(q.shape[:-1], dtype=bool)
+                    for d in range(self.dim):
+                        inb &= (c[d] >= 0) & (c[d] < self.n0[d])
+                    ok = inb.copy()
+                    if f.present is not None:
+                        pres = np.asarray(f.present, dtype=bool)
+                        idx = np.where(inb, np.clip(cx, 0, self.n0[0] - 1) + self.n0[0] * (
+                            np.clip(cy, 0, self.n0[1] - 1) + self.n0[1] * np.clip(cz, 0, self.n0[2] - 1)), 0)
+                        ok &= pres[idx]
+                    on |= ~ok
         return on
 
     def node_positions(self, keys) -> np.ndarray:
@@ -228,11 +252,9 @@ class Discretization:
             if d >= self.dim:
                 cand.append([0])
                 continue
-            ext = self.n0[d] << level
             c = int(q[d]) // s
-            opts = [c - 1, c] if int(q[d]) % s == 0 else [c]
-            cand.append([x for x in opts if 0 <= x < ext])
-        return list(itertools.product(*cand))
+            cand.append([c - 1, c] if int(q[d]) % s == 0 else [c])
+        return [c for c in itertools.product(*cand) if self.forest.inside(level, c)]
 
     def is_node_of(self, level: int, c, key: int) -> bool:
         q = unpack_keys(key)
@@ -346,7 +368,13 @@ class Discretization:
     def rhs_sine(self) -> np.ndarray:
         """b = C^T b_full, b_full_i = sum_K int_K f phi_i with (k+1)^d Gauss-Legendre
         points per cell (the paper does not fix the rule; this is the reading)."""
-        f = sine_rhs_function(self.dim)
+        return self._rhs(sine_rhs_function(self.dim))
+
+    def rhs_one(self) -> np.ndarray:
+        """The same for f = 1 (the Laplace example of Sec. 4.3)."""
+        return self._rhs(lambda x: np.ones(len(x)))
+
+    def _rhs(self, f) -> np.ndarray:
         nodes = gauss_lobatto_points(self.k)
         xq, wq = gauss_legendre(self.k + 1)
         V = lagrange_values(nodes, xq)

@@ -360,7 +360,12 @@ def solve(H: Hierarchy, b: np.ndarray, tol: float = 1e-8, max_iter: int = 1000,
 
 
 def setup(workload, cheb_degree: Optional[int] = None, lambdas=None) -> Hierarchy:
-    """Forest, discretisation and hierarchy for an ``inputs.Workload``."""
+    """Forest, discretisation and hierarchy for an ``inputs.Workload``, with
+    the workload's smoother and coarse solver."""
     forest = build_forest(workload.coarse, workload.rounds)
     disc = Discretization(forest, workload.degree, workload.coeff)
-    return build_hierarchy(disc, cheb_degree or workload.cheb_degree, lambdas=lambdas)
+    H = build_hierarchy(disc, cheb_degree or workload.cheb_degree, lambdas=lambdas)
+    H.smoother = getattr(workload, "smoother", "chebyshev")
+    if getattr(workload, "coarse_solver", "cholesky") != "cholesky":
+        setup_coarse(H, workload.coarse_solver)
+    return H

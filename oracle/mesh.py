@@ -28,7 +28,12 @@ class Forest:
         self.cm = coarse
         self.dim = coarse.dim
         self.n0 = [int(coarse.n0[d]) if d < self.dim else 1 for d in range(3)]
-        coarse_cells = set(itertools.product(range(self.n0[0]), range(self.n0[1]), range(self.n0[2])))
+        # the domain is the union of the present coarse cells (all of the brick
+        # unless the coarse mesh lists some as absent)
+        self.present = None if getattr(coarse, "present", None) is None else \
+            [bool(v) for v in coarse.present]
+        coarse_cells = set(c for c in itertools.product(range(self.n0[0]), range(self.n0[1]), range(self.n0[2]))
+                           if self.coarse_present(c))
         # cells[l]: coordinates (x, y, z) of every existing cell of level l
         self.cells: List[Set[Cell]] = [coarse_cells]
         # refined[l]: existing cells of level l that have children
@@ -38,9 +43,16 @@ class Forest:
     def extent(self, level: int) -> List[int]:
         return [self.n0[d] << level if d < self.dim else 1 for d in range(3)]
 
+    def coarse_present(self, c: Cell) -> bool:
+        return self.present is None or self.present[c[0] + self.n0[0] * (c[1] + self.n0[1] * c[2])]
+
     def inside(self, level: int, c: Cell) -> bool:
+        """Whether lattice cell c of level l lies in the domain: inside the
+        brick and in a present coarse cell."""
         ext = self.extent(level)
-        return all(0 <= c[d] < ext[d] for d in range(3))
+        if not all(0 <= c[d] < ext[d] for d in range(3)):
+            return False
+        return self.coarse_present(tuple(c[d] >> level if d < self.dim else 0 for d in range(3)))
 
     def exists(self, level: int, c: Cell) -> bool:
         return level < len(self.cells) and c in self.cells[level]

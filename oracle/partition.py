@@ -26,8 +26,8 @@ from oracle.mesh import Forest
 
 
 def _dfs_leaves(f: Forest) -> List[Tuple[int, Tuple[int, int, int]]]:
-    """Leaves in depth-first order: coarse cells in lexicographic (z, y, x)
-    order, children in z-order (x bit first, then y, then z)."""
+    """Leaves in depth-first order: the domain's coarse cells in lexicographic
+    (z, y, x) order, children in z-order (x bit first, then y, then z)."""
     out = []
 
     def visit(level, c):
@@ -41,7 +41,8 @@ def _dfs_leaves(f: Forest) -> List[Tuple[int, Tuple[int, int, int]]]:
     for z in range(f.n0[2]):
         for y in range(f.n0[1]):
             for x in range(f.n0[0]):
-                visit(0, (x, y, z))
+                if f.exists(0, (x, y, z)):  # coarse cells of the domain only
+                    visit(0, (x, y, z))
     return out
 
 

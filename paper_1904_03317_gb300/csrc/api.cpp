@@ -67,7 +67,7 @@ gmg_status gmg_build_info(int* has_sm103a, int* version) {
 #else
   *has_sm103a = 0;
 #endif
-  *version = 1;
+  *version = 2;
   return GMG_OK;
 }
 
@@ -110,6 +110,12 @@ gmg_status gmg_mesh_create(const gmg_coarse_mesh* cm, gmg_mesh** out) {
     CHECK_ARG(cm->n0[d] >= 1 && cm->n0[d] <= 1024, "n0 out of range [1, 1024]");
     CHECK_ARG(std::isfinite(cm->lo[d]) && std::isfinite(cm->hi[d]) && cm->hi[d] > cm->lo[d],
               "need finite lo < hi");
+  }
+  if (cm->present) {
+    const int64_t nc = (int64_t)cm->n0[0] * cm->n0[1] * (cm->dim == 3 ? cm->n0[2] : 1);
+    bool any = false;
+    for (int64_t i = 0; i < nc && !any; ++i) any = cm->present[i] != 0;
+    CHECK_ARG(any, "at least one coarse cell must be present");
   }
   GMG_GUARD_BEGIN
   gmg_mesh* m = new gmg_mesh();
@@ -449,7 +455,7 @@ gmg_status gmg_hier_export(const gmg_hier* hh, int what, int level, void* buf, u
 
 gmg_status gmg_assemble_rhs(gmg_hier* hh, int kind, uint64_t seed, double* d_b) {
   CHECK_ARG(hh && d_b, "null argument");
-  CHECK_ARG(kind == GMG_RHS_SINE || kind == GMG_RHS_RANDOM, "unknown right-hand side kind");
+  CHECK_ARG(kind == GMG_RHS_SINE || kind == GMG_RHS_ONE || kind == GMG_RHS_RANDOM, "unknown right-hand side kind");
   GMG_GUARD_BEGIN
   gmg_status st = bind_device(hh->h);
   if (st != GMG_OK) return st;

@@ -277,7 +277,7 @@ void device_free(Hier& h) {
     cudaFree(L.list_jump);
     cudaFree(L.list_rest);
   }
-  void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_inv, d->coarse_ptr, d->coarse_col, d->coarse_val, d->cell_nodes, d->cell_coeff, d->cell_level,
+  void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_slot, d->coarse_inv, d->coarse_ptr, d->coarse_col, d->coarse_val, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->perm, d->r, d->p, d->Ap,
                   d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level,
                   d->pat_nodes, d->pat_coeff, d->pat_level, d->loose_nodes, d->loose_coeff, d->loose_level,
@@ -446,6 +446,7 @@ gmg_status device_setup(Hier& h) {
   }
   for (int dd = 0; dd < 3; ++dd) d->coarse_lat[dd] = h.coarse_lattice[dd];
   d->n_coarse = h.n_coarse;
+  GMG_TRY(upload(d, &d->coarse_slot, h.coarse_slots));
   GMG_TRY(upload(d, &d->coarse_inv, h.coarse_inverse));
   GMG_TRY(upload(d, &d->coarse_ptr, h.coarse_ptr));
   GMG_TRY(upload(d, &d->coarse_col, h.coarse_col));
@@ -618,9 +619,9 @@ template <typename T>
 static cudaError_t coarse(const Hier& h, const T* g0, T* u0, cudaStream_t s) {
   const DeviceState* d = h.dev;
   if (h.params.coarse_solver == GMG_COARSE_CG)
-    return launch_coarse_cg<T>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_ptr, d->coarse_col, d->coarse_val,
+    return launch_coarse_cg<T>(d->n_coarse, d->coarse_slot, d->coarse_ptr, d->coarse_col, d->coarse_val,
                                h.params.coarse_tol, g0, u0, s);
-  return launch_coarse_solve<T>(h.dim, d->n_coarse, h.coarse_lattice, d->coarse_inv, g0, u0, s);
+  return launch_coarse_solve<T>(d->n_coarse, d->coarse_slot, d->coarse_inv, g0, u0, s);
 }
 
 // ------------------------------------------------------------- smoothing
@@ -853,12 +854,12 @@ gmg_status device_rhs(Hier& h, int kind, uint64_t seed, double* b) {
     GMG_CUDA_TRY(launch_rhs_random(d->n_unknowns, seed, b, d->stream));
     return GMG_OK;
   }
-  if (kind != GMG_RHS_SINE) {
+  if (kind != GMG_RHS_SINE && kind != GMG_RHS_ONE) {
     set_error("gmg_assemble_rhs: unknown kind");
     return GMG_EINVAL;
   }
   GMG_CUDA_TRY(cudaMemsetAsync(d->r, 0, sizeof(double) * d->n_unknowns, d->stream));
-  GMG_CUDA_TRY(launch_rhs_sine(h.dim, h.k, active_args(h), d->cell_coords, d->r, d->stream));
+  GMG_CUDA_TRY(launch_rhs_sine(h.dim, h.k, active_args(h), d->cell_coords, d->r, kind == GMG_RHS_ONE, d->stream));
   return to_canonical(d, d->r, b, d->stream);
 }
 

@@ -143,6 +143,7 @@ struct DeviceState {
   void* g = nullptr;
   void* dinv = nullptr;
   // coarse level
+  int32_t* coarse_slot = nullptr;  // level-0 slot of each coarse unknown
   double* coarse_inv = nullptr;  // n_coarse^2
   int32_t* coarse_ptr = nullptr;  // CG coarse solver: A_0 in CSR
   int32_t* coarse_col = nullptr;
@@ -271,8 +272,9 @@ struct ActiveArgs {
 cudaError_t launch_active_apply(int dim, int k, const ActiveArgs& a, const double* x, double* y,
                                 double* partials, unsigned* counter, double* energy_out,
                                 cudaStream_t s);
+// b = C^T int f phi_i with f = d pi^2 prod sin(pi x_i), or f = 1 if `one`
 cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* cell_coords,
-                            double* b, cudaStream_t s);
+                            double* b, bool one, cudaStream_t s);
 // b_i = U[-1, 1) from SplitMix64 keyed by (seed, canonical index i)
 cudaError_t launch_rhs_random(int64_t n, uint64_t seed, double* b, cudaStream_t s);
 template <typename T>
@@ -282,11 +284,14 @@ template <typename T>
 cudaError_t launch_copy_from_mg(int64_t n, const T* u, const uint32_t* home, const double* r,
                                 double* z, double* partials, unsigned* counter, double* rz_out,
                                 cudaStream_t s);
+// Coarse solves on the coarse unknowns, which sit at the level-0 slots
+// `slot` (the interior nodes of the coarse lattice, or those of the present
+// coarse cells' union).
 template <typename T>
-cudaError_t launch_coarse_solve(int dim, int64_t n_coarse, const int64_t lat[3],
-                                const double* inv, const T* g0, T* u0, cudaStream_t s);
+cudaError_t launch_coarse_solve(int64_t n_coarse, const int32_t* slot, const double* inv, const T* g0, T* u0,
+                                cudaStream_t s);
 template <typename T>
-cudaError_t launch_coarse_cg(int dim, int64_t nc, const int64_t lat[3], const int32_t* ptr, const int32_t* col,
+cudaError_t launch_coarse_cg(int64_t nc, const int32_t* slot, const int32_t* ptr, const int32_t* col,
                              const double* val, double tol, const T* g0, T* u0, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, cudaStream_t s);

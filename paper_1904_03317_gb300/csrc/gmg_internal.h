@@ -101,6 +101,12 @@ struct Forest {
   int dim = 3;
   int n0[3] = {1, 1, 1};
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  // one byte per coarse cell (x fastest), nonzero if it belongs to the
+  // domain; empty: the whole brick
+  std::vector<uint8_t> present;
+  bool coarse_present(const int64_t* cc) const {
+    return present.empty() || present[cc[0] + (int64_t)n0[0] * (cc[1] + (int64_t)n0[1] * cc[2])] != 0;
+  }
   // per level: packed coords -> 1 if refined (has children), 0 if leaf
   std::vector<HashMap64> cells;
   // leaf list in canonical order, rebuilt after each refinement
@@ -223,6 +229,7 @@ struct Hier {
   // coarse level: lattice (k n0 + 1)^d; interior nodes are the unknowns of A_0
   int64_t coarse_lattice[3] = {1, 1, 1};
   int64_t n_coarse = 0;
+  std::vector<int32_t> coarse_slots;   // level-0 slot of each coarse unknown (in slot order)
   std::vector<double> coarse_inverse;  // n_coarse^2, row-major: A_0^-1, or the Chebyshev coarse operator
   // unpreconditioned CG coarse solver: A_0 in CSR
   std::vector<int32_t> coarse_ptr, coarse_col;

@@ -384,13 +384,40 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
   };
   int64_t node_ext[3];  // largest finest-lattice node coordinate per direction
   for (int d = 0; d < 3; ++d) node_ext[d] = d < dim ? (int64_t)h.n0[d] * k << L : 0;
+  // a node is on the boundary of the domain (the union of the present coarse
+  // cells) if some coarse cell whose closure contains it is outside the brick
+  // or absent
+  const int64_t s0 = (int64_t)k << L;  // node-lattice units per coarse cell
   auto key_is_boundary = [&](uint64_t key) {
     int64_t q[3];
     unpack3(key, q);
-    for (int d = 0; d < dim; ++d)
-      if (q[d] == 0 || q[d] == node_ext[d]) return true;
+    int64_t cand[3][2];
+    int nc[3];
+    for (int d = 0; d < 3; ++d) {
+      if (d >= dim) {
+        cand[d][0] = 0;
+        nc[d] = 1;
+        continue;
+      }
+      const int64_t up = q[d] / s0;
+      cand[d][0] = up;
+      nc[d] = 1;
+      if (q[d] % s0 == 0) {
+        cand[d][1] = up - 1;
+        nc[d] = 2;
+      }
+    }
+    for (int a = 0; a < nc[0]; ++a)
+      for (int b = 0; b < nc[1]; ++b)
+        for (int c = 0; c < nc[2]; ++c) {
+          const int64_t cc[3] = {cand[0][a], cand[1][b], cand[2][c]};
+          for (int d = 0; d < dim; ++d)
+            if (cc[d] < 0 || cc[d] >= h.n0[d]) return true;
+          if (!f.coarse_present(cc)) return true;
+        }
     return false;
   };
+  (void)node_ext;
 
   h.levels.assign(L + 1, LevelHost());
   h.level_offset.assign(L + 2, 0);
@@ -417,7 +444,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
           lv.slot_class[s] = bd ? 3 : 1;
           if (!bd) ++h.n_coarse;
         }
-    lv.n_cells = (uint64_t)h.n0[0] * h.n0[1] * h.n0[2];
+    lv.n_cells = (uint64_t)f.cells[0].count;
     lv.n_S = h.n_coarse;
   }
   auto pad64 = [](int64_t v) { return (v + 63) / 64 * 64; };  // level starts 256-byte aligned
@@ -1169,13 +1196,18 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       }
     std::vector<int64_t> interior_index(h.levels[0].slot_class.size(), -1);
     int64_t ni = 0;
+    h.coarse_slots.clear();
     for (size_t s = 0; s < interior_index.size(); ++s)
-      if (h.levels[0].slot_class[s] == 1) interior_index[s] = ni++;
+      if (h.levels[0].slot_class[s] == 1) {
+        interior_index[s] = ni++;
+        h.coarse_slots.push_back((int32_t)s);
+      }
     std::vector<double> A0((size_t)ni * ni, 0.0);
     for (int64_t cz = 0; cz < h.n0[2]; ++cz)
       for (int64_t cy = 0; cy < h.n0[1]; ++cy)
         for (int64_t cx = 0; cx < h.n0[0]; ++cx) {
           int64_t cc[3] = {cx, cy, cz};
+          if (!f.coarse_present(cc)) continue;
           double a = coarse_coeff_of(0, cc);
           int64_t id[64];
           for (int j = 0; j < NLOC; ++j) {

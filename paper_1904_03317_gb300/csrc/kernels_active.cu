@@ -847,7 +847,8 @@ __device__ __forceinline__ double lagr(int j, double t) {
 }
 
 template <int DIM, int K>
-__global__ void rhs_sine_kernel(ActiveArgs a, const int32_t* __restrict__ coords, double* __restrict__ b) {
+__global__ void rhs_sine_kernel(ActiveArgs a, const int32_t* __restrict__ coords, double* __restrict__ b,
+                                bool one) {
   using G = ActGeo<DIM, K>;
   constexpr int N1 = G::N1, NC = G::NC;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -870,8 +871,11 @@ __global__ void rhs_sine_kernel(ActiveArgs a, const int32_t* __restrict__ coords
         gauss_point<K>(qx, px, wx);
         gauss_point<K>(qy, py, wy);
         if (DIM == 3) gauss_point<K>(qz, pz, wz);
-        double f = DIM * PI * PI * sin(PI * (lo[0] + h[0] * px)) * sin(PI * (lo[1] + h[1] * py));
-        if (DIM == 3) f *= sin(PI * (lo[2] + h[2] * pz));
+        double f = 1.0;
+        if (!one) {
+          f = DIM * PI * PI * sin(PI * (lo[0] + h[0] * px)) * sin(PI * (lo[1] + h[1] * py));
+          if (DIM == 3) f *= sin(PI * (lo[2] + h[2] * pz));
+        }
         double phi = lagr<K>(i[0], px) * lagr<K>(i[1], py) * (DIM == 3 ? lagr<K>(i[2], pz) : 1.0);
         acc += wx * wy * wz * f * phi;
       }
@@ -885,16 +889,16 @@ __global__ void rhs_sine_kernel(ActiveArgs a, const int32_t* __restrict__ coords
   }
 }
 
-cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* coords, double* b,
+cudaError_t launch_rhs_sine(int dim, int k, const ActiveArgs& a, const int32_t* coords, double* b, bool one,
                             cudaStream_t s) {
   int nc = (dim == 3 ? (k + 1) * (k + 1) * (k + 1) : (k + 1) * (k + 1));
   int64_t n = a.n_cells * nc;
   if (n == 0) return cudaSuccess;
   unsigned grid = (unsigned)((n + 255) / 256);
-  if (dim == 3 && k == 2) rhs_sine_kernel<3, 2><<<grid, 256, 0, s>>>(a, coords, b);
-  else if (dim == 3 && k == 1) rhs_sine_kernel<3, 1><<<grid, 256, 0, s>>>(a, coords, b);
-  else if (dim == 2 && k == 2) rhs_sine_kernel<2, 2><<<grid, 256, 0, s>>>(a, coords, b);
-  else if (dim == 2 && k == 1) rhs_sine_kernel<2, 1><<<grid, 256, 0, s>>>(a, coords, b);
+  if (dim == 3 && k == 2) rhs_sine_kernel<3, 2><<<grid, 256, 0, s>>>(a, coords, b, one);
+  else if (dim == 3 && k == 1) rhs_sine_kernel<3, 1><<<grid, 256, 0, s>>>(a, coords, b, one);
+  else if (dim == 2 && k == 2) rhs_sine_kernel<2, 2><<<grid, 256, 0, s>>>(a, coords, b, one);
+  else if (dim == 2 && k == 1) rhs_sine_kernel<2, 1><<<grid, 256, 0, s>>>(a, coords, b, one);
   else return cudaErrorInvalidValue;
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
@@ -971,15 +975,10 @@ cudaError_t launch_copy_from_mg(int64_t n, const T* u, const uint32_t* home, con
 // ------------------------------------------------------------ coarse solve
 // u0 = A0^{-1} g0 over the interior nodes of the coarse lattice (dense FP64 inverse).
 template <typename T>
-__global__ void coarse_solve_kernel(int dim, int64_t nc, int64_t lx, int64_t ly, int64_t lz,
-                                    const double* __restrict__ inv, const T* __restrict__ g0,
-                                    T* __restrict__ u0) {
+__global__ void coarse_solve_kernel(int64_t nc, const int32_t* __restrict__ slot, const double* __restrict__ inv,
+                                    const T* __restrict__ g0, T* __restrict__ u0) {
   extern __shared__ double gs[];
-  const int64_t ix = lx - 2, iy = dim > 1 ? ly - 2 : 1;
-  auto slot_of = [&](int64_t i) {
-    int64_t x = i % ix, y = (i / ix) % iy, z = i / (ix * iy);
-    return (x + 1) + lx * ((y + 1) + ly * (dim > 2 ? z + 1 : 0));
-  };
+  auto slot_of = [&](int64_t i) { return slot[i]; };
   for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) gs[i] = (double)g0[slot_of(i)];
   __syncthreads();
   // one warp per row: coalesced reads of the row, fixed-order reduction
@@ -995,8 +994,8 @@ __global__ void coarse_solve_kernel(int dim, int64_t nc, int64_t lx, int64_t ly,
 }
 
 template <typename T>
-cudaError_t launch_coarse_solve(int dim, int64_t nc, const int64_t lat[3], const double* inv, const T* g0,
-                                T* u0, cudaStream_t s) {
+cudaError_t launch_coarse_solve(int64_t nc, const int32_t* slot, const double* inv, const T* g0, T* u0,
+                                cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
   size_t sm = (size_t)nc * sizeof(double);
   if (sm > 200 * 1024) return cudaErrorInvalidValue;
@@ -1007,7 +1006,7 @@ cudaError_t launch_coarse_solve(int dim, int64_t nc, const int64_t lat[3], const
   }();
   (void)init;
   unsigned grid = (unsigned)((nc + 7) / 8);  // 8 rows (warps) per block
-  coarse_solve_kernel<T><<<grid, 256, sm, s>>>(dim, nc, lat[0], lat[1], lat[2], inv, g0, u0);
+  coarse_solve_kernel<T><<<grid, 256, sm, s>>>(nc, slot, inv, g0, u0);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -1034,7 +1033,7 @@ __device__ __forceinline__ double block_dot_all(const double* a, const double* b
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) coarse_cg_kernel(int dim, int64_t nc, int64_t lx, int64_t ly,
+__global__ void __launch_bounds__(1024) coarse_cg_kernel(int64_t nc, const int32_t* __restrict__ slot,
                                                          const int32_t* __restrict__ ptr,
                                                          const int32_t* __restrict__ col,
                                                          const double* __restrict__ val, double tol,
@@ -1045,11 +1044,7 @@ __global__ void __launch_bounds__(1024) coarse_cg_kernel(int dim, int64_t nc, in
   double* p = r + nc;
   double* Ap = p + nc;
   __shared__ double red[33];
-  const int64_t ix = lx - 2, iy = dim > 1 ? ly - 2 : 1;
-  auto slot_of = [&](int64_t i) {
-    int64_t a = i % ix, b = (i / ix) % iy, c = i / (ix * iy);
-    return (a + 1) + lx * ((b + 1) + ly * (dim > 2 ? c + 1 : 0));
-  };
+  auto slot_of = [&](int64_t i) { return slot[i]; };
   for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
     x[i] = 0.0;
     r[i] = (double)g0[slot_of(i)];
@@ -1084,7 +1079,7 @@ __global__ void __launch_bounds__(1024) coarse_cg_kernel(int dim, int64_t nc, in
 }
 
 template <typename T>
-cudaError_t launch_coarse_cg(int dim, int64_t nc, const int64_t lat[3], const int32_t* ptr, const int32_t* col,
+cudaError_t launch_coarse_cg(int64_t nc, const int32_t* slot, const int32_t* ptr, const int32_t* col,
                              const double* val, double tol, const T* g0, T* u0, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
   const size_t sm = 4 * (size_t)nc * sizeof(double);
@@ -1095,13 +1090,13 @@ cudaError_t launch_coarse_cg(int dim, int64_t nc, const int64_t lat[3], const in
     return true;
   }();
   (void)init;
-  coarse_cg_kernel<T><<<1, 1024, sm, s>>>(dim, nc, lat[0], lat[1], ptr, col, val, tol, g0, u0);
+  coarse_cg_kernel<T><<<1, 1024, sm, s>>>(nc, slot, ptr, col, val, tol, g0, u0);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
-template cudaError_t launch_coarse_cg<float>(int, int64_t, const int64_t*, const int32_t*, const int32_t*,
+template cudaError_t launch_coarse_cg<float>(int64_t, const int32_t*, const int32_t*, const int32_t*,
                                              const double*, double, const float*, float*, cudaStream_t);
-template cudaError_t launch_coarse_cg<double>(int, int64_t, const int64_t*, const int32_t*, const int32_t*,
+template cudaError_t launch_coarse_cg<double>(int64_t, const int32_t*, const int32_t*, const int32_t*,
                                               const double*, double, const double*, double*, cudaStream_t);
 
 // --------------------------------------------------------- vector kernels
@@ -1448,10 +1443,10 @@ template cudaError_t launch_copy_from_mg<float>(int64_t, const float*, const uin
                                                 double*, unsigned*, double*, cudaStream_t);
 template cudaError_t launch_copy_from_mg<double>(int64_t, const double*, const uint32_t*, const double*, double*,
                                                  double*, unsigned*, double*, cudaStream_t);
-template cudaError_t launch_coarse_solve<float>(int, int64_t, const int64_t*, const double*, const float*, float*,
+template cudaError_t launch_coarse_solve<float>(int64_t, const int32_t*, const double*, const float*, float*,
                                                 cudaStream_t);
-template cudaError_t launch_coarse_solve<double>(int, int64_t, const int64_t*, const double*, const double*,
-                                                 double*, cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(int64_t, const int32_t*, const double*, const double*, double*,
+                                                 cudaStream_t);
 template cudaError_t launch_scale_vec<float>(int64_t, const float*, const float*, float, float*, cudaStream_t);
 template cudaError_t launch_scale_vec<double>(int64_t, const double*, const double*, double, double*,
                                               cudaStream_t);

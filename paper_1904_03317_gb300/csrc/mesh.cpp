@@ -25,20 +25,30 @@ void Forest::init(const gmg_coarse_mesh& cm) {
     lo[d] = cm.lo[d];
     hi[d] = cm.hi[d];
   }
+  const size_t nc = (size_t)n0[0] * n0[1] * n0[2];
+  present.clear();
+  if (cm.present) present.assign(cm.present, cm.present + nc);
   cells.assign(1, HashMap64());
-  cells[0].reserve((size_t)n0[0] * n0[1] * n0[2]);
-  for (int z = 0; z < n0[2]; ++z)
-    for (int y = 0; y < n0[1]; ++y)
-      for (int x = 0; x < n0[0]; ++x) cells[0].insert(pack3(x, y, z), 0);
+  cells[0].reserve(nc);
+  for (int64_t z = 0; z < n0[2]; ++z)
+    for (int64_t y = 0; y < n0[1]; ++y)
+      for (int64_t x = 0; x < n0[0]; ++x) {
+        const int64_t c[3] = {x, y, z};
+        if (coarse_present(c)) cells[0].insert(pack3(x, y, z), 0);
+      }
   rebuild_leaves();
 }
 
+// A lattice cell of level l lies in the domain if it is inside the brick and
+// its coarse ancestor is present.
 bool Forest::inside(int level, const int64_t* c) const {
+  int64_t cc[3];
   for (int d = 0; d < 3; ++d) {
     int64_t ext = d < dim ? ((int64_t)n0[d] << level) : 1;
     if (c[d] < 0 || c[d] >= ext) return false;
+    cc[d] = d < dim ? c[d] >> level : 0;
   }
-  return true;
+  return coarse_present(cc);
 }
 
 bool Forest::exists(int level, const int64_t* c) const {

@@ -24,7 +24,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ENAN, ETIMEOUT, EUNSUPPORTED = 
 PREC_FP64, PREC_FP32 = 0, 1
 SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI = 0, 1
 COARSE_CHOLESKY, COARSE_CHEBYSHEV, COARSE_CG = 0, 1, 2
-RHS_SINE, RHS_RANDOM = 0, 1
+RHS_SINE, RHS_RANDOM, RHS_ONE = 0, 1, 2
 EXPORT_UNKNOWN_KEYS, EXPORT_HOME_LEVEL, EXPORT_HANGING, EXPORT_LEVEL_KEYS, EXPORT_LEVEL_CLASS, \
     EXPORT_HOME_SLOT = range(6)
 
@@ -55,7 +55,24 @@ class GmgError(RuntimeError):
 
 
 class CoarseMeshC(C.Structure):
-    _fields_ = [("dim", C.c_int), ("n0", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+    _fields_ = [("dim", C.c_int), ("n0", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("present", C.c_void_p)]
+
+
+def _coarse_struct(coarse: CoarseMesh):
+    """gmg_coarse_mesh of an inputs.CoarseMesh, and the mask array it points to
+    (kept alive by the caller for the duration of the call)."""
+    cm = CoarseMeshC()
+    cm.dim = coarse.dim
+    for d in range(3):
+        cm.n0[d] = int(coarse.n0[d]) if d < coarse.dim else 1
+        cm.lo[d] = float(coarse.lo[d])
+        cm.hi[d] = float(coarse.hi[d])
+    mask = None
+    if getattr(coarse, "present", None) is not None:
+        mask = np.ascontiguousarray(np.asarray(coarse.present, dtype=np.uint8))
+        cm.present = mask.ctypes.data
+    return cm, mask
 
 
 # gmg_refine_fn: (user, round, n_leaves, level*, coords*, flags*) -> int
@@ -205,12 +222,7 @@ class Mesh:
 
     def __init__(self, coarse: CoarseMesh):
         lib = load_library()
-        cm = CoarseMeshC()
-        cm.dim = coarse.dim
-        for d in range(3):
-            cm.n0[d] = int(coarse.n0[d]) if d < coarse.dim else 1
-            cm.lo[d] = float(coarse.lo[d])
-            cm.hi[d] = float(coarse.hi[d])
+        cm, mask = _coarse_struct(coarse)
         self.coarse = coarse
         h = C.c_void_p()
         _check(lib.gmg_mesh_create(C.byref(cm), C.byref(h)), "gmg_mesh_create")
@@ -321,9 +333,9 @@ class Hierarchy:
 
     # ---- solve path (device FP64 active vectors)
     def assemble_rhs(self, b, kind: str = "sine", seed: int = 0) -> None:
-        """gmg_assemble_rhs: kind "sine" (manufactured solution) or "random"
-        (U[-1, 1) per unknown from `seed`, as inputs.random_rhs)."""
-        k = {"sine": RHS_SINE, "random": RHS_RANDOM}[kind]
+        """gmg_assemble_rhs: kind "sine" (manufactured solution), "one" (f = 1)
+        or "random" (U[-1, 1) per unknown from `seed`, as inputs.random_rhs)."""
+        k = {"sine": RHS_SINE, "random": RHS_RANDOM, "one": RHS_ONE}[kind]
         _check(load_library().gmg_assemble_rhs(self.handle, k, C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _ptr(b)),
                "gmg_assemble_rhs")
 
@@ -428,12 +440,7 @@ def build_hierarchy(ctx: Context, coarse: CoarseMesh, rounds, degree: int, coars
     """gmg_build_hierarchy: forest, refinement rounds (each a function of the
     current leaves, as in Mesh.apply_rounds) and hierarchy in one call."""
     lib = load_library()
-    cm = CoarseMeshC()
-    cm.dim = coarse.dim
-    for d in range(3):
-        cm.n0[d] = int(coarse.n0[d]) if d < coarse.dim else 1
-        cm.lo[d] = float(coarse.lo[d])
-        cm.hi[d] = float(coarse.hi[d])
+    cm, mask = _coarse_struct(coarse)
     rounds = list(rounds)
     failure = []
 

@@ -16,7 +16,7 @@ the configurations of the solver experiments in Sec. 4.
 from __future__ import annotations
 
 import dataclasses
-from typing import Callable, List, Optional, Sequence
+from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -66,12 +66,28 @@ def cell_hash_key(level, coords) -> np.ndarray:
 
 @dataclasses.dataclass(frozen=True)
 class CoarseMesh:
-    """A Cartesian brick [lo, hi] split into n0[0] x n0[1] (x n0[2]) coarse cells."""
+    """A Cartesian brick [lo, hi] split into n0[0] x n0[1] (x n0[2]) coarse cells.
+
+    ``present`` (optional) lists, per coarse cell in lexicographic order (x
+    fastest), whether the cell belongs to the domain; the domain is the
+    union of the present cells (for instance the Fichera corner, a brick with
+    one octant removed).  None: every cell is present.
+    """
 
     dim: int
     n0: Sequence[int]
     lo: Sequence[float]
     hi: Sequence[float]
+    present: Optional[Tuple[bool, ...]] = None
+
+    def cell_present(self, coords) -> np.ndarray:
+        """Whether the coarse cells with the given coordinates (n, 3) are in the domain."""
+        c = np.asarray(coords, dtype=np.int64).reshape(-1, 3)
+        if self.present is None:
+            return np.ones(len(c), dtype=bool)
+        n = [int(self.n0[d]) if d < self.dim else 1 for d in range(3)]
+        mask = np.asarray(self.present, dtype=bool)
+        return mask[c[:, 0] + n[0] * (c[:, 1] + n[1] * c[:, 2])]
 
     def cells_per_dim(self, level: int) -> np.ndarray:
         n = np.ones(3, dtype=np.int64)
@@ -322,10 +338,12 @@ class Workload:
     degree: int
     rounds: List[RoundFn]
     coeff: Optional[np.ndarray]  # per coarse cell, None = 1
-    rhs: str  # "sine" (manufactured u = prod sin(pi x_i)) or "random"
+    rhs: str  # "sine" (manufactured u = prod sin(pi x_i)), "random" or "one" (f = 1)
     cheb_degree: int
     seed: int = 0
     tol: float = 1e-8
+    smoother: str = "chebyshev"     # or "jacobi" (undamped, cheb_degree steps)
+    coarse_solver: str = "cholesky"  # or "cg" / "chebyshev"
 
 
 def poisson2d_circle(global_refinements: int = 3, adaptive_rounds: int = 3) -> Workload:
@@ -359,6 +377,68 @@ def checkerboard3d(global_refinements: int = 5, finest_level: int = 9, seed: int
         rounds.append(round_random_interface(seed, r, prob))
     return Workload(f"checkerboard3d_q2_g{global_refinements}_L{finest_level}", cm, 2, rounds,
                     checkerboard_coefficients(cm), "random", 4, seed=seed)
+
+
+def fichera_coarse() -> CoarseMesh:
+    """The Fichera corner [-1, 1]^3 minus [0, 1]^3 (Sec. 4.3) as 56 coarse
+    cells of size 1/2: the brick's 4^3 cells without the 8 in the removed
+    octant.  (The paper's coarse mesh is the 7 unit cells; one global
+    refinement of it gives these 56, on which the coefficient below is
+    constant per cell.)"""
+    present = tuple(not (x >= 2 and y >= 2 and z >= 2) for z in range(4) for y in range(4) for x in range(4))
+    return CoarseMesh(3, (4, 4, 4), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), present)
+
+
+def fichera_coefficients(cm: CoarseMesh, low: float = 1.0, high: float = 100.0) -> np.ndarray:
+    """epsilon = 1 where min(x, y, z) > -1/2, else 100 (Sec. 4.3): per coarse
+    cell of the Fichera mesh, ``high`` on the cells with an index 0 (they
+    cover min(x, y, z) < -1/2), ``low`` elsewhere."""
+    iz, iy, ix = np.meshgrid(np.arange(cm.n0[2]), np.arange(cm.n0[1]), np.arange(cm.n0[0]), indexing="ij")
+    low_side = ((ix == 0) | (iy == 0) | (iz == 0)).ravel()
+    return np.where(low_side, high, low).astype(np.float64)
+
+
+def round_reentrant_fraction(fraction: float = 0.142) -> RoundFn:
+    """Flag the given fraction of the leaves with the largest indicator
+    h_K^3 / (h_K + d_K), d_K the distance from the cell centre to the
+    re-entrant edges of the Fichera corner (the segments from the origin to
+    (1,0,0), (0,1,0), (0,0,1)); ties go to the smaller (level, key).  It
+    stands in for the a-posteriori estimator of Sec. 4.3, whose largest
+    contributions sit at those edges, and refines a fixed fraction per round
+    as the paper does (14.2%, which roughly doubles the cells)."""
+
+    def fn(cm, level, coords, finest):
+        blo, bhi = cm.boxes(level, coords)
+        c = 0.5 * (blo + bhi)
+        h = bhi[:, 0] - blo[:, 0]
+        d = np.full(len(c), np.inf)
+        for axis in range(3):
+            t = np.clip(c[:, axis], 0.0, 1.0)
+            q = np.zeros_like(c)
+            q[:, axis] = t
+            d = np.minimum(d, np.linalg.norm(c - q, axis=1))
+        eta = h ** 3 / (h + d)
+        m = int(round(fraction * len(c)))
+        key = cell_hash_key(level, coords)
+        order = np.lexsort((key, -eta))  # eta descending, then key ascending
+        flags = np.zeros(len(c), dtype=bool)
+        flags[order[:m]] = True
+        return flags
+
+    return fn
+
+
+def fichera(adaptive_rounds: int = 2, global_refinements: int = 0) -> Workload:
+    """The Laplace example of Sec. 4.3: -div(eps grad u) = 1 on the Fichera
+    corner, u = 0 on the boundary, Q2, eps = 100 where min(x, y, z) <= -1/2;
+    global refinements of the 56 coarse cells, then rounds of the
+    re-entrant-edge fraction rule (closure after each).  Solver settings of
+    the paper's "MF" column: one undamped Jacobi step, CG coarse solver,
+    tolerance 1e-10."""
+    cm = fichera_coarse()
+    rounds = [round_uniform()] * global_refinements + [round_reentrant_fraction()] * adaptive_rounds
+    return Workload(f"fichera_q2_g{global_refinements}_a{adaptive_rounds}", cm, 2, rounds,
+                    fichera_coefficients(cm), "one", 1, tol=1e-10, smoother="jacobi", coarse_solver="cg")
 
 
 # Leaf growth of r random rounds (p = 0.2, closure after each) on a uniform

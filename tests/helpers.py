@@ -1,4 +1,5 @@
 """Shared test helpers: build the same workload on both sides and map vectors."""
+import dataclasses
 import functools
 
 import numpy as np
@@ -32,6 +33,13 @@ def small_workloads():
                                           inputs.round_sphere_surface((0.7, 0.5, 0.4), 0.3)],
                                          np.array([1.0, 100.0, 3.0, 1.0, 50.0, 1.0, 7.0, 1.0, 1.0, 100.0, 2.0, 1.0]),
                                          "random", 4, seed=7),
+        # the Fichera corner (Sec. 4.3): a brick without one octant, Dirichlet
+        # on the re-entrant faces, coefficient jumps of 100 inside the domain;
+        # here with the Chebyshev smoother of degree 4 that the step-by-step
+        # parity tests use (the paper's own solver settings for it are tested
+        # on their own)
+        "3d_q2_fichera": dataclasses.replace(inputs.fichera(3, 1), cheb_degree=4, smoother="chebyshev",
+                                             coarse_solver="cholesky"),
     }
 
 
@@ -41,6 +49,15 @@ def oracle_hierarchy(name: str, cheb: int = None):
     f = build_forest(w.coarse, w.rounds)
     d = fem.Discretization(f, w.degree, w.coeff)
     return ogmg.build_hierarchy(d, cheb or w.cheb_degree)
+
+
+def workload_rhs(O, w):
+    """The workload's right-hand side on the oracle's unknowns."""
+    if w.rhs == "sine":
+        return O.disc.rhs_sine()
+    if w.rhs == "one":
+        return O.disc.rhs_one()
+    return inputs.random_rhs(w.seed, O.disc.n)
 
 
 def level_maps(H, O, level):

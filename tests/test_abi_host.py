@@ -42,7 +42,7 @@ def test_build_info_reports_sm103a():
     import ctypes as C
     a, v = C.c_int(), C.c_int()
     assert G.load_library().gmg_build_info(C.byref(a), C.byref(v)) == 0
-    assert a.value == 1 and v.value == 1
+    assert a.value == 1 and v.value == 2
 
 
 def test_leaf_cells_partitioned_into_patches_groups_and_single_cells():

@@ -13,7 +13,7 @@ import scipy.linalg as sla
 
 from oracle import gmg as ogmg
 from paper_1904_03317_gb300 import gmg as G
-from tests.helpers import from_slots, level_maps, oracle_hierarchy, small_workloads, to_slots
+from tests.helpers import workload_rhs, from_slots, level_maps, oracle_hierarchy, small_workloads, to_slots
 
 pytestmark = pytest.mark.gpu
 
@@ -330,7 +330,7 @@ def test_rhs_rejects_unknown_kind(torch):
 
 def _rhs(O, w):
     from paper_1904_03317_gb300 import inputs
-    return O.disc.rhs_sine() if w.rhs == "sine" else inputs.random_rhs(w.seed, O.disc.n)
+    return workload_rhs(O, w)
 
 
 @pytest.mark.parametrize("name", NAMES)
@@ -465,4 +465,39 @@ def test_solver_variants_match_oracle(torch, name, variant):
     finally:
         O.smoother, O.cheb_degree = saved[0], saved[2]
         ogmg.setup_coarse(O, saved[1])
+        H.close()
+
+
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_fichera_mf_setting_matches_oracle(torch, prec):
+    """The Laplace example of Sec. 4.3 on the Fichera corner with the paper's
+    "MF" solver: one undamped Jacobi step per smoothing, unpreconditioned CG
+    on the coarse level, CG to 1e-10 with f = 1 (assembled on the device).
+    The right-hand side equals the oracle's to 1e-12; FP64 V-cycles take the
+    oracle's iteration count within one, FP32 V-cycles (the paper's single
+    precision) reach the tolerance too; both solutions agree with the
+    oracle's to the tolerance, and the true residual meets it."""
+    from paper_1904_03317_gb300 import inputs
+    w = inputs.fichera(3, 1)
+    O = ogmg.setup(w)
+    b_ref = O.disc.rhs_one()
+    ref = ogmg.solve(O, b_ref, w.tol)
+    assert ref.converged
+    ctx = G.Context(0)
+    H = G.Hierarchy(ctx, G.build_mesh(w), w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=prec,
+                    smoother=G.SMOOTHER_JACOBI, coarse_solver=G.COARSE_CG)
+    try:
+        b = torch.zeros(O.disc.n, dtype=torch.float64, device="cuda")
+        H.assemble_rhs(b, "one")
+        torch.cuda.synchronize()
+        assert rel_err(host(b), b_ref) < 1e-12
+        x = torch.zeros_like(b)
+        st = H.solve(b, x, tol=w.tol, max_iter=500)
+        assert st.converged
+        if prec == G.PREC_FP64:
+            assert abs(st.iterations - ref.iterations) <= 1
+        true_res = np.linalg.norm(b_ref - O.disc.A @ host(x)) / np.linalg.norm(b_ref)
+        assert true_res <= 2 * w.tol
+        assert rel_err(host(x), ref.x) < 1e-8
+    finally:
         H.close()

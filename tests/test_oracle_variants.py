@@ -7,7 +7,7 @@ import scipy.sparse as sp
 
 from oracle import gmg as O
 from paper_1904_03317_gb300 import inputs
-from tests.helpers import oracle_hierarchy, small_workloads
+from tests.helpers import workload_rhs, oracle_hierarchy, small_workloads
 
 
 @pytest.mark.parametrize("kappa", [2.0, 10.0, 100.0, 1e4])
@@ -83,7 +83,7 @@ def test_solver_variants_converge(variant, name):
         H.smoother, H.cheb_degree = smoother, degree
         O.setup_coarse(H, coarse)
         w = small_workloads()[name]
-        b = H.disc.rhs_sine() if w.rhs == "sine" else inputs.random_rhs(w.seed, H.disc.n)
+        b = workload_rhs(H, w)
         res = O.solve(H, b, 1e-8)
         assert res.converged
         assert res.iterations <= (12 if smoother == "chebyshev" else 40)
