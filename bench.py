@@ -221,13 +221,13 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def time_solves(torch, H, b, x, steps, stream):
+def time_solves(torch, H, b, x, steps, stream, tol=TOL):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     st = None
     for _ in range(steps):
-        st = H.solve(b, x, tol=TOL)
+        st = H.solve(b, x, tol=tol)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3, st
@@ -433,9 +433,12 @@ def main():
     ap.add_argument("--adaptive-ref", type=int, default=ADAPTIVE_REF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker", "batch", "serve"],
+    ap.add_argument("--fichera-rounds", type=int, default=13,
+                    help="fichera workload: adaptive rounds (13: 3.4M unknowns, the paper's cycle 13)")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker", "fichera", "batch", "serve"],
                     help="sphere: 3D Q2 Poisson refined at a sphere (the headline); checker: 3D Q2 with the "
-                         "{1, 100} subcube checkerboard coefficient refined at the subcube planes; batch: "
+                         "{1, 100} subcube checkerboard coefficient refined at the subcube planes; fichera: "
+                         "the Laplace example of Sec. 4.3 with its MF solver settings; batch: "
                          "512 independent 2D/3D Q1/Q2 problems solved together")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--requests", type=int, default=200, help="serve workload: measured requests")
@@ -498,16 +501,23 @@ def main():
 
     if args.workload == "sphere":
         w = inputs.poisson3d_sphere(args.global_ref, args.adaptive_ref)
+    elif args.workload == "fichera":
+        w = inputs.fichera(args.fichera_rounds)
     else:
         w = inputs.checkerboard3d(args.global_ref, args.finest_level)
+    tol = w.tol
+    solver = {"cheb_degree": w.cheb_degree,
+              "smoother": G.SMOOTHER_JACOBI if w.smoother == "jacobi" else G.SMOOTHER_CHEBYSHEV,
+              "coarse_solver": {"cholesky": G.COARSE_CHOLESKY, "chebyshev": G.COARSE_CHEBYSHEV,
+                                "cg": G.COARSE_CG}[w.coarse_solver]}
     t0 = time.perf_counter()
     mesh = G.build_mesh(w)
     t_mesh = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     ctx = G.Context(local, stream.cuda_stream)
     t0 = time.perf_counter()
-    H = G.Hierarchy(ctx, mesh, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32,
-                    solve_graph=args.solve_mode == "graph")
+    H = G.Hierarchy(ctx, mesh, w.degree, w.coeff, vcycle_prec=G.PREC_FP32, solve_graph=args.solve_mode == "graph",
+                    **solver)
     t_setup = time.perf_counter() - t0
     info = H.info
     n = H.n
@@ -515,7 +525,7 @@ def main():
     H.assemble_rhs(b, w.rhs, w.seed)  # manufactured, or seeded U[-1, 1) per unknown
     x = torch.zeros_like(b)
     for _ in range(args.warmup):
-        H.solve(b, x, tol=TOL)
+        H.solve(b, x, tol=tol)
 
     # ---- timed region: K solves, each one CUDA-graph launch whose CG loop
     # runs on the device (--solve-mode graph; launches counted by the
@@ -524,7 +534,7 @@ def main():
     sampler.start()
     H.profile_reset(timing=False)
     barrier()
-    secs, st = time_solves(torch, H, b, x, args.steps, stream)
+    secs, st = time_solves(torch, H, b, x, args.steps, stream, tol)
     barrier()
     launches = int(sum(v["launches"] for v in H.profile_read().values()))
     t_max = max_over_ranks(secs)
@@ -537,7 +547,7 @@ def main():
     # per-launch events)
     H.profile_reset(timing=True)
     barrier()
-    secs_stream, _ = time_solves(torch, H, b, x, args.steps, stream)
+    secs_stream, _ = time_solves(torch, H, b, x, args.steps, stream, tol)
     barrier()
     kern = H.profile_read()
     H.profile_reset(timing=False)
@@ -556,7 +566,7 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         db[0].copy_(hb, non_blocking=True)
-        H.solve(db[0], dx[0], tol=TOL)
+        H.solve(db[0], dx[0], tol=tol)
         hx[0].copy_(dx[0], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -580,7 +590,7 @@ def main():
         stream.wait_event(ev_in[j])
         if i >= 2:
             stream.wait_event(ev_out[j])  # x of step i-2 has left the device
-        H.solve(db[j], dx[j], tol=TOL)
+        H.solve(db[j], dx[j], tol=tol)
         ev_done.record(stream)
         copy_s.wait_event(ev_done)
         with torch.cuda.stream(copy_s):
@@ -597,10 +607,10 @@ def main():
     # ---- the FP64 V-cycle path on the same problem
     fp64 = None
     if not args.no_fp64:
-        H64 = G.Hierarchy(ctx, mesh, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP64)
+        H64 = G.Hierarchy(ctx, mesh, w.degree, w.coeff, vcycle_prec=G.PREC_FP64, **solver)
         x64 = torch.zeros_like(b)
-        H64.solve(b, x64, tol=TOL)
-        s64, st64 = time_solves(torch, H64, b, x64, max(1, min(args.steps, 3)), stream)
+        H64.solve(b, x64, tol=tol)
+        s64, st64 = time_solves(torch, H64, b, x64, max(1, min(args.steps, 3)), stream, tol)
         s64 = max_over_ranks(s64)
         steps64 = max(1, min(args.steps, 3))
         diff = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
@@ -612,12 +622,12 @@ def main():
     # ---- the batched and served workloads, measured in the same run (one
     # process; replicas run the headline only)
     batch = serve_rec = None
-    if world == 1 and not args.no_batch:
+    if world == 1 and not args.no_batch and args.workload == "sphere":
         H.close()
         rec, bclocks = batch_measure(torch, G, inputs, local, args.batch_count, 2, 2, args.serial_sample,
                                      barrier, max_over_ranks, sum_over_ranks)
         batch = dict(rec, clocks=bclocks)
-    if world == 1 and not args.no_serve:
+    if world == 1 and not args.no_serve and args.workload == "sphere":
         rec, sclocks = serve_measure(torch, G, inputs, local, args.sub_requests, args.sub_warm_requests, args.rate)
         serve_rec = dict(rec, clocks=sclocks)
 
@@ -660,7 +670,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": w.name,
                        "unknowns": n, "leaves": int(info.n_leaves), "levels": int(info.n_levels),
-                       "tol": TOL, "cheb_degree": w.cheb_degree, "cg_iterations": iters,
+                       "tol": tol, "cheb_degree": w.cheb_degree, "smoother": w.smoother,
+                       "coarse_solver": w.coarse_solver, "cg_iterations": iters,
                        "parallelism": f"replicas x{world}", "solve_mode": args.solve_mode,
                        "l2": f"inputs larger than L2 (active vector {8 * n / 1e6:.0f} MB)",
                        "setup_s": {"mesh": round(t_mesh, 3), "hierarchy_host": round(info.setup_host_s, 3),

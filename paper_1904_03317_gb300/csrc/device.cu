@@ -450,6 +450,7 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->coarse_inv, h.coarse_inverse));
   GMG_TRY(upload(d, &d->coarse_ptr, h.coarse_ptr));
   GMG_TRY(upload(d, &d->coarse_col, h.coarse_col));
+  d->coarse_nnz = (int64_t)h.coarse_col.size();
   GMG_TRY(upload(d, &d->coarse_val, h.coarse_val));
   // level vectors
   const size_t esz = d->prec == GMG_PREC_FP32 ? sizeof(float) : sizeof(double);
@@ -620,7 +621,7 @@ static cudaError_t coarse(const Hier& h, const T* g0, T* u0, cudaStream_t s) {
   const DeviceState* d = h.dev;
   if (h.params.coarse_solver == GMG_COARSE_CG)
     return launch_coarse_cg<T>(d->n_coarse, d->coarse_slot, d->coarse_ptr, d->coarse_col, d->coarse_val,
-                               h.params.coarse_tol, g0, u0, s);
+                               d->coarse_nnz, h.params.coarse_tol, g0, u0, s);
   return launch_coarse_solve<T>(d->n_coarse, d->coarse_slot, d->coarse_inv, g0, u0, s);
 }
 

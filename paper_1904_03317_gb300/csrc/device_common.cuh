@@ -145,7 +145,8 @@ struct DeviceState {
   // coarse level
   int32_t* coarse_slot = nullptr;  // level-0 slot of each coarse unknown
   double* coarse_inv = nullptr;  // n_coarse^2
-  int32_t* coarse_ptr = nullptr;  // CG coarse solver: A_0 in CSR
+  int64_t coarse_nnz = 0;         // CG coarse solver: A_0 in CSR
+  int32_t* coarse_ptr = nullptr;
   int32_t* coarse_col = nullptr;
   double* coarse_val = nullptr;
   int64_t n_coarse = 0;
@@ -292,7 +293,7 @@ cudaError_t launch_coarse_solve(int64_t n_coarse, const int32_t* slot, const dou
                                 cudaStream_t s);
 template <typename T>
 cudaError_t launch_coarse_cg(int64_t nc, const int32_t* slot, const int32_t* ptr, const int32_t* col,
-                             const double* val, double tol, const T* g0, T* u0, cudaStream_t s);
+                             const double* val, int64_t nnz, double tol, const T* g0, T* u0, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scale_vec(int64_t n, const T* dinv, const T* g, T c, T* out, cudaStream_t s);
 cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partials,

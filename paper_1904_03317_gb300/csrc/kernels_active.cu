@@ -11,6 +11,8 @@
 //
 // Reductions are deterministic: each block writes its partial sum, and the
 // last block to finish (atomic ticket) sums the partials in index order.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace gmg {
@@ -1012,92 +1014,117 @@ cudaError_t launch_coarse_solve(int64_t nc, const int32_t* slot, const double* i
 }
 
 // Unpreconditioned CG coarse solver (Sec. 4.3): one block iterates from zero
-// until ||r|| <= tol ||g|| or nc steps, with A_0 in CSR and the vectors in
-// shared memory; dot products reduce in a fixed order.
-__device__ __forceinline__ double block_dot_all(const double* a, const double* b, int64_t n, double* red) {
-  double v = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += a[i] * b[i];
+// until ||r|| <= tol ||g|| or nc steps.  The vectors live in shared memory,
+// and so does A_0 in CSR when it fits (`smem_matrix`); p.Ap is formed in the
+// matrix-vector pass and r.r in the update pass, each reduced once per
+// iteration in a fixed order (every thread sums the warp partials in warp
+// order), with the two partial buffers used alternately so that one barrier
+// per reduction suffices.
+__device__ __forceinline__ double coarse_block_sum(double v, double* red, int nwarps) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  if (l == 0) red[w] = v;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x / 32); ++i) s += red[i];
-    red[32] = s;
-  }
-  __syncthreads();
-  const double s = red[32];
-  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nwarps; ++i) s += red[i];
   return s;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(1024) coarse_cg_kernel(int64_t nc, const int32_t* __restrict__ slot,
-                                                         const int32_t* __restrict__ ptr,
-                                                         const int32_t* __restrict__ col,
-                                                         const double* __restrict__ val, double tol,
-                                                         const T* __restrict__ g0, T* __restrict__ u0) {
+                                                         const int32_t* __restrict__ gptr,
+                                                         const int32_t* __restrict__ gcol,
+                                                         const double* __restrict__ gval, int64_t nnz,
+                                                         bool smem_matrix, double tol, const T* __restrict__ g0,
+                                                         T* __restrict__ u0) {
   extern __shared__ double cg_sm[];
   double* x = cg_sm;
   double* r = x + nc;
   double* p = r + nc;
   double* Ap = p + nc;
-  __shared__ double red[33];
-  auto slot_of = [&](int64_t i) { return slot[i]; };
-  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
-    x[i] = 0.0;
-    r[i] = (double)g0[slot_of(i)];
-    p[i] = r[i];
+  __shared__ double red[2][32];
+  const int nwarps = (int)(blockDim.x >> 5);
+  const int32_t* ptr = gptr;
+  const int32_t* col = gcol;
+  const double* val = gval;
+  if (smem_matrix) {
+    double* sval = Ap + nc;
+    int32_t* scol = reinterpret_cast<int32_t*>(sval + nnz);
+    int32_t* sptr = scol + nnz;
+    for (int64_t m = threadIdx.x; m < nnz; m += blockDim.x) {
+      sval[m] = gval[m];
+      scol[m] = gcol[m];
+    }
+    for (int64_t i = threadIdx.x; i <= nc; i += blockDim.x) sptr[i] = gptr[i];
+    ptr = sptr;
+    col = scol;
+    val = sval;
   }
-  __syncthreads();
-  double rr = block_dot_all(r, r, nc, red);
+  double part = 0.0;
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
+    const double gi = (double)g0[slot[i]];
+    x[i] = 0.0;
+    r[i] = gi;
+    p[i] = gi;
+    part += gi * gi;
+  }
+  int buf = 0;
+  double rr = coarse_block_sum(part, red[buf], nwarps);  // its barrier also publishes p
   const double stop = tol * tol * rr;
   for (int64_t it = 0; it < nc && rr > stop; ++it) {
+    part = 0.0;
     for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
       double t = 0.0;
       for (int32_t m = ptr[i]; m < ptr[i + 1]; ++m) t += val[m] * p[col[m]];
       Ap[i] = t;
+      part += p[i] * t;
     }
-    __syncthreads();
-    const double pAp = block_dot_all(p, Ap, nc, red);
+    buf ^= 1;
+    const double pAp = coarse_block_sum(part, red[buf], nwarps);
     if (!(pAp > 0.0)) break;
     const double alpha = rr / pAp;
-    for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
+    part = 0.0;
+    for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {  // rows of this thread only
       x[i] += alpha * p[i];
-      r[i] -= alpha * Ap[i];
+      const double ri = r[i] - alpha * Ap[i];
+      r[i] = ri;
+      part += ri * ri;
     }
-    __syncthreads();
-    const double rr_new = block_dot_all(r, r, nc, red);
+    buf ^= 1;
+    const double rr_new = coarse_block_sum(part, red[buf], nwarps);
     const double beta = rr_new / rr;
     rr = rr_new;
     if (!(rr > stop)) break;
     for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) p[i] = r[i] + beta * p[i];
-    __syncthreads();
+    __syncthreads();  // p is read by every thread in the next product
   }
-  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) u0[slot_of(i)] = (T)x[i];
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) u0[slot[i]] = (T)x[i];
 }
 
 template <typename T>
 cudaError_t launch_coarse_cg(int64_t nc, const int32_t* slot, const int32_t* ptr, const int32_t* col,
-                             const double* val, double tol, const T* g0, T* u0, cudaStream_t s) {
+                             const double* val, int64_t nnz, double tol, const T* g0, T* u0, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
-  const size_t sm = 4 * (size_t)nc * sizeof(double);
-  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  constexpr size_t kMax = 200 * 1024;
+  const size_t vec = 4 * (size_t)nc * sizeof(double);
+  if (vec > kMax) return cudaErrorInvalidValue;
+  const size_t mat = (size_t)nnz * (sizeof(double) + sizeof(int32_t)) + (size_t)(nc + 1) * sizeof(int32_t);
+  const bool smem_matrix = vec + mat <= kMax;
+  const size_t sm = smem_matrix ? vec + mat : vec;
   // set once, thread-safe (function-local static)
   static const bool init = [&] {
-    cudaFuncSetAttribute(coarse_cg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(coarse_cg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax);
     return true;
   }();
   (void)init;
-  coarse_cg_kernel<T><<<1, 1024, sm, s>>>(nc, slot, ptr, col, val, tol, g0, u0);
+  const unsigned threads = (unsigned)std::min<int64_t>(1024, (nc + 31) / 32 * 32);
+  coarse_cg_kernel<T><<<1, threads, sm, s>>>(nc, slot, ptr, col, val, nnz, smem_matrix, tol, g0, u0);
   GMG_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_cg<float>(int64_t, const int32_t*, const int32_t*, const int32_t*,
-                                             const double*, double, const float*, float*, cudaStream_t);
+                                             const double*, int64_t, double, const float*, float*, cudaStream_t);
 template cudaError_t launch_coarse_cg<double>(int64_t, const int32_t*, const int32_t*, const int32_t*,
-                                              const double*, double, const double*, double*, cudaStream_t);
+                                              const double*, int64_t, double, const double*, double*, cudaStream_t);
 
 // --------------------------------------------------------- vector kernels
 template <typename T>
