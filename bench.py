@@ -423,6 +423,41 @@ def run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_r
         print(json.dumps(line), flush=True)
 
 
+def run_levels(args, torch, G, inputs, local):
+    """Level smoother alone: on each level of the headline workload, the
+    Chebyshev smoothing of the V-cycle (m updates from a nonzero start,
+    gmg_level_smooth) timed with CUDA events, with its algorithmic bytes
+    (4 B x (4 n_S + n_I) per update; the call also copies the level vector
+    once, 8 B per slot)."""
+    w = inputs.poisson3d_sphere(args.global_ref, args.adaptive_ref)
+    stream = torch.cuda.current_stream()
+    ctx = G.Context(local, stream.cuda_stream)
+    H = G.Hierarchy(ctx, G.build_mesh(w), w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32)
+    info, m = H.info, w.cheb_degree
+    wanted = [int(v) for v in args.levels.split(",")] if args.levels else list(range(1, info.n_levels))
+    out = []
+    for lvl in wanted:
+        n = int(info.slots[lvl])
+        g = torch.rand(n, dtype=torch.float32, device="cuda")
+        u, tmp = torch.zeros_like(g), torch.zeros_like(g)
+        for _ in range(args.warmup):
+            H.level_smooth(lvl, g, u, tmp, False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            H.level_smooth(lvl, g, u, tmp, False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3 / args.steps
+        nbytes = m * 4.0 * (4 * int(info.n_S[lvl]) + int(info.n_I[lvl])) + 8.0 * n
+        out.append({"level": lvl, "slots": n, "n_S": int(info.n_S[lvl]), "n_I": int(info.n_I[lvl]),
+                    "bricks": int(info.bricks[lvl]), "bricks_partial": int(info.bricks_partial[lvl]),
+                    "us_per_smoothing": round(1e6 * secs, 2), "GB/s": round(nbytes / secs / 1e9, 1)})
+    print(json.dumps({"metric": "level smoothing time (m Chebyshev updates)", "workload": w.name,
+                      "cheb_degree": m, "steps": args.steps, "warmup": args.warmup, "levels": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,7 +470,12 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fichera-rounds", type=int, default=13,
                     help="fichera workload: adaptive rounds (13: 3.4M unknowns, the paper's cycle 13)")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "checker", "fichera", "batch", "serve"],
+    ap.add_argument("--levels", default="", help="levels workload: comma-separated levels (default all)")
+    ap.add_argument("--brick-min-members", type=int, default=0,
+                    help="smoother tile shape (gmg_params.brick_min_members; 0 = library default)")
+    ap.add_argument("--deterministic", action="store_true", help="bitwise-repeatable solves (gmg_params)")
+    ap.add_argument("--workload", default="sphere",
+                    choices=["sphere", "checker", "fichera", "batch", "serve", "levels"],
                     help="sphere: 3D Q2 Poisson refined at a sphere (the headline); checker: 3D Q2 with the "
                          "{1, 100} subcube checkerboard coefficient refined at the subcube planes; fichera: "
                          "the Laplace example of Sec. 4.3 with its MF solver settings; batch: "
@@ -493,6 +533,9 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
+    if args.workload == "levels":
+        run_levels(args, torch, G, inputs, local)
+        return
     if args.workload == "batch":
         run_batch(args, torch, G, inputs, local, barrier, max_over_ranks, sum_over_ranks, rank, world)
         if dist:
@@ -506,7 +549,8 @@ def main():
     else:
         w = inputs.checkerboard3d(args.global_ref, args.finest_level)
     tol = w.tol
-    solver = {"cheb_degree": w.cheb_degree,
+    solver = {"cheb_degree": w.cheb_degree, "brick_min_members": args.brick_min_members,
+              "deterministic": args.deterministic,
               "smoother": G.SMOOTHER_JACOBI if w.smoother == "jacobi" else G.SMOOTHER_CHEBYSHEV,
               "coarse_solver": {"cholesky": G.COARSE_CHOLESKY, "chebyshev": G.COARSE_CHEBYSHEV,
                                 "cg": G.COARSE_CG}[w.coarse_solver]}
@@ -672,6 +716,7 @@ def main():
                        "unknowns": n, "leaves": int(info.n_leaves), "levels": int(info.n_levels),
                        "tol": tol, "cheb_degree": w.cheb_degree, "smoother": w.smoother,
                        "coarse_solver": w.coarse_solver, "cg_iterations": iters,
+                       "brick_min_members": args.brick_min_members or 4, "deterministic": args.deterministic,
                        "parallelism": f"replicas x{world}", "solve_mode": args.solve_mode,
                        "l2": f"inputs larger than L2 (active vector {8 * n / 1e6:.0f} MB)",
                        "setup_s": {"mesh": round(t_mesh, 3), "hierarchy_host": round(info.setup_host_s, 3),

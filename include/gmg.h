@@ -112,6 +112,19 @@ typedef struct gmg_params {
                                  timing on (gmg_profile_reset): one stream launch per kernel
                                  and one host check per iteration.  Both modes perform the
                                  same operations in the same order (identical results). */
+  int deterministic;          /* 0 (default): the leaf-mesh operator and the restriction add the
+                                 contributions of neighbouring elements to shared nodes with
+                                 atomics, so two runs agree to rounding.  1: they add them
+                                 without atomics, one colour of elements per launch (elements
+                                 of one colour share no node) in a fixed colour order, so a
+                                 solve gives bitwise the same result every time (and a
+                                 problem gives the same bits alone and in a batch).  Costs a
+                                 few more launches per operator application. */
+  int brick_min_members;      /* tile shape of the 3D smoother: a 2x2x2 position of sibling
+                                 groups that is not a full brick becomes a partial brick when
+                                 at least this many of its groups can be smoothed together
+                                 (2..8; 8 = full bricks only; 0 = the default, 4); the other
+                                 groups take the single-group kernel */
 } gmg_params;
 
 #define GMG_MAX_LEVELS 24

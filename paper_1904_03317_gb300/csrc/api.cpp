@@ -242,6 +242,8 @@ void gmg_params_default(gmg_params* p) {
   p->coarse_solver = GMG_COARSE_CHOLESKY;
   p->coarse_tol = 1e-3;
   p->solve_graph = 1;
+  p->deterministic = 0;
+  p->brick_min_members = 0;
 }
 
 gmg_status gmg_hier_build(gmg_ctx* ctx, const gmg_mesh* mesh, int degree, const double* coarse_coeff,
@@ -261,6 +263,10 @@ gmg_status gmg_hier_build(gmg_ctx* ctx, const gmg_mesh* mesh, int degree, const 
                 prm.coarse_solver == GMG_COARSE_CG,
             "bad coarse_solver");
   CHECK_ARG(prm.coarse_tol > 0.0 && prm.coarse_tol < 1.0, "coarse_tol must be in (0, 1)");
+  CHECK_ARG(prm.deterministic == 0 || prm.deterministic == 1, "deterministic must be 0 or 1");
+  CHECK_ARG(prm.brick_min_members == 0 || (prm.brick_min_members >= 2 && prm.brick_min_members <= 8),
+            "brick_min_members must be 0 or in [2, 8]");
+  if (prm.brick_min_members == 0) prm.brick_min_members = 4;
   const Forest& f = mesh->f;
   CHECK_ARG(f.num_levels() <= GMG_MAX_LEVELS, "too many levels");
   GMG_GUARD_BEGIN

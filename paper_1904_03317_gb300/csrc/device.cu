@@ -194,6 +194,12 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.n_uniform = L.n_uniform;
   a.n_jump = L.n_jump;
   a.nbr_coarse = l >= 2 ? h.dev->lv[l - 1].nbr : nullptr;
+  a.deterministic = h.params.deterministic != 0;
+  a.brick_off = L.brick_off.empty() ? nullptr : L.brick_off.data();
+  a.n_brick_colors = L.brick_off.empty() ? 0 : (int)L.brick_off.size() - 1;
+  a.list_color = L.list_color;
+  a.group_off = L.group_off.empty() ? nullptr : L.group_off.data();
+  a.n_group_colors = L.group_off.empty() ? 0 : (int)L.group_off.size() - 1;
   for (int d = 0; d < 3; ++d) {
     a.coarse_lat[d] = h.coarse_lattice[d];
     a.scale[d] = L.scale[d];
@@ -233,6 +239,14 @@ static ActiveArgs active_args(const Hier& h) {
   a.hm_ptr = h.dev->hm_ptr;
   a.hm_hang = h.dev->hm_hang;
   a.hm_w = h.dev->hm_w;
+  const DeviceState* d = h.dev;
+  a.deterministic = h.params.deterministic != 0;
+  a.pat_off = d->pat_off.empty() ? nullptr : d->pat_off.data();
+  a.n_pat_colors = d->pat_off.empty() ? 0 : (int)d->pat_off.size() - 1;
+  a.grp_off = d->grp_off.empty() ? nullptr : d->grp_off.data();
+  a.n_grp_colors = d->grp_off.empty() ? 0 : (int)d->grp_off.size() - 1;
+  a.loose_off = d->loose_off.empty() ? nullptr : d->loose_off.data();
+  a.n_loose_colors = d->loose_off.empty() ? 0 : (int)d->loose_off.size() - 1;
   for (int l = 0; l < GMG_MAX_LEVELS; ++l)
     for (int d = 0; d < 3; ++d) {
       a.scale[l][d] = h.dev->level_scale[l][d];
@@ -276,6 +290,7 @@ void device_free(Hier& h) {
     cudaFree(L.brick_info);
     cudaFree(L.list_jump);
     cudaFree(L.list_rest);
+    cudaFree(L.list_color);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_slot, d->coarse_inv, d->coarse_ptr, d->coarse_col, d->coarse_val, d->cell_nodes, d->cell_coeff, d->cell_level,
                   d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->perm, d->r, d->p, d->Ap,
@@ -407,9 +422,46 @@ gmg_status device_setup(Hier& h) {
     GMG_TRY(upload(d, &D.coeff32, std::vector<float>(H.coeff.begin(), H.coeff.end())));
     GMG_TRY(upload(d, &D.list_uniform, H.list_uniform));
     GMG_TRY(upload(d, &D.pmask, H.pmask));
-    GMG_TRY(upload(d, &D.bricks, H.bricks));
+    std::vector<int32_t> bricks = H.bricks;
     D.n_bricks = H.n_bricks_full;
-    D.n_bricks_all = (int64_t)H.bricks.size() / 64;
+    D.n_bricks_all = (int64_t)bricks.size() / 64;
+    if (h.params.deterministic) {
+      // restriction colours.  A full brick adds into the nodes of the eight
+      // parent cells p + {0,1}^d (p even, its first group's position), a
+      // group into those of its parent cell c: two bricks whose (p / 2) have
+      // the same parities, or two groups whose c have, are at least two
+      // parent groups (cells) apart and share no coarse node.
+      auto parity = [&](const int64_t* q, int shift) {
+        int c = 0;
+        for (int dd = 0; dd < dim; ++dd) c |= (int)((q[dd] >> shift) & 1) << dd;
+        return c;
+      };
+      const int nc = 1 << dim;
+      std::vector<std::vector<int64_t>> by(nc);
+      for (int64_t br = 0; br < D.n_bricks; ++br) {
+        const int32_t g0 = H.bricks[(size_t)br * 64 + 21];  // own group (0, 0, 0) at table position (1, 1, 1)
+        by[parity(&H.block_pos[3 * (size_t)g0], 1)].push_back(br);
+      }
+      D.brick_off.assign(1, 0);
+      int64_t at = 0;
+      for (int c = 0; c < nc; ++c) {
+        for (int64_t br : by[c]) {
+          std::copy(H.bricks.begin() + br * 64, H.bricks.begin() + br * 64 + 64, bricks.begin() + at * 64);
+          ++at;
+        }
+        D.brick_off.push_back(at);
+      }
+      std::vector<std::vector<int32_t>> gby(nc);
+      for (int64_t g = 0; g < H.n_groups; ++g) gby[parity(&H.block_pos[3 * (size_t)g], 0)].push_back((int32_t)g);
+      std::vector<int32_t> list;
+      D.group_off.assign(1, 0);
+      for (int c = 0; c < nc; ++c) {
+        list.insert(list.end(), gby[c].begin(), gby[c].end());
+        D.group_off.push_back((int64_t)list.size());
+      }
+      GMG_TRY(upload(d, &D.list_color, list));
+    }
+    GMG_TRY(upload(d, &D.bricks, bricks));
     GMG_TRY(upload(d, &D.brick_members, H.brick_members));
     {
       // per-brick flags and coefficient, read once per brick by the brick
@@ -422,7 +474,7 @@ gmg_status device_setup(Hier& h) {
         int32_t m0 = -1;
         for (int b = 0; b < 8; ++b) {
           if (!((members >> b) & 1u)) continue;
-          const int32_t gid = H.bricks[(size_t)br * 64 + ((b & 1) + 1) + 4 * ((((b >> 1) & 1) + 1) + 4 * ((b >> 2) + 1))];
+          const int32_t gid = bricks[(size_t)br * 64 + ((b & 1) + 1) + 4 * ((((b >> 1) & 1) + 1) + 4 * ((b >> 2) + 1))];
           if (m0 < 0) m0 = gid;
           if ((H.smask[gid] & full) != full) all_s = false;
         }
@@ -493,6 +545,82 @@ gmg_status device_setup(Hier& h) {
     for (int64_t i = 0; i < m; ++i) out[i] = v[i] >= 0 ? inv[v[i]] : v[i];
     return out;
   };
+  // deterministic mode: colour the patches, the groups and the single cells
+  // (each kind on its own, greedily in table order) so that elements of one
+  // colour share no node (unknown or hanging), and order each kind's tables
+  // by colour.  A launch per colour then adds to shared nodes without
+  // atomics, in a fixed order.
+  auto colour_order = [&](const std::vector<int32_t>& nodes, int nn, int64_t n, std::vector<int64_t>& off,
+                          std::vector<int64_t>& order) -> bool {
+    const int64_t nu = A.n_unknowns, nh = (int64_t)A.hang_key.size();
+    std::vector<uint64_t> used((size_t)(nu + nh), 0);
+    std::vector<int> col((size_t)n, 0);
+    int ncol = 0;
+    for (int64_t e = 0; e < n; ++e) {
+      uint64_t busy = 0;
+      for (int j = 0; j < nn; ++j) {
+        const int32_t id = nodes[(size_t)e * nn + j];
+        if (id >= 0) busy |= used[id];
+        else if (id <= -2) busy |= used[nu + (-2 - id)];
+      }
+      if (~busy == 0) return false;  // more than 64 colours
+      const int c = __builtin_ctzll(~busy);
+      col[e] = c;
+      ncol = std::max(ncol, c + 1);
+      for (int j = 0; j < nn; ++j) {
+        const int32_t id = nodes[(size_t)e * nn + j];
+        if (id >= 0) used[id] |= 1ull << c;
+        else if (id <= -2) used[nu + (-2 - id)] |= 1ull << c;
+      }
+    }
+    off.assign(ncol + 1, 0);
+    for (int64_t e = 0; e < n; ++e) ++off[col[e] + 1];
+    for (int c = 0; c < ncol; ++c) off[c + 1] += off[c];
+    std::vector<int64_t> at(off.begin(), off.end() - 1);
+    order.assign((size_t)n, 0);
+    for (int64_t e = 0; e < n; ++e) order[at[col[e]]++] = e;
+    return true;
+  };
+  auto reorder = [](const auto& v, const std::vector<int64_t>& order, int per) {
+    std::decay_t<decltype(v)> out(v.size());
+    for (size_t i = 0; i < order.size(); ++i)
+      std::copy(v.begin() + order[i] * per, v.begin() + order[i] * per + per, out.begin() + i * per);
+    return out;
+  };
+  const int NN4 = ipow_h(4 * k + 1, dim), NN2 = ipow_h(2 * k + 1, dim), NC1 = ipow_h(k + 1, dim);
+  std::vector<int32_t> pat_nodes = A.pat_nodes, grp_nodes = A.grp_nodes, loose_nodes = A.loose_nodes,
+                       loose_cells = A.loose_cells;
+  std::vector<double> pat_coeff = A.pat_coeff, grp_coeff = A.grp_coeff, loose_coeff = A.loose_coeff;
+  std::vector<uint8_t> pat_level = A.pat_level, grp_level = A.grp_level, loose_level = A.loose_level;
+  d->pat_off.clear();
+  d->grp_off.clear();
+  d->loose_off.clear();
+  if (h.params.deterministic) {
+    std::vector<int64_t> order;
+    bool ok = colour_order(A.pat_nodes, NN4, A.n_patches, d->pat_off, order);
+    if (ok) {
+      pat_nodes = reorder(A.pat_nodes, order, NN4);
+      pat_coeff = reorder(A.pat_coeff, order, 1);
+      pat_level = reorder(A.pat_level, order, 1);
+    }
+    ok = ok && colour_order(A.grp_nodes, NN2, A.n_groups, d->grp_off, order);
+    if (ok) {
+      grp_nodes = reorder(A.grp_nodes, order, NN2);
+      grp_coeff = reorder(A.grp_coeff, order, 1);
+      grp_level = reorder(A.grp_level, order, 1);
+    }
+    ok = ok && colour_order(A.loose_nodes, NC1, (int64_t)A.loose_cells.size(), d->loose_off, order);
+    if (ok) {
+      loose_nodes = reorder(A.loose_nodes, order, NC1);
+      loose_coeff = reorder(A.loose_coeff, order, 1);
+      loose_level = reorder(A.loose_level, order, 1);
+      loose_cells = reorder(A.loose_cells, order, 1);
+    }
+    if (!ok) {
+      set_error("deterministic mode: the leaf elements need more than 64 colours");
+      return GMG_EUNSUPPORTED;
+    }
+  }
   std::vector<uint32_t> home_int((size_t)A.n_unknowns);
   for (int64_t j = 0; j < A.n_unknowns; ++j) home_int[j] = A.home_global[perm[j]];
   GMG_TRY(upload(d, &d->perm, perm));
@@ -512,16 +640,16 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->hm_hang, A.hm_hang));
   GMG_TRY(upload(d, &d->hm_w, A.hm_w));
   GMG_TRY(upload(d, &d->home, home_int));
-  GMG_TRY(upload(d, &d->loose, A.loose_cells));
-  GMG_TRY(upload(d, &d->grp_nodes, renumbered(A.grp_nodes)));
-  GMG_TRY(upload(d, &d->grp_coeff, A.grp_coeff));
-  GMG_TRY(upload(d, &d->grp_level, A.grp_level));
-  GMG_TRY(upload(d, &d->loose_nodes, renumbered(A.loose_nodes)));
-  GMG_TRY(upload(d, &d->loose_coeff, A.loose_coeff));
-  GMG_TRY(upload(d, &d->loose_level, A.loose_level));
-  GMG_TRY(upload(d, &d->pat_nodes, renumbered(A.pat_nodes)));
-  GMG_TRY(upload(d, &d->pat_coeff, A.pat_coeff));
-  GMG_TRY(upload(d, &d->pat_level, A.pat_level));
+  GMG_TRY(upload(d, &d->loose, loose_cells));
+  GMG_TRY(upload(d, &d->grp_nodes, renumbered(grp_nodes)));
+  GMG_TRY(upload(d, &d->grp_coeff, grp_coeff));
+  GMG_TRY(upload(d, &d->grp_level, grp_level));
+  GMG_TRY(upload(d, &d->loose_nodes, renumbered(loose_nodes)));
+  GMG_TRY(upload(d, &d->loose_coeff, loose_coeff));
+  GMG_TRY(upload(d, &d->loose_level, loose_level));
+  GMG_TRY(upload(d, &d->pat_nodes, renumbered(pat_nodes)));
+  GMG_TRY(upload(d, &d->pat_coeff, pat_coeff));
+  GMG_TRY(upload(d, &d->pat_level, pat_level));
   d->n_loose = (int64_t)A.loose_cells.size();
   d->n_grp = A.n_groups;
   d->n_pat = A.n_patches;

@@ -55,6 +55,11 @@ struct LevelDev {
   bool iso = false;             // cubic cells: one scale factor for all directions
   int32_t* list_rest = nullptr; // groups outside full bricks
   int64_t n_rest = 0;
+  // deterministic mode: full bricks ordered by colour (offsets into them),
+  // and every group of the level in a list ordered by colour (offsets); one
+  // colour's bricks or groups share no coarse node
+  std::vector<int64_t> brick_off, group_off;
+  int32_t* list_color = nullptr;
   int64_t n_uniform = 0, n_jump = 0;
   double scale[3] = {0, 0, 0};  // K-term factor per direction: prod_{j!=i} h_j / h_i
   // Chebyshev parameters (host)
@@ -86,6 +91,14 @@ struct LevelArgs {
   const int32_t* list_rest;
   int64_t n_rest;
   bool no_ghosts;             // the level has no refinement-edge (ghost) blocks
+  // deterministic mode (host-side launch data): restriction launches one
+  // colour at a time and adds without atomics
+  bool deterministic;
+  const int64_t* brick_off;   // n_brick_colors + 1 offsets into the full bricks
+  int n_brick_colors;
+  const int32_t* list_color;  // all groups, ordered by colour
+  const int64_t* group_off;   // n_group_colors + 1 offsets into list_color
+  int n_group_colors;
   int64_t n_uniform, n_jump;
   const int32_t* nbr_coarse;  // level l-1 neighbour table (l >= 2)
   int64_t coarse_lat[3];      // coarse lattice extents (l == 1)
@@ -187,6 +200,9 @@ struct DeviceState {
   // constraints) uses the internal numbering; the entry points convert the
   // caller's canonical vectors on the way in and out.
   int32_t* perm = nullptr;
+  // deterministic mode: colour offsets of the patch, group and single-cell
+  // tables (each ordered by colour)
+  std::vector<int64_t> pat_off, grp_off, loose_off;
   double level_scale[GMG_MAX_LEVELS][3];  // leaf-cell operator factors per level
   double cell_h[GMG_MAX_LEVELS][3];       // cell sizes per level
   // CG work vectors
@@ -264,6 +280,16 @@ struct ActiveArgs {
   const int32_t* hm_ptr;     // n_masters + 1
   const int32_t* hm_hang;    // hanging node of each entry
   const double* hm_w;        // its weight
+  // deterministic mode: shared nodes are added to without atomics, one
+  // colour of patches, groups and single cells per launch (offsets into the
+  // colour-ordered tables; host-side launch data)
+  bool deterministic;
+  const int64_t* pat_off;
+  int n_pat_colors;
+  const int64_t* grp_off;
+  int n_grp_colors;
+  const int64_t* loose_off;
+  int n_loose_colors;
   // per-level factors of the hierarchy (kernel parameters, so hierarchies
   // that live side by side never share them)
   double scale[GMG_MAX_LEVELS][3];  // s_i = prod_{j != i} h_j / h_i

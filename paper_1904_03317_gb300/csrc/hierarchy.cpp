@@ -698,7 +698,7 @@ void build_host_hierarchy(Hier& h, const Forest& f) {
       // ghost block) and are read as halo only; a position without a block
       // reads zeros: the stencil of an S node of a member covers only cells
       // of this level, whose nodes all lie in blocks.
-      constexpr int kMinMembers = 4;
+      const int kMinMembers = h.params.brick_min_members > 0 ? h.params.brick_min_members : 4;
       std::unordered_set<uint64_t> seen;
       for (int32_t g0 : lv.list_uniform) {
         if (taken[g0]) continue;

@@ -115,7 +115,17 @@ __device__ __forceinline__ double gather_node(int32_t id, const double* __restri
 
 // Adds a cell contribution to node `id`; contributions to a hanging node are
 // summed per hanging node and passed on to its masters by hang_scatter_kernel.
-__device__ __forceinline__ void scatter_node(int32_t id, double v, double* __restrict__ y, double* __restrict__ yh) {
+// In deterministic mode the launch holds one colour of elements, which share
+// no node, so a plain addition is race-free and the colours fix the order.
+__device__ __forceinline__ void scatter_node(int32_t id, double v, double* __restrict__ y, double* __restrict__ yh,
+                                             bool det = false) {
+  if (det) {
+    if (id >= 0)
+      y[id] += v;
+    else if (id <= -2)
+      yh[-2 - id] += v;
+    return;
+  }
   if (id >= 0)
     atomicAdd(y + id, v);
   else if (id <= -2)
@@ -232,7 +242,7 @@ active_apply_kernel(ActiveArgs a, const double* __restrict__ x, double* __restri
     }
     if (active) {
       e += X[cl][n] * out;
-      scatter_node(id, out, y, a.yh);
+      scatter_node(id, out, y, a.yh, a.deterministic);
     }
     __syncthreads();  // X / T arrays are reused by the next batch
   }
@@ -390,7 +400,7 @@ active_group_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__ grp
             if (interior && id >= 0)
               y[id] = out;  // interior nodes belong to this group's cells only
             else
-              scatter_node(id, out, y, a.yh);
+              scatter_node(id, out, y, a.yh, a.deterministic);
           });
         }
       }
@@ -420,7 +430,7 @@ active_group_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__ grp
             if (interior && id >= 0)
               y[id] = out;
             else
-              scatter_node(id, out, y, a.yh);
+              scatter_node(id, out, y, a.yh, a.deterministic);
           });
         }
       }
@@ -727,7 +737,7 @@ active_group_int_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__
           if (interior && id >= 0)
             y[id] = out;
           else
-            scatter_node(id, out, y, a.yh);
+            scatter_node(id, out, y, a.yh, a.deterministic);
         });
       }
     }
@@ -779,31 +789,57 @@ static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double*
                                                                                 a.hang_w, x, a.xh, a.yh);
     GMG_COUNT_LAUNCH();
   }
-  if (a.n_patches > 0) {
-    group_launch<DIM, K, 4>(a, a.n_patches, a.pat_nodes, a.pat_coeff, a.pat_level, x, y, partials, counter,
-                            energy, false, s);
-    wrote = true;
-  }
-  if (a.n_groups > 0) {
-    group_launch<DIM, K, 2>(a, a.n_groups, a.grp_nodes, a.grp_coeff, a.grp_level, x, y, partials, counter,
+  // one launch per kind, or in deterministic mode one per colour of the kind
+  // (colour-ordered tables, offsets off[0..n])
+  auto ranges = [&](int64_t n, const int64_t* off, int ncol, auto&& launch) {
+    if (n == 0) return;
+    if (!a.deterministic || !off) {
+      launch((int64_t)0, n);
+      return;
+    }
+    for (int c = 0; c < ncol; ++c)
+      if (off[c + 1] > off[c]) launch(off[c], off[c + 1] - off[c]);
+  };
+  constexpr int NN4 = AGrp<DIM, K, 4>::NN, NN2 = AGrp<DIM, K, 2>::NN, NN1 = AGrp<DIM, K, 1>::NN;
+  ranges(a.n_patches, a.pat_off, a.n_pat_colors, [&](int64_t b, int64_t n) {
+    group_launch<DIM, K, 4>(a, n, a.pat_nodes + b * NN4, a.pat_coeff + b, a.pat_level + b, x, y, partials, counter,
                             energy, wrote, s);
     wrote = true;
-  }
+  });
+  ranges(a.n_groups, a.grp_off, a.n_grp_colors, [&](int64_t b, int64_t n) {
+    group_launch<DIM, K, 2>(a, n, a.grp_nodes + b * NN2, a.grp_coeff + b, a.grp_level + b, x, y, partials, counter,
+                            energy, wrote, s);
+    wrote = true;
+  });
   const int64_t ncell = a.cell_list ? a.n_list : a.n_cells;
   const bool iso = a.scale[0][0] == a.scale[0][1] && (DIM == 2 || a.scale[0][1] == a.scale[0][2]);
   if (ncell > 0 && iso && a.cell_list) {
     // single cells of cubic shape: the split-integer kernel with one cell per group
-    group_launch<DIM, K, 1>(a, a.n_list, a.loose_nodes, a.loose_coeff, a.loose_level, x, y, partials, counter,
-                            energy, wrote, s);
-    wrote = true;
+    ranges(a.n_list, a.loose_off, a.n_loose_colors, [&](int64_t b, int64_t n) {
+      group_launch<DIM, K, 1>(a, n, a.loose_nodes + b * NN1, a.loose_coeff + b, a.loose_level + b, x, y, partials,
+                              counter, energy, wrote, s);
+      wrote = true;
+    });
   } else if (ncell > 0) {
     using G = ActGeo<DIM, K>;
-    int64_t blocks = (ncell + G::CPB - 1) / G::CPB;
-    if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
     static_assert(G::MAX_GRID <= kMaxReduceBlocks, "reduction partials");
-    active_apply_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(a, x, y, partials, counter, energy, wrote);
-    GMG_COUNT_LAUNCH();
-    wrote = true;
+    auto cells = [&](const ActiveArgs& aa, int64_t n) {
+      int64_t blocks = (n + G::CPB - 1) / G::CPB;
+      if (blocks > G::MAX_GRID) blocks = G::MAX_GRID;
+      active_apply_kernel<DIM, K><<<(unsigned)blocks, G::BS, 0, s>>>(aa, x, y, partials, counter, energy, wrote);
+      GMG_COUNT_LAUNCH();
+      wrote = true;
+    };
+    if (a.cell_list) {
+      ranges(a.n_list, a.loose_off, a.n_loose_colors, [&](int64_t b, int64_t n) {
+        ActiveArgs aa = a;
+        aa.cell_list = a.cell_list + b;
+        aa.n_list = n;
+        cells(aa, n);
+      });
+    } else {
+      cells(a, ncell);
+    }
   }
   if (a.n_masters > 0) {
     const int64_t b = (a.n_masters + 255) / 256;

@@ -1259,7 +1259,7 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
           float* dst = out + (int64_t)blk * NO * NO * NO + (cx - 2 * K * ox) +
                        NO * ((cy - 2 * K * oy) + NO * ((int)cz - 2 * K * oz));
           const bool inner = cx > 0 && cx < 2 * K && cy > 0 && cy < 2 * K && (int)cz > 0 && (int)cz < 2 * K;
-          if (inner) *dst += t;
+          if (inner || a.deterministic) *dst += t;  // deterministic: this launch's bricks share no node
           else atomicAdd(dst, t);
         }
       });
@@ -1685,7 +1685,10 @@ level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __
           });
           const int jd[3] = {line % N1, line / N1, j};
           const int64_t slot = parent_node_slot<DIM, K>(a, parent, st, jd);
-          if (slot >= 0) atomicAdd(gc + slot, rg - coef * op);
+          if (slot >= 0) {
+            if (a.deterministic) gc[slot] += rg - coef * op;  // one colour: parent cells share no node
+            else atomicAdd(gc + slot, rg - coef * op);
+          }
         });
       }
     }
@@ -1708,7 +1711,10 @@ level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __
           });
           const int jd[3] = {jx, j, 0};
           const int64_t slot = parent_node_slot<DIM, K>(a, parent, st, jd);
-          if (slot >= 0) atomicAdd(gc + slot, rg - coef * op);
+          if (slot >= 0) {
+            if (a.deterministic) gc[slot] += rg - coef * op;  // one colour: parent cells share no node
+            else atomicAdd(gc + slot, rg - coef * op);
+          }
         });
       }
     }
@@ -2046,6 +2052,9 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
   // takes each group's own cells' A u: the two do not mix on one level.)
   const bool bricks = DIM == 3 && std::is_same<T, float>::value && a.level >= 2 && a.n_bricks > 0 &&
                       a.n_rest == 0 && a.no_ghosts;
+  // deterministic mode: one launch per colour of bricks (groups), which share
+  // no coarse node, in a fixed colour order
+  const bool det = a.deterministic && a.n_brick_colors > 0;
   if constexpr (DIM == 3 && std::is_same<T, float>::value) {
     if (bricks) {
       const size_t smb = Brick2S<K>::bytes();
@@ -2054,9 +2063,17 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
         return true;
       }();
       (void)initb;
-      level_cheb_brick_f2_kernel<K, 2><<<(unsigned)a.n_bricks, Brick2S<K>::TB, smb, s>>>(a, u, nullptr, g, gc, 0.f,
-                                                                                           0.f);
-      GMG_COUNT_LAUNCH();
+      for (int c = 0; c < (det ? a.n_brick_colors : 1); ++c) {
+        LevelArgs ac = a;
+        int64_t nb = a.n_bricks;
+        if (det) {
+          ac.bricks = a.bricks + a.brick_off[c] * 64;
+          nb = a.brick_off[c + 1] - a.brick_off[c];
+        }
+        if (nb == 0) continue;
+        level_cheb_brick_f2_kernel<K, 2><<<(unsigned)nb, Brick2S<K>::TB, smb, s>>>(ac, u, nullptr, g, gc, 0.f, 0.f);
+        GMG_COUNT_LAUNCH();
+      }
     }
   }
   const int32_t* list = bricks ? a.list_rest : nullptr;
@@ -2069,6 +2086,16 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
     return true;
   }();
   (void)init;
+  if (a.deterministic && a.n_group_colors > 0 && !bricks) {
+    for (int c = 0; c < a.n_group_colors; ++c) {
+      const int64_t nc = a.group_off[c + 1] - a.group_off[c];
+      if (nc == 0) continue;
+      level_residual_restrict_kernel<T, DIM, K><<<(unsigned)((nc + F::TPB - 1) / F::TPB), 256, sm, s>>>(
+          a, u, g, gc, a.list_color + a.group_off[c], nc);
+      GMG_COUNT_LAUNCH();
+    }
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((n + F::TPB - 1) / F::TPB));
   level_residual_restrict_kernel<T, DIM, K><<<grid, 256, sm, s>>>(a, u, g, gc, list, n);
   GMG_COUNT_LAUNCH();

@@ -84,7 +84,8 @@ class ParamsC(C.Structure):
     _fields_ = [("cheb_degree", C.c_int), ("eig_lo", C.c_double), ("eig_hi", C.c_double),
                 ("eig_iters", C.c_int), ("vcycle_prec", C.c_int),
                 ("fixed_lambda", C.POINTER(C.c_double)), ("smoother", C.c_int), ("coarse_solver", C.c_int),
-                ("coarse_tol", C.c_double), ("solve_graph", C.c_int)]
+                ("coarse_tol", C.c_double), ("solve_graph", C.c_int), ("deterministic", C.c_int),
+                ("brick_min_members", C.c_int)]
 
 
 class PartitionModelC(C.Structure):
@@ -277,12 +278,14 @@ class Mesh:
 
 def _make_params(cheb_degree: int = 5, vcycle_prec: int = PREC_FP32, eig_lo: float = 0.08, eig_hi: float = 1.2,
                  eig_iters: int = 10, fixed_lambda: Optional[Sequence[float]] = None, solve_graph: bool = True,
-                 smoother: int = 0, coarse_solver: int = 0, coarse_tol: float = 1e-3):
+                 smoother: int = 0, coarse_solver: int = 0, coarse_tol: float = 1e-3, deterministic: bool = False,
+                 brick_min_members: int = 0):
     """gmg_params from keyword arguments; returns (params, array to keep alive)."""
     p = ParamsC()
     load_library().gmg_params_default(C.byref(p))
     p.cheb_degree, p.eig_lo, p.eig_hi, p.eig_iters, p.vcycle_prec = cheb_degree, eig_lo, eig_hi, eig_iters, vcycle_prec
     p.solve_graph = int(solve_graph)
+    p.deterministic, p.brick_min_members = int(deterministic), int(brick_min_members)
     p.smoother, p.coarse_solver, p.coarse_tol = smoother, coarse_solver, coarse_tol
     lam = None
     if fixed_lambda is not None:
@@ -297,7 +300,8 @@ class Hierarchy:
     def __init__(self, ctx: Context, mesh: Mesh, degree: int, coarse_coeff=None, **params):
         """params: cheb_degree (5), vcycle_prec (PREC_FP32), eig_lo (0.08), eig_hi (1.2),
         eig_iters (10), fixed_lambda (None), solve_graph (True), smoother (0),
-        coarse_solver (0), coarse_tol (1e-3) -- the fields of gmg_params."""
+        coarse_solver (0), coarse_tol (1e-3), deterministic (False),
+        brick_min_members (0: default 4) -- the fields of gmg_params."""
         p, keep = _make_params(**params)
         coeff = None if coarse_coeff is None else np.ascontiguousarray(np.asarray(coarse_coeff, dtype=np.float64))
         h = C.c_void_p()

@@ -85,7 +85,7 @@ class _Live:
 class Server:
     def __init__(self, torch, device: int = 0, mem_budget: Optional[float] = None, setup_workers: int = 8,
                  max_live: int = 64, tol: float = 1e-8, vcycle_prec: int = G.PREC_FP32, keep_x: bool = False,
-                 cache: bool = True):
+                 cache: bool = True, deterministic: bool = False):
         self.torch = torch
         self.device = device
         if mem_budget is None:
@@ -98,6 +98,7 @@ class Server:
         self.prec = vcycle_prec
         self.keep_x = keep_x
         self.use_cache = cache
+        self.deterministic = deterministic  # bitwise-repeatable solves (gmg_params.deterministic)
         self.bytes_per_leaf = INITIAL_BYTES_PER_LEAF
         self.cache_hits = 0
         self._measured = False
@@ -113,7 +114,7 @@ class Server:
             h.update(a.tobytes())
         coeff = b"" if w.coeff is None else np.ascontiguousarray(w.coeff, dtype=np.float64).tobytes()
         h.update(repr((w.coarse.dim, tuple(w.coarse.n0), tuple(w.coarse.lo), tuple(w.coarse.hi), w.degree,
-                       w.cheb_degree, self.prec)).encode())
+                       w.cheb_degree, self.prec, self.deterministic)).encode())
         h.update(coeff)
         return h.digest()
 
@@ -126,7 +127,8 @@ class Server:
     def _hierarchy(self, w: inputs.Workload, m, stream, t0: float):
         """Phase 2 (host, then device on the request's stream): the hierarchy."""
         ctx = G.Context(self.device, stream.cuda_stream)
-        h = G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=self.prec)
+        h = G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=self.prec,
+                        deterministic=self.deterministic)
         return ctx, h, time.perf_counter() - t0
 
     def _vectors(self, w: inputs.Workload, h, stream):

@@ -240,3 +240,21 @@ def test_build_hierarchy_errors():
     assert lib.gmg_build_hierarchy(ctx.handle, C.byref(cm), 1, G.REFINE_FN(), None, 1, None, None,
                                    C.byref(out)) == G.EINVAL
     assert lib.gmg_build_hierarchy(ctx.handle, C.byref(cm), -1, halt, None, 1, None, None, C.byref(out)) == G.EINVAL
+
+
+def test_brick_min_members_is_the_partial_brick_threshold():
+    """gmg_params.brick_min_members (the smoother's tile shape): lowering it
+    forms more partial bricks, 8 forms none (a position with all eight
+    groups smoothable is a full brick); every group stays in at most one
+    brick; values outside [2, 8] other than 0 are rejected."""
+    w = small_workloads()["3d_q2_checker"]
+    m = G.build_mesh(w)
+    counts = {}
+    for t in (2, 3, 4, 8):
+        i = G.Hierarchy(G.Context(-1), m, w.degree, w.coeff, brick_min_members=t).info
+        counts[t] = sum(i.bricks_partial[l] for l in range(i.n_levels))
+        assert all(8 * i.bricks[l] + t * i.bricks_partial[l] <= i.groups[l] for l in range(1, i.n_levels))
+    assert counts[2] >= counts[3] >= counts[4] >= counts[8] == 0 and counts[2] > counts[4]
+    for bad in (1, 9, -1):
+        with pytest.raises(G.GmgError):
+            G.Hierarchy(G.Context(-1), m, w.degree, w.coeff, brick_min_members=bad)

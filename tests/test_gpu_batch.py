@@ -83,3 +83,26 @@ def test_batch_isolates_a_failing_problem(torch):
     for i, (rc, st) in enumerate(zip(status, stats)):
         if i != 2:
             assert rc in (G.OK, G.ENOTCONV) and st.iterations == 2 or (rc == G.OK and st.converged)
+
+
+def test_deterministic_batch_equals_alone_bitwise(torch):
+    """In deterministic mode a problem's result in the batch has the same bits
+    as the problem solved alone (FP32 V-cycle)."""
+    ctx = G.Context(0)
+    probs = []
+    for w in _problems():
+        H = G.Hierarchy(ctx, G.build_mesh(w), w.degree, w.coeff, cheb_degree=w.cheb_degree,
+                        vcycle_prec=G.PREC_FP32, deterministic=True)
+        b = torch.empty(H.n, dtype=torch.float64, device="cuda")
+        H.assemble_rhs(b, "random", w.seed + 11)
+        probs.append((H, b))
+    alone = []
+    for H, b in probs:
+        x = torch.zeros_like(b)
+        H.solve(b, x, tol=1e-8)
+        alone.append(x.clone())
+    xs = [torch.full_like(b, 3.0) for _, b in probs]
+    stats, status = G.solve_batch([H for H, _ in probs], [b for _, b in probs], xs, tol=1e-8, n_streams=4)
+    torch.cuda.synchronize()
+    for xa, xb, rc in zip(alone, xs, status):
+        assert rc == G.OK and torch.equal(xa, xb)

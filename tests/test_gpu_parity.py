@@ -501,3 +501,47 @@ def test_fichera_mf_setting_matches_oracle(torch, prec):
         assert rel_err(host(x), ref.x) < 1e-8
     finally:
         H.close()
+
+
+@pytest.mark.parametrize("name", ["3d_q2_sphere", "3d_q2_checker", "3d_q2_fichera", "2d_q1_circle"])
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_deterministic_mode_is_bitwise_repeatable(torch, name, prec):
+    """gmg_params.deterministic: the leaf operator and the restriction add to
+    shared nodes one colour of elements at a time, without atomics, so
+    repeated solves give the same bits, in graph and stream mode alike (the
+    same operations in the same order); the FP64 result still agrees with
+    the oracle to 1e-10 at the oracle's iteration count, and with the
+    default (atomic) mode to rounding."""
+    O = oracle_hierarchy(name)
+    w = small_workloads()[name]
+    lam = [lev.lam for lev in O.levels]
+    ctx = G.Context(0)
+    m = G.build_mesh(w)
+    kw = dict(cheb_degree=O.cheb_degree, vcycle_prec=prec, fixed_lambda=lam)
+    Hd = G.Hierarchy(ctx, m, w.degree, w.coeff, deterministic=True, **kw)
+    Hs = G.Hierarchy(ctx, m, w.degree, w.coeff, deterministic=True, solve_graph=False, **kw)
+    Ha = G.Hierarchy(ctx, m, w.degree, w.coeff, **kw)
+    try:
+        b = dev(torch, _rhs(O, w))
+        ref = ogmg.solve(O, _rhs(O, w), 1e-8)
+        xs = []
+        for H in (Hd, Hd, Hs):
+            x = torch.zeros_like(b)
+            H.solve(b, x, fixed_iterations=ref.iterations)
+            xs.append(x)
+        torch.cuda.synchronize()
+        assert torch.equal(xs[0], xs[1]) and torch.equal(xs[0], xs[2])
+        xa = torch.zeros_like(b)
+        Ha.solve(b, xa, fixed_iterations=ref.iterations)
+        tol = 1e-10 if prec == G.PREC_FP64 else 1e-4
+        assert rel_err(host(xs[0]), host(xa)) < tol
+        if prec == G.PREC_FP64:
+            assert rel_err(host(xs[0]), ref.x) < 1e-10
+        y1, y2 = torch.zeros_like(b), torch.zeros_like(b)
+        Hd.apply(b, y1)
+        Hd.apply(b, y2)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, y2)
+    finally:
+        for H in (Hd, Hs, Ha):
+            H.close()

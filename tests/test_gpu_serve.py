@@ -96,3 +96,23 @@ def test_memory_budget_serialises_hierarchies(torch):
     spans = sorted((r.hier_start, r.ready) for r in res)
     for (a0, e0), (a1, e1) in zip(spans, spans[1:]):
         assert a1 >= e0 - 1e-6
+
+
+def test_deterministic_mix_equals_alone_bitwise(torch):
+    """Deterministic mode: every request's result in the mix (FP32 V-cycles,
+    overlapping on the device) has the same bits as the request solved
+    alone."""
+    arrivals, ws = inputs.serving_requests(6, n_min=1e4, n_max=6e4, rate=500.0)
+    srv = serve.Server(torch, setup_workers=3, max_live=6, keep_x=True, deterministic=True)
+    res = srv.run(arrivals, ws)
+    ctx = G.Context(0)
+    for r, w in zip(res, ws):
+        assert r.status == G.OK and r.converged
+        h = G.Hierarchy(ctx, G.build_mesh(w), w.degree, w.coeff, cheb_degree=w.cheb_degree,
+                        vcycle_prec=G.PREC_FP32, deterministic=True)
+        b = torch.empty(h.n, dtype=torch.float64, device="cuda")
+        h.assemble_rhs(b, "random", w.seed)
+        x = torch.zeros_like(b)
+        st = h.solve(b, x, tol=1e-8)
+        h.close()
+        assert st.iterations == r.iterations and torch.equal(x, r.x)
