@@ -195,6 +195,66 @@ def test_uniform_mesh_has_no_interface():
         assert not iface.any()
 
 
+def _corner_refined(dim, n0x, k):
+    """Coarse cells n0x x 1 (x 1) on [0, n0x] x [0, 1] (x [0, 1]): the cell at
+    the origin refined, then its child at the origin refined again."""
+    cm = inputs.CoarseMesh(dim, (n0x, 1, 1), (0, 0, 0), (n0x, 1, 1))
+
+    def at_origin(level):
+        return lambda cm_, lv, co, maxl: (lv == level) & np.all(co == 0, axis=1)
+
+    f = build_forest(cm, [at_origin(0), at_origin(1)])
+    assert [len(c) for c in f.cells] == [n0x, 2 ** dim, 2 ** dim]
+    return fem.Discretization(f, k)
+
+
+def _level_nodes(d, level):
+    keys, iface, _ = d.level_space(level)
+    pos = d.node_positions(keys)[:, :d.dim]
+    fr = lambda p: tuple(float(v) for v in p)
+    return {fr(p) for p in pos}, {fr(p) for p in pos[iface]}
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_interface_nodes_listed_by_hand_2d(k):
+    """Sec. 2.3's I set on a hand-built 2D mesh: coarse cells [0,1]x[0,1] and
+    [1,2]x[0,1]; the first refined once and its child at the origin once more.
+    Level 1 (h = 1/2) has its four cells in [0,1]^2: a level-1 node is I iff a
+    level-1 lattice cell touching it is missing, which happens only on x = 1,
+    next to the unrefined coarse cell.  Level 2 (h = 1/4) has its four cells
+    in [0,1/2]^2: its I nodes are those on x = 1/2 or y = 1/2.  The domain's
+    boundary (x in {0, 2}, y in {0, 1}) is Dirichlet and holds no level node."""
+    d = _corner_refined(2, 2, k)
+    grid = lambda hi, step: [step * i for i in range(1, int(round(hi / step)) + 1)]
+    h1, h2 = 0.5 / k, 0.25 / k  # node spacing on levels 1 and 2
+    nodes1, iface1 = _level_nodes(d, 1)
+    assert nodes1 == {(x, y) for x in grid(1.0, h1) for y in grid(1.0, h1) if y < 1.0}
+    assert iface1 == {(1.0, y) for y in grid(1.0, h1) if y < 1.0}
+    nodes2, iface2 = _level_nodes(d, 2)
+    assert nodes2 == {(x, y) for x in grid(0.5, h2) for y in grid(0.5, h2)}
+    assert iface2 == {(x, y) for (x, y) in nodes2 if x == 0.5 or y == 0.5}
+    assert len(iface2) == (3 if k == 1 else 7)
+    # level 0: Q1 has no interior vertex (every vertex has y in {0, 1}); Q2
+    # has the two cell centres and the midpoint of the shared edge; no level-0
+    # cell is missing
+    nodes0, iface0 = _level_nodes(d, 0)
+    want0 = set() if k == 1 else {(0.5, 0.5), (1.0, 0.5), (1.5, 0.5)}
+    assert nodes0 == want0 and not iface0
+
+
+def test_interface_nodes_listed_by_hand_3d():
+    """The same construction on the unit cube (Q1): level 2's cells fill
+    [0,1/2]^3, and its I nodes are the seven non-Dirichlet nodes with a
+    coordinate equal to 1/2; level 1's one interior node is not I."""
+    d = _corner_refined(3, 1, 1)
+    nodes1, iface1 = _level_nodes(d, 1)
+    assert nodes1 == {(0.5, 0.5, 0.5)} and not iface1
+    nodes2, iface2 = _level_nodes(d, 2)
+    q = (0.25, 0.5)
+    assert nodes2 == {(x, y, z) for x in q for y in q for z in q}
+    assert iface2 == nodes2 - {(0.25, 0.25, 0.25)}
+
+
 def test_adaptive_mesh_has_interface():
     d = _adaptive(2, 1)
     assert any(d.level_space(l)[1].any() for l in range(1, d.L + 1))
