@@ -317,6 +317,7 @@ def batch_measure(torch, G, inputs, local, count, steps, warmup, serial_sample, 
     with the plain FP64 V-cycle are timed beside it.  Returns (record,
     clocks)."""
     from concurrent.futures import ThreadPoolExecutor
+    from paper_1904_03317_gb300 import batch
     ws = inputs.batched_problems(count)
     stream = torch.cuda.current_stream()
     ctx = G.Context(local, stream.cuda_stream)
@@ -324,8 +325,13 @@ def batch_measure(torch, G, inputs, local, count, steps, warmup, serial_sample, 
     with ThreadPoolExecutor(max_workers=8) as ex:  # host setup in parallel (the ABI releases the GIL)
         meshes = list(ex.map(G.build_mesh, ws))
     t_mesh = time.perf_counter() - t0
+    # tile shape per problem class, timed on each class's median problem
     t0 = time.perf_counter()
-    hs = [G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32)
+    tun = batch.tune_tiles(torch, ctx, ws, meshes, tol=TOL, vcycle_prec=G.PREC_FP32)
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hs = [G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32,
+                      brick_min_members=batch.tile_for(tun, w.coarse.dim, w.degree, m.num_leaves()))
           for m, w in zip(meshes, ws)]
     t_setup = time.perf_counter() - t0
     ns = [h.n for h in hs]
@@ -333,18 +339,8 @@ def batch_measure(torch, G, inputs, local, count, steps, warmup, serial_sample, 
     for h, b, w in zip(hs, bs, ws):
         h.assemble_rhs(b, "random", w.seed)
     xs = [torch.zeros_like(b) for b in bs]
-    # warm-up, and pick the stream count (a one-parameter autotune)
-    best = None
-    for nst in (8, 16, 32, 64):
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        stats, status = G.solve_batch(hs, bs, xs, tol=TOL, n_streams=nst)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - a
-        assert all(rc == G.OK for rc in status), status
-        if best is None or dt < best[1]:
-            best = (nst, dt)
-    nst = best[0]
+    # warm-up, and pick the stream count
+    nst = batch.tune_streams(torch, tun, hs, bs, xs, tol=TOL)
     for _ in range(max(0, warmup - 1)):
         G.solve_batch(hs, bs, xs, tol=TOL, n_streams=nst)
     sampler = ClockSampler(local)
@@ -395,7 +391,9 @@ def batch_measure(torch, G, inputs, local, count, steps, warmup, serial_sample, 
            "unknowns_median": int(np.median(ns)), "unknowns_max": int(max(ns)),
            "problems_3d": int(sum(1 for d in dims if d == 3)),
            "cg_iterations_min_max": [int(min(its)), int(max(its))], "n_streams": nst,
-           "setup_s": {"mesh": round(t_mesh, 2), "hierarchies": round(t_setup, 2)},
+           "setup_s": {"mesh": round(t_mesh, 2), "tuning": round(t_tune, 2), "hierarchies": round(t_setup, 2)},
+           "tuning": dict(tun.record(), problems_per_class={
+               batch.class_name(c): v for c, v in sorted(batch.class_counts(ws, meshes).items())}),
            "gpu_launches": launches,
            "serial_fp32_graph": {"value": serial32, "unit": "DoFs/s"},
            "serial_fp64": {"value": serial64, "unit": "DoFs/s", "sample": f"first {k} problems",

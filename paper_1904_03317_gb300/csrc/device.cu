@@ -2,6 +2,7 @@
 // Sec. 2.3), Chebyshev-Jacobi smoothing and eigenvalue estimate (Sec. 4.1),
 // and the outer preconditioned CG.
 #include <algorithm>
+#include <cstring>
 #include <chrono>
 #include <cmath>
 #include <mutex>
@@ -230,7 +231,9 @@ static ActiveArgs active_args(const Hier& h) {
   a.cell_level = h.dev->cell_level;
   a.hang_ptr = h.dev->hang_ptr;
   a.hang_col = h.dev->hang_col;
-  a.hang_w = h.dev->hang_w;
+  a.hang_wc = h.dev->hang_wc;
+  a.hw_table = h.dev->hw_table;
+  a.n_hw = h.dev->n_hw;
   a.n_hang = h.dev->n_hang;
   a.xh = h.dev->xh;
   a.yh = h.dev->yh;
@@ -238,7 +241,7 @@ static ActiveArgs active_args(const Hier& h) {
   a.hm_node = h.dev->hm_node;
   a.hm_ptr = h.dev->hm_ptr;
   a.hm_hang = h.dev->hm_hang;
-  a.hm_w = h.dev->hm_w;
+  a.hm_wc = h.dev->hm_wc;
   const DeviceState* d = h.dev;
   a.deterministic = h.params.deterministic != 0;
   a.pat_off = d->pat_off.empty() ? nullptr : d->pat_off.data();
@@ -293,11 +296,11 @@ void device_free(Hier& h) {
     cudaFree(L.list_color);
   }
   void* ptrs[] = {d->uA, d->uB, d->g, d->dinv, d->coarse_slot, d->coarse_inv, d->coarse_ptr, d->coarse_col, d->coarse_val, d->cell_nodes, d->cell_coeff, d->cell_level,
-                  d->cell_coords, d->hang_ptr, d->hang_col, d->hang_w, d->home, d->perm, d->r, d->p, d->Ap,
+                  d->cell_coords, d->hang_ptr, d->hang_col, d->hang_wc, d->hw_table, d->home, d->perm, d->r, d->p, d->Ap,
                   d->partials, d->counter, d->scal, d->loose, d->grp_nodes, d->grp_coeff, d->grp_level,
                   d->pat_nodes, d->pat_coeff, d->pat_level, d->loose_nodes, d->loose_coeff, d->loose_level,
                   d->xh, d->yh, d->hm_node, d->hm_ptr,
-                  d->hm_hang, d->hm_w};
+                  d->hm_hang, d->hm_wc};
   for (void* p : ptrs) cudaFree(p);
   if (d->scal_host) cudaFreeHost(d->scal_host);
   if (d->cg_exec) cudaGraphExecDestroy(d->cg_exec);
@@ -630,7 +633,36 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->cell_coords, A.cell_coords));
   GMG_TRY(upload(d, &d->hang_ptr, A.hang_ptr));
   GMG_TRY(upload(d, &d->hang_col, renumbered(A.hang_col)));
-  GMG_TRY(upload(d, &d->hang_w, A.hang_w));
+  {
+    // distinct weights (bit-exact) and a code per entry
+    std::vector<double> table;
+    std::vector<uint8_t> wc(A.hang_w.size()), mc(A.hm_w.size());
+    auto code = [&](double w, uint8_t& out) {
+      for (size_t i = 0; i < table.size(); ++i)
+        if (std::memcmp(&table[i], &w, sizeof(double)) == 0) {
+          out = (uint8_t)i;
+          return true;
+        }
+      if (table.size() == 256) return false;
+      table.push_back(w);
+      out = (uint8_t)(table.size() - 1);
+      return true;
+    };
+    for (size_t m = 0; m < A.hang_w.size(); ++m)
+      if (!code(A.hang_w[m], wc[m])) {
+        set_error("more than 256 distinct hanging-node weights");
+        return GMG_EUNSUPPORTED;
+      }
+    for (size_t m = 0; m < A.hm_w.size(); ++m)
+      if (!code(A.hm_w[m], mc[m])) {
+        set_error("more than 256 distinct hanging-node weights");
+        return GMG_EUNSUPPORTED;
+      }
+    d->n_hw = (int)table.size();
+    GMG_TRY(upload(d, &d->hw_table, table));
+    GMG_TRY(upload(d, &d->hang_wc, wc));
+    GMG_TRY(upload(d, &d->hm_wc, mc));
+  }
   d->n_hang = (int64_t)A.hang_key.size();
   d->n_masters = (int64_t)A.hm_node.size();
   GMG_TRY(dev_alloc(d, &d->xh, (size_t)d->n_hang));
@@ -638,7 +670,6 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->hm_node, renumbered(A.hm_node)));
   GMG_TRY(upload(d, &d->hm_ptr, A.hm_ptr));
   GMG_TRY(upload(d, &d->hm_hang, A.hm_hang));
-  GMG_TRY(upload(d, &d->hm_w, A.hm_w));
   GMG_TRY(upload(d, &d->home, home_int));
   GMG_TRY(upload(d, &d->loose, loose_cells));
   GMG_TRY(upload(d, &d->grp_nodes, renumbered(grp_nodes)));
@@ -678,7 +709,7 @@ gmg_status device_setup(Hier& h) {
     const double nnzc = (double)A.hang_col.size();
     d->active_flops = cell_flops * nl + group_flops(2) * ng2 + group_flops(4) * ng4 + 4.0 * nnzc;
     d->active_bytes = 4.0 * (nc * nl + ngn2 * ng2 + ngn4 * ng4) + 9.0 * (nl + ng2 + ng4) +
-                      24.0 * (double)A.n_unknowns + 2.0 * 12.0 * nnzc + 32.0 * (double)A.hang_key.size() +
+                      24.0 * (double)A.n_unknowns + 2.0 * 5.0 * nnzc + 32.0 * (double)A.hang_key.size() +
                       16.0 * (double)A.hm_node.size();
   }
   GMG_TRY(dev_alloc(d, &d->r, A.n_unknowns));

@@ -184,14 +184,18 @@ struct DeviceState {
   uint8_t* pat_level = nullptr;
   int32_t* hang_ptr = nullptr;
   int32_t* hang_col = nullptr;
-  double* hang_w = nullptr;
+  // constraint weights as 1-byte codes into a table of the distinct values
+  // (a handful for Q1 and Q2 on 2:1 meshes)
+  uint8_t* hang_wc = nullptr;
+  double* hw_table = nullptr;
+  int n_hw = 0;
   int64_t n_hang = 0, n_masters = 0;
   double* xh = nullptr;
   double* yh = nullptr;
   int32_t* hm_node = nullptr;
   int32_t* hm_ptr = nullptr;
   int32_t* hm_hang = nullptr;
-  double* hm_w = nullptr;
+  uint8_t* hm_wc = nullptr;
   uint32_t* home = nullptr;
   // The device numbers the unknowns in the order of their home slots, so that
   // the copies between active and level vectors and the leaf operator's
@@ -271,7 +275,9 @@ struct ActiveArgs {
   const uint8_t* cell_level;
   const int32_t* hang_ptr;
   const int32_t* hang_col;
-  const double* hang_w;
+  const uint8_t* hang_wc;    // weight of each entry: hw_table[code]
+  const double* hw_table;    // n_hw distinct constraint weights
+  int n_hw;
   int64_t n_hang;
   double* xh;                // hanging-node values of the operand
   double* yh;                // contributions to hanging nodes
@@ -279,7 +285,7 @@ struct ActiveArgs {
   const int32_t* hm_node;    // their unknown indices
   const int32_t* hm_ptr;     // n_masters + 1
   const int32_t* hm_hang;    // hanging node of each entry
-  const double* hm_w;        // its weight
+  const uint8_t* hm_wc;      // its weight's code
   // deterministic mode: shared nodes are added to without atomics, one
   // colour of patches, groups and single cells per launch (offsets into the
   // colour-ordered tables; host-side launch data)

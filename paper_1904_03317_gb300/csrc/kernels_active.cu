@@ -136,12 +136,16 @@ __device__ __forceinline__ void scatter_node(int32_t id, double v, double* __res
 // accumulators for their contributions.
 __global__ void __launch_bounds__(256) hang_gather_kernel(int64_t nh, const int32_t* __restrict__ hp,
                                                           const int32_t* __restrict__ hc,
-                                                          const double* __restrict__ hw,
+                                                          const uint8_t* __restrict__ hwc,
+                                                          const double* __restrict__ table, int n_table,
                                                           const double* __restrict__ x, double* __restrict__ xh,
                                                           double* __restrict__ yh) {
+  __shared__ double w[256];
+  for (int i = threadIdx.x; i < n_table; i += blockDim.x) w[i] = table[i];
+  __syncthreads();
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
-    for (int m = hp[h]; m < hp[h + 1]; ++m) v += hw[m] * x[hc[m]];
+    for (int m = hp[h]; m < hp[h + 1]; ++m) v += w[hwc[m]] * x[hc[m]];
     xh[h] = v;
     yh[h] = 0.0;
   }
@@ -152,11 +156,15 @@ __global__ void __launch_bounds__(256) hang_gather_kernel(int64_t nh, const int3
 __global__ void __launch_bounds__(256) hang_scatter_kernel(int64_t nm, const int32_t* __restrict__ node,
                                                            const int32_t* __restrict__ mp,
                                                            const int32_t* __restrict__ mh,
-                                                           const double* __restrict__ mw,
+                                                           const uint8_t* __restrict__ mwc,
+                                                           const double* __restrict__ table, int n_table,
                                                            const double* __restrict__ yh, double* __restrict__ y) {
+  __shared__ double w[256];
+  for (int i = threadIdx.x; i < n_table; i += blockDim.x) w[i] = table[i];
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int j = mp[i]; j < mp[i + 1]; ++j) s += mw[j] * yh[mh[j]];
+    for (int j = mp[i]; j < mp[i + 1]; ++j) s += w[mwc[j]] * yh[mh[j]];
     y[node[i]] += s;
   }
 }
@@ -275,13 +283,14 @@ struct AGrp {
   static constexpr int NG = P * K + 1;
   static constexpr int NN = DIM == 3 ? NG * NG * NG : NG * NG;
   static constexpr int LINES = DIM == 3 ? NG * NG : NG;
-  // groups per block: as many lines as fit 128 threads (256 for Q2 3D patches)
-  static constexpr int TARGET = (DIM == 3 && P == 4 && K == 2) ? 256 : 128;
+  // groups per block: as many lines as fit 128 threads (two Q2 3D patches,
+  // 162 lines in 192 threads: measured faster than one or three)
+  static constexpr int TARGET = (DIM == 3 && P == 4 && K == 2) ? 162 : 128;
   static constexpr int Q = TARGET / LINES > 0 ? TARGET / LINES : 1;
   static constexpr int BS = (Q * LINES + 31) / 32 * 32;
   static constexpr int MAX_GRID = 152 * 16;
   // resident blocks per SM the register budget is sized for
-  static constexpr int MIN_BLOCKS = BS >= 256 ? 3 : 8;
+  static constexpr int MIN_BLOCKS = BS >= 256 ? 3 : (BS >= 192 ? 4 : 8);
   // dynamic shared memory: X, A (later C) and B (later D) per group
   static constexpr size_t SMEM = sizeof(double) * (3 * Q * NN + 4 * Q + BS / 32);
 };
@@ -453,11 +462,17 @@ active_group_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__ grp
 // value is split exactly into x / q = P1 + 2^-15 (P2 + r) with integers
 // |P1|, |P2| < 2^15 and r in [0, 1) rounded to 24 bits.  P1 and P2 go
 // through the int32 sum factorisation (the bound of the integer Kronecker sum
-// keeps every partial sum below 2^31), r through an FP32 one, and only the
-// recombination 2^15 y(P1) + y(P2) + y(r) and the scaling are FP64: four FP64
-// operations per node instead of about thirty.  The result is exact up to
-// the 24-bit rounding of r, which is below 2^-38 of the largest input, and
-// the final FP64 rounding.
+// keeps every partial sum below 2^31), r through an FP32 one.  The three
+// results are recombined in integers, 2^(15+kR) y(P1) + 2^kR y(P2) +
+// rint(2^kR y(r)) with kR as large as the same bound keeps this below 2^51
+// (5 for 3D Q2, up to 15 for 2D Q1), converted to FP64 exactly, and scaled:
+// three FP64 operations per node (conversion, scaling, the energy) instead
+// of about thirty.  In units of 2^-15 q the result differs from the exact
+// one by 2^-(kR+1) from the rounding of 2^kR y(r) to an integer and by
+// B 2^-24 from the 24-bit roundings of r and of the FP32 sum y(r), B the
+// bound of the integer Kronecker sum; partial sums reach B 2^30 units, so
+// both are near 2^-52 of them, as the roundings of a direct FP64 sum
+// factorisation are.
 template <int K>
 struct IntElem {
   static constexpr int DM = K == 1 ? 6 : 30, DK = K == 1 ? 1 : 3;
@@ -545,14 +560,26 @@ __device__ __forceinline__ void split_exact(double x, int eq, int& p1, int& p2, 
 __device__ __forceinline__ double i64_to_double(long long v) {  // |v| < 2^51
   return __longlong_as_double(0x4338000000000000LL + v) - 6755399441055744.0;
 }
-__device__ __forceinline__ double f32_to_double(float f) {  // normal or zero (subnormals flushed)
-  const unsigned u = (unsigned)__float_as_int(f);
-  const unsigned ex = (u >> 23) & 0xFFu;
-  if (ex == 0) return 0.0;
-  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
-                                  ((unsigned long long)(ex - 127 + 1023) << 52) |
-                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)bits);
+// 2^(15+k) o1 + 2^k o2 + rint(2^k o3) below 2^51 and 2^k o3 below 2^22
+template <int DIM, int K, int P>
+constexpr bool int_recombination_fits(int k) {
+  const long long b = ikron_bound<DIM, K, P>();
+  return b * ((1LL << (30 + k)) + (1LL << (15 + k)) + (1LL << k)) < (1LL << 51) && b * (1LL << k) < (1LL << 22);
+}
+// fixed-point bits of the r component in the integer recombination: the most
+// that fit (5 for 3D Q2, 10 for 2D Q2, 12 for 3D Q1, 15 for 2D Q1), so the
+// rounding of 2^kR y(r) stays near 2^-52 of the integer sum's scale
+template <int DIM, int K, int P>
+constexpr int int_recombination_bits() {
+  int k = 0;
+  while (k < 20 && int_recombination_fits<DIM, K, P>(k + 1)) ++k;
+  return k;
+}
+// rint(f 2^KR) for |f 2^KR| < 2^22: the sum lands in [2^23, 2^24), where the
+// FP32 spacing is 1, so its low mantissa bits are the rounded integer
+template <int KR>
+__device__ __forceinline__ int f32_fixed_rint(float f) {
+  return __float_as_int(fmaf(f, (float)(1 << KR), 12582912.0f)) - 0x4B400000;
 }
 
 template <int DIM, int K, int P>
@@ -562,7 +589,7 @@ struct AGrpI {
   // X (FP64) and, per component (P1, P2, r), the in-place array and the
   // second stage-1 output, 4 bytes each
   static constexpr size_t SMEM = sizeof(double) * ((size_t)Q * NN + 2 * Q + BS / 32) + 4 * (6 * (size_t)Q * NN + Q);
-  static constexpr int MIN_BLOCKS = BS >= 256 ? 3 : 6;
+  static constexpr int MIN_BLOCKS = BS >= 256 ? 3 : (BS >= 192 ? 4 : 6);
 };
 
 template <int DIM, int K, int P>
@@ -574,6 +601,8 @@ active_group_int_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__
   using G = AGrp<DIM, K, P>;
   constexpr int NG = G::NG, NN = G::NN, Q = G::Q, BS = G::BS;
   static_assert(ikron_bound<DIM, K, P>() * 32768LL < 2147483648LL, "integer Kronecker sum exceeds int32");
+  constexpr int KR = int_recombination_bits<DIM, K, P>();
+  static_assert(KR >= 5 && int_recombination_fits<DIM, K, P>(KR), "integer recombination exceeds 2^51");
   extern __shared__ double smem_g[];
   double (*X)[NN] = reinterpret_cast<double (*)[NN]>(smem_g);
   double* scl = smem_g + Q * NN;       // per group: q 2^-15 a s / (DM^(d-1) DK)
@@ -624,8 +653,8 @@ active_group_int_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__
       const bool ok = grp < n_grp;
       const int lvl = ok ? grp_level[grp] : 0;
       const double cs = ok ? grp_coeff[grp] * a.scale[lvl][0] / DEN : 0.0;
-      // q 2^-15 = 2^(emax - 1023 - 14 - 15); a NaN or Inf input makes the group's output NaN
-      const int eo = emax[tid] - 1023 - 29;
+      // q 2^-15 2^-KR = 2^(emax - 1023 - 14 - 15 - KR); a NaN or Inf input makes the group's output NaN
+      const int eo = emax[tid] - 1023 - 29 - KR;
       scl[tid] = emax[tid] == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
                                      : cs * ldexp(1.0, eo);
     }
@@ -727,7 +756,8 @@ active_group_int_kernel(ActiveArgs a, int64_t n_grp, const int32_t* __restrict__
               o3 += (float)kk * c3[c];
             }
           });
-          const double t = i64_to_double(((long long)o1 << 15) + (long long)o2) + f32_to_double(o3);
+          const double t = i64_to_double(((long long)o1 << (15 + KR)) + ((long long)o2 << KR) +
+                                         (long long)f32_fixed_rint<KR>(o3));
           const double out = t * sc;
           const int n = DIM == 3 ? ix + NG * (iy + NG * r) : ix + NG * r;
           e += X[q][n] * out;
@@ -786,7 +816,8 @@ static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double*
   if (a.n_hang > 0) {
     const int64_t b = (a.n_hang + 255) / 256;
     hang_gather_kernel<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(a.n_hang, a.hang_ptr, a.hang_col,
-                                                                                a.hang_w, x, a.xh, a.yh);
+                                                                                a.hang_wc, a.hw_table, a.n_hw, x,
+                                                                                a.xh, a.yh);
     GMG_COUNT_LAUNCH();
   }
   // one launch per kind, or in deterministic mode one per colour of the kind
@@ -844,7 +875,8 @@ static cudaError_t active_dispatch(const ActiveArgs& a, const double* x, double*
   if (a.n_masters > 0) {
     const int64_t b = (a.n_masters + 255) / 256;
     hang_scatter_kernel<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(a.n_masters, a.hm_node, a.hm_ptr,
-                                                                                 a.hm_hang, a.hm_w, a.yh, y);
+                                                                                 a.hm_hang, a.hm_wc, a.hw_table,
+                                                                                 a.n_hw, a.yh, y);
     GMG_COUNT_LAUNCH();
   }
   if (!wrote && energy) cudaMemsetAsync(energy, 0, sizeof(double), s);
@@ -923,7 +955,8 @@ __global__ void rhs_sine_kernel(ActiveArgs a, const int32_t* __restrict__ coords
     atomicAdd(b + id, acc);
   } else if (id <= -2) {
     int hh = -2 - id;
-    for (int m = a.hang_ptr[hh]; m < a.hang_ptr[hh + 1]; ++m) atomicAdd(b + a.hang_col[m], a.hang_w[m] * acc);
+    for (int m = a.hang_ptr[hh]; m < a.hang_ptr[hh + 1]; ++m)
+      atomicAdd(b + a.hang_col[m], a.hw_table[a.hang_wc[m]] * acc);
   }
 }
 

@@ -498,10 +498,13 @@ __device__ __forceinline__ double merged_diag(int i) {
   return v;
 }
 
+// One single group (list entry t of list_uniform; none if t >= n_uniform)
+// smoothed by one team of TW threads: its mask and coefficient slots, its
+// 3^d neighbour table and its S::PER values of shared memory.
 template <typename T, int DIM, int K, int MODE>
-__global__ void __launch_bounds__(256)
-level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, const T* __restrict__ gvec,
-                       const T* __restrict__ dinv, T* out, T c1, T c2) {
+__device__ __forceinline__ void fast_group_step(const LevelArgs& a, int64_t t, int lane, uint64_t* mask_slot,
+                                                T* coef_slot, int32_t* nb, T* T1M, const T* __restrict__ x,
+                                                const T* xprev, const T* __restrict__ gvec, T* out, T c1, T c2) {
   using F = Fast<DIM, K>;
   using S = FastSmem<T, DIM, K>;
   constexpr int NH = F::NH, NO = F::NO, TW = F::TW;
@@ -509,16 +512,8 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   constexpr int L3 = DIM == 3 ? NO * NO : NO;
   constexpr int R = TW / L3 > 0 ? TW / L3 : 1;
   constexpr int OPT = (NO + R - 1) / R;  // outputs per thread
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int team = threadIdx.x / TW;
-  const int lane = threadIdx.x % TW;
-  const int64_t t = (int64_t)blockIdx.x * F::TPB + team;
   const bool active = t < a.n_uniform;
   const int64_t g = active ? a.list_uniform[t] : 0;
-  uint64_t* masks = reinterpret_cast<uint64_t*>(smem_raw);
-  T* coefs = reinterpret_cast<T*>(masks + F::TPB);
-  int32_t* nb = reinterpret_cast<int32_t*>(coefs + F::TPB) + team * F::NNB;
-  T* T1M = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
   T* T1K = T1M + S::T1;
   T* T2MM = T1K + S::T1;
   T* T2MK = T2MM + S::T2;
@@ -545,8 +540,8 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   if (active) {
     for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
     if (lane == 0) {
-      masks[team] = a.smask[g];
-      coefs[team] = group_coef<T>(a, g);
+      *mask_slot = a.smask[g];
+      *coef_slot = group_coef<T>(a, g);
     }
   }
   __syncwarp();
@@ -583,8 +578,8 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
   }
   __syncwarp();
   const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
-  const uint64_t smask = masks[team];
-  const T coef = coefs[team];
+  const uint64_t smask = *mask_slot;
+  const T coef = *coef_slot;
   // Chebyshev update of stored node `node`.  D^{-1} of an S node of a uniform
   // group is the inverse of coef * sum_d s_d prod_e (diagonal of the merged
   // 1-D matrices); that diagonal depends on an index only through its parity,
@@ -699,6 +694,23 @@ level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, con
     }
   }
 }
+
+template <typename T, int DIM, int K, int MODE>
+__global__ void __launch_bounds__(256)
+level_cheb_fast_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, const T* __restrict__ gvec, T* out,
+                       T c1, T c2) {
+  using F = Fast<DIM, K>;
+  using S = FastSmem<T, DIM, K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / F::TW, lane = threadIdx.x % F::TW;
+  uint64_t* masks = reinterpret_cast<uint64_t*>(smem_raw);
+  T* coefs = reinterpret_cast<T*>(masks + F::TPB);
+  int32_t* nb = reinterpret_cast<int32_t*>(coefs + F::TPB) + team * F::NNB;
+  T* base = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
+  fast_group_step<T, DIM, K, MODE>(a, (int64_t)blockIdx.x * F::TPB + team, lane, masks + team, coefs + team, nb,
+                                   base, x, xprev, gvec, out, c1, c2);
+}
+
 
 // ------------------------------- smoothing kernel, groups at coefficient jumps
 // The extended operator of level_cheb_kernel (rows 0..2K-1 for the group's
@@ -1346,12 +1358,25 @@ struct BrickQ2 {
   static constexpr size_t T2B = ((size_t)HB * ZS * 8 + 15) / 16 * 16;
   static constexpr size_t XOB = (size_t)OB * OB * OB * 4;
   static constexpr size_t bytes() { return T1B + T2B + XOB + 64 * 4; }
+  // single groups after the bricks, one per warp: per warp a mask, a
+  // coefficient, a neighbour table and the single-group kernel's arrays,
+  // over the same shared memory
+  static constexpr int WARPS = TB / 32;
+  static constexpr size_t SG_HEAD = ((size_t)WARPS * (8 + 4 + 4 * 27) + 15) / 16 * 16;
+  static constexpr size_t SG_PER = (size_t)FastSmem<float, 3, 2>::PER * 4;
+  static_assert(SG_HEAD + WARPS * SG_PER <= T1B + T2B + XOB + 64 * 4, "single groups fit the brick layout");
 };
 
+// Persistent blocks over the work items [0, n_bricks_all + n_single_chunks):
+// first the bricks, then chunks of four single groups (list_uniform), one
+// group per warp with the single-group kernel's code, so that the groups
+// outside bricks need no launch of their own and fill the tail of the brick
+// phase.
 template <int MODE, bool ISO>
 __global__ void __launch_bounds__(BrickQ2::TB, 9)
-level_cheb_brick_q2_kernel(LevelArgs a, const float* __restrict__ x, const float* __restrict__ xprev,
-                           const float* __restrict__ gvec, float* __restrict__ out, float c1, float c2) {
+level_cheb_brick_q2_kernel(LevelArgs a, int64_t n_single_chunks, const float* __restrict__ x,
+                           const float* __restrict__ xprev, const float* __restrict__ gvec,
+                           float* __restrict__ out, float c1, float c2) {
   using B = BrickQ2;
   constexpr int K = B::K, NO = B::NO, OB = B::OB, HB = B::HB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1404,7 +1429,21 @@ level_cheb_brick_q2_kernel(LevelArgs a, const float* __restrict__ x, const float
     }
   }
 
-  for (int64_t br = blockIdx.x; br < a.n_bricks_all; br += gridDim.x) {
+  const int64_t n_items = a.n_bricks_all + n_single_chunks;
+  for (int64_t br = blockIdx.x; br < n_items; br += gridDim.x) {
+    if (br >= a.n_bricks_all) {
+      // a chunk of single groups; the barrier ends every warp's use of the
+      // brick arrays that this layout overlays
+      __syncthreads();
+      const int warp = tid / 32, lane = tid % 32;
+      uint64_t* masks = reinterpret_cast<uint64_t*>(smem_raw);
+      float* coefs = reinterpret_cast<float*>(masks + B::WARPS);
+      int32_t* nb = reinterpret_cast<int32_t*>(coefs + B::WARPS) + warp * 27;
+      float* mine = reinterpret_cast<float*>(smem_raw + B::SG_HEAD + warp * B::SG_PER);
+      fast_group_step<float, 3, K, MODE>(a, (br - a.n_bricks_all) * B::WARPS + warp, lane, masks + warp,
+                                         coefs + warp, nb, mine, x, xprev, gvec, out, c1, c2);
+      continue;
+    }
     if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
     const uint2 info = a.brick_info[br];
     __syncthreads();
@@ -1943,12 +1982,16 @@ static unsigned persistent_grid(KERN kern, int threads, size_t smem, int64_t wor
 template <typename T, int DIM, int K, int MODE>
 static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, const T* g, const T* dinv,
                                T* out, T c1, T c2, cudaStream_t s) {
+  bool singles_done = false;
   if constexpr (DIM == 3) {
     if (a.n_bricks_all > 0) {  // full and partial bricks
       if constexpr (std::is_same<T, float>::value && K == 2) {
+        // the single groups of the level run in the same launch, after the bricks
+        const int64_t chunks = (a.n_uniform + BrickQ2::WARPS - 1) / BrickQ2::WARPS;
+        singles_done = true;
         auto kern = a.iso ? level_cheb_brick_q2_kernel<MODE, true> : level_cheb_brick_q2_kernel<MODE, false>;
-        const unsigned grid = persistent_grid(kern, BrickQ2::TB, BrickQ2::bytes(), a.n_bricks_all);
-        kern<<<grid, BrickQ2::TB, BrickQ2::bytes(), s>>>(a, x, xprev, g, out, c1, c2);
+        const unsigned grid = persistent_grid(kern, BrickQ2::TB, BrickQ2::bytes(), a.n_bricks_all + chunks);
+        kern<<<grid, BrickQ2::TB, BrickQ2::bytes(), s>>>(a, chunks, x, xprev, g, out, c1, c2);
         GMG_COUNT_LAUNCH();
       } else if constexpr (std::is_same<T, float>::value) {
         const size_t sm = Brick2S<K>::bytes();
@@ -1977,7 +2020,7 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
       }
     }
   }
-  if (a.n_uniform > 0) {
+  if (a.n_uniform > 0 && !singles_done) {
     using F = Fast<DIM, K>;
     const size_t sm = FastSmem<T, DIM, K>::bytes();
     // set once, thread-safe (function-local static)
@@ -1987,7 +2030,7 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
     }();
     (void)init;
     dim3 grid((unsigned)((a.n_uniform + F::TPB - 1) / F::TPB));
-    level_cheb_fast_kernel<T, DIM, K, MODE><<<grid, 256, sm, s>>>(a, x, xprev, g, dinv, out, c1, c2);
+    level_cheb_fast_kernel<T, DIM, K, MODE><<<grid, 256, sm, s>>>(a, x, xprev, g, out, c1, c2);
     GMG_COUNT_LAUNCH();
   }
   if constexpr (DIM == 3) {

@@ -106,3 +106,44 @@ def test_deterministic_batch_equals_alone_bitwise(torch):
     torch.cuda.synchronize()
     for xa, xb, rc in zip(alone, xs, status):
         assert rc == G.OK and torch.equal(xa, xb)
+
+
+def test_tile_shape_does_not_change_the_solve(torch):
+    """The smoother's partial-brick threshold (2, the default 4, full bricks
+    only) moves groups between the brick and the single-group kernels; with
+    FP64 V-cycles each setting matches the oracle's solve at its iteration
+    count."""
+    name = "3d_q2_checker"
+    w = small_workloads()[name]
+    O = oracle_hierarchy(name)
+    b = inputs.random_rhs(w.seed + 5, O.disc.n)
+    ref = ogmg.solve(O, b, 1e-10)
+    ctx = G.Context(0)
+    m = G.build_mesh(w)
+    seen = set()
+    for t in (2, 4, 8):
+        H = G.Hierarchy(ctx, m, w.degree, w.coeff, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP64,
+                        brick_min_members=t, fixed_lambda=[lev.lam for lev in O.levels])
+        seen.add(tuple(int(v) for v in H.info.bricks_partial[:H.info.n_levels]))
+        x = torch.zeros(H.n, dtype=torch.float64, device="cuda")
+        st = H.solve(torch.tensor(b, device="cuda"), x, tol=1e-10)
+        assert st.converged and abs(st.iterations - ref.iterations) <= 1
+        if st.iterations == ref.iterations:
+            xh = x.cpu().numpy()
+            assert np.abs(xh - ref.x).max() <= 1e-10 * np.abs(ref.x).max(), t
+        H.close()
+    assert len(seen) > 1  # the thresholds really give different partitions
+
+
+def test_autotuner_picks_a_tile_per_3d_class(torch):
+    from paper_1904_03317_gb300 import batch
+    pool = list(inputs.batched_problems(48, n_max=6e4))
+    ws = [w for w in pool if w.coarse.dim == 3][:3] + [w for w in pool if w.coarse.dim == 2][:2]
+    meshes = [G.build_mesh(w) for w in ws]
+    ctx = G.Context(0)
+    tun = batch.tune_tiles(torch, ctx, ws, meshes, reps=1, candidates=(2, 8))
+    want = {batch.problem_class(3, w.degree, m.num_leaves()) for w, m in zip(ws, meshes) if w.coarse.dim == 3}
+    assert want and set(tun.tile) == want
+    for c, v in tun.tile.items():
+        assert v in (2, 8) and set(tun.tile_ms[c]) == {2, 8} and all(t > 0 for t in tun.tile_ms[c].values())
+    assert len(tun.record()["tile_brick_min_members"]) == len(want)

@@ -144,6 +144,24 @@ def test_inverse_diagonal(torch, name):
 
 
 @pytest.mark.parametrize("name", NAMES)
+def test_fp32_inverse_diagonal_is_the_rounded_fp64_one(torch, name):
+    """An FP32 hierarchy's inverse diagonal is its FP64 one rounded to
+    nearest (numpy's float32 cast), bit for bit: the two precisions share
+    the diagonal's FP64 evaluation."""
+    O, H64 = gpu_hier(torch, name)
+    _, H32 = gpu_hier(torch, name, G.PREC_FP32)
+    for l in range(1, len(O.levels)):
+        n = int(H64.info.slots[l])
+        d64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        d32 = torch.zeros(n, dtype=torch.float32, device="cuda")
+        H64.level_inv_diag(l, d64)
+        H32.level_inv_diag(l, d32)
+        torch.cuda.synchronize()
+        want = d64.cpu().numpy().astype(np.float32)
+        assert np.array_equal(d32.cpu().numpy().view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("name", NAMES)
 def test_coarse_solve(torch, name):
     O, H = gpu_hier(torch, name)
     lev = O.levels[0]
@@ -247,6 +265,9 @@ def test_vcycle_fp32(torch, name):
     H.vcycle(dev(torch, r), z)
     torch.cuda.synchronize()
     assert rel_err(host(z), want) < 1e-4
+    # z is the FP32 level solution widened to FP64: every value is a float
+    zh = host(z)
+    assert np.array_equal(zh.astype(np.float32).astype(np.float64), zh)
 
 
 @pytest.mark.parametrize("name", NAMES)
