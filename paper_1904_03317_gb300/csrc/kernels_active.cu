@@ -1089,15 +1089,20 @@ cudaError_t launch_coarse_solve(int64_t nc, const int32_t* slot, const double* i
 // iteration in a fixed order (every thread sums the warp partials in warp
 // order), with the two partial buffers used alternately so that one barrier
 // per reduction suffices.
-__device__ __forceinline__ double coarse_block_sum(double v, double* red, int nwarps) {
+template <typename T>
+__device__ __forceinline__ T coarse_block_sum(T v, T* red, int nwarps) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = 0;
   for (int i = 0; i < nwarps; ++i) s += red[i];
   return s;
 }
 
+// The iteration runs in the level vectors' precision T: an FP32 V-cycle
+// solves its coarse problem in FP32 (A_0 rounded to FP32 when it is staged),
+// which on GB300 runs on the FP32 pipe instead of the FP64 pipe that issues
+// two operations per clock per SM; an FP64 V-cycle solves it in FP64.
 template <typename T>
 __global__ void __launch_bounds__(1024) coarse_cg_kernel(int64_t nc, const int32_t* __restrict__ slot,
                                                          const int32_t* __restrict__ gptr,
@@ -1105,68 +1110,69 @@ __global__ void __launch_bounds__(1024) coarse_cg_kernel(int64_t nc, const int32
                                                          const double* __restrict__ gval, int64_t nnz,
                                                          bool smem_matrix, double tol, const T* __restrict__ g0,
                                                          T* __restrict__ u0) {
-  extern __shared__ double cg_sm[];
-  double* x = cg_sm;
-  double* r = x + nc;
-  double* p = r + nc;
-  double* Ap = p + nc;
-  __shared__ double red[2][32];
+  extern __shared__ __align__(16) unsigned char cg_raw[];
+  T* x = reinterpret_cast<T*>(cg_raw);
+  T* r = x + nc;
+  T* p = r + nc;
+  T* Ap = p + nc;
+  __shared__ T red[2][32];
   const int nwarps = (int)(blockDim.x >> 5);
   const int32_t* ptr = gptr;
   const int32_t* col = gcol;
-  const double* val = gval;
+  T* sval = Ap + nc;
   if (smem_matrix) {
-    double* sval = Ap + nc;
     int32_t* scol = reinterpret_cast<int32_t*>(sval + nnz);
     int32_t* sptr = scol + nnz;
     for (int64_t m = threadIdx.x; m < nnz; m += blockDim.x) {
-      sval[m] = gval[m];
+      sval[m] = (T)gval[m];
       scol[m] = gcol[m];
     }
     for (int64_t i = threadIdx.x; i <= nc; i += blockDim.x) sptr[i] = gptr[i];
     ptr = sptr;
     col = scol;
-    val = sval;
   }
-  double part = 0.0;
+  T part = 0;
   for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
-    const double gi = (double)g0[slot[i]];
-    x[i] = 0.0;
+    const T gi = g0[slot[i]];
+    x[i] = 0;
     r[i] = gi;
     p[i] = gi;
     part += gi * gi;
   }
   int buf = 0;
-  double rr = coarse_block_sum(part, red[buf], nwarps);  // its barrier also publishes p
-  const double stop = tol * tol * rr;
+  T rr = coarse_block_sum<T>(part, red[buf], nwarps);  // its barrier also publishes p
+  const T stop = (T)(tol * tol) * rr;
   for (int64_t it = 0; it < nc && rr > stop; ++it) {
-    part = 0.0;
+    part = 0;
     for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {
-      double t = 0.0;
-      for (int32_t m = ptr[i]; m < ptr[i + 1]; ++m) t += val[m] * p[col[m]];
+      T t = 0;
+      if (smem_matrix)
+        for (int32_t m = ptr[i]; m < ptr[i + 1]; ++m) t += sval[m] * p[col[m]];
+      else
+        for (int32_t m = ptr[i]; m < ptr[i + 1]; ++m) t += (T)gval[m] * p[col[m]];
       Ap[i] = t;
       part += p[i] * t;
     }
     buf ^= 1;
-    const double pAp = coarse_block_sum(part, red[buf], nwarps);
-    if (!(pAp > 0.0)) break;
-    const double alpha = rr / pAp;
-    part = 0.0;
+    const T pAp = coarse_block_sum<T>(part, red[buf], nwarps);
+    if (!(pAp > 0)) break;
+    const T alpha = rr / pAp;
+    part = 0;
     for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) {  // rows of this thread only
       x[i] += alpha * p[i];
-      const double ri = r[i] - alpha * Ap[i];
+      const T ri = r[i] - alpha * Ap[i];
       r[i] = ri;
       part += ri * ri;
     }
     buf ^= 1;
-    const double rr_new = coarse_block_sum(part, red[buf], nwarps);
-    const double beta = rr_new / rr;
+    const T rr_new = coarse_block_sum<T>(part, red[buf], nwarps);
+    const T beta = rr_new / rr;
     rr = rr_new;
     if (!(rr > stop)) break;
     for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) p[i] = r[i] + beta * p[i];
     __syncthreads();  // p is read by every thread in the next product
   }
-  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) u0[slot[i]] = (T)x[i];
+  for (int64_t i = threadIdx.x; i < nc; i += blockDim.x) u0[slot[i]] = x[i];
 }
 
 template <typename T>
@@ -1174,9 +1180,9 @@ cudaError_t launch_coarse_cg(int64_t nc, const int32_t* slot, const int32_t* ptr
                              const double* val, int64_t nnz, double tol, const T* g0, T* u0, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
   constexpr size_t kMax = 200 * 1024;
-  const size_t vec = 4 * (size_t)nc * sizeof(double);
+  const size_t vec = 4 * (size_t)nc * sizeof(T);
   if (vec > kMax) return cudaErrorInvalidValue;
-  const size_t mat = (size_t)nnz * (sizeof(double) + sizeof(int32_t)) + (size_t)(nc + 1) * sizeof(int32_t);
+  const size_t mat = (size_t)nnz * (sizeof(T) + sizeof(int32_t)) + (size_t)(nc + 1) * sizeof(int32_t);
   const bool smem_matrix = vec + mat <= kMax;
   const size_t sm = smem_matrix ? vec + mat : vec;
   // set once, thread-safe (function-local static)

@@ -489,6 +489,32 @@ def test_solver_variants_match_oracle(torch, name, variant):
         H.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(G.PREC_FP64, 1e-8), (G.PREC_FP32, 1e-3)])
+def test_cg_coarse_solver_meets_its_tolerance(torch, prec, tol):
+    """The unpreconditioned CG coarse solver (Sec. 4.3) iterates in the
+    V-cycle's precision until ||g - A_0 u|| <= tol ||g||: on the Fichera
+    coarse problem (279 unknowns) the true residual of its result, taken
+    with the oracle's A_0 in FP64, meets the tolerance (1e-8 in FP64; the
+    default 1e-3 in FP32, whose rounding stays far below it)."""
+    name = "3d_q2_fichera"
+    O = oracle_hierarchy(name)
+    w = small_workloads()[name]
+    H = G.Hierarchy(G.Context(0), G.build_mesh(w), w.degree, w.coeff, cheb_degree=w.cheb_degree,
+                    vcycle_prec=prec, coarse_solver=G.COARSE_CG, coarse_tol=tol)
+    lev = O.levels[0]
+    idx, cls = level_maps(H, O, 0)
+    rng = np.random.default_rng(23)
+    for _ in range(2):
+        g = rng.uniform(-1, 1, len(lev.keys))
+        u0 = torch.zeros(len(idx), dtype=torch.float64 if prec == G.PREC_FP64 else torch.float32, device="cuda")
+        H.coarse_solve(dev(torch, to_slots(g, idx, len(idx)), prec), u0)
+        torch.cuda.synchronize()
+        u = from_slots(host(u0), idx, len(lev.keys))
+        res = np.linalg.norm(g - lev.A @ u) / np.linalg.norm(g)
+        assert res <= 1.05 * tol, res
+    H.close()
+
+
 @pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
 def test_fichera_mf_setting_matches_oracle(torch, prec):
     """The Laplace example of Sec. 4.3 on the Fichera corner with the paper's
