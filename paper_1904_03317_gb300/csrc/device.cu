@@ -541,11 +541,20 @@ gmg_status device_setup(Hier& h) {
     inv.assign((size_t)nu, 0);
     for (int64_t j = 0; j < nu; ++j) inv[perm[j]] = (int32_t)j;
   }
+  // hanging rows in the order of their number of masters (stable), so that
+  // the threads of a warp in the constraint kernels take rows of one length
+  const int64_t nh = (int64_t)A.hang_key.size();
+  std::vector<int32_t> hold((size_t)nh), hnew((size_t)nh);
+  std::iota(hold.begin(), hold.end(), 0);
+  std::stable_sort(hold.begin(), hold.end(), [&](int32_t x, int32_t y) {
+    return A.hang_ptr[x + 1] - A.hang_ptr[x] < A.hang_ptr[y + 1] - A.hang_ptr[y];
+  });
+  for (int64_t k = 0; k < nh; ++k) hnew[hold[k]] = (int32_t)k;
   auto renumbered = [&](const std::vector<int32_t>& v) {
     std::vector<int32_t> out(v.size());
     const int64_t m = (int64_t)v.size();
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < m; ++i) out[i] = v[i] >= 0 ? inv[v[i]] : v[i];
+    for (int64_t i = 0; i < m; ++i) out[i] = v[i] >= 0 ? inv[v[i]] : (v[i] <= -2 ? -2 - hnew[-2 - v[i]] : v[i]);
     return out;
   };
   // deterministic mode: colour the patches, the groups and the single cells
@@ -631,12 +640,45 @@ gmg_status device_setup(Hier& h) {
   GMG_TRY(upload(d, &d->cell_coeff, A.cell_coeff));
   GMG_TRY(upload(d, &d->cell_level, A.cell_level));
   GMG_TRY(upload(d, &d->cell_coords, A.cell_coords));
-  GMG_TRY(upload(d, &d->hang_ptr, A.hang_ptr));
-  GMG_TRY(upload(d, &d->hang_col, renumbered(A.hang_col)));
+  // constraint rows in the new hanging order; master rows (C^T) ordered by
+  // their number of entries (stable)
+  std::vector<int32_t> hptr(1, 0), hcol, mptr(1, 0), mnode, mhang;
+  std::vector<double> hw, mw;
+  hcol.reserve(A.hang_col.size());
+  hw.reserve(A.hang_w.size());
+  for (int64_t k = 0; k < nh; ++k) {
+    const int32_t h0 = hold[k];
+    for (int32_t m = A.hang_ptr[h0]; m < A.hang_ptr[h0 + 1]; ++m) {
+      hcol.push_back(inv[A.hang_col[m]]);
+      hw.push_back(A.hang_w[m]);
+    }
+    hptr.push_back((int32_t)hcol.size());
+  }
+  {
+    const int64_t nm = (int64_t)A.hm_node.size();
+    std::vector<int32_t> mold((size_t)nm);
+    std::iota(mold.begin(), mold.end(), 0);
+    std::stable_sort(mold.begin(), mold.end(), [&](int32_t x, int32_t y) {
+      return A.hm_ptr[x + 1] - A.hm_ptr[x] < A.hm_ptr[y + 1] - A.hm_ptr[y];
+    });
+    mhang.reserve(A.hm_hang.size());
+    mw.reserve(A.hm_w.size());
+    for (int64_t k = 0; k < nm; ++k) {
+      const int32_t i0 = mold[k];
+      mnode.push_back(inv[A.hm_node[i0]]);
+      for (int32_t j = A.hm_ptr[i0]; j < A.hm_ptr[i0 + 1]; ++j) {
+        mhang.push_back(hnew[A.hm_hang[j]]);
+        mw.push_back(A.hm_w[j]);
+      }
+      mptr.push_back((int32_t)mhang.size());
+    }
+  }
+  GMG_TRY(upload(d, &d->hang_ptr, hptr));
+  GMG_TRY(upload(d, &d->hang_col, hcol));
   {
     // distinct weights (bit-exact) and a code per entry
     std::vector<double> table;
-    std::vector<uint8_t> wc(A.hang_w.size()), mc(A.hm_w.size());
+    std::vector<uint8_t> wc(hw.size()), mc(mw.size());
     auto code = [&](double w, uint8_t& out) {
       for (size_t i = 0; i < table.size(); ++i)
         if (std::memcmp(&table[i], &w, sizeof(double)) == 0) {
@@ -648,13 +690,13 @@ gmg_status device_setup(Hier& h) {
       out = (uint8_t)(table.size() - 1);
       return true;
     };
-    for (size_t m = 0; m < A.hang_w.size(); ++m)
-      if (!code(A.hang_w[m], wc[m])) {
+    for (size_t m = 0; m < hw.size(); ++m)
+      if (!code(hw[m], wc[m])) {
         set_error("more than 256 distinct hanging-node weights");
         return GMG_EUNSUPPORTED;
       }
-    for (size_t m = 0; m < A.hm_w.size(); ++m)
-      if (!code(A.hm_w[m], mc[m])) {
+    for (size_t m = 0; m < mw.size(); ++m)
+      if (!code(mw[m], mc[m])) {
         set_error("more than 256 distinct hanging-node weights");
         return GMG_EUNSUPPORTED;
       }
@@ -667,9 +709,9 @@ gmg_status device_setup(Hier& h) {
   d->n_masters = (int64_t)A.hm_node.size();
   GMG_TRY(dev_alloc(d, &d->xh, (size_t)d->n_hang));
   GMG_TRY(dev_alloc(d, &d->yh, (size_t)d->n_hang));
-  GMG_TRY(upload(d, &d->hm_node, renumbered(A.hm_node)));
-  GMG_TRY(upload(d, &d->hm_ptr, A.hm_ptr));
-  GMG_TRY(upload(d, &d->hm_hang, A.hm_hang));
+  GMG_TRY(upload(d, &d->hm_node, mnode));
+  GMG_TRY(upload(d, &d->hm_ptr, mptr));
+  GMG_TRY(upload(d, &d->hm_hang, mhang));
   GMG_TRY(upload(d, &d->home, home_int));
   GMG_TRY(upload(d, &d->loose, loose_cells));
   GMG_TRY(upload(d, &d->grp_nodes, renumbered(grp_nodes)));
