@@ -1282,7 +1282,6 @@ static gmg_status enqueue_graph_solve(Hier& h, const double* b, double* x, doubl
                                       int fixed_iterations, cudaStream_t s) {
   DeviceState* d = h.dev;
   if (!d->cg_exec) GMG_TRY(build_solve_graph(h));
-  const int64_t n = d->n_unknowns;
   GraphCtl* c = d->ctl_host;
   *c = GraphCtl();
   c->tol = tol;
