@@ -187,6 +187,7 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.n_bricks_all = L.n_bricks_all;
   a.brick_members = L.brick_members;
   a.brick_info = L.brick_info;
+  a.brick_cnb = L.brick_cnb;
   a.iso = L.iso;
   a.list_rest = L.list_rest;
   a.n_rest = L.n_rest;
@@ -291,6 +292,7 @@ void device_free(Hier& h) {
     cudaFree(L.bricks);
     cudaFree(L.brick_members);
     cudaFree(L.brick_info);
+    cudaFree(L.brick_cnb);
     cudaFree(L.list_jump);
     cudaFree(L.list_rest);
     cudaFree(L.list_color);
@@ -466,6 +468,17 @@ gmg_status device_setup(Hier& h) {
     }
     GMG_TRY(upload(d, &D.bricks, bricks));
     GMG_TRY(upload(d, &D.brick_members, H.brick_members));
+    if (dim == 3 && l >= 2 && D.n_bricks > 0) {
+      // the parent group (level l-1) of a full brick's groups and its 27 neighbours
+      const std::vector<int32_t>& cn = h.levels[l - 1].nbr;
+      std::vector<int32_t> cnb((size_t)D.n_bricks * 27);
+      for (int64_t br = 0; br < D.n_bricks; ++br) {
+        const int32_t g0 = bricks[(size_t)br * 64 + 21];  // own group (0, 0, 0)
+        const int64_t p = H.parent[g0];
+        std::copy(cn.begin() + p * 27, cn.begin() + p * 27 + 27, cnb.begin() + br * 27);
+      }
+      GMG_TRY(upload(d, &D.brick_cnb, cnb));
+    }
     {
       // per-brick flags and coefficient, read once per brick by the brick
       // smoother instead of per node

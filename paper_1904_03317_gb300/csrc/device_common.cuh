@@ -52,6 +52,10 @@ struct LevelDev {
   // per brick (full and partial): x = member bits 0..7 | kBrickAllS, y = the
   // bits of the bricks' FP32 coefficient
   uint2* brick_info = nullptr;
+  // per full brick (levels >= 2): the level l-1 neighbour row of the parent
+  // group of its eight groups, so that the transfer kernels need not chase
+  // parent -> neighbour table
+  int32_t* brick_cnb = nullptr;
   bool iso = false;             // cubic cells: one scale factor for all directions
   int32_t* list_rest = nullptr; // groups outside full bricks
   int64_t n_rest = 0;
@@ -87,6 +91,7 @@ struct LevelArgs {
   int64_t n_bricks_all;       // with the partial bricks (smoothing only)
   const uint8_t* brick_members;
   const uint2* brick_info;    // per brick: member bits | kBrickAllS, coefficient bits
+  const int32_t* brick_cnb;   // per full brick: parent group's 27 level l-1 neighbours (l >= 2)
   bool iso;                   // s_x = s_y = s_z (cubic cells)
   const int32_t* list_rest;
   int64_t n_rest;

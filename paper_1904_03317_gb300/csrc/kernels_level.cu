@@ -1126,6 +1126,11 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
   const int tid = threadIdx.x;
   const int64_t br = blockIdx.x;
   if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
+  // mode 2: the parent group's coarse neighbour row, needed only at the end
+  int32_t cnb_pre = 0;
+  if constexpr (MODE == 2) {
+    if (tid < 27) cnb_pre = a.brick_cnb[br * 27 + tid];
+  }
   __syncthreads();
   auto own_group = [&](int bx, int by, int bz) { return tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))]; };
   const unsigned members = MODE == 2 ? 0xFFu : brick_members(a, br);
@@ -1227,7 +1232,7 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
     float* Q1 = Rs + OB * OB * OB;  // [fz][fy][cx]
     float* Q2 = Q1 + OB * OB * NC;  // [fz][cy][cx]
     int32_t* cnb = reinterpret_cast<int32_t*>(Q2 + OB * NC * NC);
-    if (tid < 27) cnb[tid] = a.nbr_coarse[(int64_t)a.parent[own_group(0, 0, 0)] * 27 + tid];
+    if (tid < 27) cnb[tid] = cnb_pre;
     for (int line = tid; line < OB * OB; line += TB) {  // x: (fy, fz)
       float v[OB];
       static_for<0, OB>([&](auto f) { v[f] = Rs[f + OB * line]; });
@@ -2111,6 +2116,7 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
         int64_t nb = a.n_bricks;
         if (det) {
           ac.bricks = a.bricks + a.brick_off[c] * 64;
+          ac.brick_cnb = a.brick_cnb + a.brick_off[c] * 27;
           nb = a.brick_off[c + 1] - a.brick_off[c];
         }
         if (nb == 0) continue;
@@ -2188,10 +2194,28 @@ level_prolongate_brick_kernel(LevelArgs a, const T* __restrict__ uc, T* __restri
   const int tid = threadIdx.x;
   const int64_t br = blockIdx.x;
   if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
+  if (tid < 27) cnb[tid] = a.brick_cnb[br * 27 + tid];
   __syncthreads();
   auto own = [&](int gx, int gy, int gz) { return tab[(gx + 1) + 4 * ((gy + 1) + 4 * (gz + 1))]; };
   if (tid < 32) masks[tid] = a.pmask[(int64_t)own((tid >> 2) & 1, (tid >> 3) & 1, (tid >> 4) & 1) * 4 + (tid & 3)];
-  if (tid < 27) cnb[tid] = a.nbr_coarse[(int64_t)a.parent[own(0, 0, 0)] * 27 + tid];
+  // u at the nodes of this thread's z line that lie in a group's own block
+  // (the only nodes the update adds to), loaded now so that the update does
+  // not wait for them; every fine node has one writer, so the values are
+  // current
+  static_assert(NF * NF <= TB, "one z line per thread: the prefetched line is the written one");
+  T u_pre[NF];
+  {
+    const int line = tid < NF * NF ? tid : 0;
+    const int fx = line % NF, fy = line / NF;
+    const int gx = fx / NO > 1 ? 1 : fx / NO, gy = fy / NO > 1 ? 1 : fy / NO;
+    const int lx = fx - NO * gx, ly = fy - NO * gy;
+    static_for<0, NF>([&](auto r) {
+      constexpr int gz = r / NO > 1 ? 1 : r / NO, lz = r - NO * gz;
+      u_pre[r] = (tid < NF * NF && lx < NO && ly < NO && lz < NO)
+                     ? u[(int64_t)own(gx, gy, gz) * P::NOWN + lx + NO * (ly + NO * lz)]
+                     : T(0);
+    });
+  }
   __syncthreads();
   // coarse nodes of the parent group (its +1 faces from the neighbours)
   for (int i = tid; i < P::C; i += TB) {
@@ -2250,7 +2274,7 @@ level_prolongate_brick_kernel(LevelArgs a, const T* __restrict__ uc, T* __restri
       const int n = lx + NG * (ly + NG * lz);
       const uint64_t bit = 1ull << (n & 63);
       if (masks[gsel * 4 + (n >> 6)] & bit) {
-        u[(int64_t)own(gx, gy, gz) * P::NOWN + lx + NO * (ly + NO * lz)] += v;
+        u[(int64_t)own(gx, gy, gz) * P::NOWN + lx + NO * (ly + NO * lz)] = u_pre[r] + v;
       } else if (masks[gsel * 4 + 2 + (n >> 6)] & bit) {
         const int32_t blk = tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))];
         const int64_t s = (int64_t)blk * P::NOWN + (fx - NO * bx) + NO * ((fy - NO * by) + NO * (r - NO * bz));
