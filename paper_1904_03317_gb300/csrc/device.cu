@@ -188,6 +188,7 @@ static LevelArgs level_args(const Hier& h, int l) {
   a.brick_members = L.brick_members;
   a.brick_info = L.brick_info;
   a.brick_cnb = L.brick_cnb;
+  a.group_cnb = L.group_cnb;
   a.iso = L.iso;
   a.list_rest = L.list_rest;
   a.n_rest = L.n_rest;
@@ -293,6 +294,7 @@ void device_free(Hier& h) {
     cudaFree(L.brick_members);
     cudaFree(L.brick_info);
     cudaFree(L.brick_cnb);
+    cudaFree(L.group_cnb);
     cudaFree(L.list_jump);
     cudaFree(L.list_rest);
     cudaFree(L.list_color);
@@ -468,6 +470,17 @@ gmg_status device_setup(Hier& h) {
     }
     GMG_TRY(upload(d, &D.bricks, bricks));
     GMG_TRY(upload(d, &D.brick_members, H.brick_members));
+    if (l >= 2) {
+      // each group's parent group (level l-1) and its 3^d neighbours
+      const int nnb = ipow_h(3, dim);
+      const std::vector<int32_t>& cn = h.levels[l - 1].nbr;
+      std::vector<int32_t> rows((size_t)H.n_groups * nnb, -1);
+      for (int64_t g = 0; g < H.n_groups; ++g) {
+        const int64_t p = H.parent[g];
+        if (p >= 0) std::copy(cn.begin() + p * nnb, cn.begin() + (p + 1) * nnb, rows.begin() + g * nnb);
+      }
+      GMG_TRY(upload(d, &D.group_cnb, rows));
+    }
     if (dim == 3 && l >= 2 && D.n_bricks > 0) {
       // the parent group (level l-1) of a full brick's groups and its 27 neighbours
       const std::vector<int32_t>& cn = h.levels[l - 1].nbr;

@@ -56,6 +56,7 @@ struct LevelDev {
   // group of its eight groups, so that the transfer kernels need not chase
   // parent -> neighbour table
   int32_t* brick_cnb = nullptr;
+  int32_t* group_cnb = nullptr;  // the same per group (levels >= 2)
   bool iso = false;             // cubic cells: one scale factor for all directions
   int32_t* list_rest = nullptr; // groups outside full bricks
   int64_t n_rest = 0;
@@ -92,6 +93,7 @@ struct LevelArgs {
   const uint8_t* brick_members;
   const uint2* brick_info;    // per brick: member bits | kBrickAllS, coefficient bits
   const int32_t* brick_cnb;   // per full brick: parent group's 27 level l-1 neighbours (l >= 2)
+  const int32_t* group_cnb;   // per group: its parent group's level l-1 neighbours (l >= 2)
   bool iso;                   // s_x = s_y = s_z (cubic cells)
   const int32_t* list_rest;
   int64_t n_rest;

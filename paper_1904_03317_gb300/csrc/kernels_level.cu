@@ -1582,6 +1582,26 @@ __device__ __forceinline__ int64_t parent_node_slot(const LevelArgs& a, int64_t 
   return (int64_t)blk * G::NOWN + loc;
 }
 
+// parent_node_slot with the parent group's level l-1 neighbour row already
+// at hand (`cnb`, levels l >= 2)
+template <int DIM, int K>
+__device__ __forceinline__ int64_t parent_node_slot_row(uint64_t st, const int* jd, const int32_t* cnb) {
+  using G = Geo<DIM, K>;
+  int ni = 0, loc = 0, mul3 = 1, mulo = 1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int pl = (int)((st >> (60 + d)) & 1) * K + jd[d];
+    const int o = pl == 2 * K ? 1 : 0;
+    ni += (o + 1) * mul3;
+    loc += (pl - 2 * K * o) * mulo;
+    mul3 *= 3;
+    mulo *= G::NO;
+  }
+  const int32_t blk = cnb[ni];
+  if (blk < 0) return -1;
+  return (int64_t)blk * G::NOWN + loc;
+}
+
 // ------------------------------------------------- residual + restriction
 // Per group: g_{l-1} += R (w g) - a R A_G u on the parent cell's (K+1)^d nodes.
 // R A_G is again a Kronecker sum, of the (K+1) x (2K+1) products E^T K and
@@ -1777,7 +1797,8 @@ struct ProlongSmem {
   static constexpr int PX = (DIM == 3 ? N1 * N1 : N1) * NG;
   static constexpr int PY = DIM == 3 ? N1 * NG * NG : 0;
   static constexpr int PER = NC + PX + PY;
-  static constexpr size_t HEADER = ((size_t)F::TPB * (8 * 5 + 4 * F::NNB) + 15) / 16 * 16;
+  // per team: state, add[2], set[2], neighbour table, parent's coarse row
+  static constexpr size_t HEADER = ((size_t)F::TPB * (8 * 5 + 8 * F::NNB) + 15) / 16 * 16;
   static constexpr size_t bytes() { return HEADER + (size_t)F::TPB * PER * sizeof(T); }
 };
 
@@ -1796,31 +1817,49 @@ level_prolongate_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u
   const int64_t g = active ? (list ? (int64_t)list[gi] : gi) : 0;
   uint64_t* hdr = reinterpret_cast<uint64_t*>(smem_raw) + team * 5;  // state, add[2], set[2]
   int32_t* nb = reinterpret_cast<int32_t*>(reinterpret_cast<uint64_t*>(smem_raw) + F::TPB * 5) + team * F::NNB;
+  int32_t* crow = reinterpret_cast<int32_t*>(reinterpret_cast<uint64_t*>(smem_raw) + F::TPB * 5) +
+                  (F::TPB + team) * F::NNB;
   T* C = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
   T* PXa = C + S::NC;
   T* PYa = PXa + S::PX;
+  const bool rows = a.group_cnb != nullptr;  // levels >= 2: the coarse row comes with the header
   if (active) {
     for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
+    if (rows)
+      for (int i = lane; i < F::NNB; i += TW) crow[i] = a.group_cnb[g * F::NNB + i];
     if (lane == 0) hdr[0] = a.state[g];
     if (lane < 4) hdr[1 + lane] = a.pmask[g * 4 + lane];
   }
+  // 3D: u at the own-block nodes of this lane's z line (the line it writes
+  // below), loaded with the coarse values so that the update does not wait;
+  // every fine node has one writer
+  constexpr bool PRE = DIM == 3 && NG * NG <= TW;
+  T u_pre[NG];
+  if constexpr (PRE) {
+    const int px = lane % NG, py = lane / NG;
+#pragma unroll
+    for (int r = 0; r < NG; ++r)
+      u_pre[r] = (active && lane < NG * NG && px < NO && py < NO && r < NO) ? u[g * F::NOWN + px + NO * (py + NO * r)]
+                                                                              : T(0);
+  }
   __syncwarp();
   if (active) {
-    const int64_t parent = a.parent[g];
+    const int64_t parent = rows ? 0 : a.parent[g];
     const uint64_t st = hdr[0];
     for (int n = lane; n < S::NC; n += TW) {
       const int jd[3] = {n % N1, DIM > 1 ? (n / N1) % N1 : 0, DIM > 2 ? n / (N1 * N1) : 0};
-      const int64_t s = parent_node_slot<DIM, K>(a, parent, st, jd);
+      const int64_t s = rows ? parent_node_slot_row<DIM, K>(st, jd, crow) : parent_node_slot<DIM, K>(a, parent, st, jd);
       C[n] = s >= 0 ? uc[s] : T(0);
     }
   }
   __syncwarp();
-  auto write = [&](int n, T v) {
+  auto write = [&](int n, T v, T pre) {  // pre: u at n, loaded early (PRE)
     const uint64_t add = hdr[1 + (n >> 6)], set = hdr[3 + (n >> 6)];
     const uint64_t bit = 1ull << (n & 63);
     const int x = n % NG, y = DIM > 1 ? (n / NG) % NG : 0, z = DIM > 2 ? n / (NG * NG) : 0;
     if (add & bit) {
-      u[g * F::NOWN + x + NO * (y + NO * z)] += v;
+      if constexpr (PRE) u[g * F::NOWN + x + NO * (y + NO * z)] = pre + v;
+      else u[g * F::NOWN + x + NO * (y + NO * z)] += v;
     } else if (set & bit) {
       const int ox = x == 2 * K, oy = y == 2 * K, oz = z == 2 * K;
       const int32_t blk = nb[nbi<DIM>(ox, oy, oz)];
@@ -1874,7 +1913,7 @@ level_prolongate_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u
             constexpr double e = embed1<K>(r, j);
             if constexpr (e != 0.0) v += (T)e * c[j];
           });
-          write(line + NG * NG * r, v);
+          write(line + NG * NG * r, v, PRE ? u_pre[r] : T(0));
         });
       }
     }
@@ -1904,7 +1943,7 @@ level_prolongate_kernel(LevelArgs a, const T* __restrict__ uc, T* __restrict__ u
             constexpr double e = embed1<K>(r, j);
             if constexpr (e != 0.0) v += (T)e * c[j];
           });
-          write(x + NG * r, v);
+          write(x + NG * r, v, T(0));
         });
       }
     }
