@@ -1628,7 +1628,8 @@ struct RestrictSmem {
   static constexpr int SX = LX * N1;                       // per array
   static constexpr int SY = DIM == 3 ? NG * N1 * N1 : 0;   // per array
   static constexpr int PER = 3 * SX + 4 * SY;
-  static constexpr size_t HEADER = ((size_t)F::TPB * (8 + sizeof(T) + 4 * F::NNB) + 15) / 16 * 16;
+  // per team: state, coefficient, neighbour table, parent's coarse row
+  static constexpr size_t HEADER = ((size_t)F::TPB * (8 + sizeof(T) + 8 * F::NNB) + 15) / 16 * 16;
   static constexpr size_t bytes() { return HEADER + (size_t)F::TPB * PER * sizeof(T); }
 };
 
@@ -1648,6 +1649,8 @@ level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __
   uint64_t* states = reinterpret_cast<uint64_t*>(smem_raw);
   T* coefs = reinterpret_cast<T*>(states + F::TPB);
   int32_t* nb = reinterpret_cast<int32_t*>(coefs + F::TPB) + team * F::NNB;
+  int32_t* crow = reinterpret_cast<int32_t*>(coefs + F::TPB) + (F::TPB + team) * F::NNB;
+  const bool rows = a.group_cnb != nullptr;  // levels >= 2: the coarse row comes with the header
   T* XM = reinterpret_cast<T*>(smem_raw + S::HEADER) + (size_t)team * S::PER;
   T* XK = XM + S::SX;
   T* XG = XK + S::SX;
@@ -1657,6 +1660,8 @@ level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __
   T* YG = YKM + S::SY;
   if (active) {
     for (int i = lane; i < F::NNB; i += TW) nb[i] = a.nbr[g * F::NNB + i];
+    if (rows)
+      for (int i = lane; i < F::NNB; i += TW) crow[i] = a.group_cnb[g * F::NNB + i];
     if (lane == 0) {
       states[team] = a.state[g];
       coefs[team] = group_coef<T>(a, g);
@@ -1698,7 +1703,7 @@ level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __
   const T sx = level_scale<T>(a, 0), sy = level_scale<T>(a, 1), sz = level_scale<T>(a, 2);
   const T coef = coefs[team];
   const uint64_t st = states[team];
-  const int64_t parent = active ? a.parent[g] : 0;
+  const int64_t parent = active && !rows ? a.parent[g] : 0;
   if constexpr (DIM == 3) {
     // stage y: lines (z, jx); X layout [z][y][jx] -> Y layout [z][jy][jx]
     if (active) {
@@ -1748,7 +1753,7 @@ level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __
             if constexpr (ew != 0.0) rg += (T)ew * pg[c];
           });
           const int jd[3] = {line % N1, line / N1, j};
-          const int64_t slot = parent_node_slot<DIM, K>(a, parent, st, jd);
+          const int64_t slot = rows ? parent_node_slot_row<DIM, K>(st, jd, crow) : parent_node_slot<DIM, K>(a, parent, st, jd);
           if (slot >= 0) {
             if (a.deterministic) gc[slot] += rg - coef * op;  // one colour: parent cells share no node
             else atomicAdd(gc + slot, rg - coef * op);
@@ -1774,7 +1779,7 @@ level_residual_restrict_kernel(LevelArgs a, const T* __restrict__ u, const T* __
             if constexpr (ew != 0.0) rg += (T)ew * vg[c];
           });
           const int jd[3] = {jx, j, 0};
-          const int64_t slot = parent_node_slot<DIM, K>(a, parent, st, jd);
+          const int64_t slot = rows ? parent_node_slot_row<DIM, K>(st, jd, crow) : parent_node_slot<DIM, K>(a, parent, st, jd);
           if (slot >= 0) {
             if (a.deterministic) gc[slot] += rg - coef * op;  // one colour: parent cells share no node
             else atomicAdd(gc + slot, rg - coef * op);
