@@ -1076,309 +1076,6 @@ level_cheb_brick_kernel(LevelArgs a, const T* __restrict__ x, const T* xprev, co
   }
 }
 
-// ------------------- FP64 brick smoother, exact split-integer evaluation
-// For cubic cells (s_x = s_y = s_z = s) the merged brick matrices are the
-// integer matrices ibrick over the element denominators, so the operator of
-// a brick is a s / (DM^2 DK) times an integer Kronecker sum, evaluated as
-// the leaf operator's integer kernels do (int_split.cuh): the halo is loaded
-// once in FP64, split exactly against the brick's largest exponent into
-// P1, P2 (int32) and r (FP32), the three contractions run per component, and
-// the results are recombined in integers and converted to FP64 exactly.  The
-// Chebyshev update stays in FP64.  This takes the FP64 smoother's
-// contractions off the FP64 pipe, a small fraction of this GPU's int32/FP32
-// throughput.  Layout, halo and outputs are those of level_cheb_brick_kernel.
-template <int K, bool STIFF>
-__host__ __device__ constexpr int ibrick(int r, int c) {
-  const int p = c - K;
-  int v = 0;
-  for (int cell = -1; cell < 4; ++cell) {
-    const int lo = K * cell;
-    if (r >= lo && r <= lo + K && p >= lo && p <= lo + K) v += ielem1<K, STIFF>(r - lo, p - lo);
-  }
-  return v;
-}
-
-// the integer brick matrices are the FP64 ones times the element denominators
-template <int K>
-constexpr bool ibrick_matches() {
-  for (int r = 0; r < 4 * K; ++r)
-    for (int c = 0; c <= 5 * K; ++c) {
-      const double dm = bbrick<K, false>(r, c) * IntElem<K>::DM - ibrick<K, false>(r, c);
-      const double dk = bbrick<K, true>(r, c) * IntElem<K>::DK - ibrick<K, true>(r, c);
-      if (dm > 1e-12 || dm < -1e-12 || dk > 1e-12 || dk < -1e-12) return false;
-    }
-  return true;
-}
-static_assert(ibrick_matches<1>() && ibrick_matches<2>(), "integer brick matrices");
-
-// largest sum of |entries| over the rows of an integer brick matrix
-template <int K, bool STIFF>
-constexpr long long ibrick_rowsum() {
-  long long best = 0;
-  for (int r = 0; r < 4 * K; ++r) {
-    long long t = 0;
-    for (int c = 0; c <= 5 * K; ++c) t += ibrick<K, STIFF>(r, c) < 0 ? -ibrick<K, STIFF>(r, c) : ibrick<K, STIFF>(r, c);
-    best = t > best ? t : best;
-  }
-  return best;
-}
-
-template <int K>
-struct BrickI {
-  using B = BrickG<K>;
-  static constexpr int HB = B::HB, OB = B::OB;
-  static constexpr int NH = HB * HB * HB;     // halo values
-  static constexpr int T1 = HB * HB * OB;     // stage-1 outputs per matrix and component
-  static constexpr int ZS = OB * OB + (OB == 8 ? 8 : 4);  // padded z stride of the stage-2 arrays
-  static constexpr int T2 = HB * ZS;
-  // bound of the integer Kronecker sum per unit input (38,400 for Q2)
-  static constexpr long long BOUND =
-      3 * ibrick_rowsum<K, false>() * ibrick_rowsum<K, false>() * ibrick_rowsum<K, true>();
-  static constexpr int KR = int_recombination_bits_bound(BOUND);
-  // region 1: the stage-1 outputs (M, K) of the three components; region 2:
-  // the FP64 halo with its split parts (P1 and P2 as int2, r), overwritten by
-  // the stage-2 outputs (MM, MK, KM) of the three components
-  static constexpr size_t R1 = (size_t)6 * T1 * 4;
-  static constexpr size_t HALO = (size_t)NH * (8 + 8 + 4);
-  static constexpr size_t STAGE2 = (size_t)9 * T2 * 4;
-  static constexpr size_t R2 = ((HALO > STAGE2 ? HALO : STAGE2) + 15) / 16 * 16;
-  static constexpr size_t bytes() { return R1 + R2 + 64 * 4 + 8 * 8 + 16; }
-  static_assert(R1 % 16 == 0 && (6 * T2 * 4) % 16 == 0, "16-byte aligned arrays");
-};
-
-// four 4-byte values to 16-byte aligned shared memory
-template <typename T>
-__device__ __forceinline__ void st4(T* p, const T* v) {
-  if constexpr (std::is_same<T, int>::value) *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
-  else *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-
-template <int K, int MODE>
-__global__ void __launch_bounds__(BrickG<K>::TB)
-level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const double* xprev,
-                            const double* __restrict__ gvec, double* out, double c1, double c2) {
-  using B = BrickG<K>;
-  using S = BrickI<K>;
-  constexpr int NO = B::NO, OB = B::OB, HB = B::HB, TB = B::TB, L3 = B::L3, R = B::R, OPT = B::OPT;
-  constexpr int NH = S::NH, T1 = S::T1, T2 = S::T2, ZS = S::ZS, KR = S::KR;
-  static_assert(S::BOUND * 32768LL < 2147483648LL, "integer Kronecker sum exceeds int32");
-  static_assert(KR >= 5 && int_recombination_fits_bound(S::BOUND, KR), "integer recombination exceeds 2^51");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int* T1i = reinterpret_cast<int*>(smem_raw);          // P1 (M, K), P2 (M, K)
-  float* T1f = reinterpret_cast<float*>(T1i + 4 * T1);  // r (M, K)
-  unsigned char* r2 = smem_raw + S::R1;
-  double* X = reinterpret_cast<double*>(r2);
-  int2* P12 = reinterpret_cast<int2*>(X + NH);
-  float* Rr = reinterpret_cast<float*>(P12 + NH);
-  int* T2i = reinterpret_cast<int*>(r2);                // P1 (MM, MK, KM), P2 (MM, MK, KM)
-  float* T2f = reinterpret_cast<float*>(T2i + 6 * T2);  // r (MM, MK, KM)
-  int32_t* tab = reinterpret_cast<int32_t*>(r2 + S::R2);
-  uint64_t* smask = reinterpret_cast<uint64_t*>(tab + 64);
-  int* emax = reinterpret_cast<int*>(smask + 8);
-  const int tid = threadIdx.x;
-  const int64_t br = blockIdx.x;
-  if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
-  if (tid == 0) *emax = 1;
-  __syncthreads();
-  auto own_group = [&](int bx, int by, int bz) { return tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))]; };
-  const unsigned members = brick_members(a, br);
-  if (tid < 8) smask[tid] = ((members >> tid) & 1u) ? a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)] : 0ull;
-  const int m0 = __ffs(members) - 1;  // a member: the coefficient is common to all
-  const double coef = a.coeff[own_group(m0 & 1, (m0 >> 1) & 1, m0 >> 2)];
-  // this thread's outputs: line ol = (i, j), k = part + R * o
-  const int ol = tid % L3, part = tid / L3;
-  const bool has_out = tid < L3 * R;
-  const int oi = ol % OB, oj = ol / OB;
-  double pre_xp[OPT], pre_g[OPT], xv[OPT];
-  int64_t slots[OPT];
-#pragma unroll
-  for (int o = 0; o < OPT; ++o) {
-    const int kk = part + R * o;
-    slots[o] = -1;
-    pre_xp[o] = pre_g[o] = xv[o] = 0.0;
-    if (has_out && kk < OB && ((members >> ((oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO)))) & 1u)) {
-      const int32_t gid = own_group(oi / NO, oj / NO, kk / NO);
-      slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
-      if constexpr (MODE == 1) {
-        pre_g[o] = gvec[slots[o]];
-        if (xprev) pre_xp[o] = xprev[slots[o]];
-      }
-    }
-  }
-  // the halo in FP64 (four segments per x line: groups -1, 0, 1, 2) and its
-  // largest biased exponent
-  int ex = 0;
-  for (int line = tid; line < HB * HB; line += TB) {
-    int gy, ly, gz, lz;
-    brick_seg<K>(line % HB, gy, ly);
-    brick_seg<K>(line / HB, gz, lz);
-    const int row = NO * (ly + NO * lz);
-    const int tb = 4 * ((gy + 1) + 4 * (gz + 1));
-    double v[HB];
-    const int32_t b0 = tab[tb + 0], b1 = tab[tb + 1], b2 = tab[tb + 2], b3 = tab[tb + 3];
-    if (b0 >= 0) load_run<double, K>(x + (int64_t)b0 * B::NOWN + row + K, v);
-    else for (int i = 0; i < K; ++i) v[i] = 0.0;
-    if (b1 >= 0) load_run<double, 2 * K>(x + (int64_t)b1 * B::NOWN + row, v + K);
-    else for (int i = 0; i < 2 * K; ++i) v[K + i] = 0.0;
-    if (b2 >= 0) load_run<double, 2 * K>(x + (int64_t)b2 * B::NOWN + row, v + 3 * K);
-    else for (int i = 0; i < 2 * K; ++i) v[3 * K + i] = 0.0;
-    v[5 * K] = b3 >= 0 ? x[(int64_t)b3 * B::NOWN + row] : 0.0;
-    static_for<0, HB>([&](auto c) {
-      X[line * HB + c] = v[c];
-      const int e = (int)((__double_as_longlong(v[c]) >> 52) & 0x7FF);
-      ex = e > ex ? e : ex;
-    });
-  }
-  ex = __reduce_max_sync(0xffffffffu, ex);
-  if ((tid & 31) == 0) atomicMax(emax, ex);
-  __syncthreads();
-  // exact split against q = 2^(emax - 1037): |x| < 2^15 q; a NaN or Inf in
-  // the halo makes the brick's outputs NaN
-  const int em = *emax;
-  const int eq = em == 0x7FF ? 1010 : em - 1037;
-  for (int e = tid; e < NH; e += TB) {
-    int p1, p2;
-    float r;
-    split_exact(X[e], eq, p1, p2, r);
-    P12[e] = make_int2(p1, p2);
-    Rr[e] = r;
-  }
-  // own values for the update, read before the stage-2 outputs overwrite the halo
-  if constexpr (MODE == 1) {
-#pragma unroll
-    for (int o = 0; o < OPT; ++o) {
-      const int kk = part + R * o;
-      if (slots[o] >= 0) xv[o] = X[(oi + K) + HB * ((oj + K) + HB * (kk + K))];
-    }
-  }
-  __syncthreads();
-  // stage 1: x direction per halo line (M and K rows), per component
-  for (int line = tid; line < HB * HB; line += TB) {
-    auto xrows = [&](const auto* v, auto* oM, auto* oK) {
-      using T = std::remove_const_t<std::remove_reference_t<decltype(v[0])>>;
-      T m[OB], k[OB];
-      static_for<0, OB>([&](auto r) {
-        T sm = 0, sk = 0;
-        static_for<0, HB>([&](auto c) {
-          constexpr int bm = ibrick<K, false>(r, c), bk = ibrick<K, true>(r, c);
-          if constexpr (bm != 0) sm += (T)bm * v[c];
-          if constexpr (bk != 0) sk += (T)bk * v[c];
-        });
-        m[r] = sm;
-        k[r] = sk;
-      });
-      static_for<0, OB / 4>([&](auto h) {
-        st4<T>(oM + line * OB + 4 * h, m + 4 * h);
-        st4<T>(oK + line * OB + 4 * h, k + 4 * h);
-      });
-    };
-    int v1[HB], v2[HB];
-    float v3[HB];
-    static_for<0, HB>([&](auto c) {
-      const int2 p = P12[line * HB + c];
-      v1[c] = p.x;
-      v2[c] = p.y;
-      v3[c] = Rr[line * HB + c];
-    });
-    xrows(v1, T1i, T1i + T1);
-    xrows(v2, T1i + 2 * T1, T1i + 3 * T1);
-    xrows(v3, T1f, T1f + T1);
-  }
-  __syncthreads();
-  // stage 2: y direction, lines (z, i), per component
-  for (int line = tid; line < HB * OB; line += TB) {
-    const int z = line / OB, i = line % OB;
-    auto yrows = [&](const auto* iM, const auto* iK, auto* oMM, auto* oMK, auto* oKM) {
-      using T = std::remove_const_t<std::remove_reference_t<decltype(iM[0])>>;
-      T vm[HB], vk[HB];
-      static_for<0, HB>([&](auto y) {
-        vm[y] = iM[(z * HB + y) * OB + i];
-        vk[y] = iK[(z * HB + y) * OB + i];
-      });
-      static_for<0, OB>([&](auto j) {
-        T mm = 0, mk = 0, km = 0;
-        static_for<0, HB>([&](auto c) {
-          constexpr int bm = ibrick<K, false>(j, c), bk = ibrick<K, true>(j, c);
-          if constexpr (bm != 0) {
-            mm += (T)bm * vm[c];
-            km += (T)bm * vk[c];
-          }
-          if constexpr (bk != 0) mk += (T)bk * vm[c];
-        });
-        const int o = z * ZS + j * OB + i;
-        oMM[o] = mm;
-        oMK[o] = mk;
-        oKM[o] = km;
-      });
-    };
-    yrows(T1i, T1i + T1, T2i, T2i + T2, T2i + 2 * T2);
-    yrows(T1i + 2 * T1, T1i + 3 * T1, T2i + 3 * T2, T2i + 4 * T2, T2i + 5 * T2);
-    yrows(T1f, T1f + T1, T2f, T2f + T2, T2f + 2 * T2);
-  }
-  __syncthreads();
-  // stage 3: z direction per component, then the recombination and the update
-  if (!has_out) return;
-  int o1[OPT], o2[OPT];
-  float o3[OPT];
-  auto zrows = [&](const auto* iMM, const auto* iMK, const auto* iKM, auto* acc) {
-    using T = std::remove_const_t<std::remove_reference_t<decltype(iMM[0])>>;
-    T p[HB], q[HB];
-    static_for<0, HB>([&](auto z) {
-      p[z] = iMM[z * ZS + ol];
-      q[z] = iMK[z * ZS + ol] + iKM[z * ZS + ol];
-    });
-    own_rows<OB, R>(part, [&](auto o, auto r) {
-      T y = 0;
-      static_for<0, HB>([&](auto c) {
-        constexpr int bm = ibrick<K, false>(r, c), bk = ibrick<K, true>(r, c);
-        if constexpr (bk != 0) y += (T)bk * p[c];
-        if constexpr (bm != 0) y += (T)bm * q[c];
-      });
-      acc[o] = y;
-    });
-  };
-#pragma unroll
-  for (int o = 0; o < OPT; ++o) {
-    o1[o] = o2[o] = 0;
-    o3[o] = 0.f;
-  }
-  zrows(T2i, T2i + T2, T2i + 2 * T2, o1);
-  zrows(T2i + 3 * T2, T2i + 4 * T2, T2i + 5 * T2, o2);
-  zrows(T2f, T2f + T2, T2f + 2 * T2, o3);
-  constexpr double DEN = (double)IntElem<K>::DM * IntElem<K>::DM * IntElem<K>::DK;
-  // q 2^-15 2^-KR = 2^(emax - 1037 - 15 - KR)
-  const double sc = em == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
-                                : coef * a.scale[0] / DEN * ldexp(1.0, em - 1052 - KR);
-  double c2d = 0.0;
-  if constexpr (MODE == 1) {
-    // one reciprocal of the diagonal per thread, as in level_cheb_brick_kernel
-    const double s = a.scale[0];
-    const double md0 = bbrick<K, false>(0, K), kd0 = bbrick<K, true>(0, K);
-    const double md1 = bbrick<K, false>(1, K + 1), kd1 = bbrick<K, true>(1, K + 1);
-    const double mdx = (oi & 1) ? md1 : md0, kdx = (oi & 1) ? kd1 : kd0;
-    const double mdy = (oj & 1) ? md1 : md0, kdy = (oj & 1) ? kd1 : kd0;
-    const double mdz = (part & 1) ? md1 : md0, kdz = (part & 1) ? kd1 : kd0;
-    c2d = c2 / (coef * (s * kdx * mdy * mdz + s * mdx * kdy * mdz + s * mdx * mdy * kdz));
-  }
-  static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share the parity of k");
-#pragma unroll
-  for (int o = 0; o < OPT; ++o) {
-    const int kk = part + R * o;
-    if (kk >= OB) break;
-    const int gsel = (oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO));
-    const int node = (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
-    if (!((smask[gsel] >> node) & 1ull)) continue;
-    const double t = i64_to_double(((long long)o1[o] << (15 + KR)) + ((long long)o2[o] << KR) +
-                                   (long long)f32_fixed_rint<KR>(o3[o]));
-    const double y = t * sc;
-    if constexpr (MODE == 0) {
-      out[slots[o]] = y;
-    } else {
-      out[slots[o]] = xv[o] + c1 * (xv[o] - pre_xp[o]) + c2d * (pre_g[o] - y);
-    }
-  }
-}
-
 // FP32 brick kernel with packed two-wide FMAs (fma.rn.f32x2): stage 1 forms
 // the mass and stiffness rows of a halo line as one pair, stage 2 pairs the
 // two stage-1 results and stores the two stage-3 operands (p, q) as a pair,
@@ -1625,6 +1322,389 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
       out[slots[o]] = xv + c1 * (xv - pre_xp[o]) + c2d[r & 1] * (pre_g[o] - y);
     }
   });
+}
+
+// ------------------- FP64 brick smoother, exact split-integer evaluation
+// For cubic cells (s_x = s_y = s_z = s) the merged brick matrices are the
+// integer matrices ibrick over the element denominators, so the operator of
+// a brick is a s / (DM^2 DK) times an integer Kronecker sum, evaluated as
+// the leaf operator's integer kernels do (int_split.cuh): the halo is loaded
+// once in FP64, split exactly against the brick's largest exponent into
+// P1, P2 (int32) and r (FP32), the three contractions run per component, and
+// the results are recombined in integers and converted to FP64 exactly.  The
+// Chebyshev update stays in FP64.  This takes the FP64 smoother's
+// contractions off the FP64 pipe, a small fraction of this GPU's int32/FP32
+// throughput.  Layout, halo and outputs are those of level_cheb_brick_kernel;
+// MODE 2 is the residual + restriction pass of level_cheb_brick_f2_kernel
+// (full bricks, levels >= 2 without refinement-edge nodes), with the
+// restriction in FP64.
+template <int K, bool STIFF>
+__host__ __device__ constexpr int ibrick(int r, int c) {
+  const int p = c - K;
+  int v = 0;
+  for (int cell = -1; cell < 4; ++cell) {
+    const int lo = K * cell;
+    if (r >= lo && r <= lo + K && p >= lo && p <= lo + K) v += ielem1<K, STIFF>(r - lo, p - lo);
+  }
+  return v;
+}
+
+// the integer brick matrices are the FP64 ones times the element denominators
+template <int K>
+constexpr bool ibrick_matches() {
+  for (int r = 0; r < 4 * K; ++r)
+    for (int c = 0; c <= 5 * K; ++c) {
+      const double dm = bbrick<K, false>(r, c) * IntElem<K>::DM - ibrick<K, false>(r, c);
+      const double dk = bbrick<K, true>(r, c) * IntElem<K>::DK - ibrick<K, true>(r, c);
+      if (dm > 1e-12 || dm < -1e-12 || dk > 1e-12 || dk < -1e-12) return false;
+    }
+  return true;
+}
+static_assert(ibrick_matches<1>() && ibrick_matches<2>(), "integer brick matrices");
+
+// largest sum of |entries| over the rows of an integer brick matrix
+template <int K, bool STIFF>
+constexpr long long ibrick_rowsum() {
+  long long best = 0;
+  for (int r = 0; r < 4 * K; ++r) {
+    long long t = 0;
+    for (int c = 0; c <= 5 * K; ++c) t += ibrick<K, STIFF>(r, c) < 0 ? -ibrick<K, STIFF>(r, c) : ibrick<K, STIFF>(r, c);
+    best = t > best ? t : best;
+  }
+  return best;
+}
+
+template <int K>
+struct BrickI {
+  using B = BrickG<K>;
+  static constexpr int HB = B::HB, OB = B::OB;
+  static constexpr int NH = HB * HB * HB;     // halo values
+  static constexpr int T1 = HB * HB * OB;     // stage-1 outputs per matrix and component
+  static constexpr int ZS = OB * OB + (OB == 8 ? 8 : 4);  // padded z stride of the stage-2 arrays
+  static constexpr int T2 = HB * ZS;
+  // bound of the integer Kronecker sum per unit input (38,400 for Q2)
+  static constexpr long long BOUND =
+      3 * ibrick_rowsum<K, false>() * ibrick_rowsum<K, false>() * ibrick_rowsum<K, true>();
+  static constexpr int KR = int_recombination_bits_bound(BOUND);
+  // region 1: the stage-1 outputs (M, K) of the three components; region 2:
+  // the FP64 halo with its split parts (P1 and P2 as int2, r), overwritten by
+  // the stage-2 outputs (MM, MK, KM) of the three components
+  static constexpr size_t R1 = (size_t)6 * T1 * 4;
+  static constexpr size_t HALO = (size_t)NH * (8 + 8 + 4);
+  static constexpr size_t STAGE2 = (size_t)9 * T2 * 4;
+  static constexpr size_t R2 = ((HALO > STAGE2 ? HALO : STAGE2) + 15) / 16 * 16;
+  static constexpr size_t bytes() { return R1 + R2 + 64 * 4 + 8 * 8 + 16; }
+  static_assert(R1 % 16 == 0 && (6 * T2 * 4) % 16 == 0, "16-byte aligned arrays");
+};
+
+// four 4-byte values to 16-byte aligned shared memory
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T* v) {
+  if constexpr (std::is_same<T, int>::value) *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(BrickG<K>::TB)
+level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const double* xprev,
+                            const double* __restrict__ gvec, double* out, double c1, double c2) {
+  using B = BrickG<K>;
+  using S = BrickI<K>;
+  constexpr int NO = B::NO, OB = B::OB, HB = B::HB, TB = B::TB, L3 = B::L3, R = B::R, OPT = B::OPT;
+  constexpr int NH = S::NH, T1 = S::T1, T2 = S::T2, ZS = S::ZS, KR = S::KR;
+  static_assert(S::BOUND * 32768LL < 2147483648LL, "integer Kronecker sum exceeds int32");
+  static_assert(KR >= 5 && int_recombination_fits_bound(S::BOUND, KR), "integer recombination exceeds 2^51");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* T1i = reinterpret_cast<int*>(smem_raw);          // P1 (M, K), P2 (M, K)
+  float* T1f = reinterpret_cast<float*>(T1i + 4 * T1);  // r (M, K)
+  unsigned char* r2 = smem_raw + S::R1;
+  double* X = reinterpret_cast<double*>(r2);
+  int2* P12 = reinterpret_cast<int2*>(X + NH);
+  float* Rr = reinterpret_cast<float*>(P12 + NH);
+  int* T2i = reinterpret_cast<int*>(r2);                // P1 (MM, MK, KM), P2 (MM, MK, KM)
+  float* T2f = reinterpret_cast<float*>(T2i + 6 * T2);  // r (MM, MK, KM)
+  int32_t* tab = reinterpret_cast<int32_t*>(r2 + S::R2);
+  uint64_t* smask = reinterpret_cast<uint64_t*>(tab + 64);
+  int* emax = reinterpret_cast<int*>(smask + 8);
+  const int tid = threadIdx.x;
+  const int64_t br = blockIdx.x;
+  if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
+  if (tid == 0) *emax = 1;
+  // mode 2: the parent group's coarse neighbour row, needed only at the end
+  int32_t cnb_pre = 0;
+  if constexpr (MODE == 2) {
+    if (tid < 27) cnb_pre = a.brick_cnb[br * 27 + tid];
+  }
+  __syncthreads();
+  auto own_group = [&](int bx, int by, int bz) { return tab[(bx + 1) + 4 * ((by + 1) + 4 * (bz + 1))]; };
+  const unsigned members = MODE == 2 ? 0xFFu : brick_members(a, br);
+  if (tid < 8) smask[tid] = ((members >> tid) & 1u) ? a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)] : 0ull;
+  const int m0 = __ffs(members) - 1;  // a member: the coefficient is common to all
+  const double coef = a.coeff[own_group(m0 & 1, (m0 >> 1) & 1, m0 >> 2)];
+  // this thread's outputs: line ol = (i, j), k = part + R * o
+  const int ol = tid % L3, part = tid / L3;
+  const bool has_out = tid < L3 * R;
+  const int oi = ol % OB, oj = ol / OB;
+  double pre_xp[OPT], pre_g[OPT], xv[OPT];
+  int64_t slots[OPT];
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    slots[o] = -1;
+    pre_xp[o] = pre_g[o] = xv[o] = 0.0;
+    if (has_out && kk < OB && ((members >> ((oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO)))) & 1u)) {
+      const int32_t gid = own_group(oi / NO, oj / NO, kk / NO);
+      slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
+      if constexpr (MODE >= 1) pre_g[o] = gvec[slots[o]];
+      if constexpr (MODE == 1) {
+        if (xprev) pre_xp[o] = xprev[slots[o]];
+      }
+    }
+  }
+  // the halo in FP64 (four segments per x line: groups -1, 0, 1, 2) and its
+  // largest biased exponent
+  int ex = 0;
+  for (int line = tid; line < HB * HB; line += TB) {
+    int gy, ly, gz, lz;
+    brick_seg<K>(line % HB, gy, ly);
+    brick_seg<K>(line / HB, gz, lz);
+    const int row = NO * (ly + NO * lz);
+    const int tb = 4 * ((gy + 1) + 4 * (gz + 1));
+    double v[HB];
+    const int32_t b0 = tab[tb + 0], b1 = tab[tb + 1], b2 = tab[tb + 2], b3 = tab[tb + 3];
+    if (b0 >= 0) load_run<double, K>(x + (int64_t)b0 * B::NOWN + row + K, v);
+    else for (int i = 0; i < K; ++i) v[i] = 0.0;
+    if (b1 >= 0) load_run<double, 2 * K>(x + (int64_t)b1 * B::NOWN + row, v + K);
+    else for (int i = 0; i < 2 * K; ++i) v[K + i] = 0.0;
+    if (b2 >= 0) load_run<double, 2 * K>(x + (int64_t)b2 * B::NOWN + row, v + 3 * K);
+    else for (int i = 0; i < 2 * K; ++i) v[3 * K + i] = 0.0;
+    v[5 * K] = b3 >= 0 ? x[(int64_t)b3 * B::NOWN + row] : 0.0;
+    static_for<0, HB>([&](auto c) {
+      X[line * HB + c] = v[c];
+      const int e = (int)((__double_as_longlong(v[c]) >> 52) & 0x7FF);
+      ex = e > ex ? e : ex;
+    });
+  }
+  ex = __reduce_max_sync(0xffffffffu, ex);
+  if ((tid & 31) == 0) atomicMax(emax, ex);
+  __syncthreads();
+  // exact split against q = 2^(emax - 1037): |x| < 2^15 q; a NaN or Inf in
+  // the halo makes the brick's outputs NaN
+  const int em = *emax;
+  const int eq = em == 0x7FF ? 1010 : em - 1037;
+  for (int e = tid; e < NH; e += TB) {
+    int p1, p2;
+    float r;
+    split_exact(X[e], eq, p1, p2, r);
+    P12[e] = make_int2(p1, p2);
+    Rr[e] = r;
+  }
+  // own values for the update, read before the stage-2 outputs overwrite the halo
+  if constexpr (MODE == 1) {
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+      const int kk = part + R * o;
+      if (slots[o] >= 0) xv[o] = X[(oi + K) + HB * ((oj + K) + HB * (kk + K))];
+    }
+  }
+  __syncthreads();
+  // stage 1: x direction per halo line (M and K rows), per component
+  for (int line = tid; line < HB * HB; line += TB) {
+    auto xrows = [&](const auto* v, auto* oM, auto* oK) {
+      using T = std::remove_const_t<std::remove_reference_t<decltype(v[0])>>;
+      T m[OB], k[OB];
+      static_for<0, OB>([&](auto r) {
+        T sm = 0, sk = 0;
+        static_for<0, HB>([&](auto c) {
+          constexpr int bm = ibrick<K, false>(r, c), bk = ibrick<K, true>(r, c);
+          if constexpr (bm != 0) sm += (T)bm * v[c];
+          if constexpr (bk != 0) sk += (T)bk * v[c];
+        });
+        m[r] = sm;
+        k[r] = sk;
+      });
+      static_for<0, OB / 4>([&](auto h) {
+        st4<T>(oM + line * OB + 4 * h, m + 4 * h);
+        st4<T>(oK + line * OB + 4 * h, k + 4 * h);
+      });
+    };
+    int v1[HB], v2[HB];
+    float v3[HB];
+    static_for<0, HB>([&](auto c) {
+      const int2 p = P12[line * HB + c];
+      v1[c] = p.x;
+      v2[c] = p.y;
+      v3[c] = Rr[line * HB + c];
+    });
+    xrows(v1, T1i, T1i + T1);
+    xrows(v2, T1i + 2 * T1, T1i + 3 * T1);
+    xrows(v3, T1f, T1f + T1);
+  }
+  __syncthreads();
+  // stage 2: y direction, lines (z, i), per component
+  for (int line = tid; line < HB * OB; line += TB) {
+    const int z = line / OB, i = line % OB;
+    auto yrows = [&](const auto* iM, const auto* iK, auto* oMM, auto* oMK, auto* oKM) {
+      using T = std::remove_const_t<std::remove_reference_t<decltype(iM[0])>>;
+      T vm[HB], vk[HB];
+      static_for<0, HB>([&](auto y) {
+        vm[y] = iM[(z * HB + y) * OB + i];
+        vk[y] = iK[(z * HB + y) * OB + i];
+      });
+      static_for<0, OB>([&](auto j) {
+        T mm = 0, mk = 0, km = 0;
+        static_for<0, HB>([&](auto c) {
+          constexpr int bm = ibrick<K, false>(j, c), bk = ibrick<K, true>(j, c);
+          if constexpr (bm != 0) {
+            mm += (T)bm * vm[c];
+            km += (T)bm * vk[c];
+          }
+          if constexpr (bk != 0) mk += (T)bk * vm[c];
+        });
+        const int o = z * ZS + j * OB + i;
+        oMM[o] = mm;
+        oMK[o] = mk;
+        oKM[o] = km;
+      });
+    };
+    yrows(T1i, T1i + T1, T2i, T2i + T2, T2i + 2 * T2);
+    yrows(T1i + 2 * T1, T1i + 3 * T1, T2i + 3 * T2, T2i + 4 * T2, T2i + 5 * T2);
+    yrows(T1f, T1f + T1, T2f, T2f + T2, T2f + 2 * T2);
+  }
+  __syncthreads();
+  // stage 3: z direction per component, then the recombination and the update
+  int o1[OPT], o2[OPT];
+  float o3[OPT];
+  auto zrows = [&](const auto* iMM, const auto* iMK, const auto* iKM, auto* acc) {
+    using T = std::remove_const_t<std::remove_reference_t<decltype(iMM[0])>>;
+    T p[HB], q[HB];
+    static_for<0, HB>([&](auto z) {
+      p[z] = iMM[z * ZS + ol];
+      q[z] = iMK[z * ZS + ol] + iKM[z * ZS + ol];
+    });
+    own_rows<OB, R>(part, [&](auto o, auto r) {
+      T y = 0;
+      static_for<0, HB>([&](auto c) {
+        constexpr int bm = ibrick<K, false>(r, c), bk = ibrick<K, true>(r, c);
+        if constexpr (bk != 0) y += (T)bk * p[c];
+        if constexpr (bm != 0) y += (T)bm * q[c];
+      });
+      acc[o] = y;
+    });
+  };
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    o1[o] = o2[o] = 0;
+    o3[o] = 0.f;
+  }
+  if (has_out) {
+    zrows(T2i, T2i + T2, T2i + 2 * T2, o1);
+    zrows(T2i + 3 * T2, T2i + 4 * T2, T2i + 5 * T2, o2);
+    zrows(T2f, T2f + T2, T2f + 2 * T2, o3);
+  }
+  constexpr double DEN = (double)IntElem<K>::DM * IntElem<K>::DM * IntElem<K>::DK;
+  // q 2^-15 2^-KR = 2^(emax - 1037 - 15 - KR)
+  const double sc = em == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
+                                : coef * a.scale[0] / DEN * ldexp(1.0, em - 1052 - KR);
+  auto result = [&](int o) {
+    return sc * i64_to_double(((long long)o1[o] << (15 + KR)) + ((long long)o2[o] << KR) +
+                              (long long)f32_fixed_rint<KR>(o3[o]));
+  };
+  if constexpr (MODE == 2) {
+    // residual on the own nodes (region 1 is free after stage 2), then
+    // g_{l-1} += R r over the parent group's coarse nodes, in FP64
+    double* Rs = reinterpret_cast<double*>(smem_raw);
+    if (has_out) {
+#pragma unroll
+      for (int o = 0; o < OPT; ++o) {
+        const int kk = part + R * o;
+        if (kk < OB) Rs[oi + OB * (oj + OB * kk)] = pre_g[o] - result(o);
+      }
+    }
+    __syncthreads();
+    constexpr int NC = 2 * K + 1;     // coarse nodes per direction of the parent group
+    double* Q1 = Rs + OB * OB * OB;   // [fz][fy][cx]
+    double* Q2 = Q1 + OB * OB * NC;   // [fz][cy][cx]
+    int32_t* cnb = reinterpret_cast<int32_t*>(Q2 + OB * NC * NC);
+    static_assert((OB * OB * OB + OB * OB * NC + OB * NC * NC) * 8 + 27 * 4 <= S::R1, "restriction fits region 1");
+    if (tid < 27) cnb[tid] = cnb_pre;
+    for (int line = tid; line < OB * OB; line += TB) {  // x: (fy, fz)
+      double v[OB];
+      static_for<0, OB>([&](auto f) { v[f] = Rs[f + OB * line]; });
+      static_for<0, NC>([&](auto c) {
+        double t = 0.0;
+        static_for<0, OB>([&](auto f) {
+          constexpr double e = ebrick<K>(f, c);
+          if constexpr (e != 0.0) t += e * v[f];
+        });
+        Q1[line * NC + c] = t;
+      });
+    }
+    __syncthreads();
+    for (int line = tid; line < OB * NC; line += TB) {  // y: (fz, cx)
+      const int fz = line / NC, cx = line % NC;
+      double v[OB];
+      static_for<0, OB>([&](auto f) { v[f] = Q1[(fz * OB + f) * NC + cx]; });
+      static_for<0, NC>([&](auto c) {
+        double t = 0.0;
+        static_for<0, OB>([&](auto f) {
+          constexpr double e = ebrick<K>(f, c);
+          if constexpr (e != 0.0) t += e * v[f];
+        });
+        Q2[(fz * NC + c) * NC + cx] = t;
+      });
+    }
+    __syncthreads();
+    for (int line = tid; line < NC * NC; line += TB) {  // z: (cx, cy), then add into g_{l-1}
+      const int cx = line % NC, cy = line / NC;
+      double v[OB];
+      static_for<0, OB>([&](auto f) { v[f] = Q2[(f * NC + cy) * NC + cx]; });
+      static_for<0, NC>([&](auto cz) {
+        double t = 0.0;
+        static_for<0, OB>([&](auto f) {
+          constexpr double e = ebrick<K>(f, cz);
+          if constexpr (e != 0.0) t += e * v[f];
+        });
+        const int ox = cx == 2 * K, oy = cy == 2 * K, oz = (int)cz == 2 * K;
+        const int32_t blk = cnb[(ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1))];
+        if (blk >= 0) {
+          double* dst = out + (int64_t)blk * NO * NO * NO + (cx - 2 * K * ox) +
+                        NO * ((cy - 2 * K * oy) + NO * ((int)cz - 2 * K * oz));
+          const bool inner = cx > 0 && cx < 2 * K && cy > 0 && cy < 2 * K && (int)cz > 0 && (int)cz < 2 * K;
+          if (inner || a.deterministic) *dst += t;  // deterministic: this launch's bricks share no node
+          else atomicAdd(dst, t);
+        }
+      });
+    }
+    return;
+  }
+  if (!has_out) return;
+  double c2d = 0.0;
+  if constexpr (MODE == 1) {
+    // one reciprocal of the diagonal per thread, as in level_cheb_brick_kernel
+    const double s = a.scale[0];
+    const double md0 = bbrick<K, false>(0, K), kd0 = bbrick<K, true>(0, K);
+    const double md1 = bbrick<K, false>(1, K + 1), kd1 = bbrick<K, true>(1, K + 1);
+    const double mdx = (oi & 1) ? md1 : md0, kdx = (oi & 1) ? kd1 : kd0;
+    const double mdy = (oj & 1) ? md1 : md0, kdy = (oj & 1) ? kd1 : kd0;
+    const double mdz = (part & 1) ? md1 : md0, kdz = (part & 1) ? kd1 : kd0;
+    c2d = c2 / (coef * (s * kdx * mdy * mdz + s * mdx * kdy * mdz + s * mdx * mdy * kdz));
+  }
+  static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share the parity of k");
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    if (kk >= OB) break;
+    const int gsel = (oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO));
+    const int node = (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
+    if (!((smask[gsel] >> node) & 1ull)) continue;
+    const double y = result(o);
+    if constexpr (MODE == 0) {
+      out[slots[o]] = y;
+    } else {
+      out[slots[o]] = xv[o] + c1 * (xv[o] - pre_xp[o]) + c2d * (pre_g[o] - y);
+    }
+  }
 }
 
 // ------------------------------------- Q2 brick smoother, persistent blocks
@@ -2453,12 +2533,13 @@ template <typename T, int DIM, int K>
 static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* gc, cudaStream_t s) {
   using F = Fast<DIM, K>;
   if (a.n_groups == 0) return cudaSuccess;
-  // FP32, above level 1, every group of the level in a brick and no
-  // refinement-edge nodes: one brick pass for residual and restriction.  (The
-  // brick pass assigns each fine node's whole residual to the brick owning
-  // it, the per-group kernel splits g between the groups touching a node and
-  // takes each group's own cells' A u: the two do not mix on one level.)
-  const bool bricks = DIM == 3 && std::is_same<T, float>::value && a.level >= 2 && a.n_bricks > 0 &&
+  // FP32 (FP64: cubic cells), above level 1, every group of the level in a
+  // brick and no refinement-edge nodes: one brick pass for residual and
+  // restriction.  (The brick pass assigns each fine node's whole residual to
+  // the brick owning it, the per-group kernel splits g between the groups
+  // touching a node and takes each group's own cells' A u: the two do not mix
+  // on one level.)
+  const bool bricks = DIM == 3 && (std::is_same<T, float>::value || a.iso) && a.level >= 2 && a.n_bricks > 0 &&
                       a.n_rest == 0 && a.no_ghosts;
   // deterministic mode: one launch per colour of bricks (groups), which share
   // no coarse node, in a fixed colour order
@@ -2481,6 +2562,27 @@ static cudaError_t res_dispatch(const LevelArgs& a, const T* u, const T* g, T* g
         }
         if (nb == 0) continue;
         level_cheb_brick_f2_kernel<K, 2><<<(unsigned)nb, Brick2S<K>::TB, smb, s>>>(ac, u, nullptr, g, gc, 0.f, 0.f);
+        GMG_COUNT_LAUNCH();
+      }
+    }
+  } else if constexpr (DIM == 3) {
+    if (bricks) {  // FP64 on cubic cells: the split-integer brick kernel
+      const size_t smb = BrickI<K>::bytes();
+      static const bool initb = [&] {
+        cudaFuncSetAttribute(level_cheb_brick_int_kernel<K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+        return true;
+      }();
+      (void)initb;
+      for (int c = 0; c < (det ? a.n_brick_colors : 1); ++c) {
+        LevelArgs ac = a;
+        int64_t nb = a.n_bricks;
+        if (det) {
+          ac.bricks = a.bricks + a.brick_off[c] * 64;
+          ac.brick_cnb = a.brick_cnb + a.brick_off[c] * 27;
+          nb = a.brick_off[c + 1] - a.brick_off[c];
+        }
+        if (nb == 0) continue;
+        level_cheb_brick_int_kernel<K, 2><<<(unsigned)nb, BrickG<K>::TB, smb, s>>>(ac, u, nullptr, g, gc, 0.0, 0.0);
         GMG_COUNT_LAUNCH();
       }
     }
