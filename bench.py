@@ -425,18 +425,21 @@ def run_levels(args, torch, G, inputs, local):
     """Level smoother alone: on each level of the headline workload, the
     Chebyshev smoothing of the V-cycle (m updates from a nonzero start,
     gmg_level_smooth) timed with CUDA events, with its algorithmic bytes
-    (4 B x (4 n_S + n_I) per update; the call also copies the level vector
-    once, 8 B per slot)."""
+    (s B x (4 n_S + n_I) per update, s = 4 in FP32 and 8 in FP64; the call
+    also copies the level vector once, 2 s B per slot)."""
     w = inputs.poisson3d_sphere(args.global_ref, args.adaptive_ref)
     stream = torch.cuda.current_stream()
     ctx = G.Context(local, stream.cuda_stream)
-    H = G.Hierarchy(ctx, G.build_mesh(w), w.degree, cheb_degree=w.cheb_degree, vcycle_prec=G.PREC_FP32)
+    fp64 = args.level_prec == "fp64"
+    dt, sb = (torch.float64, 8.0) if fp64 else (torch.float32, 4.0)
+    H = G.Hierarchy(ctx, G.build_mesh(w), w.degree, cheb_degree=w.cheb_degree,
+                    vcycle_prec=G.PREC_FP64 if fp64 else G.PREC_FP32)
     info, m = H.info, w.cheb_degree
     wanted = [int(v) for v in args.levels.split(",")] if args.levels else list(range(1, info.n_levels))
     out = []
     for lvl in wanted:
         n = int(info.slots[lvl])
-        g = torch.rand(n, dtype=torch.float32, device="cuda")
+        g = torch.rand(n, dtype=dt, device="cuda")
         u, tmp = torch.zeros_like(g), torch.zeros_like(g)
         for _ in range(args.warmup):
             H.level_smooth(lvl, g, u, tmp, False)
@@ -448,11 +451,12 @@ def run_levels(args, torch, G, inputs, local):
         e1.record(stream)
         torch.cuda.synchronize()
         secs = e0.elapsed_time(e1) / 1e3 / args.steps
-        nbytes = m * 4.0 * (4 * int(info.n_S[lvl]) + int(info.n_I[lvl])) + 8.0 * n
+        nbytes = m * sb * (4 * int(info.n_S[lvl]) + int(info.n_I[lvl])) + 2 * sb * n
         out.append({"level": lvl, "slots": n, "n_S": int(info.n_S[lvl]), "n_I": int(info.n_I[lvl]),
                     "bricks": int(info.bricks[lvl]), "bricks_partial": int(info.bricks_partial[lvl]),
                     "us_per_smoothing": round(1e6 * secs, 2), "GB/s": round(nbytes / secs / 1e9, 1)})
     print(json.dumps({"metric": "level smoothing time (m Chebyshev updates)", "workload": w.name,
+                      "precision": args.level_prec,
                       "cheb_degree": m, "steps": args.steps, "warmup": args.warmup, "levels": out}), flush=True)
 
 
@@ -469,6 +473,8 @@ def main():
     ap.add_argument("--fichera-rounds", type=int, default=13,
                     help="fichera workload: adaptive rounds (13: 3.4M unknowns, the paper's cycle 13)")
     ap.add_argument("--levels", default="", help="levels workload: comma-separated levels (default all)")
+    ap.add_argument("--level-prec", default="fp32", choices=["fp32", "fp64"],
+                    help="levels workload: precision of the level vectors")
     ap.add_argument("--brick-min-members", type=int, default=0,
                     help="smoother tile shape (gmg_params.brick_min_members; 0 = library default)")
     ap.add_argument("--deterministic", action="store_true", help="bitwise-repeatable solves (gmg_params)")

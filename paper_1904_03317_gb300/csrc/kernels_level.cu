@@ -1378,7 +1378,6 @@ template <int K>
 struct BrickI {
   using B = BrickG<K>;
   static constexpr int HB = B::HB, OB = B::OB;
-  static constexpr int NH = HB * HB * HB;     // halo values
   static constexpr int T1 = HB * HB * OB;     // stage-1 outputs per matrix and component
   static constexpr int ZS = OB * OB + (OB == 8 ? 8 : 4);  // padded z stride of the stage-2 arrays
   static constexpr int T2 = HB * ZS;
@@ -1387,14 +1386,16 @@ struct BrickI {
       3 * ibrick_rowsum<K, false>() * ibrick_rowsum<K, false>() * ibrick_rowsum<K, true>();
   static constexpr int KR = int_recombination_bits_bound(BOUND);
   // region 1: the stage-1 outputs (M, K) of the three components; region 2:
-  // the FP64 halo with its split parts (P1 and P2 as int2, r), overwritten by
-  // the stage-2 outputs (MM, MK, KM) of the three components
+  // the stage-2 outputs (MM and MK + KM: the scales are equal) of the three
+  // components.  The halo never goes to shared memory: each thread loads,
+  // splits and contracts one halo line in registers.
   static constexpr size_t R1 = (size_t)6 * T1 * 4;
-  static constexpr size_t HALO = (size_t)NH * (8 + 8 + 4);
-  static constexpr size_t STAGE2 = (size_t)9 * T2 * 4;
-  static constexpr size_t R2 = ((HALO > STAGE2 ? HALO : STAGE2) + 15) / 16 * 16;
+  static constexpr size_t R2 = ((size_t)6 * T2 * 4 + 15) / 16 * 16;
   static constexpr size_t bytes() { return R1 + R2 + 64 * 4 + 8 * 8 + 16; }
-  static_assert(R1 % 16 == 0 && (6 * T2 * 4) % 16 == 0, "16-byte aligned arrays");
+  static_assert(R1 % 16 == 0 && (4 * T2 * 4) % 16 == 0, "16-byte aligned arrays");
+  static_assert(HB * HB <= B::TB, "one halo line per thread");
+  // blocks per SM the registers are sized for (shared memory admits five Q2 blocks)
+  static constexpr int MIN_BLOCKS = K == 2 ? 5 : 8;
 };
 
 // four 4-byte values to 16-byte aligned shared memory
@@ -1405,24 +1406,21 @@ __device__ __forceinline__ void st4(T* p, const T* v) {
 }
 
 template <int K, int MODE>
-__global__ void __launch_bounds__(BrickG<K>::TB)
+__global__ void __launch_bounds__(BrickG<K>::TB, BrickI<K>::MIN_BLOCKS)
 level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const double* xprev,
                             const double* __restrict__ gvec, double* out, double c1, double c2) {
   using B = BrickG<K>;
   using S = BrickI<K>;
   constexpr int NO = B::NO, OB = B::OB, HB = B::HB, TB = B::TB, L3 = B::L3, R = B::R, OPT = B::OPT;
-  constexpr int NH = S::NH, T1 = S::T1, T2 = S::T2, ZS = S::ZS, KR = S::KR;
+  constexpr int T1 = S::T1, T2 = S::T2, ZS = S::ZS, KR = S::KR;
   static_assert(S::BOUND * 32768LL < 2147483648LL, "integer Kronecker sum exceeds int32");
   static_assert(KR >= 5 && int_recombination_fits_bound(S::BOUND, KR), "integer recombination exceeds 2^51");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* T1i = reinterpret_cast<int*>(smem_raw);          // P1 (M, K), P2 (M, K)
   float* T1f = reinterpret_cast<float*>(T1i + 4 * T1);  // r (M, K)
   unsigned char* r2 = smem_raw + S::R1;
-  double* X = reinterpret_cast<double*>(r2);
-  int2* P12 = reinterpret_cast<int2*>(X + NH);
-  float* Rr = reinterpret_cast<float*>(P12 + NH);
-  int* T2i = reinterpret_cast<int*>(r2);                // P1 (MM, MK, KM), P2 (MM, MK, KM)
-  float* T2f = reinterpret_cast<float*>(T2i + 6 * T2);  // r (MM, MK, KM)
+  int* T2i = reinterpret_cast<int*>(r2);                // P1 (MM, MK + KM), P2 (MM, MK + KM)
+  float* T2f = reinterpret_cast<float*>(T2i + 4 * T2);  // r (MM, MK + KM)
   int32_t* tab = reinterpret_cast<int32_t*>(r2 + S::R2);
   uint64_t* smask = reinterpret_cast<uint64_t*>(tab + 64);
   int* emax = reinterpret_cast<int*>(smask + 8);
@@ -1457,20 +1455,23 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
       slots[o] = (int64_t)gid * B::NOWN + (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
       if constexpr (MODE >= 1) pre_g[o] = gvec[slots[o]];
       if constexpr (MODE == 1) {
+        xv[o] = x[slots[o]];
         if (xprev) pre_xp[o] = xprev[slots[o]];
       }
     }
   }
-  // the halo in FP64 (four segments per x line: groups -1, 0, 1, 2) and its
-  // largest biased exponent
+  // this thread's halo line in FP64 (four segments: groups -1, 0, 1, 2) and
+  // the brick's largest biased exponent
+  const int line = tid;
+  const bool has_line = line < HB * HB;
+  double v[HB];
   int ex = 0;
-  for (int line = tid; line < HB * HB; line += TB) {
+  if (has_line) {
     int gy, ly, gz, lz;
     brick_seg<K>(line % HB, gy, ly);
     brick_seg<K>(line / HB, gz, lz);
     const int row = NO * (ly + NO * lz);
     const int tb = 4 * ((gy + 1) + 4 * (gz + 1));
-    double v[HB];
     const int32_t b0 = tab[tb + 0], b1 = tab[tb + 1], b2 = tab[tb + 2], b3 = tab[tb + 3];
     if (b0 >= 0) load_run<double, K>(x + (int64_t)b0 * B::NOWN + row + K, v);
     else for (int i = 0; i < K; ++i) v[i] = 0.0;
@@ -1480,7 +1481,6 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
     else for (int i = 0; i < 2 * K; ++i) v[3 * K + i] = 0.0;
     v[5 * K] = b3 >= 0 ? x[(int64_t)b3 * B::NOWN + row] : 0.0;
     static_for<0, HB>([&](auto c) {
-      X[line * HB + c] = v[c];
       const int e = (int)((__double_as_longlong(v[c]) >> 52) & 0x7FF);
       ex = e > ex ? e : ex;
     });
@@ -1491,25 +1491,9 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
   // exact split against q = 2^(emax - 1037): |x| < 2^15 q; a NaN or Inf in
   // the halo makes the brick's outputs NaN
   const int em = *emax;
-  const int eq = em == 0x7FF ? 1010 : em - 1037;
-  for (int e = tid; e < NH; e += TB) {
-    int p1, p2;
-    float r;
-    split_exact(X[e], eq, p1, p2, r);
-    P12[e] = make_int2(p1, p2);
-    Rr[e] = r;
-  }
-  // own values for the update, read before the stage-2 outputs overwrite the halo
-  if constexpr (MODE == 1) {
-#pragma unroll
-    for (int o = 0; o < OPT; ++o) {
-      const int kk = part + R * o;
-      if (slots[o] >= 0) xv[o] = X[(oi + K) + HB * ((oj + K) + HB * (kk + K))];
-    }
-  }
-  __syncthreads();
-  // stage 1: x direction per halo line (M and K rows), per component
-  for (int line = tid; line < HB * HB; line += TB) {
+  // stage 1: the line's split parts, x direction (M and K rows), per component
+  if (has_line) {
+    const int eq = em == 0x7FF ? 1010 : em - 1037;
     auto xrows = [&](const auto* v, auto* oM, auto* oK) {
       using T = std::remove_const_t<std::remove_reference_t<decltype(v[0])>>;
       T m[OB], k[OB];
@@ -1530,21 +1514,16 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
     };
     int v1[HB], v2[HB];
     float v3[HB];
-    static_for<0, HB>([&](auto c) {
-      const int2 p = P12[line * HB + c];
-      v1[c] = p.x;
-      v2[c] = p.y;
-      v3[c] = Rr[line * HB + c];
-    });
+    static_for<0, HB>([&](auto c) { split_exact(v[c], eq, v1[c], v2[c], v3[c]); });
     xrows(v1, T1i, T1i + T1);
     xrows(v2, T1i + 2 * T1, T1i + 3 * T1);
     xrows(v3, T1f, T1f + T1);
   }
   __syncthreads();
   // stage 2: y direction, lines (z, i), per component
-  for (int line = tid; line < HB * OB; line += TB) {
-    const int z = line / OB, i = line % OB;
-    auto yrows = [&](const auto* iM, const auto* iK, auto* oMM, auto* oMK, auto* oKM) {
+  for (int l2 = tid; l2 < HB * OB; l2 += TB) {
+    const int z = l2 / OB, i = l2 % OB;
+    auto yrows = [&](const auto* iM, const auto* iK, auto* oMM, auto* oQ) {
       using T = std::remove_const_t<std::remove_reference_t<decltype(iM[0])>>;
       T vm[HB], vk[HB];
       static_for<0, HB>([&](auto y) {
@@ -1563,24 +1542,23 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
         });
         const int o = z * ZS + j * OB + i;
         oMM[o] = mm;
-        oMK[o] = mk;
-        oKM[o] = km;
+        oQ[o] = mk + km;
       });
     };
-    yrows(T1i, T1i + T1, T2i, T2i + T2, T2i + 2 * T2);
-    yrows(T1i + 2 * T1, T1i + 3 * T1, T2i + 3 * T2, T2i + 4 * T2, T2i + 5 * T2);
-    yrows(T1f, T1f + T1, T2f, T2f + T2, T2f + 2 * T2);
+    yrows(T1i, T1i + T1, T2i, T2i + T2);
+    yrows(T1i + 2 * T1, T1i + 3 * T1, T2i + 2 * T2, T2i + 3 * T2);
+    yrows(T1f, T1f + T1, T2f, T2f + T2);
   }
   __syncthreads();
   // stage 3: z direction per component, then the recombination and the update
   int o1[OPT], o2[OPT];
   float o3[OPT];
-  auto zrows = [&](const auto* iMM, const auto* iMK, const auto* iKM, auto* acc) {
+  auto zrows = [&](const auto* iMM, const auto* iQ, auto* acc) {
     using T = std::remove_const_t<std::remove_reference_t<decltype(iMM[0])>>;
     T p[HB], q[HB];
     static_for<0, HB>([&](auto z) {
       p[z] = iMM[z * ZS + ol];
-      q[z] = iMK[z * ZS + ol] + iKM[z * ZS + ol];
+      q[z] = iQ[z * ZS + ol];
     });
     own_rows<OB, R>(part, [&](auto o, auto r) {
       T y = 0;
@@ -1598,9 +1576,9 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
     o3[o] = 0.f;
   }
   if (has_out) {
-    zrows(T2i, T2i + T2, T2i + 2 * T2, o1);
-    zrows(T2i + 3 * T2, T2i + 4 * T2, T2i + 5 * T2, o2);
-    zrows(T2f, T2f + T2, T2f + 2 * T2, o3);
+    zrows(T2i, T2i + T2, o1);
+    zrows(T2i + 2 * T2, T2i + 3 * T2, o2);
+    zrows(T2f, T2f + T2, o3);
   }
   constexpr double DEN = (double)IntElem<K>::DM * IntElem<K>::DM * IntElem<K>::DK;
   // q 2^-15 2^-KR = 2^(emax - 1037 - 15 - KR)
