@@ -86,6 +86,20 @@ __device__ __forceinline__ void split_exact(double x, int eq, int& p1, int& p2, 
 __device__ __forceinline__ double i64_to_double(long long v) {  // |v| < 2^51
   return __longlong_as_double(0x4338000000000000LL + v) - 6755399441055744.0;
 }
+// exact int64 -> double for |v| < 2^53 with integer operations only, for
+// kernels whose FP64 pipe is the scarce unit: the normalised magnitude plus
+// the exponent field, the implicit bit carrying into the exponent
+__device__ __forceinline__ double i64_to_double_alu(long long v) {
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int e = 63 - __clzll((long long)a);  // a in [2^e, 2^(e+1)); -1 for a = 0
+  const unsigned long long bits = a == 0 ? 0ull : ((unsigned long long)(e + 1022) << 52) + (a << (52 - e));
+  return __longlong_as_double((long long)(sgn | bits));
+}
+// 2^n for -1022 <= n <= 1023 from its bit pattern
+__device__ __forceinline__ double pow2_normal(int n) {
+  return __longlong_as_double((long long)(n + 1023) << 52);
+}
 // rint(f 2^KR) for |f 2^KR| < 2^22: the sum lands in [2^23, 2^24), where the
 // FP32 spacing is 1, so its low mantissa bits are the rounded integer
 template <int KR>

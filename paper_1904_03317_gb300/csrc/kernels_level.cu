@@ -1391,7 +1391,10 @@ struct BrickI {
   // splits and contracts one halo line in registers.
   static constexpr size_t R1 = (size_t)6 * T1 * 4;
   static constexpr size_t R2 = ((size_t)6 * T2 * 4 + 15) / 16 * 16;
-  static constexpr size_t bytes() { return R1 + R2 + 64 * 4 + 8 * 8 + 16; }
+  // after the arrays: brick table, S masks, largest exponent (16 bytes), the
+  // Chebyshev factor c2 / diagonal per parity class of (i, j, k) and the
+  // brick's scale a s / (DM^2 DK)
+  static constexpr size_t bytes() { return R1 + R2 + 64 * 4 + 8 * 8 + 16 + 9 * 8; }
   static_assert(R1 % 16 == 0 && (4 * T2 * 4) % 16 == 0, "16-byte aligned arrays");
   static_assert(HB * HB <= B::TB, "one halo line per thread");
   // blocks per SM the registers are sized for (shared memory admits five Q2 blocks)
@@ -1424,6 +1427,8 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
   int32_t* tab = reinterpret_cast<int32_t*>(r2 + S::R2);
   uint64_t* smask = reinterpret_cast<uint64_t*>(tab + 64);
   int* emax = reinterpret_cast<int*>(smask + 8);
+  double* c2cls = reinterpret_cast<double*>(smask + 10);
+  double* sbase = c2cls + 8;
   const int tid = threadIdx.x;
   const int64_t br = blockIdx.x;
   if (tid < 64) tab[tid] = a.bricks[br * 64 + tid];
@@ -1438,7 +1443,24 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
   const unsigned members = MODE == 2 ? 0xFFu : brick_members(a, br);
   if (tid < 8) smask[tid] = ((members >> tid) & 1u) ? a.smask[own_group(tid & 1, (tid >> 1) & 1, tid >> 2)] : 0ull;
   const int m0 = __ffs(members) - 1;  // a member: the coefficient is common to all
-  const double coef = a.coeff[own_group(m0 & 1, (m0 >> 1) & 1, m0 >> 2)];
+  constexpr double DEN = (double)IntElem<K>::DM * IntElem<K>::DM * IntElem<K>::DK;
+  if (tid < 9) {
+    // per brick, not per thread: the divisions would load the FP64 pipe.  The
+    // diagonal of the merged brick matrices depends on a node only through
+    // the parities of (i, j, k): class tid = px + 2 py + 4 pz.
+    const double coef = a.coeff[own_group(m0 & 1, (m0 >> 1) & 1, m0 >> 2)];
+    const double s = a.scale[0];
+    if (tid == 8) {
+      *sbase = coef * s / DEN;
+    } else if constexpr (MODE == 1) {
+      const double md0 = bbrick<K, false>(0, K), kd0 = bbrick<K, true>(0, K);
+      const double md1 = bbrick<K, false>(1, K + 1), kd1 = bbrick<K, true>(1, K + 1);
+      const double mdx = (tid & 1) ? md1 : md0, kdx = (tid & 1) ? kd1 : kd0;
+      const double mdy = (tid & 2) ? md1 : md0, kdy = (tid & 2) ? kd1 : kd0;
+      const double mdz = (tid & 4) ? md1 : md0, kdz = (tid & 4) ? kd1 : kd0;
+      c2cls[tid] = c2 / (coef * (s * kdx * mdy * mdz + s * mdx * kdy * mdz + s * mdx * mdy * kdz));
+    }
+  }
   // this thread's outputs: line ol = (i, j), k = part + R * o
   const int ol = tid % L3, part = tid / L3;
   const bool has_out = tid < L3 * R;
@@ -1580,14 +1602,16 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
     zrows(T2i + 2 * T2, T2i + 3 * T2, o2);
     zrows(T2f, T2f + T2, o3);
   }
-  constexpr double DEN = (double)IntElem<K>::DM * IntElem<K>::DM * IntElem<K>::DK;
-  // q 2^-15 2^-KR = 2^(emax - 1037 - 15 - KR)
+  // q 2^-15 2^-KR = 2^(emax - 1023) 2^-(29 + KR); the recombined integer T
+  // converts to FP64 exactly with integer operations
+  constexpr double LOW = 1.0 / (double)(1LL << (29 + KR));
   const double sc = em == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
-                                : coef * a.scale[0] / DEN * ldexp(1.0, em - 1052 - KR);
-  auto result = [&](int o) {
-    return sc * i64_to_double(((long long)o1[o] << (15 + KR)) + ((long long)o2[o] << KR) +
-                              (long long)f32_fixed_rint<KR>(o3[o]));
+                                : *sbase * LOW * pow2_normal(em - 1023);
+  auto tsum = [&](int o) {
+    return i64_to_double_alu(((long long)o1[o] << (15 + KR)) + ((long long)o2[o] << KR) +
+                             (long long)f32_fixed_rint<KR>(o3[o]));
   };
+  auto result = [&](int o) { return sc * tsum(o); };
   if constexpr (MODE == 2) {
     // residual on the own nodes (region 1 is free after stage 2), then
     // g_{l-1} += R r over the parent group's coarse nodes, in FP64
@@ -1657,16 +1681,11 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
     return;
   }
   if (!has_out) return;
-  double c2d = 0.0;
+  // out = x + c1 (x - x_prev) + c2d g - (c2d sc) T: four FP64 operations per node
+  double c2d = 0.0, c2s = 0.0;
   if constexpr (MODE == 1) {
-    // one reciprocal of the diagonal per thread, as in level_cheb_brick_kernel
-    const double s = a.scale[0];
-    const double md0 = bbrick<K, false>(0, K), kd0 = bbrick<K, true>(0, K);
-    const double md1 = bbrick<K, false>(1, K + 1), kd1 = bbrick<K, true>(1, K + 1);
-    const double mdx = (oi & 1) ? md1 : md0, kdx = (oi & 1) ? kd1 : kd0;
-    const double mdy = (oj & 1) ? md1 : md0, kdy = (oj & 1) ? kd1 : kd0;
-    const double mdz = (part & 1) ? md1 : md0, kdz = (part & 1) ? kd1 : kd0;
-    c2d = c2 / (coef * (s * kdx * mdy * mdz + s * mdx * kdy * mdz + s * mdx * mdy * kdz));
+    c2d = c2cls[(oi & 1) + 2 * (oj & 1) + 4 * (part & 1)];
+    c2s = c2d * sc;
   }
   static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share the parity of k");
 #pragma unroll
@@ -1676,11 +1695,10 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
     const int gsel = (oi / NO) + 2 * ((oj / NO) + 2 * (kk / NO));
     const int node = (oi % NO) + NO * ((oj % NO) + NO * (kk % NO));
     if (!((smask[gsel] >> node) & 1ull)) continue;
-    const double y = result(o);
     if constexpr (MODE == 0) {
-      out[slots[o]] = y;
+      out[slots[o]] = result(o);
     } else {
-      out[slots[o]] = xv[o] + c1 * (xv[o] - pre_xp[o]) + c2d * (pre_g[o] - y);
+      out[slots[o]] = fma(-c2s, tsum(o), fma(c2d, pre_g[o], fma(c1, xv[o] - pre_xp[o], xv[o])));
     }
   }
 }
