@@ -1703,6 +1703,275 @@ level_cheb_brick_int_kernel(LevelArgs a, const double* __restrict__ x, const dou
   }
 }
 
+// FP64 single groups on cubic cells, split-integer contractions: the single-
+// group smoother of level_cheb_fast_kernel (one team of TW threads per group,
+// the (3K+1)^3 halo, the merged 1-D matrices) with the split-integer scheme of
+// level_cheb_brick_int_kernel.  A team takes its group's largest exponent by
+// a team-wide max, splits its halo lines in registers and contracts P1, P2
+// (int32) and r (FP32); the update is the brick kernel's four FP64
+// operations per node.
+template <int K, bool STIFF>
+__host__ __device__ constexpr int imerged(int r, int c) {
+  // integer counterpart of bmerged: rows 0..2K-1, halo columns 0..3K
+  const int p = c - K;
+  int v = 0;
+  for (int cell = 0; cell < 2; ++cell) {
+    const int lo = K * cell;
+    if (r >= lo && r <= lo + K && p >= lo && p <= lo + K) v += ielem1<K, STIFF>(r - lo, p - lo);
+  }
+  if (r == 0 && p >= -K && p <= 0) v += ielem1<K, STIFF>(K, p + K);  // the lower neighbour's cell
+  return v;
+}
+
+template <int K>
+constexpr bool imerged_matches() {
+  for (int r = 0; r < 2 * K; ++r)
+    for (int c = 0; c <= 3 * K; ++c) {
+      const double dm = bmerged<K, false>(r, c) * IntElem<K>::DM - imerged<K, false>(r, c);
+      const double dk = bmerged<K, true>(r, c) * IntElem<K>::DK - imerged<K, true>(r, c);
+      if (dm > 1e-12 || dm < -1e-12 || dk > 1e-12 || dk < -1e-12) return false;
+    }
+  return true;
+}
+static_assert(imerged_matches<1>() && imerged_matches<2>(), "integer merged matrices");
+
+template <int K, bool STIFF>
+constexpr long long imerged_rowsum() {
+  long long best = 0;
+  for (int r = 0; r < 2 * K; ++r) {
+    long long t = 0;
+    for (int c = 0; c <= 3 * K; ++c) t += imerged<K, STIFF>(r, c) < 0 ? -imerged<K, STIFF>(r, c) : imerged<K, STIFF>(r, c);
+    best = t > best ? t : best;
+  }
+  return best;
+}
+
+template <int K>
+struct SingleI {
+  using F = Fast<3, K>;
+  static constexpr int NH = F::NH, NO = F::NO, TW = F::TW, TPB = F::TPB;
+  static constexpr int L1 = NH * NH;              // stage-1 lines
+  static constexpr int LPT = (L1 + TW - 1) / TW;  // stage-1 lines per thread
+  static constexpr int T1 = L1 * NO;              // per matrix and component
+  static constexpr int T2 = NH * NO * NO;         // per array and component
+  static constexpr long long BOUND =
+      3 * imerged_rowsum<K, false>() * imerged_rowsum<K, false>() * imerged_rowsum<K, true>();
+  static constexpr int KR = int_recombination_bits_bound(BOUND);
+  // per team: c2 / diagonal per parity class and the scale (9 doubles), the
+  // stage-1 outputs (M, K) and the stage-2 outputs (MM, MK + KM) of the three
+  // components
+  // (the arrays start 80 bytes into the team's slice, 16-byte aligned)
+  static constexpr size_t PER = ((size_t)80 + (size_t)(6 * T1 + 6 * T2) * 4 + 15) / 16 * 16;
+  static constexpr size_t bytes() { return (size_t)TPB * PER; }
+};
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(256, 3)
+level_cheb_single_int_kernel(LevelArgs a, const double* __restrict__ x, const double* xprev,
+                             const double* __restrict__ gvec, double* out, double c1, double c2) {
+  using F = Fast<3, K>;
+  using S = SingleI<K>;
+  constexpr int NH = S::NH, NO = S::NO, TW = S::TW, L1 = S::L1, LPT = S::LPT, T1 = S::T1, T2 = S::T2;
+  constexpr int KR = S::KR;
+  constexpr int L3 = NO * NO;
+  constexpr int R = TW / L3 > 0 ? TW / L3 : 1;
+  constexpr int OPT = (NO + R - 1) / R;
+  static_assert(S::BOUND * 32768LL < 2147483648LL, "integer Kronecker sum exceeds int32");
+  static_assert(KR >= 5 && int_recombination_fits_bound(S::BOUND, KR), "integer recombination exceeds 2^51");
+  static_assert(R % 2 == 0 || OPT == 1, "outputs of a thread must share one parity pattern");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.x / TW, lane = threadIdx.x % TW;
+  const unsigned tmask = TW == 32 ? 0xffffffffu : (((1u << TW) - 1u) << ((threadIdx.x % 32) / TW * TW));
+  unsigned char* base = smem_raw + (size_t)team * S::PER;
+  double* c2cls = reinterpret_cast<double*>(base);
+  double* sbase = c2cls + 8;
+  int* T1i = reinterpret_cast<int*>(base + 80);         // P1 (M, K), P2 (M, K)
+  float* T1f = reinterpret_cast<float*>(T1i + 4 * T1);  // r (M, K)
+  int* T2i = reinterpret_cast<int*>(T1f + 2 * T1);      // P1 (MM, MK + KM), P2 (MM, MK + KM)
+  float* T2f = reinterpret_cast<float*>(T2i + 4 * T2);  // r (MM, MK + KM)
+  const int64_t t = (int64_t)blockIdx.x * S::TPB + team;
+  const bool active = t < a.n_uniform;
+  const int64_t g = active ? a.list_uniform[t] : 0;
+  const uint64_t smask = active ? a.smask[g] : 0ull;
+  constexpr double DEN = (double)IntElem<K>::DM * IntElem<K>::DM * IntElem<K>::DK;
+  if (active && lane < 9) {
+    const double coef = a.coeff[g];
+    const double s = a.scale[0];
+    if (lane == 8) {
+      *sbase = coef * s / DEN;
+    } else if constexpr (MODE == 1) {
+      const double md0 = bmerged<K, false>(0, K), kd0 = bmerged<K, true>(0, K);
+      const double md1 = bmerged<K, false>(1, K + 1), kd1 = bmerged<K, true>(1, K + 1);
+      const double mdx = (lane & 1) ? md1 : md0, kdx = (lane & 1) ? kd1 : kd0;
+      const double mdy = (lane & 2) ? md1 : md0, kdy = (lane & 2) ? kd1 : kd0;
+      const double mdz = (lane & 4) ? md1 : md0, kdz = (lane & 4) ? kd1 : kd0;
+      c2cls[lane] = c2 / (coef * (s * kdx * mdy * mdz + s * mdx * kdy * mdz + s * mdx * mdy * kdz));
+    }
+  }
+  // this thread's outputs: line ol = (i, j), k = part + R * o
+  const int ol = lane % L3, part = lane / L3;
+  const bool has_out = lane < L3 * R;
+  double pre_xp[OPT], pre_g[OPT], xv[OPT];
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    pre_xp[o] = pre_g[o] = xv[o] = 0.0;
+    if constexpr (MODE == 1) {
+      if (active && has_out && kk < NO) {
+        const int64_t slot = g * F::NOWN + ol + L3 * kk;
+        pre_g[o] = gvec[slot];
+        xv[o] = x[slot];
+        if (xprev) pre_xp[o] = xprev[slot];
+      }
+    }
+  }
+  // the halo lines of this thread in FP64 (three segments: neighbours -1, 0, +1)
+  double v[LPT][NH];
+  int ex = 0;
+#pragma unroll
+  for (int q = 0; q < LPT; ++q) {
+    const int line = lane + q * TW;
+#pragma unroll
+    for (int c = 0; c < NH; ++c) v[q][c] = 0.0;
+    if (active && line < L1) {
+      int oy, ly, oz, lz;
+      halo_seg<K>(line % NH, oy, ly);
+      halo_seg<K>(line / NH, oz, lz);
+      const int row = NO * (ly + NO * lz);
+      const int32_t* nb = a.nbr + g * F::NNB;
+      const int32_t b0 = nb[nbi<3>(-1, oy, oz)], b1 = nb[nbi<3>(0, oy, oz)], b2 = nb[nbi<3>(1, oy, oz)];
+      if (b0 >= 0) load_run<double, K>(x + (int64_t)b0 * F::NOWN + row + K, v[q]);
+      if (b1 >= 0) load_run<double, 2 * K>(x + (int64_t)b1 * F::NOWN + row, v[q] + K);
+      if (b2 >= 0) v[q][3 * K] = x[(int64_t)b2 * F::NOWN + row];
+#pragma unroll
+      for (int c = 0; c < NH; ++c) {
+        const int e = (int)((__double_as_longlong(v[q][c]) >> 52) & 0x7FF);
+        ex = e > ex ? e : ex;
+      }
+    }
+  }
+  // the group's largest biased exponent (1 for an all-zero halo)
+  const int em = max(1, (int)__reduce_max_sync(tmask, (unsigned)ex));
+  const int eq = em == 0x7FF ? 1010 : em - 1037;
+  // stage 1: x direction per halo line, per component
+#pragma unroll
+  for (int q = 0; q < LPT; ++q) {
+    const int line = lane + q * TW;
+    if (!active || line >= L1) continue;
+    auto xrows = [&](const auto* w, auto* oM, auto* oK) {
+      using T = std::remove_const_t<std::remove_reference_t<decltype(w[0])>>;
+      T m[NO], k[NO];
+      static_for<0, NO>([&](auto r) {
+        T sm = 0, sk = 0;
+        static_for<0, NH>([&](auto c) {
+          constexpr int bm = imerged<K, false>(r, c), bk = imerged<K, true>(r, c);
+          if constexpr (bm != 0) sm += (T)bm * w[c];
+          if constexpr (bk != 0) sk += (T)bk * w[c];
+        });
+        m[r] = sm;
+        k[r] = sk;
+      });
+      static_for<0, NO / 2>([&](auto h) {
+        oM[line * NO + 2 * h] = m[2 * h];
+        oM[line * NO + 2 * h + 1] = m[2 * h + 1];
+        oK[line * NO + 2 * h] = k[2 * h];
+        oK[line * NO + 2 * h + 1] = k[2 * h + 1];
+      });
+    };
+    int w1[NH], w2[NH];
+    float w3[NH];
+    static_for<0, NH>([&](auto c) { split_exact(v[q][c], eq, w1[c], w2[c], w3[c]); });
+    xrows(w1, T1i, T1i + T1);
+    xrows(w2, T1i + 2 * T1, T1i + 3 * T1);
+    xrows(w3, T1f, T1f + T1);
+  }
+  __syncwarp(tmask);
+  // stage 2: y direction; T1 layout [z][y][i] -> T2 layout [z][j][i]
+  if (active) {
+    for (int l2 = lane; l2 < NH * NO; l2 += TW) {
+      const int z = l2 / NO, i = l2 % NO;
+      auto yrows = [&](const auto* iM, const auto* iK, auto* oMM, auto* oQ) {
+        using T = std::remove_const_t<std::remove_reference_t<decltype(iM[0])>>;
+        T vm[NH], vk[NH];
+        static_for<0, NH>([&](auto y) {
+          vm[y] = iM[(z * NH + y) * NO + i];
+          vk[y] = iK[(z * NH + y) * NO + i];
+        });
+        static_for<0, NO>([&](auto j) {
+          T mm = 0, mk = 0, km = 0;
+          static_for<0, NH>([&](auto c) {
+            constexpr int bm = imerged<K, false>(j, c), bk = imerged<K, true>(j, c);
+            if constexpr (bm != 0) {
+              mm += (T)bm * vm[c];
+              km += (T)bm * vk[c];
+            }
+            if constexpr (bk != 0) mk += (T)bk * vm[c];
+          });
+          const int o = (z * NO + j) * NO + i;
+          oMM[o] = mm;
+          oQ[o] = mk + km;
+        });
+      };
+      yrows(T1i, T1i + T1, T2i, T2i + T2);
+      yrows(T1i + 2 * T1, T1i + 3 * T1, T2i + 2 * T2, T2i + 3 * T2);
+      yrows(T1f, T1f + T1, T2f, T2f + T2);
+    }
+  }
+  __syncwarp(tmask);
+  if (!active || !has_out) return;
+  // stage 3: z direction per component, the recombination and the update
+  int o1[OPT], o2[OPT];
+  float o3[OPT];
+  auto zrows = [&](const auto* iMM, const auto* iQ, auto* acc) {
+    using T = std::remove_const_t<std::remove_reference_t<decltype(iMM[0])>>;
+    T p[NH], q[NH];
+    static_for<0, NH>([&](auto z) {
+      p[z] = iMM[z * L3 + ol];
+      q[z] = iQ[z * L3 + ol];
+    });
+    own_rows<NO, R>(part, [&](auto o, auto r) {
+      T y = 0;
+      static_for<0, NH>([&](auto c) {
+        constexpr int bm = imerged<K, false>(r, c), bk = imerged<K, true>(r, c);
+        if constexpr (bk != 0) y += (T)bk * p[c];
+        if constexpr (bm != 0) y += (T)bm * q[c];
+      });
+      acc[o] = y;
+    });
+  };
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    o1[o] = o2[o] = 0;
+    o3[o] = 0.f;
+  }
+  zrows(T2i, T2i + T2, o1);
+  zrows(T2i + 2 * T2, T2i + 3 * T2, o2);
+  zrows(T2f, T2f + T2, o3);
+  constexpr double LOW = 1.0 / (double)(1LL << (29 + KR));
+  const double sc = em == 0x7FF ? __longlong_as_double(0x7FF8000000000000LL)
+                                : *sbase * LOW * pow2_normal(em - 1023);
+  double c2d = 0.0, c2s = 0.0;
+  if constexpr (MODE == 1) {
+    c2d = c2cls[(ol % NO & 1) + 2 * (ol / NO & 1) + 4 * (part & 1)];
+    c2s = c2d * sc;
+  }
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int kk = part + R * o;
+    if (kk >= NO) break;
+    const int node = ol + L3 * kk;
+    if (!((smask >> node) & 1ull)) continue;
+    const double ts = i64_to_double_alu(((long long)o1[o] << (15 + KR)) + ((long long)o2[o] << KR) +
+                                        (long long)f32_fixed_rint<KR>(o3[o]));
+    const int64_t slot = g * F::NOWN + node;
+    if constexpr (MODE == 0) {
+      out[slot] = sc * ts;
+    } else {
+      out[slot] = fma(-c2s, ts, fma(c2d, pre_g[o], fma(c1, xv[o] - pre_xp[o], xv[o])));
+    }
+  }
+}
+
 // ------------------------------------- Q2 brick smoother, persistent blocks
 // The FP32 Q2 brick smoother (apply and Chebyshev step) with the same three
 // packed contractions as level_cheb_brick_f2_kernel, arranged so that the
@@ -2459,6 +2728,22 @@ static cudaError_t cheb_launch(const LevelArgs& a, const T* x, const T* xprev, c
                                                                                                c1, c2);
         GMG_COUNT_LAUNCH();
       }
+    }
+  }
+  if constexpr (DIM == 3 && std::is_same<T, double>::value) {
+    if (a.n_uniform > 0 && !singles_done && a.iso) {
+      // FP64 single groups on cubic cells: the split-integer team kernel
+      using SI = SingleI<K>;
+      static const bool init = [&] {
+        cudaFuncSetAttribute(level_cheb_single_int_kernel<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SI::bytes());
+        return true;
+      }();
+      (void)init;
+      level_cheb_single_int_kernel<K, MODE><<<(unsigned)((a.n_uniform + SI::TPB - 1) / SI::TPB), 256, SI::bytes(),
+                                              s>>>(a, x, xprev, g, out, c1, c2);
+      GMG_COUNT_LAUNCH();
+      singles_done = true;
     }
   }
   if (a.n_uniform > 0 && !singles_done) {
