@@ -315,6 +315,52 @@ def test_active_apply_propagates_nan(torch):
     assert np.all(np.isnan(yh[rows]))
 
 
+@pytest.mark.parametrize("name", NAMES)
+def test_level_apply_wide_range(torch, name):
+    """FP64 level operators on inputs spanning sixteen decades, with exact
+    zeros and subnormals: within FP64 rounding of |A| |x| in the max norm.
+    On cubic cells the brick and single-group kernels split each brick's or
+    group's values against its largest one (the leaf operator's scheme)."""
+    O, H = gpu_hier(torch, name)
+    rng = np.random.default_rng(23)
+    for l in range(1, len(O.levels)):
+        lev = O.levels[l]
+        idx, cls = level_maps(H, O, l)
+        n = len(lev.keys)
+        x = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-8, 8, n)
+        x[rng.random(n) < 0.1] = 0.0
+        x[rng.random(n) < 0.02] = 5e-324
+        want = lev.A_S @ x[lev.S] + lev.A_SI @ x[lev.I]
+        bound = (abs(lev.A_S) @ np.abs(x[lev.S]) + abs(lev.A_SI) @ np.abs(x[lev.I])).max()
+        xs = dev(torch, to_slots(x, idx, len(idx)))
+        ys = torch.zeros_like(xs)
+        H.level_apply(l, xs, ys)
+        torch.cuda.synchronize()
+        got = from_slots(host(ys), idx, n)[lev.S]
+        assert np.all(np.isfinite(got))
+        assert np.abs(got - want).max() <= 1e-13 * bound
+
+
+def test_level_apply_propagates_nan(torch):
+    """A NaN in the input reaches every S row of the level operator that
+    couples to it (the split-integer kernels turn the outputs of the brick
+    or group whose halo holds it into NaN)."""
+    O, H = gpu_hier(torch, "3d_q2_patches")
+    for l in range(1, len(O.levels)):
+        lev = O.levels[l]
+        idx, cls = level_maps(H, O, l)
+        x = np.ones(len(lev.keys))
+        k = len(lev.S) // 2
+        x[lev.S[k]] = np.nan
+        xs = dev(torch, to_slots(x, idx, len(idx)))
+        ys = torch.zeros_like(xs)
+        H.level_apply(l, xs, ys)
+        torch.cuda.synchronize()
+        got = from_slots(host(ys), idx, len(lev.keys))[lev.S]
+        rows = lev.A_S[:, k].nonzero()[0]
+        assert len(rows) > 0 and np.all(np.isnan(got[rows]))
+
+
 @pytest.mark.parametrize("name", [n for n in NAMES if small_workloads()[n].coeff is None])
 def test_rhs_sine(torch, name):
     O, H = gpu_hier(torch, name)
