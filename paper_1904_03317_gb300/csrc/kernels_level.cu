@@ -1328,13 +1328,15 @@ level_cheb_brick_f2_kernel(LevelArgs a, const float* __restrict__ x, const float
 // For cubic cells (s_x = s_y = s_z = s) the merged brick matrices are the
 // integer matrices ibrick over the element denominators, so the operator of
 // a brick is a s / (DM^2 DK) times an integer Kronecker sum, evaluated as
-// the leaf operator's integer kernels do (int_split.cuh): the halo is loaded
-// once in FP64, split exactly against the brick's largest exponent into
-// P1, P2 (int32) and r (FP32), the three contractions run per component, and
-// the results are recombined in integers and converted to FP64 exactly.  The
-// Chebyshev update stays in FP64.  This takes the FP64 smoother's
-// contractions off the FP64 pipe, a small fraction of this GPU's int32/FP32
-// throughput.  Layout, halo and outputs are those of level_cheb_brick_kernel;
+// the leaf operator's integer kernels do (int_split.cuh): each thread loads
+// one halo line in FP64, the block takes the brick's largest exponent, the
+// thread splits its line exactly into P1, P2 (int32) and r (FP32) in
+// registers, the three contractions run per component, and the results are
+// recombined in integers and converted to FP64 exactly (integer operations
+// only).  The Chebyshev update stays in FP64: four operations per node, with
+// its diagonal factors and scale formed once per brick.  This takes the FP64
+// smoother's contractions off the FP64 pipe, a small fraction of this GPU's
+// int32/FP32 throughput.  Layout, halo and outputs are those of level_cheb_brick_kernel;
 // MODE 2 is the residual + restriction pass of level_cheb_brick_f2_kernel
 // (full bricks, levels >= 2 without refinement-edge nodes), with the
 // restriction in FP64.
